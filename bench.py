@@ -1,0 +1,349 @@
+"""Benchmark: QPS of adaptive-precision vs plain-FP32 IVF-PQ search on one GB300.
+
+A step is one batched search (CL -> precision choice -> RC + LC + quantise +
+DC + TS) of the whole query batch of the SIFT-shaped workload (N = 1M,
+D = 128, nlist = 1024, M = 32, 10k queries, k = 10), queries resident in HBM.
+The index's codes (32 MB) fit in L2, so L2 is flushed (a 512 MB write)
+between timed steps.
+
+Default: python bench.py [--gpus 1 --steps K --warmup W]
+Reference arm: python bench.py --impl reference (the CPU oracle, a bounded sample).
+Under torchrun each rank searches its own replica of the workload (weak
+scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CACHE = os.environ.get("ANNS_BENCH_CACHE", os.path.join(tempfile.gettempdir(), "anns_amp_cache"))
+METRIC = "QPS at recall@10 >= 0.9 on 1 GB300: adaptive-precision vs plain FP32; scan HBM GB/s % peak"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ workload
+
+def workload(key: str, nq: int | None = None, device=None):
+    """Dataset, index arrays and exact ground truth (cached on disk)."""
+    from workloads import CONFIGS, exact_knn, make_dataset, train_ivfpq
+    cfg = CONFIGS[key]
+    nq = nq or cfg["nq"]
+    os.makedirs(CACHE, exist_ok=True)
+    path = os.path.join(CACHE, f"{key}_{cfg['n']}_{nq}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return cfg, {k: z[k] for k in z.files}
+    t = time.time()
+    d = make_dataset(key, nq=nq)
+    ix = train_ivfpq(d["base"], cfg["nlist"], cfg["M"], seed=cfg["seed"], device=device)
+    gt, _ = exact_knn(d["base"], d["queries"], 100, device=device)
+    out = dict(queries=d["queries"], gt=gt, **ix)
+    np.savez(path, **out)
+    log(f"workload {key}: generated in {time.time() - t:.1f}s")
+    return cfg, out
+
+
+def recall(found: np.ndarray, gt: np.ndarray, k: int) -> float:
+    hits = 0
+    for f, g in zip(found[:, :k], gt[:, :k]):
+        hits += len(np.intersect1d(f[f >= 0], g))
+    return hits / (k * len(found))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.path = gpu, None, None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v and "Not" not in v})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def time_steps(fn, steps: int, warmup: int, stream, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 255)
+        evs[i][0].record(stream)
+        fn()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def scan_bytes(index, probes: np.ndarray, M: int) -> int:
+    """Algorithmic bytes of one scan launch: n_l * M code bytes per probed (query, list)."""
+    sizes = index.list_sizes()
+    p = probes[probes >= 0]
+    return int(sizes[p].sum()) * M
+
+
+def traffic_from_profile(kernel_src: str, workload_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha") != sha or rec.get("workload") != workload_name:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_07156_gb300 as amp
+    from paper_2606_07156_gb300 import abi
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cfg, W = workload(args.config, device=dev)
+    index = amp.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"], device=local_rank)
+    Q = torch.from_numpy(W["queries"]).to(dev)
+    nq, k = Q.shape[0], cfg["k"]
+    stream = torch.cuda.current_stream(dev)
+    out = (torch.empty((nq, k), dtype=torch.int64, device=dev), torch.empty((nq, k), dtype=torch.float32, device=dev))
+
+    def run(nprobe, pol):
+        ids, _ = index.search(Q, nprobe, k, pol, stream=stream, out=out)
+        torch.cuda.synchronize()
+        return ids.cpu().numpy()
+
+    # plain FP32 recall sweep; nprobe = smallest reaching recall@10 >= 0.9, else the largest
+    sweep = cfg.get("nprobe_sweep", (cfg["nprobe"],)) if args.nprobe is None else (args.nprobe,)
+    plain = amp.policy("plain")
+    rec_plain = {npb: recall(run(npb, plain), W["gt"], 10) for npb in sweep}
+    ok = [npb for npb in sweep if rec_plain[npb] >= 0.9]
+    nprobe = ok[0] if ok else max(sweep)
+    # adaptive policy: the fewest uniform bits within 1 recall point of plain at this nprobe
+    chosen, rec_ad = 16, None
+    for b in (4, 6, 8, 12, 16):
+        r = recall(run(nprobe, amp.policy("fixed", bits=b)), W["gt"], 10)
+        if r >= rec_plain[nprobe] - 0.01:
+            chosen, rec_ad = b, r
+            break
+    adaptive = amp.policy("fixed", bits=chosen)
+    log(f"recall@10 plain {rec_plain}, nprobe {nprobe}, fixed {chosen} bits -> {rec_ad}")
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    abi.anns_profile(index.handle, 1)
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        ms_ad = time_steps(lambda: index.search(Q, nprobe, k, adaptive, stream=stream, out=out),
+                           args.steps, args.warmup, stream, flush)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    stage_ms, cnt = abi.anns_profile(index.handle, 0)
+    ms_plain = time_steps(lambda: index.search(Q, nprobe, k, plain, stream=stream, out=out),
+                          args.steps, args.warmup, stream, flush)
+    # end to end through the host-buffer entry point (pinned in, pinned out)
+    Qh = torch.from_numpy(W["queries"]).pin_memory()
+    ih = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    dh = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    for _ in range(args.warmup):
+        index.search_host(Qh, nprobe, k, adaptive, stream=stream, out=(ih, dh))
+    e2e_t = []
+    for i in range(args.steps):
+        flush.fill_(i & 255)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        index.search_host(Qh, nprobe, k, adaptive, stream=stream, out=(ih, dh))
+        e2e_t.append(time.perf_counter() - t)
+    rec_e2e = recall(ih.numpy(), W["gt"], 10)
+
+    total_ad = sum(ms_ad) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ad, sum(ms_plain) / 1e3, sum(e2e_t)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ad, total_plain, total_e2e = tt.tolist()
+    else:
+        total_plain, total_e2e = sum(ms_plain) / 1e3, sum(e2e_t)
+    if rank != 0:
+        return None
+    qps = world * nq * args.steps / total_ad
+    qps_plain = world * nq * args.steps / total_plain
+    qps_e2e = world * nq * args.steps / total_e2e
+    probes = index.tap(abi.TAP_PROBES, (nq, nprobe), np.int32)
+    nbytes = scan_bytes(index, probes, cfg["M"])
+    scan_ms = stage_ms[3] / max(cnt, 1)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = nbytes / (scan_ms / 1e3) / 1e9
+    src = os.path.join(ROOT, "paper_2606_07156_gb300", "csrc", "search.cu")
+    wl = f"{cfg['name']} nq={nq} nprobe={nprobe} k={k}"
+    line = {
+        "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ad * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8-lut/i32-acc",
+        "data": "synthetic (seeded SIFT-shaped gamma mixture; no public dataset)",
+        "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
+                   "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq, "policy": f"fixed-{chosen}bit",
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "recall_at_10": round(rec_ad, 4) if rec_ad is not None else None,
+        "plain_fp32": {"qps": round(qps_plain, 1), "recall_at_10": round(rec_plain[nprobe], 4),
+                       "ms_per_step": round(total_plain * 1e3 / args.steps, 4)},
+        "speedup_vs_plain_fp32": round(qps / qps_plain, 3),
+        "recall_sweep_plain": {str(a): round(b, 4) for a, b in rec_plain.items()},
+        "stage_ms_per_step": {n: round(v / max(cnt, 1), 4) for n, v in
+                              zip(("cl_distances", "cl_select", "precision_choice", "lut_scan_topk"), stage_ms)},
+        "roofline": {"bound": "hbm", "kernel": "search_kernel (LUT build + quantise + ADC scan + top-k)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
+                     "traffic": traffic_from_profile(src, wl), "algorithmic_bytes_per_launch": nbytes},
+        "e2e": {"value": round(qps_e2e, 1), "unit": "queries/s", "h2d_bytes_per_step": int(Qh.numel() * 4),
+                "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4), "recall_at_10": round(rec_e2e, 4)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed": round(wall, 3),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(W, cfg, nprobe, chosen, args.cpu_seconds)
+    index.close()
+    return line
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def cpu_baseline(W, cfg, nprobe: int, bits: int, seconds: float) -> dict:
+    """The oracle as it stands, on a bounded sample of the same queries."""
+    from oracle import ivfpq
+    ref = ivfpq.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"])
+    Qs = W["queries"]
+    done, t0, chunk = 0, time.perf_counter(), 8
+    while time.perf_counter() - t0 < seconds and done < len(Qs):
+        ivfpq.search(ref, Qs[done:done + chunk], nprobe, cfg["k"], bits=bits)
+        done += chunk
+    el = time.perf_counter() - t0
+    return {"value": round(done / el, 2), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of {len(Qs)} queries, nprobe={nprobe}, {bits}-bit LUTs, numpy single thread",
+            "seconds": round(el, 2)}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return None
+    cfg, W = workload(args.config)
+    nprobe = args.nprobe or cfg["nprobe"]
+    from oracle import ivfpq
+    ref = ivfpq.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"])
+    Qs = W["queries"]
+    per_step = max(8, args.ref_queries)
+    for i in range(args.warmup):
+        ivfpq.search(ref, Qs[:8], nprobe, cfg["k"], bits=8)
+    ts, done = [], 0
+    for i in range(args.steps):
+        q = Qs[(i * per_step) % len(Qs):][:per_step]
+        t = time.perf_counter()
+        ivfpq.search(ref, q, nprobe, cfg["k"], bits=8)
+        ts.append(time.perf_counter() - t)
+        done += len(q)
+    qps = done / sum(ts)
+    wl = f"{cfg['name']} nq={len(Qs)} nprobe={nprobe} k={cfg['k']}"
+    return {"impl": "reference", "metric": METRIC, "value": round(qps, 2), "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(ts) / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-rule/f64",
+            "data": "synthetic (seeded SIFT-shaped gamma mixture)",
+            "config": {"workload": wl, "policy": "fixed-8bit", "sample_queries_per_step": per_step},
+            "cpu_baseline": {"value": round(qps, 2), "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} queries per step, numpy single thread"},
+            "e2e": {"value": round(qps, 2), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
+    ap.add_argument("--config", default="B")
+    ap.add_argument("--nprobe", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-queries", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        line = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

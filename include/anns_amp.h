@@ -1,0 +1,186 @@
+/*
+ * anns_amp.h — C ABI of the GB300 (sm_103a) adaptive mixed-precision IVF-PQ search.
+ *
+ * The search is the five-stage cluster-based ANNS pipeline of Section 2.1
+ * (Fig. 1): cluster locating (CL), residual calculation (RC), LUT construction
+ * (LC), distance calculation (DC) and top-k selection (TS), with a per-(query,
+ * probed list) precision choice in the spirit of Section 3 (cluster-level
+ * precision predicted from scale, radius and query distance, Section 3.3).
+ *
+ * Conventions for every entry point:
+ *  - Return ANNS_OK (0) on success or a negative ANNS_ERR_* code. The message
+ *    of the last failure on the calling thread is returned by anns_last_error().
+ *    No C++ exception crosses this boundary.
+ *  - Pointers documented "device" must be CUDA device (or managed) memory on
+ *    the index's device; "host" pointers are ordinary host memory. The caller
+ *    owns every buffer it passes; the library copies what it keeps.
+ *  - Distances are squared L2. Results are sorted by ascending (distance, id);
+ *    missing results are padded with id -1 and distance +inf.
+ *  - Work is enqueued on the given cudaStream_t (passed as void*, NULL = the
+ *    legacy default stream) and is asynchronous unless stated otherwise.
+ *  - Only one search may run on an index at a time: the index owns its
+ *    workspace. Searches on distinct indexes may run concurrently.
+ */
+#ifndef ANNS_AMP_H
+#define ANNS_AMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ANNS_OK 0
+#define ANNS_ERR_INVALID_ARG (-1)
+#define ANNS_ERR_OOM (-2)
+#define ANNS_ERR_CUDA (-3)
+#define ANNS_ERR_TIMEOUT (-4)
+#define ANNS_ERR_UNSUPPORTED (-5)
+
+#define ANNS_KSUB 256      /* codebook entries per sub-space: codes are uint8 */
+#define ANNS_MAX_M 128     /* sub-spaces per vector */
+#define ANNS_MAX_NPROBE 128
+#define ANNS_MAX_K 128
+
+typedef struct anns_index anns_index; /* opaque, library-owned */
+
+/* Index arrays (Section 2.1: IVF lists + PQ with one codebook shared by all
+ * clusters, trained on residuals).
+ *  centroids [nlist * dim] float32, row-major.
+ *  codebooks [M * 256 * dsub] float32, dsub = dim / M; entry (m, c) holds the
+ *            sub-vector for dimensions [m*dsub, (m+1)*dsub).
+ *  codes     [n * M] uint8, row-major; codes[i*M + m] indexes codebook m.
+ *  list_of   [n] int32 in [0, nlist): the list (cluster) of each vector.
+ *  ids       [n] int64 user ids, or NULL for the row index. Ties in distance
+ *            are broken by ascending id.
+ *  on_device 1 if the five arrays are device pointers, 0 if host pointers. */
+typedef struct {
+  int64_t n, dim, nlist, M, ksub;
+  const float* centroids;
+  const float* codebooks;
+  const uint8_t* codes;
+  const int32_t* list_of;
+  const int64_t* ids;
+  int32_t on_device;
+  int32_t device; /* CUDA device ordinal the index lives on */
+} anns_build_desc;
+
+/* Builds an index on desc->device: copies the arrays, packs each list's codes
+ * into the warp-interleaved 16-byte layout and derives per-list sizes and
+ * covering radii (FP64, the r of Eq. 1). Synchronous. Errors: INVALID_ARG
+ * (shape or value out of range, dim % M != 0, ksub != 256, M > 128, a list id
+ * outside [0, nlist)), OOM, CUDA. *out is set only on success. */
+int anns_build_index_from_arrays(const anns_build_desc* desc, anns_index** out);
+
+/* Frees the index and all device memory it owns. NULL is a no-op. */
+void anns_free(anns_index* index);
+
+/* Precision of each (query, probed list) LUT (Section 3: cluster-level
+ * precision). */
+enum {
+  ANNS_LUT_PLAIN_FP32 = 0,    /* FP32 LUT, FP32 accumulation, every pair */
+  ANNS_LUT_FIXED_BITS = 1,    /* every pair at fixed_bits */
+  ANNS_LUT_HEURISTIC_EQ2 = 2, /* Eq. 2 feature f = d' - 3 r1 - r2 against thresholds */
+  ANNS_LUT_MLP = 3,           /* learned predictor with full-precision fallback */
+  ANNS_LUT_EXPLICIT = 4       /* caller-provided bits per (query, probe rank) */
+};
+enum { ANNS_PREC_FP32 = 0, ANNS_PREC_BF16 = 1, ANNS_PREC_FP8E4M3 = 2 };
+
+typedef struct {
+  int32_t lut_mode;        /* ANNS_LUT_* */
+  int32_t fixed_bits;      /* 4, 6, 8, 12 or 16 (FIXED_BITS) */
+  int32_t cl_prec;         /* ANNS_PREC_* for the coarse distances; FP32 only for now */
+  int32_t lc_prec;         /* ANNS_PREC_* for the LUT build; FP32 only for now */
+  float eq2_thresholds[4]; /* HEURISTIC_EQ2: g thresholds for 4, 6, 8, 12 bits */
+  float fallback_margin;   /* MLP: FP32 LUT when top1 - top2 logit < margin */
+  const uint8_t* pair_bits;/* EXPLICIT: device [nq * nprobe], 0 = FP32 */
+} anns_precision_policy;
+
+/* Batched search (Section 2.1, stages CL -> RC -> LC -> DC -> TS).
+ *  queries      device float32 [nq * dim].
+ *  nprobe       lists probed per query, 1 <= nprobe <= min(nlist, 128).
+ *  nprobe_per_q NULL, or device int32 [nq]: per-query nprobe, clamped to [0, nprobe].
+ *  k            results per query, 1 <= k <= 128.
+ *  k_per_q      NULL, or device int32 [nq]: per-query k, clamped to [0, k];
+ *               slots beyond a query's k are padding.
+ *  policy       precision choice (NULL = plain FP32).
+ *  ids_out      device int64 [nq * k], dists_out device float32 [nq * k].
+ * Within one precision policy the output is deterministic and equals the
+ * CPU oracle's bit for bit. Errors: INVALID_ARG, OOM, CUDA. */
+int anns_search(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
+                const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,
+                const anns_precision_policy* policy, int64_t* ids_out, float* dists_out,
+                void* cuda_stream);
+
+/* anns_search with HOST buffers: queries (host float32 [nq*dim]),
+ * nprobe_per_q / k_per_q (host int32 [nq] or NULL) and ids_out / dists_out
+ * (host). Copies in, searches and copies out on cuda_stream, then waits for
+ * the stream. Host buffers should be pinned for full copy speed.
+ * policy->pair_bits, if used, is still a device pointer. */
+int anns_search_host(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
+                     const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,
+                     const anns_precision_policy* policy, int64_t* ids_out, float* dists_out,
+                     void* cuda_stream);
+
+/* Index facts. */
+typedef struct {
+  int64_t n, dim, nlist, M, dsub, Mp; /* Mp = M rounded up to 16 (packed code row) */
+  int64_t code_bytes;                 /* bytes of packed codes in device memory */
+  int64_t max_list;                   /* largest list */
+  int32_t device;
+} anns_index_info;
+int anns_get_info(const anns_index* index, anns_index_info* out);
+
+/* Debug taps: copy library state to a HOST buffer of `bytes` bytes
+ * (synchronous). Taps of the last search (valid until the next search):
+ *   PROBES   int32 [nq * nprobe]  probed lists by rank (-1 past a query's nprobe)
+ *   PROBE_D2 float [nq * nprobe]  their FP32 coarse distances
+ *   BITS     uint8 [nq * nprobe]  chosen bits per pair (0 = FP32 LUT)
+ *   FEATURES float [nq * nprobe * 5] predictor features (MLP / EQ2 modes)
+ * Index taps:
+ *   LIST_SIZES int64 [nlist], LIST_RADIUS float [nlist],
+ *   PACKED_IDS int64 [n] (ids in list order, lists ascending). */
+enum {
+  ANNS_TAP_PROBES = 0, ANNS_TAP_PROBE_D2 = 1, ANNS_TAP_BITS = 2, ANNS_TAP_FEATURES = 3,
+  ANNS_TAP_LIST_SIZES = 10, ANNS_TAP_LIST_RADIUS = 11, ANNS_TAP_PACKED_IDS = 12
+};
+int anns_debug_tap(anns_index* index, int32_t what, void* out, size_t bytes);
+
+/* LUT construction + quantisation for explicit pairs (RC + LC of Section 2.1
+ * and the per-pair precision), with the same device code the search uses.
+ *  queries  device float32 [nq * dim]; pair_q, pair_l device int32 [npairs];
+ *  pair_bits device uint8 [npairs] (0 = FP32 only).
+ *  T_out     device float32 [npairs * M * 256] FP32 LUT, or NULL.
+ *  t_out     device uint16  [npairs * M * 256] quantised levels, or NULL.
+ *  scale_out device float64 [npairs * 4]: (Delta, B, range, s), or NULL. */
+int anns_compute_luts(anns_index* index, const float* queries, int64_t nq,
+                      const int32_t* pair_q, const int32_t* pair_l, const uint8_t* pair_bits,
+                      int64_t npairs, float* T_out, uint16_t* t_out, double* scale_out,
+                      void* cuda_stream);
+
+/* ADC scan of whole lists for explicit pairs (DC of Section 2.1): for pair p,
+ * the n_l distances of list pair_l[p] in list order are written at
+ * dist_out + out_off[p] (device int64 [npairs]), and, for quantised pairs,
+ * the integer sums S at S_out + out_off[p] (device int32, or NULL). */
+int anns_scan_pairs(anns_index* index, const float* queries, int64_t nq,
+                    const int32_t* pair_q, const int32_t* pair_l, const uint8_t* pair_bits,
+                    int64_t npairs, const int64_t* out_off, float* dist_out, int32_t* S_out,
+                    void* cuda_stream);
+
+/* Stage timing with CUDA events recorded on the search stream around each
+ * kernel of anns_search: CL distances, CL selection, precision choice, and the
+ * fused LUT + scan + top-k kernel.
+ *  enable  1 = start recording (and clear the totals), 0 = stop, -1 = leave as is.
+ *  out_ms  host double [4] or NULL: accumulated milliseconds per stage since
+ *          recording started (waits for the recorded searches to finish).
+ *  count   host int64 or NULL: number of searches accumulated. */
+int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* count);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* anns_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANNS_AMP_H */

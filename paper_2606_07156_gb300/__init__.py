@@ -1,0 +1,143 @@
+"""Adaptive mixed-precision IVF-PQ search on one GB300 (sm_103a).
+
+The compute lives in ``libanns_amp.so`` (hand-written CUDA kernels behind the C
+ABI of include/anns_amp.h). This package is the thin Python side: ``abi``
+binds the C entry points by name, and ``Index`` below marshals numpy arrays
+and torch tensors (used only as device memory) into those calls.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import abi
+from .abi import AnnsError  # noqa: F401
+
+_MODES = {"plain": abi.LUT_PLAIN_FP32, "fixed": abi.LUT_FIXED_BITS, "eq2": abi.LUT_HEURISTIC_EQ2,
+          "mlp": abi.LUT_MLP, "explicit": abi.LUT_EXPLICIT}
+
+
+def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), margin: float = 0.0,
+           pair_bits=None) -> abi.anns_precision_policy:
+    """Builds an anns_precision_policy. ``pair_bits`` (EXPLICIT) is a uint8 CUDA tensor."""
+    p = abi.anns_precision_policy()
+    p.lut_mode = _MODES[mode]
+    p.fixed_bits = int(bits)
+    p.cl_prec = abi.PREC_FP32
+    p.lc_prec = abi.PREC_FP32
+    for i, t in enumerate(thresholds):
+        p.eq2_thresholds[i] = float(t)
+    p.fallback_margin = float(margin)
+    p.pair_bits = None if pair_bits is None else pair_bits.data_ptr()
+    return p
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Index:
+    """An index owned by the library, built from host arrays (Section 2.1)."""
+
+    def __init__(self, centroids, codebooks, codes, list_of, ids=None, device: int = 0):
+        cent = np.ascontiguousarray(centroids, dtype=np.float32)
+        books = np.ascontiguousarray(codebooks, dtype=np.float32)
+        codes = np.ascontiguousarray(codes, dtype=np.uint8)
+        lo = np.ascontiguousarray(list_of, dtype=np.int32)
+        uid = None if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+        d = abi.anns_build_desc()
+        d.n, d.dim = codes.shape[0], cent.shape[1]
+        d.nlist, d.M, d.ksub = cent.shape[0], codes.shape[1] if codes.ndim == 2 else books.shape[0], 256
+        d.centroids, d.codebooks, d.codes = cent.ctypes.data, books.ctypes.data, codes.ctypes.data
+        d.list_of = lo.ctypes.data
+        d.ids = None if uid is None else uid.ctypes.data
+        d.on_device, d.device = 0, device
+        self.device = device
+        self.handle = abi.anns_build_index_from_arrays(d)
+        self.info = abi.anns_get_info(self.handle)
+        self.dim, self.nlist, self.M = self.info.dim, self.info.nlist, self.info.M
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.anns_free(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def search(self, queries, nprobe: int, k: int, pol=None, nprobe_per_q=None, k_per_q=None,
+               stream=None, out=None):
+        """queries: float32 CUDA tensor [nq, dim]. Returns (ids int64, dists float32) CUDA tensors."""
+        import torch
+        nq = queries.shape[0]
+        if out is None:
+            ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+            dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+        else:
+            ids, dists = out
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_search(self.handle, _ptr(queries), nq, nprobe, _ptr(nprobe_per_q), k, _ptr(k_per_q),
+                        pol, _ptr(ids), _ptr(dists), s)
+        return ids, dists
+
+    def search_host(self, queries, nprobe: int, k: int, pol=None, nprobe_per_q=None, k_per_q=None,
+                    stream=None, out=None):
+        """Host buffers in and out (pinned torch CPU tensors or numpy arrays); synchronous."""
+        nq = queries.shape[0]
+        if out is None:
+            ids = np.empty((nq, k), dtype=np.int64)
+            dists = np.empty((nq, k), dtype=np.float32)
+        else:
+            ids, dists = out
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_search_host(self.handle, _ptr(queries), nq, nprobe, _ptr(nprobe_per_q), k,
+                             _ptr(k_per_q), pol, _ptr(ids), _ptr(dists), s)
+        return ids, dists
+
+    def tap(self, what: int, shape, dtype):
+        out = np.empty(shape, dtype=dtype)
+        abi.anns_debug_tap(self.handle, what, out.ctypes.data, out.nbytes)
+        return out
+
+    def list_sizes(self):
+        return self.tap(abi.TAP_LIST_SIZES, (self.nlist,), np.int64)
+
+    def list_radius(self):
+        return self.tap(abi.TAP_LIST_RADIUS, (self.nlist,), np.float32)
+
+    def packed_ids(self):
+        return self.tap(abi.TAP_PACKED_IDS, (self.info.n,), np.int64)
+
+    def compute_luts(self, queries, pair_q, pair_l, pair_bits, stream=None):
+        """FP32 LUTs, quantised levels and (Delta, B, range, s) for explicit pairs (CUDA tensors)."""
+        import torch
+        n = pair_q.shape[0]
+        dev = queries.device
+        T = torch.empty((n, self.M, 256), dtype=torch.float32, device=dev)
+        t = torch.empty((n, self.M, 256), dtype=torch.int16, device=dev)
+        sc = torch.empty((n, 4), dtype=torch.float64, device=dev)
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_compute_luts(self.handle, _ptr(queries), queries.shape[0], _ptr(pair_q), _ptr(pair_l),
+                              _ptr(pair_bits), n, _ptr(T), _ptr(t), _ptr(sc), s)
+        return T, t, sc
+
+    def scan_pairs(self, queries, pair_q, pair_l, pair_bits, stream=None):
+        """Every distance (and integer sum) of each pair's list, concatenated in pair order."""
+        import torch
+        sizes = self.list_sizes()
+        pl = pair_l.cpu().numpy()
+        n_each = sizes[pl]
+        off = np.concatenate([[0], np.cumsum(n_each)[:-1]]).astype(np.int64)
+        total = int(n_each.sum())
+        dev = queries.device
+        offt = torch.from_numpy(off).to(dev)
+        dist = torch.empty(max(total, 1), dtype=torch.float32, device=dev)
+        S = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_scan_pairs(self.handle, _ptr(queries), queries.shape[0], _ptr(pair_q), _ptr(pair_l),
+                            _ptr(pair_bits), pair_q.shape[0], _ptr(offt), _ptr(dist), _ptr(S), s)
+        return dist[:total], S[:total], off, n_each

@@ -1,0 +1,146 @@
+"""ctypes binding of include/anns_amp.h — argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the search: device buffers are passed as raw pointers (torch
+tensors are used only to own device memory). If the shared library is
+missing, importing this module raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libanns_amp.so")
+
+ANNS_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSUPPORTED"}
+LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT = 0, 1, 2, 3, 4
+PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
+TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
+TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS = 10, 11, 12
+
+SYMBOLS = (
+    "anns_build_index_from_arrays", "anns_free", "anns_search", "anns_search_host",
+    "anns_get_info", "anns_debug_tap", "anns_compute_luts", "anns_scan_pairs", "anns_profile",
+    "anns_last_error",
+)
+
+
+class AnnsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class anns_build_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int64), ("nlist", ctypes.c_int64),
+                ("M", ctypes.c_int64), ("ksub", ctypes.c_int64),
+                ("centroids", ctypes.c_void_p), ("codebooks", ctypes.c_void_p),
+                ("codes", ctypes.c_void_p), ("list_of", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class anns_precision_policy(ctypes.Structure):
+    _fields_ = [("lut_mode", ctypes.c_int32), ("fixed_bits", ctypes.c_int32),
+                ("cl_prec", ctypes.c_int32), ("lc_prec", ctypes.c_int32),
+                ("eq2_thresholds", ctypes.c_float * 4), ("fallback_margin", ctypes.c_float),
+                ("pair_bits", ctypes.c_void_p)]
+
+
+class anns_index_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int64), ("nlist", ctypes.c_int64),
+                ("M", ctypes.c_int64), ("dsub", ctypes.c_int64), ("Mp", ctypes.c_int64),
+                ("code_bytes", ctypes.c_int64), ("max_list", ctypes.c_int64),
+                ("device", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2606_07156_gb300.build.build() "
+                          "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+    sig = {
+        "anns_build_index_from_arrays": ([ctypes.POINTER(anns_build_desc), ctypes.POINTER(vp)], i32),
+        "anns_free": ([vp], None),
+        "anns_search": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), vp, vp, vp], i32),
+        "anns_search_host": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), vp, vp, vp], i32),
+        "anns_get_info": ([vp, ctypes.POINTER(anns_index_info)], i32),
+        "anns_debug_tap": ([vp, i32, vp, sz], i32),
+        "anns_compute_luts": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
+        "anns_scan_pairs": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
+        "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
+        "anns_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def anns_last_error() -> str:
+    return _lib.anns_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != ANNS_OK:
+        raise AnnsError(rc, anns_last_error())
+
+
+def anns_build_index_from_arrays(desc: anns_build_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.anns_build_index_from_arrays(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def anns_free(index: int) -> None:
+    _lib.anns_free(index)
+
+
+def anns_search(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, policy, ids_out, dists_out,
+                stream=None) -> None:
+    _check(_lib.anns_search(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q,
+                            ctypes.byref(policy) if policy is not None else None,
+                            ids_out, dists_out, stream))
+
+
+def anns_search_host(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, policy, ids_out,
+                     dists_out, stream=None) -> None:
+    _check(_lib.anns_search_host(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q,
+                                 ctypes.byref(policy) if policy is not None else None,
+                                 ids_out, dists_out, stream))
+
+
+def anns_get_info(index) -> anns_index_info:
+    info = anns_index_info()
+    _check(_lib.anns_get_info(index, ctypes.byref(info)))
+    return info
+
+
+def anns_debug_tap(index, what: int, out_ptr: int, nbytes: int) -> None:
+    _check(_lib.anns_debug_tap(index, what, out_ptr, nbytes))
+
+
+def anns_compute_luts(index, queries, nq, pair_q, pair_l, pair_bits, npairs, T_out, t_out, scale_out,
+                      stream=None) -> None:
+    _check(_lib.anns_compute_luts(index, queries, nq, pair_q, pair_l, pair_bits, npairs,
+                                  T_out, t_out, scale_out, stream))
+
+
+def anns_scan_pairs(index, queries, nq, pair_q, pair_l, pair_bits, npairs, out_off, dist_out, S_out,
+                    stream=None) -> None:
+    _check(_lib.anns_scan_pairs(index, queries, nq, pair_q, pair_l, pair_bits, npairs,
+                                out_off, dist_out, S_out, stream))
+
+
+def anns_profile(index, enable: int):
+    """Returns (ms per stage [4], number of searches) accumulated since recording started."""
+    ms = (ctypes.c_double * 4)()
+    cnt = ctypes.c_int64()
+    _check(_lib.anns_profile(index, enable, ms, ctypes.byref(cnt)))
+    return list(ms), cnt.value

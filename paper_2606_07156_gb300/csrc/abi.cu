@@ -1,0 +1,304 @@
+// anns_search and friends: argument checks, workspace, and the launch sequence
+// CL -> precision choice -> (RC + LC + quantise + DC + TS) of Section 2.1.
+#include <cstring>
+#include <utility>
+
+#include "common.cuh"
+#include "internal.h"
+#include "predictor.cuh"
+
+namespace anns {
+namespace {
+
+struct PolicyArgs {
+  int64_t nq; int nprobe; const int32_t* npq;
+  const int32_t* probes; const float* probe_d2;
+  const int32_t* list_len; const float* radius;
+  int mode, fixed_bits; float th[4]; float margin;
+  const uint8_t* pair_bits; const void* mlp;
+  uint8_t* bits; float* feat;
+};
+
+__device__ __forceinline__ uint8_t sanitize_bits(int b) { return (b >= 1 && b <= 16) ? (uint8_t)b : 0; }
+
+// Features of probe rank j (Section 3.3: query distance d', radii r1 and r2,
+// size n; plus the probe rank): (sqrt(D2_j) - sqrt(D2_0), r_0, r_j, sqrt(n_j), j/nprobe_q).
+__device__ __forceinline__ void features_of(const PolicyArgs& p, int64_t q, int j, int np, float f[5]) {
+  const int64_t row = q * p.nprobe;
+  const int l0 = p.probes[row], lj = p.probes[row + j];
+  if (l0 < 0 || lj < 0) return;
+  f[0] = sub_rn(__fsqrt_rn(p.probe_d2[row + j]), __fsqrt_rn(p.probe_d2[row]));
+  f[1] = p.radius[l0];
+  f[2] = p.radius[lj];
+  f[3] = __fsqrt_rn((float)p.list_len[lj]);
+  f[4] = __fdiv_rn((float)j, (float)np);
+}
+
+// Eq. 2 heuristic: g = f / r_j with f = d' - 3 r_0 - r_j; the fewest bits whose
+// threshold g reaches (thresholds non-increasing), else 16.
+__device__ __forceinline__ uint8_t eq2_bits(const float f[5], const float th[4]) {
+  const float fe = sub_rn(sub_rn(f[0], mul_rn(3.f, f[1])), f[2]);
+  const float g = f[2] > 0.f ? __fdiv_rn(fe, f[2]) : -INFINITY;
+  uint8_t b = 16;
+  if (g >= th[3]) b = 12;
+  if (g >= th[2]) b = 8;
+  if (g >= th[1]) b = 6;
+  if (g >= th[0]) b = 4;
+  return b;
+}
+
+__global__ void policy_kernel(const PolicyArgs p) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p.nq * p.nprobe) return;
+  const int64_t q = idx / p.nprobe;
+  const int j = (int)(idx % p.nprobe);
+  const int np = p.npq ? min(max(p.npq[q], 0), p.nprobe) : p.nprobe;
+  const int l = p.probes[idx];
+  float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  uint8_t b = 0;
+  if (j < np && l >= 0) {
+    switch (p.mode) {
+      case ANNS_LUT_PLAIN_FP32: b = 0; break;
+      case ANNS_LUT_FIXED_BITS: b = (uint8_t)p.fixed_bits; break;
+      case ANNS_LUT_EXPLICIT: b = sanitize_bits(p.pair_bits[idx]); break;
+      case ANNS_LUT_HEURISTIC_EQ2:
+        features_of(p, q, j, np, f);
+        b = eq2_bits(f, p.th);
+        break;
+      case ANNS_LUT_MLP:
+        features_of(p, q, j, np, f);
+        b = mlp_decide(*(const MlpParams16*)p.mlp, f, p.margin);
+        break;
+    }
+  }
+  p.bits[idx] = b;
+  if (p.feat) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) p.feat[idx * 5 + i] = f[i];
+  }
+}
+
+bool valid_bits(int b) { return b == 4 || b == 6 || b == 8 || b == 12 || b == 16; }
+
+struct DeviceGuard {
+  int prev = 0;
+  explicit DeviceGuard(int d) { cudaGetDevice(&prev); cudaSetDevice(d); }
+  ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+int ensure_workspace(Index& ix, int64_t nq, int nprobe) {
+  int rc = grow((void**)&ix.ws_d2, &ix.ws_d2_cap, (size_t)nq * ix.nlist * 4);
+  if (rc) return rc;
+  const size_t P = (size_t)nq * nprobe;
+  // one block: probes (4P) | probe_d2 (4P) | features (20P) | bits (P)
+  void* blk = ix.ws_probes;
+  rc = grow(&blk, &ix.ws_pair_cap, P * 29 + 64);
+  if (rc) return rc;
+  ix.ws_probes = (int32_t*)blk;
+  ix.ws_probe_d2 = (float*)((char*)blk + 4 * P);
+  ix.ws_feat = (float*)((char*)blk + 8 * P);
+  ix.ws_bits = (uint8_t*)((char*)blk + 28 * P);
+  ix.ws_nq = nq;
+  ix.ws_nprobe = nprobe;
+  return ANNS_OK;
+}
+
+// Folds finished event sets into the totals; with `all`, waits for every set.
+int drain_profile(Index& ix, bool all) {
+  int keep = 0;
+  for (int i = 0; i < ix.prof_pending; ++i) {
+    cudaEvent_t* ev = ix.prof_ev[i];
+    cudaError_t q = all ? cudaEventSynchronize(ev[Index::kStages]) : cudaEventQuery(ev[Index::kStages]);
+    if (q == cudaSuccess) {
+      for (int st = 0; st < Index::kStages; ++st) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[st], ev[st + 1]);
+        ix.prof_ms[st] += ms;
+      }
+      ix.prof_count++;
+    } else if (q == cudaErrorNotReady) {
+      if (keep != i)
+        for (int st = 0; st <= Index::kStages; ++st) std::swap(ix.prof_ev[keep][st], ix.prof_ev[i][st]);
+      keep++;
+    } else {
+      return cuda_fail(q, "profile event");
+    }
+  }
+  ix.prof_pending = keep;
+  return ANNS_OK;
+}
+
+// Event set for the next search, or nullptr when profiling is off.
+cudaEvent_t* next_profile_slot(Index& ix) {
+  if (!ix.prof_on) return nullptr;
+  if (ix.prof_pending == Index::kProfSlots && drain_profile(ix, true)) return nullptr;
+  cudaEvent_t* ev = ix.prof_ev[ix.prof_pending];
+  for (int st = 0; st <= Index::kStages; ++st)
+    if (!ev[st] && cudaEventCreate(&ev[st]) != cudaSuccess) return nullptr;
+  ix.prof_pending++;
+  return ev;
+}
+
+}  // namespace
+
+int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq, int nprobe,
+                  const int32_t* nprobe_per_q, const int32_t* probes, const float* probe_d2,
+                  uint8_t* bits, float* feat, cudaStream_t s) {
+  PolicyArgs p{};
+  p.nq = nq; p.nprobe = nprobe; p.npq = nprobe_per_q; p.probes = probes; p.probe_d2 = probe_d2;
+  p.list_len = ix.list_len; p.radius = ix.radius; p.mode = pol.lut_mode;
+  p.fixed_bits = pol.fixed_bits;
+  for (int i = 0; i < 4; ++i) p.th[i] = pol.eq2_thresholds[i];
+  p.margin = pol.fallback_margin; p.pair_bits = pol.pair_bits; p.mlp = ix.mlp_dev;
+  p.bits = bits; p.feat = feat;
+  const int64_t n = nq * nprobe;
+  policy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "policy kernel");
+}
+
+}  // namespace anns
+
+using namespace anns;
+
+static int check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe, int32_t k,
+                             const anns_precision_policy* pol, const void* ids_out,
+                             const void* dists_out) {
+  if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
+  if (nq < 0) return fail(ANNS_ERR_INVALID_ARG, "nq must be >= 0");
+  if (nq > 0 && (!Q || !ids_out || !dists_out)) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
+  if (nprobe < 1 || nprobe > ix->nlist || nprobe > ANNS_MAX_NPROBE)
+    return fail(ANNS_ERR_INVALID_ARG, "nprobe must be in [1, min(nlist, 128)]");
+  if (k < 1 || k > ANNS_MAX_K) return fail(ANNS_ERR_INVALID_ARG, "k must be in [1, 128]");
+  if (nq > (int64_t)INT32_MAX) return fail(ANNS_ERR_INVALID_ARG, "nq too large");
+  if (pol) {
+    switch (pol->lut_mode) {
+      case ANNS_LUT_PLAIN_FP32: case ANNS_LUT_HEURISTIC_EQ2: break;
+      case ANNS_LUT_FIXED_BITS:
+        if (!valid_bits(pol->fixed_bits)) return fail(ANNS_ERR_INVALID_ARG, "fixed_bits must be 4/6/8/12/16");
+        break;
+      case ANNS_LUT_EXPLICIT:
+        if (!pol->pair_bits && nq > 0) return fail(ANNS_ERR_INVALID_ARG, "EXPLICIT needs pair_bits");
+        break;
+      case ANNS_LUT_MLP:
+        if (!ix->has_mlp) return fail(ANNS_ERR_INVALID_ARG, "MLP policy needs a trained or loaded predictor");
+        break;
+      default: return fail(ANNS_ERR_INVALID_ARG, "unknown lut_mode");
+    }
+    if (pol->cl_prec != ANNS_PREC_FP32 || pol->lc_prec != ANNS_PREC_FP32)
+      return fail(ANNS_ERR_UNSUPPORTED, "only FP32 CL/LC operands are available");
+  }
+  return ANNS_OK;
+}
+
+extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe,
+                           const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,
+                           const anns_precision_policy* pol, int64_t* ids_out, float* dists_out,
+                           void* stream) {
+  int rc = check_search_args(ix, Q, nq, nprobe, k, pol, ids_out, dists_out);
+  if (rc) return rc;
+  if (nq == 0) return ANNS_OK;
+  DeviceGuard g(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = ensure_workspace(*ix, nq, nprobe))) return rc;
+  anns_precision_policy plain{};
+  plain.lut_mode = ANNS_LUT_PLAIN_FP32;
+  const anns_precision_policy& P = pol ? *pol : plain;
+  cudaEvent_t* ev = next_profile_slot(*ix);
+  if (ev) cudaEventRecord(ev[0], s);
+  cudaError_t e = launch_coarse(*ix, Q, nq, nprobe, nprobe_per_q, ix->ws_d2, ix->ws_probes,
+                                ix->ws_probe_d2, s, ev ? ev[1] : nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "coarse kernels");
+  if (ev) cudaEventRecord(ev[2], s);
+  const bool want_feat = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2;
+  if ((rc = launch_policy(*ix, P, nq, nprobe, nprobe_per_q, ix->ws_probes, ix->ws_probe_d2,
+                          ix->ws_bits, want_feat ? ix->ws_feat : nullptr, s)))
+    return rc;
+  if (ev) cudaEventRecord(ev[3], s);
+  e = launch_search(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes, ix->ws_bits,
+                    ids_out, dists_out, s);
+  if (e != cudaSuccess) return cuda_fail(e, "search kernel");
+  if (ev) cudaEventRecord(ev[4], s);
+  return ANNS_OK;
+}
+
+extern "C" int anns_search_host(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe,
+                                const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,
+                                const anns_precision_policy* pol, int64_t* ids_out,
+                                float* dists_out, void* stream) {
+  int rc = check_search_args(ix, Q, nq, nprobe, k, pol, ids_out, dists_out);
+  if (rc) return rc;
+  if (nq == 0) return ANNS_OK;
+  DeviceGuard g(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t qb = (size_t)nq * ix->dim * 4, ob = (size_t)nq * k * 12, pb = (size_t)nq * 8;
+  if ((rc = grow(&ix->st_q, &ix->st_q_cap, qb)) || (rc = grow(&ix->st_out, &ix->st_out_cap, ob)) ||
+      (rc = grow(&ix->st_pq, &ix->st_pq_cap, pb)))
+    return rc;
+  float* dq = (float*)ix->st_q;
+  int64_t* di = (int64_t*)ix->st_out;
+  float* dd = (float*)((char*)ix->st_out + (size_t)nq * k * 8);
+  int32_t* dnp = nprobe_per_q ? (int32_t*)ix->st_pq : nullptr;
+  int32_t* dk = k_per_q ? (int32_t*)ix->st_pq + nq : nullptr;
+  cudaError_t e = cudaMemcpyAsync(dq, Q, qb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && dnp) e = cudaMemcpyAsync(dnp, nprobe_per_q, nq * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && dk) e = cudaMemcpyAsync(dk, k_per_q, nq * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy queries in");
+  if ((rc = anns_search(ix, dq, nq, nprobe, dnp, k, dk, pol, di, dd, stream))) return rc;
+  e = cudaMemcpyAsync(ids_out, di, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dists_out, dd, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy results out");
+  return ANNS_OK;
+}
+
+static int check_pairs(anns_index* ix, const float* Q, int64_t nq, const int32_t* pq,
+                       const int32_t* pl, const uint8_t* pb, int64_t npairs) {
+  if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
+  if (npairs < 0 || nq < 0) return fail(ANNS_ERR_INVALID_ARG, "negative size");
+  if (npairs > 0 && (!Q || !pq || !pl || !pb)) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
+  return ANNS_OK;
+}
+
+extern "C" int anns_compute_luts(anns_index* ix, const float* Q, int64_t nq, const int32_t* pq,
+                                 const int32_t* pl, const uint8_t* pb, int64_t npairs,
+                                 float* T_out, uint16_t* t_out, double* scale_out, void* stream) {
+  int rc = check_pairs(ix, Q, nq, pq, pl, pb, npairs);
+  if (rc) return rc;
+  if (npairs == 0) return ANNS_OK;
+  DeviceGuard g(ix->device);
+  cudaError_t e = launch_compute_luts(*ix, Q, nq, pq, pl, pb, npairs, T_out, t_out, scale_out,
+                                      (cudaStream_t)stream);
+  return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "LUT kernel");
+}
+
+extern "C" int anns_scan_pairs(anns_index* ix, const float* Q, int64_t nq, const int32_t* pq,
+                               const int32_t* pl, const uint8_t* pb, int64_t npairs,
+                               const int64_t* off, float* dist_out, int32_t* S_out, void* stream) {
+  int rc = check_pairs(ix, Q, nq, pq, pl, pb, npairs);
+  if (rc) return rc;
+  if (npairs == 0) return ANNS_OK;
+  if (!off || !dist_out) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
+  DeviceGuard g(ix->device);
+  cudaError_t e = launch_scan_pairs(*ix, Q, nq, pq, pl, pb, npairs, off, dist_out, S_out,
+                                    (cudaStream_t)stream);
+  return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "scan kernel");
+}
+
+extern "C" int anns_profile(anns_index* ix, int32_t enable, double* out_ms, int64_t* count) {
+  if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
+  DeviceGuard g(ix->device);
+  int rc = drain_profile(*ix, true);
+  if (rc) return rc;
+  if (enable == 1) {
+    ix->prof_on = true;
+    for (double& v : ix->prof_ms) v = 0.0;
+    ix->prof_count = 0;
+  } else if (enable == 0) {
+    ix->prof_on = false;
+  }
+  if (out_ms)
+    for (int st = 0; st < Index::kStages; ++st) out_ms[st] = ix->prof_ms[st];
+  if (count) *count = ix->prof_count;
+  return ANNS_OK;
+}

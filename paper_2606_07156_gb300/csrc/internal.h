@@ -1,0 +1,99 @@
+// Library-internal declarations shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "anns_amp.h"
+
+namespace anns {
+
+constexpr int kKsub = 256;
+constexpr int kTileVecs = 32;         // vectors per code tile (one per lane)
+constexpr int kChunkBytes = 16;       // code bytes a lane loads at once
+constexpr int kTileChunkBytes = 512;  // one 16-byte chunk for all 32 lanes
+constexpr int kNFeat = 5, kH1 = 32, kH2 = 32, kNCls = 5;
+
+// Device-resident index (Section 2.1: IVF lists + PQ codes, one shared codebook).
+//
+// Packed code layout: list l owns tiles [tile_off[l], tile_off[l+1]); a tile
+// holds 32 vectors and nchunk = Mp/16 chunks of 512 bytes. Byte m of vector
+// (tile t, lane i) sits at  codes + (t*nchunk + m/16)*512 + i*16 + m%16, so a
+// warp reads one chunk of a tile with one coalesced 16-byte load per lane.
+// Vectors past n_l in a list's last tile have all-zero codes and are masked.
+struct Index {
+  int device = 0;
+  int64_t n = 0, dim = 0, nlist = 0, M = 0, dsub = 0, Mp = 0, nchunk = 0;
+  int64_t ntiles = 0, max_list = 0;
+  float* centroids = nullptr;   // [nlist*dim]
+  float* codebooks = nullptr;   // [M*256*dsub]
+  uint8_t* codes = nullptr;     // [ntiles*nchunk*512]
+  int64_t* ids = nullptr;       // [n] user ids in list order
+  int32_t* list_len = nullptr;  // [nlist]
+  int64_t* vec_off = nullptr;   // [nlist+1]
+  int64_t* tile_off = nullptr;  // [nlist+1]
+  float* radius = nullptr;      // [nlist] covering radius, FP64-derived
+  // host copies of the small per-list tables
+  std::string err;
+  int64_t* h_list_len64 = nullptr;
+  float* h_radius = nullptr;
+  // workspace of the last search
+  int64_t ws_nq = 0, ws_nprobe = 0;
+  float* ws_d2 = nullptr;        // [nq*nlist]
+  int32_t* ws_probes = nullptr;  // [nq*nprobe]
+  float* ws_probe_d2 = nullptr;  // [nq*nprobe]
+  uint8_t* ws_bits = nullptr;    // [nq*nprobe]
+  float* ws_feat = nullptr;      // [nq*nprobe*5]
+  size_t ws_d2_cap = 0, ws_pair_cap = 0;
+  // staging for anns_search_host
+  void* st_q = nullptr; size_t st_q_cap = 0;
+  void* st_out = nullptr; size_t st_out_cap = 0;
+  void* st_pq = nullptr; size_t st_pq_cap = 0;
+  // stage timing (anns_profile): pending event sets, accumulated ms
+  static constexpr int kProfSlots = 64, kStages = 4;
+  bool prof_on = false;
+  cudaEvent_t prof_ev[kProfSlots][kStages + 1] = {};
+  int prof_pending = 0;
+  double prof_ms[kStages] = {0, 0, 0, 0};
+  int64_t prof_count = 0;
+  // learned predictor (FP16 inference copy + normalisation), see predictor.cu
+  bool has_mlp = false;
+  void* mlp_dev = nullptr;       // device MlpParams16
+};
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Grows *p to at least `bytes` (cudaFree + cudaMalloc). Returns 0 or an error.
+int grow(void** p, size_t* cap, size_t bytes);
+
+// ---- launchers (all asynchronous on `s`) ----
+// CL: D2[q][l] by the FP32 rule, then per-query top-nprobe by (d, l).
+cudaError_t launch_coarse(const Index& ix, const float* Q, int64_t nq, int nprobe,
+                          const int32_t* nprobe_per_q, float* d2, int32_t* probes,
+                          float* probe_d2, cudaStream_t s, cudaEvent_t between = nullptr);
+// Precision choice per (query, probe rank).
+int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq, int nprobe,
+                  const int32_t* nprobe_per_q, const int32_t* probes, const float* probe_d2,
+                  uint8_t* bits, float* feat, cudaStream_t s);
+// RC + LC + quantise + DC + TS for every query.
+cudaError_t launch_search(const Index& ix, const float* Q, int64_t nq, int nprobe,
+                          const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
+                          const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
+                          float* dists_out, cudaStream_t s);
+cudaError_t launch_compute_luts(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
+                                const int32_t* pl, const uint8_t* pb, int64_t npairs,
+                                float* T_out, uint16_t* t_out, double* scale_out,
+                                cudaStream_t s);
+cudaError_t launch_scan_pairs(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
+                              const int32_t* pl, const uint8_t* pb, int64_t npairs,
+                              const int64_t* off, float* dist_out, int32_t* S_out,
+                              cudaStream_t s);
+
+}  // namespace anns
+
+// The opaque handle of the C ABI is the internal index.
+struct anns_index : public anns::Index {};

@@ -1,0 +1,66 @@
+// Learned precision predictor: inference rule (the PPM of Section 4.1; the
+// regressor of Section 3.4 is replaced by a 5-32-32-5 MLP classifier over the
+// bit widths 4/6/8/12/16).
+//
+// FP16 operands (weights, biases, normalised inputs, hidden activations) and
+// FP32 accumulation: acc = b; for i ascending: acc = fma(W[o][i], x[i], acc).
+// The product of two FP16 values is exact in FP32, so the FMA rounds exactly
+// once, like fl32(acc + W*x). Hidden layers apply ReLU and round to FP16;
+// logits stay FP32. The class is the argmax (ties to the lower class); the
+// pair falls back to the FP32 LUT (bits 0) when top1 - top2 < margin.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace anns {
+
+struct MlpParams16 {
+  __half W1[32 * 5], b1[32], W2[32 * 32], b2[32], W3[5 * 32], b3[5];
+  float mean[5], inv_std[5];
+};
+
+__device__ __forceinline__ uint8_t mlp_decide(const MlpParams16& P, const float f[5], float margin) {
+  constexpr uint8_t kBits[5] = {4, 6, 8, 12, 16};
+  float x[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    x[i] = __half2float(__float2half_rn(mul_rn(sub_rn(f[i], P.mean[i]), P.inv_std[i])));
+  float h1[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) {
+    float acc = __half2float(P.b1[o]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) acc = fmaf(__half2float(P.W1[o * 5 + i]), x[i], acc);
+    h1[o] = __half2float(__float2half_rn(fmaxf(acc, 0.f)));
+  }
+  float h2[32];
+#pragma unroll 4
+  for (int o = 0; o < 32; ++o) {
+    float acc = __half2float(P.b2[o]);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc = fmaf(__half2float(P.W2[o * 32 + i]), h1[i], acc);
+    h2[o] = __half2float(__float2half_rn(fmaxf(acc, 0.f)));
+  }
+  float z[5];
+#pragma unroll
+  for (int o = 0; o < 5; ++o) {
+    float acc = __half2float(P.b3[o]);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc = fmaf(__half2float(P.W3[o * 32 + i]), h2[i], acc);
+    z[o] = acc;
+  }
+  int c = 0;
+#pragma unroll
+  for (int o = 1; o < 5; ++o)
+    if (z[o] > z[c]) c = o;
+  float t2 = -INFINITY;
+#pragma unroll
+  for (int o = 0; o < 5; ++o)
+    if (o != c) t2 = fmaxf(t2, z[o]);
+  return sub_rn(z[c], t2) < margin ? (uint8_t)0 : kBits[c];
+}
+
+}  // namespace anns

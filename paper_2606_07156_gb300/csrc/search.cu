@@ -1,0 +1,452 @@
+// RC + LC + precision + DC + TS (Section 2.1) for one query per thread block.
+//
+// Per probed list l of query q, the block
+//   1. forms the residual r = fl32(q - c_l) in shared memory (RC),
+//   2. builds the FP32 LUT T[m][c] = sum_j fl32((r_{m,j} - y_{m,c,j})^2),
+//      j ascending, explicitly rounded (LC), into shared memory,
+//   3. if the pair's precision is b bits, quantises T with one shared step
+//      Delta = range/(2^b-1) and per-sub-table biases (scale/offset in FP64),
+//      into a uint8 (b <= 8) or uint16 table in shared memory,
+//   4. scans the list's packed codes tile by tile, one vector per lane,
+//      accumulating LUT entries in ascending m — FP32 sums for the plain LUT,
+//      exact int32 sums S for quantised LUTs, whose estimate is
+//      fl32(fl32(Delta32 * S) + B32) (DC),
+//   5. offers each distance to a per-warp sorted top-k list (TS).
+// The LUT never leaves shared memory. At the end the warps' lists are merged.
+#include "common.cuh"
+#include "internal.h"
+
+namespace anns {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct PairScal {
+  double delta64, B64;
+  float s32, delta32, B32, range;
+  int L;
+};
+
+struct SmemLayout {
+  size_t r = 0, T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, md = 0, mi = 0, total = 0;
+  static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
+  SmemLayout() = default;
+  SmemLayout(int64_t dim, int64_t Mp, int R) {
+    size_t o = 0;
+    r = o; o += al(dim * 4);
+    T = o; o += al(Mp * kKsub * 4);
+    q = o; o += al(Mp * kKsub * 2);
+    bias = o; o += al(Mp * 4);
+    rowmax = o; o += al(Mp * 4);
+    scal = o; o += al(sizeof(PairScal));
+    md = o; o += al((size_t)kWarps * R * 32 * 4);
+    mi = o; o += al((size_t)kWarps * R * 32 * 8);
+    total = o;
+  }
+};
+
+struct Smem {
+  float* r; float* T; void* q; float* bias; float* rowmax; PairScal* sc; float* md; int64_t* mi;
+  __device__ Smem(unsigned char* base, const SmemLayout& L)
+      : r((float*)(base + L.r)), T((float*)(base + L.T)), q(base + L.q),
+        bias((float*)(base + L.bias)), rowmax((float*)(base + L.rowmax)),
+        sc((PairScal*)(base + L.scal)), md((float*)(base + L.md)), mi((int64_t*)(base + L.mi)) {}
+};
+
+// Steps 1-3 for pair (q, c): all threads of the block take part.
+__device__ void build_lut(const float* __restrict__ qv, const float* __restrict__ cv,
+                          const float* __restrict__ cb, int dim, int M, int Mp, int dsub, int b,
+                          Smem& s) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int d = tid; d < dim; d += blockDim.x) s.r[d] = sub_rn(qv[d], cv[d]);
+  __syncthreads();
+  const int nent = Mp * kKsub;
+  for (int e = tid; e < nent; e += blockDim.x) {
+    const int m = e >> 8;
+    float acc = 0.f;
+    if (m < M) {
+      const float* y = cb + (size_t)e * dsub;
+      const float* rr = s.r + m * dsub;
+      for (int j = 0; j < dsub; ++j) {
+        const float x = sub_rn(rr[j], __ldg(y + j));
+        acc = add_rn(acc, mul_rn(x, x));
+      }
+    }
+    s.T[e] = acc;
+  }
+  __syncthreads();
+  if (b == 0) return;
+  for (int m = warp; m < M; m += blockDim.x / 32) {
+    const float* row = s.T + m * kKsub;
+    float mn = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mn = fminf(mn, row[lane + 32 * i]);
+    mn = warp_min(mn);
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mx = fmaxf(mx, sub_rn(row[lane + 32 * i], mn));
+    mx = warp_max(mx);
+    if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float range = 0.f;
+    for (int m = 0; m < M; ++m) range = fmaxf(range, s.rowmax[m]);
+    const int L = (1 << b) - 1;
+    PairScal sc;
+    if (range > 0.f) {
+      sc.delta64 = __ddiv_rn((double)range, (double)L);
+      sc.s32 = __double2float_rn(__ddiv_rn((double)L, (double)range));
+    } else {
+      sc.delta64 = 0.0;
+      sc.s32 = 0.f;
+    }
+    double B = 0.0;
+    for (int m = 0; m < M; ++m) B = __dadd_rn(B, (double)s.bias[m]);
+    sc.B64 = B;
+    sc.delta32 = __double2float_rn(sc.delta64);
+    sc.B32 = __double2float_rn(B);
+    sc.range = range;
+    sc.L = L;
+    *s.sc = sc;
+  }
+  __syncthreads();
+  const float s32 = s.sc->s32;
+  const int L = s.sc->L;
+  if (b <= 8) {
+    uint8_t* t8 = (uint8_t*)s.q;
+    for (int e = tid; e < nent; e += blockDim.x) {
+      const int m = e >> 8;
+      int t = 0;
+      if (m < M) t = min(__float2int_rn(mul_rn(sub_rn(s.T[e], s.bias[m]), s32)), L);
+      t8[e] = (uint8_t)t;
+    }
+  } else {
+    uint16_t* t16 = (uint16_t*)s.q;
+    for (int e = tid; e < nent; e += blockDim.x) {
+      const int m = e >> 8;
+      int t = 0;
+      if (m < M) t = min(__float2int_rn(mul_rn(sub_rn(s.T[e], s.bias[m]), s32)), L);
+      t16[e] = (uint16_t)t;
+    }
+  }
+  __syncthreads();
+}
+
+template <int NCHUNK>
+__device__ __forceinline__ void load_tile(const uint8_t* __restrict__ tile, int lane, uint4 (&w)[NCHUNK]) {
+#pragma unroll
+  for (int c = 0; c < NCHUNK; ++c)
+    w[c] = __ldg(reinterpret_cast<const uint4*>(tile + c * kTileChunkBytes + lane * kChunkBytes));
+}
+
+__device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// FP32 ADC: acc = fl32(acc + T[m][code_m]) for m ascending.
+template <int NCHUNK>
+__device__ __forceinline__ float adc_f32(const float* __restrict__ T, const uint4 (&w)[NCHUNK], int M) {
+  float acc = 0.f;
+#pragma unroll
+  for (int c = 0; c < NCHUNK; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const unsigned x = word_of(w[c], i);
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) {
+        const int m = c * 16 + i * 4 + bb;
+        if (m < M) acc = add_rn(acc, T[m * kKsub + ((x >> (8 * bb)) & 255u)]);
+      }
+    }
+  return acc;
+}
+
+// Integer ADC: S = sum_m t[m][code_m], exact.
+template <int NCHUNK, typename LT>
+__device__ __forceinline__ int adc_int(const LT* __restrict__ t, const uint4 (&w)[NCHUNK], int M) {
+  int acc = 0;
+#pragma unroll
+  for (int c = 0; c < NCHUNK; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const unsigned x = word_of(w[c], i);
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) {
+        const int m = c * 16 + i * 4 + bb;
+        if (m < M) acc += (int)t[m * kKsub + ((x >> (8 * bb)) & 255u)];
+      }
+    }
+  return acc;
+}
+
+__device__ __forceinline__ float dequant(int S, const PairScal& sc) {
+  return add_rn(mul_rn(sc.delta32, __int2float_rn(S)), sc.B32);
+}
+
+struct SearchArgs {
+  const float* Q; int64_t nq, dim, nlist;
+  const float* centroids; const float* codebooks;
+  const uint8_t* codes; const int64_t* ids;
+  const int32_t* list_len; const int64_t* vec_off; const int64_t* tile_off;
+  int M, Mp, dsub, nprobe, k;
+  const int32_t* npq; const int32_t* kpq;
+  const int32_t* probes; const uint8_t* bits;
+  int64_t* ids_out; float* dists_out;
+  SmemLayout lay;
+};
+
+template <int NCHUNK, int R, typename Fd>
+__device__ __forceinline__ void scan_list(const SearchArgs& a, int l, int n_l, int kq, Fd dist,
+                                          WarpTopK<R, int64_t>& top, float& thd, int64_t& thi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
+  const uint8_t* base = a.codes + (size_t)a.tile_off[l] * NCHUNK * kTileChunkBytes;
+  const int64_t vbase = a.vec_off[l];
+  for (int t = warp; t < ntile; t += kWarps) {
+    uint4 w[NCHUNK];
+    load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
+    const float d = dist(w);
+    const int v = t * kTileVecs + lane;
+    const bool pre = v < n_l && d <= thd;
+    const int64_t id = pre ? __ldg(a.ids + vbase + v) : INT64_MAX;
+    top.offer(pre, d, id, kq, thd, thi);
+  }
+}
+
+template <int NCHUNK, int R>
+__global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem s(smem_raw, a.lay);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+    const int np = a.npq ? min(max(a.npq[q], 0), a.nprobe) : a.nprobe;
+    const int kq = a.kpq ? min(max(a.kpq[q], 0), a.k) : a.k;
+    WarpTopK<R, int64_t> top;
+    top.init();
+    float thd = INFINITY;
+    int64_t thi = INT64_MAX;
+    const float* qv = a.Q + q * a.dim;
+    for (int j = 0; kq > 0 && j < np; ++j) {
+      const int l = a.probes[q * a.nprobe + j];
+      if (l < 0) continue;
+      const int n_l = a.list_len[l];
+      if (n_l == 0) continue;
+      const int b = a.bits[q * a.nprobe + j];
+      build_lut(qv, a.centroids + (size_t)l * a.dim, a.codebooks, (int)a.dim, a.M, a.Mp, a.dsub, b, s);
+      const int M = a.M;
+      if (b == 0) {
+        const float* T = s.T;
+        scan_list<NCHUNK, R>(a, l, n_l, kq, [&](const uint4 (&w)[NCHUNK]) { return adc_f32<NCHUNK>(T, w, M); },
+                             top, thd, thi);
+      } else {
+        const PairScal sc = *s.sc;
+        if (b <= 8) {
+          const uint8_t* t8 = (const uint8_t*)s.q;
+          scan_list<NCHUNK, R>(a, l, n_l, kq,
+                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK>(t8, w, M), sc); },
+                               top, thd, thi);
+        } else {
+          const uint16_t* t16 = (const uint16_t*)s.q;
+          scan_list<NCHUNK, R>(a, l, n_l, kq,
+                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK>(t16, w, M), sc); },
+                               top, thd, thi);
+        }
+      }
+      __syncthreads();  // the next pair overwrites the LUT
+    }
+    // merge the per-warp lists into warp 0
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      s.md[(warp * R + r) * 32 + lane] = top.d[r];
+      s.mi[(warp * R + r) * 32 + lane] = top.id[r];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int w2 = 1; w2 < kWarps && kq > 0; ++w2)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float cd = s.md[(w2 * R + r) * 32 + lane];
+          const int64_t ci = s.mi[(w2 * R + r) * 32 + lane];
+          top.offer(cd != INFINITY, cd, ci, kq, thd, thi);
+        }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        if (e < a.k) {
+          const bool ok = e < kq && top.d[r] != INFINITY;
+          a.ids_out[q * a.k + e] = ok ? top.id[r] : -1;
+          a.dists_out[q * a.k + e] = ok ? top.d[r] : INFINITY;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One block per pair: LUT build + quantisation, written out (anns_compute_luts).
+__global__ void __launch_bounds__(kThreads) luts_kernel(const SearchArgs a, const int32_t* pq,
+                                                        const int32_t* pl, const uint8_t* pb,
+                                                        int64_t npairs, float* T_out,
+                                                        uint16_t* t_out, double* scale_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem s(smem_raw, a.lay);
+  for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
+    const int q = pq[p], l = pl[p], b = pb[p] <= 16 ? pb[p] : 0;
+    if (q < 0 || q >= a.nq || l < 0 || l >= a.nlist) continue;  // out-of-range pair: skipped
+    build_lut(a.Q + (size_t)q * a.dim, a.centroids + (size_t)l * a.dim, a.codebooks, (int)a.dim,
+              a.M, a.Mp, a.dsub, b, s);
+    const int nent = a.M * kKsub;
+    for (int e = threadIdx.x; e < nent; e += blockDim.x) {
+      if (T_out) T_out[p * nent + e] = s.T[e];
+      if (t_out) t_out[p * nent + e] = b == 0 ? 0 : b <= 8 ? ((const uint8_t*)s.q)[e] : ((const uint16_t*)s.q)[e];
+    }
+    if (scale_out && threadIdx.x == 0) {
+      scale_out[p * 4 + 0] = b ? s.sc->delta64 : 0.0;
+      scale_out[p * 4 + 1] = b ? s.sc->B64 : 0.0;
+      scale_out[p * 4 + 2] = b ? (double)s.sc->range : 0.0;
+      scale_out[p * 4 + 3] = b ? (double)s.sc->s32 : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// One block per pair: every distance of the list (anns_scan_pairs).
+template <int NCHUNK>
+__global__ void __launch_bounds__(kThreads) scan_pairs_kernel(const SearchArgs a, const int32_t* pq,
+                                                              const int32_t* pl, const uint8_t* pb,
+                                                              int64_t npairs, const int64_t* off,
+                                                              float* dist_out, int32_t* S_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem s(smem_raw, a.lay);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
+    const int q = pq[p], l = pl[p], b = pb[p] <= 16 ? pb[p] : 0;
+    if (q < 0 || q >= a.nq || l < 0 || l >= a.nlist) continue;  // out-of-range pair: skipped
+    build_lut(a.Q + (size_t)q * a.dim, a.centroids + (size_t)l * a.dim, a.codebooks, (int)a.dim,
+              a.M, a.Mp, a.dsub, b, s);
+    const int n_l = a.list_len[l];
+    const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
+    const uint8_t* base = a.codes + (size_t)a.tile_off[l] * NCHUNK * kTileChunkBytes;
+    const PairScal sc = *s.sc;
+    for (int t = warp; t < ntile; t += kWarps) {
+      uint4 w[NCHUNK];
+      load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
+      const int v = t * kTileVecs + lane;
+      float d;
+      int S = 0;
+      if (b == 0) d = adc_f32<NCHUNK>(s.T, w, a.M);
+      else {
+        S = b <= 8 ? adc_int<NCHUNK>((const uint8_t*)s.q, w, a.M) : adc_int<NCHUNK>((const uint16_t*)s.q, w, a.M);
+        d = dequant(S, sc);
+      }
+      if (v < n_l) {
+        dist_out[off[p] + v] = d;
+        if (S_out) S_out[off[p] + v] = S;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+SearchArgs make_args(const Index& ix, const float* Q, int R) {
+  SearchArgs a{};
+  a.Q = Q; a.dim = ix.dim; a.nlist = ix.nlist;
+  a.centroids = ix.centroids; a.codebooks = ix.codebooks; a.codes = ix.codes; a.ids = ix.ids;
+  a.list_len = ix.list_len; a.vec_off = ix.vec_off; a.tile_off = ix.tile_off;
+  a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.dsub = (int)ix.dsub;
+  a.lay = SmemLayout(ix.dim, ix.Mp, R);
+  return a;
+}
+
+template <typename K>
+cudaError_t prep(K kernel, size_t smem) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;  // index too wide for one block
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int NCHUNK, int R>
+cudaError_t run_search(const SearchArgs& a, cudaStream_t s) {
+  auto kern = search_kernel<NCHUNK, R>;
+  cudaError_t e = prep(kern, a.lay.total);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>(a.nq, 1 << 30);
+  kern<<<grid, kThreads, a.lay.total, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NCHUNK>
+cudaError_t run_search_r(const SearchArgs& a, int R, cudaStream_t s) {
+  return R == 1 ? run_search<NCHUNK, 1>(a, s) : run_search<NCHUNK, 4>(a, s);
+}
+
+template <int NCHUNK>
+cudaError_t run_scan_pairs(const SearchArgs& a, const int32_t* pq, const int32_t* pl, const uint8_t* pb,
+                           int64_t npairs, const int64_t* off, float* dist_out, int32_t* S_out,
+                           cudaStream_t s) {
+  auto kern = scan_pairs_kernel<NCHUNK>;
+  cudaError_t e = prep(kern, a.lay.total);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>(npairs, 1 << 30);
+  kern<<<grid, kThreads, a.lay.total, s>>>(a, pq, pl, pb, npairs, off, dist_out, S_out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_search(const Index& ix, const float* Q, int64_t nq, int nprobe,
+                          const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
+                          const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
+                          float* dists_out, cudaStream_t s) {
+  const int R = k <= 32 ? 1 : 4;
+  SearchArgs a = make_args(ix, Q, R);
+  a.nq = nq; a.nprobe = nprobe; a.k = k; a.npq = nprobe_per_q; a.kpq = k_per_q;
+  a.probes = probes; a.bits = bits; a.ids_out = ids_out; a.dists_out = dists_out;
+  switch (ix.nchunk) {
+    case 1: return run_search_r<1>(a, R, s);
+    case 2: return run_search_r<2>(a, R, s);
+    case 3: return run_search_r<3>(a, R, s);
+    case 4: return run_search_r<4>(a, R, s);
+    case 5: return run_search_r<5>(a, R, s);
+    case 6: return run_search_r<6>(a, R, s);
+    case 7: return run_search_r<7>(a, R, s);
+    default: return run_search_r<8>(a, R, s);
+  }
+}
+
+cudaError_t launch_compute_luts(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
+                                const int32_t* pl, const uint8_t* pb, int64_t npairs,
+                                float* T_out, uint16_t* t_out, double* scale_out,
+                                cudaStream_t s) {
+  SearchArgs a = make_args(ix, Q, 1);
+  a.nq = nq;
+  cudaError_t e = prep(luts_kernel, a.lay.total);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>(npairs, 1 << 30);
+  luts_kernel<<<grid, kThreads, a.lay.total, s>>>(a, pq, pl, pb, npairs, T_out, t_out, scale_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_pairs(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
+                              const int32_t* pl, const uint8_t* pb, int64_t npairs,
+                              const int64_t* off, float* dist_out, int32_t* S_out,
+                              cudaStream_t s) {
+  SearchArgs a = make_args(ix, Q, 1);
+  a.nq = nq;
+  switch (ix.nchunk) {
+    case 1: return run_scan_pairs<1>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+    case 2: return run_scan_pairs<2>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+    case 3: return run_scan_pairs<3>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+    case 4: return run_scan_pairs<4>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+    case 5: return run_scan_pairs<5>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+    case 6: return run_scan_pairs<6>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+    case 7: return run_scan_pairs<7>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+    default: return run_scan_pairs<8>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);
+  }
+}
+
+}  // namespace anns

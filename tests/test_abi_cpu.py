@@ -1,0 +1,63 @@
+"""The C ABI without a GPU: the library loads, exports every declared symbol,
+its structs match the header's layout, and argument errors come back as codes
+with a message (no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "anns_amp.h")
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2606_07156_gb300 import build
+    build.build()
+    from paper_2606_07156_gb300 import abi as a
+    return a
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(anns_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("anns_build_index_from_arrays", "anns_search", "anns_free", "anns_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(abi):
+    lib = ctypes.CDLL(abi.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(abi.SYMBOLS) <= set(declared_functions())
+
+
+def test_struct_layouts(abi):
+    assert ctypes.sizeof(abi.anns_build_desc) == 5 * 8 + 5 * 8 + 2 * 4
+    assert ctypes.sizeof(abi.anns_precision_policy) == 4 * 4 + 4 * 4 + 4 + 4 + 8
+    assert abi.anns_precision_policy.pair_bits.offset == 40
+
+
+def test_argument_errors_without_gpu(abi):
+    d = abi.anns_build_desc()
+    d.n, d.dim, d.nlist, d.M, d.ksub = 10, 12, 2, 5, 256      # 12 % 5 != 0
+    with pytest.raises(abi.AnnsError) as e:
+        abi.anns_build_index_from_arrays(d)
+    assert e.value.code == -1 and "multiple of M" in str(e.value)
+    d.M, d.ksub = 4, 16
+    with pytest.raises(abi.AnnsError, match="ksub"):
+        abi.anns_build_index_from_arrays(d)
+    d.ksub, d.M = 256, 256
+    d.dim = 256
+    with pytest.raises(abi.AnnsError, match="M must be"):
+        abi.anns_build_index_from_arrays(d)
+    with pytest.raises(abi.AnnsError, match="null index"):
+        abi.anns_search(None, None, 1, 1, None, 1, None, None, None, None)
+    assert "null index" in abi.anns_last_error()
+    abi.anns_free(None)
