@@ -14,8 +14,8 @@ HEADER = os.path.join(ROOT, "include", "anns_amp.h")
 
 @pytest.fixture(scope="module")
 def abi():
-    from paper_2606_07156_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_2606_07156_gb300 import abi as a
     return a
 
