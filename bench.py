@@ -58,6 +58,11 @@ def workload(key: str, nq: int | None = None, device=None):
     return cfg, out
 
 
+def nn_in_top(found: np.ndarray, gt: np.ndarray, k: int) -> float:
+    """Fraction of queries whose exact nearest neighbour is among the first k results."""
+    return float(np.mean([g[0] in f[:k] for f, g in zip(found, gt)]))
+
+
 def recall(found: np.ndarray, gt: np.ndarray, k: int) -> float:
     hits = 0
     for f, g in zip(found[:, :k], gt[:, :k]):
@@ -211,6 +216,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         index.search_host(Qh, nprobe, k, adaptive, stream=stream, out=(ih, dh))
         e2e_t.append(time.perf_counter() - t)
     rec_e2e = recall(ih.numpy(), W["gt"], 10)
+    nn10 = nn_in_top(ih.numpy(), W["gt"], 10)
 
     total_ad = sum(ms_ad) / 1e3
     if world > 1:
@@ -243,6 +249,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq, "policy": f"fixed-{chosen}bit",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "recall_at_10": round(rec_ad, 4) if rec_ad is not None else None,
+        "nn_in_top10": round(nn10, 4),
         "plain_fp32": {"qps": round(qps_plain, 1), "recall_at_10": round(rec_plain[nprobe], 4),
                        "ms_per_step": round(total_plain * 1e3 / args.steps, 4)},
         "speedup_vs_plain_fp32": round(qps / qps_plain, 3),

@@ -177,6 +177,19 @@ int anns_scan_pairs(anns_index* index, const float* queries, int64_t nq,
  *  count   host int64 or NULL: number of searches accumulated. */
 int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* count);
 
+/* Index options.
+ *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
+ *    ANNS_KERNEL_AUTO (default): the persistent kernel when the codebook fits
+ *      in registers (M * 256 * dsub floats over 512 threads, at most 64 each),
+ *      else the one-block-per-query kernel.
+ *    ANNS_KERNEL_BASIC: one block per query; codebook read through L1/L2.
+ *    ANNS_KERNEL_PERSISTENT: one block per SM, codebook in registers;
+ *      UNSUPPORTED at search time if it does not fit.
+ * Both kernels return identical results. Errors: INVALID_ARG. */
+enum { ANNS_OPT_KERNEL = 0 };
+enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_PERSISTENT = 2 };
+int anns_set_option(anns_index* index, int32_t option, int64_t value);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* anns_last_error(void);
 

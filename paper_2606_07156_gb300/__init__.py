@@ -98,6 +98,11 @@ class Index:
                              _ptr(k_per_q), pol, _ptr(ids), _ptr(dists), s)
         return ids, dists
 
+    def set_kernel(self, which: str):
+        """'auto', 'basic' (one block per query) or 'persistent' (codebook in registers)."""
+        v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "persistent": abi.KERNEL_PERSISTENT}[which]
+        abi.anns_set_option(self.handle, abi.OPT_KERNEL, v)
+
     def tap(self, what: int, shape, dtype):
         out = np.empty(shape, dtype=dtype)
         abi.anns_debug_tap(self.handle, what, out.ctypes.data, out.nbytes)

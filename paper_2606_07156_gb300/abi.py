@@ -19,11 +19,13 @@ LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT = 0, 1,
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS = 10, 11, 12
+OPT_KERNEL = 0
+KERNEL_AUTO, KERNEL_BASIC, KERNEL_PERSISTENT = 0, 1, 2
 
 SYMBOLS = (
     "anns_build_index_from_arrays", "anns_free", "anns_search", "anns_search_host",
     "anns_get_info", "anns_debug_tap", "anns_compute_luts", "anns_scan_pairs", "anns_profile",
-    "anns_last_error",
+    "anns_set_option", "anns_last_error",
 )
 
 
@@ -71,6 +73,7 @@ def _load():
         "anns_compute_luts": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
         "anns_scan_pairs": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
+        "anns_set_option": ([vp, i32, i64], i32),
         "anns_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -144,3 +147,7 @@ def anns_profile(index, enable: int):
     cnt = ctypes.c_int64()
     _check(_lib.anns_profile(index, enable, ms, ctypes.byref(cnt)))
     return list(ms), cnt.value
+
+
+def anns_set_option(index, option: int, value: int) -> None:
+    _check(_lib.anns_set_option(index, option, value))

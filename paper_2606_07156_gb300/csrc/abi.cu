@@ -100,7 +100,7 @@ int ensure_workspace(Index& ix, int64_t nq, int nprobe) {
   ix.ws_bits = (uint8_t*)((char*)blk + 28 * P);
   ix.ws_nq = nq;
   ix.ws_nprobe = nprobe;
-  return ANNS_OK;
+  return grow((void**)&ix.ws_counter, &ix.ws_counter_cap, 64);
 }
 
 // Folds finished event sets into the totals; with `all`, waits for every set.
@@ -215,8 +215,16 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
                           ix->ws_bits, want_feat ? ix->ws_feat : nullptr, s)))
     return rc;
   if (ev) cudaEventRecord(ev[3], s);
-  e = launch_search(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes, ix->ws_bits,
-                    ids_out, dists_out, s);
+  const bool persistent = ix->opt_kernel == ANNS_KERNEL_PERSISTENT ||
+                          (ix->opt_kernel == ANNS_KERNEL_AUTO && persistent_supported(*ix));
+  if (ix->opt_kernel == ANNS_KERNEL_PERSISTENT && !persistent_supported(*ix))
+    return fail(ANNS_ERR_UNSUPPORTED, "persistent kernel needs M*256*dsub to fit the register codebook");
+  if (persistent)
+    e = launch_search_persistent(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
+                                 ix->ws_bits, ids_out, dists_out, ix->ws_counter, s);
+  else
+    e = launch_search(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes, ix->ws_bits,
+                      ids_out, dists_out, s);
   if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   if (ev) cudaEventRecord(ev[4], s);
   return ANNS_OK;
@@ -301,4 +309,16 @@ extern "C" int anns_profile(anns_index* ix, int32_t enable, double* out_ms, int6
     for (int st = 0; st < Index::kStages; ++st) out_ms[st] = ix->prof_ms[st];
   if (count) *count = ix->prof_count;
   return ANNS_OK;
+}
+
+extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
+  if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
+  switch (option) {
+    case ANNS_OPT_KERNEL:
+      if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_PERSISTENT)
+        return fail(ANNS_ERR_INVALID_ARG, "unknown kernel choice");
+      ix->opt_kernel = (int)value;
+      return ANNS_OK;
+    default: return fail(ANNS_ERR_INVALID_ARG, "unknown option");
+  }
 }

@@ -44,7 +44,7 @@ static void free_index(anns_index* ix) {
   void* ptrs[] = {ix->centroids, ix->codebooks, ix->codes, ix->ids, ix->list_len,
                   ix->vec_off, ix->tile_off, ix->radius, ix->ws_d2,
                   ix->ws_probes /* base of the pair block; the other ws_* alias it */,
-                  ix->st_q, ix->st_out, ix->st_pq, ix->mlp_dev};
+                  ix->st_q, ix->st_out, ix->st_pq, ix->mlp_dev, ix->ws_counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& set : ix->prof_ev)

@@ -47,6 +47,9 @@ struct Index {
   uint8_t* ws_bits = nullptr;    // [nq*nprobe]
   float* ws_feat = nullptr;      // [nq*nprobe*5]
   size_t ws_d2_cap = 0, ws_pair_cap = 0;
+  int* ws_counter = nullptr;     // work counter of the persistent kernel
+  size_t ws_counter_cap = 0;
+  int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   // staging for anns_search_host
   void* st_q = nullptr; size_t st_q_cap = 0;
   void* st_out = nullptr; size_t st_out_cap = 0;
@@ -84,6 +87,12 @@ cudaError_t launch_search(const Index& ix, const float* Q, int64_t nq, int nprob
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
                           float* dists_out, cudaStream_t s);
+// Persistent variant (codebook in registers); see search_persistent.cu.
+bool persistent_supported(const Index& ix);
+cudaError_t launch_search_persistent(const Index& ix, const float* Q, int64_t nq, int nprobe,
+                                     const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
+                                     const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
+                                     float* dists_out, int* counter, cudaStream_t s);
 cudaError_t launch_compute_luts(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
                                 const int32_t* pl, const uint8_t* pb, int64_t npairs,
                                 float* T_out, uint16_t* t_out, double* scale_out,

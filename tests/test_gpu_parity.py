@@ -29,10 +29,12 @@ def _pair(amp, ix, ids=None):
     return g, o
 
 
-@pytest.fixture(scope="module")
-def case_a(amp, small_a):
+@pytest.fixture(scope="module", params=["basic", "persistent"])
+def case_a(amp, small_a, request):
+    """Config A shape, searched by each of the two search kernels."""
     d, ix = small_a
     g, o = _pair(amp, ix)
+    g.set_kernel(request.param)
     yield d, ix, g, o
     g.close()
 
@@ -215,7 +217,9 @@ def test_ties_broken_by_user_id_and_padding(amp):
     uids = r.permutation(10_000_000)[:300].astype(np.int64) * 7 + 3
     g, o = _pair(amp, ix, ids=uids)
     Q = r.integers(0, 4, size=(30, 8)).astype(np.float32)
-    for npb, k, bits in ((4, 20, 0), (1, 128, 0), (2, 50, 4), (4, 7, 16)):
+    for kern, npb, k, bits in ((kn, *c) for kn in ("basic", "persistent")
+                               for c in ((4, 20, 0), (1, 128, 0), (2, 50, 4), (4, 7, 16))):
+        g.set_kernel(kern)
         pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
         ids, dists = g.search(cuda(Q), npb, k, pol)
         ri, rd = ivfpq.search(o, Q, npb, k, bits=bits)
@@ -240,12 +244,19 @@ def test_odd_subspace_counts(amp, M, dim):
     ix["list_of"][ix["list_of"] == 5] = 6                     # list 5 becomes empty
     g, o = _pair(amp, ix)
     Q = r.standard_normal((12, dim)).astype(np.float32)
-    for bits in (0, 8, 12):
-        pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
-        ids, dists = g.search(cuda(Q), 7, 12, pol)
-        ri, rd = ivfpq.search(o, Q, 7, 12, bits=bits)
-        np.testing.assert_array_equal(ids.cpu().numpy(), ri)
-        np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+    fits = (M + 15) // 16 * 256 * (dim // M) <= 64 * 32 and M <= 64
+    for kern in ("basic", "persistent"):
+        g.set_kernel(kern)
+        for bits in (0, 8, 12):
+            pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
+            if kern == "persistent" and not fits:
+                with pytest.raises(amp.AnnsError, match="persistent"):
+                    g.search(cuda(Q), 7, 12, pol)
+                continue
+            ids, dists = g.search(cuda(Q), 7, 12, pol)
+            ri, rd = ivfpq.search(o, Q, 7, 12, bits=bits)
+            np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+            np.testing.assert_array_equal(dists.cpu().numpy(), rd)
     g.close()
 
 
