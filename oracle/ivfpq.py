@@ -34,7 +34,9 @@ set, tie rule or feature normalisation):
   sums over m are coherent), t = round-half-even((T - bias_m) * s) with
   s = fl32((2^b - 1) / range) clamped to [0, 2^b - 1]; the distance estimate is
   fl32(fl32(Delta32 * S) + B32) with S the exact integer sum and B the sum of
-  the biases. The per-pair scale and offset are derived in FP64.
+  the biases. The per-pair scale and offset are derived in FP64; B is summed
+  in a fixed 32-lane tree order (lane l adds the biases m = l, l+32, ...
+  ascending, then five butterfly steps with offsets 16, 8, 4, 2, 1).
 """
 from __future__ import annotations
 
@@ -141,11 +143,21 @@ def quantize_lut(T32: np.ndarray, b: int) -> dict:
         s32 = F32(0.0)
     y = (Tp * s32).astype(F32)
     t = np.minimum(np.rint(y), L).astype(np.int64)          # rint: half to even
-    B64 = F64(0.0)
-    for m in range(T32.shape[0]):                           # ascending m
-        B64 = F64(B64 + F64(bias[m]))
+    B64 = tree_sum64(bias)
     return dict(t=t, bias=bias, range=rng, delta64=delta64, s32=s32, B64=B64,
                 delta32=F32(delta64), B32=F32(B64), L=L)
+
+
+def tree_sum64(v: np.ndarray) -> np.float64:
+    """FP64 sum in the 32-lane tree order: lane l accumulates v[l], v[l+32], ...
+    (ascending), then lanes combine by butterfly with offsets 16, 8, 4, 2, 1."""
+    lanes = np.zeros(32, dtype=F64)
+    for m in range(len(v)):
+        lanes[m % 32] = F64(lanes[m % 32] + F64(v[m]))
+    idx = np.arange(32)
+    for o in (16, 8, 4, 2, 1):
+        lanes = (lanes + lanes[idx ^ o]).astype(F64)
+    return F64(lanes[0])
 
 
 # ----------------------------------------------------------- DC (Section 2.1)

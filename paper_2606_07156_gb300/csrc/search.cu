@@ -90,26 +90,30 @@ __device__ void build_lut(const float* __restrict__ qv, const float* __restrict_
     if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
   }
   __syncthreads();
-  if (tid == 0) {
-    float range = 0.f;
-    for (int m = 0; m < M; ++m) range = fmaxf(range, s.rowmax[m]);
-    const int L = (1 << b) - 1;
-    PairScal sc;
-    if (range > 0.f) {
-      sc.delta64 = __ddiv_rn((double)range, (double)L);
-      sc.s32 = __double2float_rn(__ddiv_rn((double)L, (double)range));
-    } else {
-      sc.delta64 = 0.0;
-      sc.s32 = 0.f;
-    }
+  if (warp == 0) {
+    // B: FP64 sum of the row minima in the fixed 32-lane tree order
     double B = 0.0;
-    for (int m = 0; m < M; ++m) B = __dadd_rn(B, (double)s.bias[m]);
-    sc.B64 = B;
-    sc.delta32 = __double2float_rn(sc.delta64);
-    sc.B32 = __double2float_rn(B);
-    sc.range = range;
-    sc.L = L;
-    *s.sc = sc;
+    float range = 0.f;
+    for (int m = lane; m < M; m += 32) {
+      B = __dadd_rn(B, (double)s.bias[m]);
+      range = fmaxf(range, s.rowmax[m]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+    range = warp_max(range);
+    if (lane == 0) {
+      const int L = (1 << b) - 1;
+      PairScal sc;
+      // fl32 of the FP64 quotient equals the correctly rounded FP32 quotient
+      sc.delta64 = range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
+      sc.s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
+      sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
+      sc.B64 = B;
+      sc.B32 = __double2float_rn(B);
+      sc.range = range;
+      sc.L = L;
+      *s.sc = sc;
+    }
   }
   __syncthreads();
   const float s32 = s.sc->s32;

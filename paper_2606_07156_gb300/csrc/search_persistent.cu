@@ -24,7 +24,6 @@ constexpr int kNW = 16;                 // warps per block
 constexpr int kThreadsP = kNW * 32;
 
 struct PairScalP {
-  double delta64, B64;
   float delta32, B32;
 };
 
@@ -46,18 +45,20 @@ struct PArgs {
   size_t off_r, off_rowmin, off_rowmax, off_scal, off_info, off_md, off_mi, total;
 };
 
+constexpr int kTabSlots = 3, kInfoSlots = 4;
+
 template <int NCHUNK>
 __host__ __device__ constexpr size_t table_bytes() { return (size_t)NCHUNK * 16 * kKsub * 4; }
 
 template <int NCHUNK, int R>
 size_t layout(PArgs& a) {
   auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
-  size_t o = 2 * table_bytes<NCHUNK>();   // two table slots at offset 0
+  size_t o = kTabSlots * table_bytes<NCHUNK>();   // table slots at offset 0
   a.off_r = o; o += al(2 * a.dim * 4);
   a.off_rowmin = o; o += al(2 * NCHUNK * 16 * 4);
   a.off_rowmax = o; o += al(2 * NCHUNK * 16 * 4);
   a.off_scal = o; o += al(2 * sizeof(PairScalP));
-  a.off_info = o; o += al(2 * sizeof(PairInfo));
+  a.off_info = o; o += al(kInfoSlots * sizeof(PairInfo));
   a.off_md = o; o += al((size_t)kNW * R * 32 * 4);
   a.off_mi = o; o += al((size_t)kNW * R * 32 * 8);
   a.total = o;
@@ -68,16 +69,19 @@ __device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// Steps of one pipeline stage, parameterised at compile time by the code
-// width (NCHUNK 16-byte chunks), the top-k capacity R*32, the codebook rows
-// per warp NROW and the sub-vector length DSUB.
+// One block's state. Pair p (probe rank p of the current query) moves through
+// the stages  load/store inputs (stage p-3) -> build rows (p-2) -> quantise
+// (p-1) -> scan (p), one block barrier per stage, so three pairs are in
+// flight. Slots: tables p%3, residuals / row statistics / scales p%2, list
+// facts p%4 — each is rewritten only after the barrier that ends its last use.
 template <int NCHUNK, int R, int NROW, int DSUB>
 struct Pipe {
   static constexpr int Mp = NCHUNK * 16;
   const PArgs& a;
   unsigned char* sm;
   float y[NROW][8][DSUB];   // this thread's codebook entries
-  float tq[NROW][8];        // LUT values of the pair being built
+  float tq[NROW][8];        // LUT values of the pair between build and quantise
+  uint4 pf[NCHUNK];         // prefetched code tile
   int warp, lane;
 
   __device__ Pipe(const PArgs& args, unsigned char* s) : a(args), sm(s) {
@@ -94,40 +98,49 @@ struct Pipe {
     }
   }
 
-  __device__ unsigned char* table(int slot) const { return sm + slot * table_bytes<NCHUNK>(); }
-  __device__ float* resid(int slot) const { return (float*)(sm + a.off_r) + slot * a.dim; }
-  __device__ float* rowmin(int slot) const { return (float*)(sm + a.off_rowmin) + slot * Mp; }
-  __device__ float* rowmax(int slot) const { return (float*)(sm + a.off_rowmax) + slot * Mp; }
-  __device__ PairScalP* scal(int slot) const { return (PairScalP*)(sm + a.off_scal) + slot; }
-  __device__ PairInfo* info(int slot) const { return (PairInfo*)(sm + a.off_info) + slot; }
+  __device__ unsigned char* table(int p) const { return sm + (p % kTabSlots) * table_bytes<NCHUNK>(); }
+  __device__ float* resid(int p) const { return (float*)(sm + a.off_r) + (p & 1) * a.dim; }
+  __device__ float* rowmin(int p) const { return (float*)(sm + a.off_rowmin) + (p & 1) * Mp; }
+  __device__ float* rowmax(int p) const { return (float*)(sm + a.off_rowmax) + (p & 1) * Mp; }
+  __device__ PairScalP* scal(int p) const { return (PairScalP*)(sm + a.off_scal) + (p & 1); }
+  __device__ PairInfo* info(int p) const { return (PairInfo*)(sm + a.off_info) + (p % kInfoSlots); }
 
-  // Residual r = fl32(q - c_l) and list facts of probe rank j into `slot`.
-  __device__ void stage_pair(int64_t q, int j, int slot) {
-    const int l = a.probes[q * a.nprobe + j];
-    const float* qv = a.Q + q * a.dim;
-    float* r = resid(slot);
-    if (l >= 0) {
-      const float* cv = a.centroids + (size_t)l * a.dim;
-      for (int d = threadIdx.x; d < a.dim; d += kThreadsP) r[d] = sub_rn(qv[d], cv[d]);
+  // Inputs of pair p: q - c_l into resid(p), list facts into info(p). The
+  // loads are issued first (load_inputs) and stored after the stage's other
+  // work (store_inputs), so their latency overlaps that work.
+  struct Staged { float qd, cd; int l, n_l, b; int64_t tile0, vbase; };
+  __device__ void load_inputs(int64_t q, int p, Staged& st) const {
+    st.l = a.probes[q * a.nprobe + p];
+    const int d = threadIdx.x;
+    st.qd = 0.f; st.cd = 0.f;
+    if (st.l >= 0 && d < a.dim) {
+      st.qd = a.Q[q * a.dim + d];
+      st.cd = a.centroids[(size_t)st.l * a.dim + d];
     }
     if (threadIdx.x == 0) {
+      st.n_l = st.l >= 0 ? a.list_len[st.l] : 0;
+      st.b = a.bits[q * a.nprobe + p];
+      st.tile0 = st.l >= 0 ? a.tile_off[st.l] : 0;
+      st.vbase = st.l >= 0 ? a.vec_off[st.l] : 0;
+    }
+  }
+  __device__ void store_inputs(int p, const Staged& st) const {
+    if (threadIdx.x < a.dim && st.l >= 0) resid(p)[threadIdx.x] = sub_rn(st.qd, st.cd);
+    if (threadIdx.x == 0) {
       PairInfo pi;
-      pi.l = l;
-      pi.n_l = l >= 0 ? a.list_len[l] : 0;
-      pi.b = a.bits[q * a.nprobe + j];
-      pi.ntile = (pi.n_l + kTileVecs - 1) / kTileVecs;
-      pi.tile0 = l >= 0 ? a.tile_off[l] : 0;
-      pi.vbase = l >= 0 ? a.vec_off[l] : 0;
-      *info(slot) = pi;
+      pi.l = st.l; pi.n_l = st.n_l; pi.b = st.b;
+      pi.ntile = (st.n_l + kTileVecs - 1) / kTileVecs;
+      pi.tile0 = st.tile0; pi.vbase = st.vbase;
+      *info(p) = pi;
     }
   }
 
-  // Build step 1: T for this warp's rows; FP32 tables are written out, for
-  // quantised pairs the row minimum and the row range go to shared memory.
-  __device__ void build_rows(int slot) {
-    const PairInfo pi = *info(slot);
+  // T for this warp's rows of pair p (FP32 rule). Plain pairs write the FP32
+  // table now; quantised pairs keep T in registers and publish row min/range.
+  __device__ void build_rows(int p) {
+    const PairInfo pi = *info(p);
     if (pi.n_l == 0) return;
-    const float* r = resid(slot);
+    const float* r = resid(p);
 #pragma unroll
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
@@ -146,7 +159,7 @@ struct Pipe {
         tq[i][e] = acc;
       }
       if (pi.b == 0) {
-        float* T = (float*)table(slot);
+        float* T = (float*)table(p);
 #pragma unroll
         for (int e = 0; e < 8; ++e) T[m * kKsub + lane + 32 * e] = tq[i][e];
       } else {
@@ -158,49 +171,63 @@ struct Pipe {
 #pragma unroll
         for (int e = 0; e < 8; ++e) mx = fmaxf(mx, sub_rn(tq[i][e], mn));
         mx = warp_max(mx);
-        if (lane == 0) { rowmin(slot)[m] = mn; rowmax(slot)[m] = mx; }
+        if (lane == 0) { rowmin(p)[m] = mn; rowmax(p)[m] = mx; }
       }
     }
   }
 
-  // Build step 2 (after a barrier): the shared step from the largest row
-  // range, then this warp's rows quantised into the table; warp 0 also forms
-  // the FP64 offset B = sum of the row minima, m ascending.
-  __device__ void quantise_rows(int slot) {
-    const PairInfo pi = *info(slot);
+  // Quantises this warp's rows of pair p with the shared step from the
+  // largest row range; warp 0 also forms Delta32 and B32 (B summed in FP64 in
+  // the fixed 32-lane tree order).
+  __device__ void quantise_rows(int p) {
+    const PairInfo pi = *info(p);
     if (pi.n_l == 0 || pi.b == 0) return;
     float range = 0.f;
-    for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax(slot)[m]);
+    for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax(p)[m]);
     range = warp_max(range);
     const int L = (1 << pi.b) - 1;
-    const float s32 = range > 0.f ? __double2float_rn(__ddiv_rn((double)L, (double)range)) : 0.f;
-    if (warp == 0 && lane == 0) {
-      PairScalP sc;
-      sc.delta64 = range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
+    const float s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
+    if (warp == 0) {
       double B = 0.0;
-      for (int m = 0; m < a.M; ++m) B = __dadd_rn(B, (double)rowmin(slot)[m]);
-      sc.B64 = B;
-      sc.delta32 = __double2float_rn(sc.delta64);
-      sc.B32 = __double2float_rn(B);
-      *scal(slot) = sc;
+      for (int m = lane; m < a.M; m += 32) B = __dadd_rn(B, (double)rowmin(p)[m]);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+      if (lane == 0) {
+        PairScalP sc;
+        sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
+        sc.B32 = __double2float_rn(B);
+        *scal(p) = sc;
+      }
     }
 #pragma unroll
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
       if (m >= a.M) continue;
-      const float mn = rowmin(slot)[m];
+      const float mn = rowmin(p)[m];
       if (pi.b <= 8) {
-        uint8_t* t8 = table(slot);
+        uint8_t* t8 = table(p);
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           t8[m * kKsub + lane + 32 * e] = (uint8_t)min(__float2int_rn(mul_rn(sub_rn(tq[i][e], mn), s32)), L);
       } else {
-        uint16_t* t16 = (uint16_t*)table(slot);
+        uint16_t* t16 = (uint16_t*)table(p);
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           t16[m * kKsub + lane + 32 * e] = (uint16_t)min(__float2int_rn(mul_rn(sub_rn(tq[i][e], mn), s32)), L);
       }
     }
+  }
+
+  __device__ __forceinline__ void load_tile(const PairInfo& pi, int t, uint4 (&w)[NCHUNK]) const {
+    const uint8_t* tile = a.codes + ((size_t)(pi.tile0 + t) * NCHUNK) * kTileChunkBytes + lane * kChunkBytes;
+#pragma unroll
+    for (int c = 0; c < NCHUNK; ++c) w[c] = __ldg(reinterpret_cast<const uint4*>(tile + c * kTileChunkBytes));
+  }
+
+  // Issues the load of this warp's first tile of pair p into pf.
+  __device__ void prefetch_first(int p) {
+    const PairInfo pi = *info(p);
+    if (warp < pi.ntile) load_tile(pi, warp, pf);
   }
 
   template <typename LT>
@@ -236,20 +263,24 @@ struct Pipe {
     return acc;
   }
 
-  // Scans tiles [t0, t1) of the pair in `slot`, offering distances to the warp list.
-  __device__ void scan(int slot, int t0, int t1, int kq, WarpTopK<R, int64_t>& top, float& thd,
-                       int64_t& thi) const {
-    const PairInfo pi = *info(slot);
-    if (pi.n_l == 0) return;
-    const uint8_t* base = a.codes + (size_t)pi.tile0 * NCHUNK * kTileChunkBytes;
-    const unsigned char* tab = table(slot);
+  // Scans this warp's tiles of pair p (the first one is already in pf) and
+  // leaves the first tile of pair p+1 (if has_next) prefetched in pf.
+  __device__ void scan(int p, bool has_next, int kq, WarpTopK<R, int64_t>& top, float& thd,
+                       int64_t& thi) {
+    const PairInfo pi = *info(p);
+    const unsigned char* tab = table(p);
     PairScalP sc{};
-    if (pi.b) sc = *scal(slot);
-    for (int t = t0 + warp; t < t1; t += kNW) {
+    if (pi.b) sc = *scal(p);
+    if (warp >= pi.ntile) {
+      if (has_next) prefetch_first(p + 1);
+      return;
+    }
+    for (int t = warp; t < pi.ntile; t += kNW) {
       uint4 w[NCHUNK];
-      const uint8_t* tile = base + (size_t)t * NCHUNK * kTileChunkBytes + lane * kChunkBytes;
 #pragma unroll
-      for (int c = 0; c < NCHUNK; ++c) w[c] = __ldg(reinterpret_cast<const uint4*>(tile + c * kTileChunkBytes));
+      for (int c = 0; c < NCHUNK; ++c) w[c] = pf[c];
+      if (t + kNW < pi.ntile) load_tile(pi, t + kNW, pf);
+      else if (has_next) prefetch_first(p + 1);
       float d;
       if (pi.b == 0) d = adc_f32((const float*)tab, w);
       else if (pi.b <= 8) d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int((const uint8_t*)tab, w))), sc.B32);
@@ -266,7 +297,8 @@ template <int NCHUNK, int R, int NROW, int DSUB>
 __global__ void __launch_bounds__(kThreadsP, 1) search_persistent_kernel(const PArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t next_q;
-  Pipe<NCHUNK, R, NROW, DSUB> P(a, smem);
+  using PipeT = Pipe<NCHUNK, R, NROW, DSUB>;
+  PipeT P(a, smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* md = (float*)(smem + a.off_md);
   int64_t* mi = (int64_t*)(smem + a.off_mi);
@@ -281,29 +313,16 @@ __global__ void __launch_bounds__(kThreadsP, 1) search_persistent_kernel(const P
     top.init();
     float thd = INFINITY;
     int64_t thi = INT64_MAX;
-    if (kq > 0 && np > 0) {
-      // prologue: pair 0 into slot 0
-      P.stage_pair(q, 0, 0);
-      __syncthreads();
-      P.build_rows(0);
-      __syncthreads();
-      P.quantise_rows(0);
-      if (np > 1) P.stage_pair(q, 1, 1);
-      __syncthreads();
-      for (int j = 0; j < np; ++j) {
-        const int cur = j & 1, nxt = cur ^ 1;
-        const bool more = j + 1 < np;
-        const int nt = P.info(cur)->ntile;
-        const int half = (nt + 1) / 2;
-        // stage A: rows of pair j+1, first half of pair j's tiles
-        if (more) P.build_rows(nxt);
-        P.scan(cur, 0, half, kq, top, thd, thi);
-        __syncthreads();
-        // stage B: quantise pair j+1, second half of pair j's tiles
-        if (more) P.quantise_rows(nxt);
-        P.scan(cur, half, nt, kq, top, thd, thi);
-        __syncthreads();
-        if (j + 2 < np) P.stage_pair(q, j + 2, cur);
+    if (kq > 0) {
+      for (int s = -3; s < np; ++s) {
+        typename PipeT::Staged st;
+        const bool stage_in = s + 3 < np;
+        if (stage_in) P.load_inputs(q, s + 3, st);
+        if (s >= 0) P.scan(s, s + 1 < np, kq, top, thd, thi);
+        else if (s == -1) P.prefetch_first(0);
+        if (s + 1 >= 0 && s + 1 < np) P.quantise_rows(s + 1);
+        if (s + 2 >= 0 && s + 2 < np) P.build_rows(s + 2);
+        if (stage_in) P.store_inputs(s + 3, st);
         __syncthreads();
       }
     }
@@ -370,6 +389,7 @@ cudaError_t run_shape(PArgs& a, cudaStream_t s) {
 }  // namespace
 
 bool persistent_supported(const Index& ix) {
+  if (ix.dim > kThreadsP) return false;
   const int nrow = (int)((ix.M + kNW - 1) / kNW);
   const int d = (int)ix.dsub;
   return (nrow == 1 && (d == 8 || d == 4)) || (nrow == 2 && (d == 4 || d == 2)) ||

@@ -107,6 +107,35 @@ def test_quantiser_hand_worked():
     assert ivfpq.dequant32(S, qz["delta32"], qz["B32"])[0] == np.float32(9.0)
 
 
+def test_tree_sum_is_a_sum():
+    """The fixed-order FP64 tree sum equals the exact sum when every partial
+    sum is exact (small integers), and stays within the FP64 rounding bound of
+    math.fsum otherwise."""
+    import math
+    r = np.random.Generator(np.random.PCG64(12))
+    ints = r.integers(-1000, 1000, size=120).astype(np.float32)
+    assert ivfpq.tree_sum64(ints) == float(ints.astype(np.int64).sum())
+    x = (r.standard_normal(97) * 10.0 ** r.integers(-6, 6, size=97)).astype(np.float32)
+    exact = math.fsum(float(v) for v in x)
+    assert abs(ivfpq.tree_sum64(x) - exact) <= 10 * 2.0 ** -53 * np.abs(x.astype(np.float64)).sum()
+
+
+def test_single_rounding_of_fp32_scale():
+    """s = fl32(fl64(L) / fl64(range)) equals the correctly rounded FP32
+    quotient (double rounding through FP64 is innocuous for division since
+    53 >= 2*24 + 2); checked against exact rational arithmetic."""
+    from fractions import Fraction
+    r = np.random.Generator(np.random.PCG64(13))
+    for rng in r.uniform(1e-3, 1e6, size=2000).astype(np.float32):
+        for L in (15, 63, 255, 4095, 65535):
+            s = np.float32(np.float64(L) / np.float64(rng))
+            q = Fraction(L) / Fraction(float(rng))
+            lo = Fraction(float(np.nextafter(s, np.float32(0))))
+            hi = Fraction(float(np.nextafter(s, np.float32(np.inf))))
+            sv = Fraction(float(s))
+            assert abs(sv - q) <= abs(lo - q) and abs(sv - q) <= abs(hi - q)
+
+
 def test_quantiser_range_zero():
     """A constant table has range 0: every level is 0, step 0, estimate = offset."""
     T = np.full((4, 256), 2.5, dtype=np.float32)
