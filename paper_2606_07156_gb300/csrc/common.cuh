@@ -90,6 +90,21 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
+// Packed FP32x2 (Blackwell): two independent IEEE round-to-nearest operations.
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Element `base + code_bb(x) + m*256` of a LUT of LT in shared memory, where
+// code_bb(x) is byte bb of the packed code word x and `base` (in elements)
+// has a zero low byte: one byte-permute forms the index, m*256 stays an
+// immediate offset.
+template <typename LT, int BB>
+__device__ __forceinline__ LT lut_at(const unsigned char* smem, unsigned base, unsigned x, int m) {
+  const unsigned idx = __byte_perm(x, base, 0x7650u + BB);
+  return reinterpret_cast<const LT*>(smem)[idx + (unsigned)m * 256u];
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));

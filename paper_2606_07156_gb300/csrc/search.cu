@@ -33,10 +33,10 @@ struct SmemLayout {
   static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   SmemLayout() = default;
   SmemLayout(int64_t dim, int64_t Mp, int R) {
-    size_t o = 0;
-    r = o; o += al(dim * 4);
+    size_t o = 0;   // the tables first: their element offsets have a zero low byte
     T = o; o += al(Mp * kKsub * 4);
     q = o; o += al(Mp * kKsub * 2);
+    r = o; o += al(dim * 4);
     bias = o; o += al(Mp * 4);
     rowmax = o; o += al(Mp * 4);
     scal = o; o += al(sizeof(PairScal));
@@ -149,40 +149,39 @@ __device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// FP32 ADC: acc = fl32(acc + T[m][code_m]) for m ascending.
+// FP32 ADC over all Mp sub-tables: acc = fl32(acc + T[m][code_m]), m ascending
+// (padding rows are zero). The FP32 table sits at shared offset 0.
 template <int NCHUNK>
-__device__ __forceinline__ float adc_f32(const float* __restrict__ T, const uint4 (&w)[NCHUNK], int M) {
+__device__ __forceinline__ float adc_f32(const unsigned char* sm, const uint4 (&w)[NCHUNK]) {
   float acc = 0.f;
 #pragma unroll
   for (int c = 0; c < NCHUNK; ++c)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const unsigned x = word_of(w[c], i);
-#pragma unroll
-      for (int bb = 0; bb < 4; ++bb) {
-        const int m = c * 16 + i * 4 + bb;
-        if (m < M) acc = add_rn(acc, T[m * kKsub + ((x >> (8 * bb)) & 255u)]);
-      }
+      const int m = c * 16 + i * 4;
+      acc = add_rn(acc, lut_at<float, 0>(sm, 0u, x, m));
+      acc = add_rn(acc, lut_at<float, 1>(sm, 0u, x, m + 1));
+      acc = add_rn(acc, lut_at<float, 2>(sm, 0u, x, m + 2));
+      acc = add_rn(acc, lut_at<float, 3>(sm, 0u, x, m + 3));
     }
   return acc;
 }
 
-// Integer ADC: S = sum_m t[m][code_m], exact.
+// Integer ADC: S = sum_m t[m][code_m], exact; `base` is the table's element offset.
 template <int NCHUNK, typename LT>
-__device__ __forceinline__ int adc_int(const LT* __restrict__ t, const uint4 (&w)[NCHUNK], int M) {
-  int acc = 0;
+__device__ __forceinline__ int adc_int(const unsigned char* sm, unsigned base, const uint4 (&w)[NCHUNK]) {
+  int acc0 = 0, acc1 = 0;
 #pragma unroll
   for (int c = 0; c < NCHUNK; ++c)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const unsigned x = word_of(w[c], i);
-#pragma unroll
-      for (int bb = 0; bb < 4; ++bb) {
-        const int m = c * 16 + i * 4 + bb;
-        if (m < M) acc += (int)t[m * kKsub + ((x >> (8 * bb)) & 255u)];
-      }
+      const int m = c * 16 + i * 4;
+      acc0 += (int)lut_at<LT, 0>(sm, base, x, m) + (int)lut_at<LT, 1>(sm, base, x, m + 1);
+      acc1 += (int)lut_at<LT, 2>(sm, base, x, m + 2) + (int)lut_at<LT, 3>(sm, base, x, m + 3);
     }
-  return acc;
+  return acc0 + acc1;
 }
 
 __device__ __forceinline__ float dequant(int S, const PairScal& sc) {
@@ -239,22 +238,19 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
       if (n_l == 0) continue;
       const int b = a.bits[q * a.nprobe + j];
       build_lut(qv, a.centroids + (size_t)l * a.dim, a.codebooks, (int)a.dim, a.M, a.Mp, a.dsub, b, s);
-      const int M = a.M;
+      const unsigned qoff = (unsigned)a.lay.q;   // bytes; a multiple of 256 elements of either width
       if (b == 0) {
-        const float* T = s.T;
-        scan_list<NCHUNK, R>(a, l, n_l, kq, [&](const uint4 (&w)[NCHUNK]) { return adc_f32<NCHUNK>(T, w, M); },
+        scan_list<NCHUNK, R>(a, l, n_l, kq, [&](const uint4 (&w)[NCHUNK]) { return adc_f32<NCHUNK>(smem_raw, w); },
                              top, thd, thi);
       } else {
         const PairScal sc = *s.sc;
         if (b <= 8) {
-          const uint8_t* t8 = (const uint8_t*)s.q;
           scan_list<NCHUNK, R>(a, l, n_l, kq,
-                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK>(t8, w, M), sc); },
+                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK, uint8_t>(smem_raw, qoff, w), sc); },
                                top, thd, thi);
         } else {
-          const uint16_t* t16 = (const uint16_t*)s.q;
           scan_list<NCHUNK, R>(a, l, n_l, kq,
-                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK>(t16, w, M), sc); },
+                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK, uint16_t>(smem_raw, qoff / 2, w), sc); },
                                top, thd, thi);
         }
       }
@@ -340,9 +336,10 @@ __global__ void __launch_bounds__(kThreads) scan_pairs_kernel(const SearchArgs a
       const int v = t * kTileVecs + lane;
       float d;
       int S = 0;
-      if (b == 0) d = adc_f32<NCHUNK>(s.T, w, a.M);
+      const unsigned qoff = (unsigned)a.lay.q;
+      if (b == 0) d = adc_f32<NCHUNK>(smem_raw, w);
       else {
-        S = b <= 8 ? adc_int<NCHUNK>((const uint8_t*)s.q, w, a.M) : adc_int<NCHUNK>((const uint16_t*)s.q, w, a.M);
+        S = b <= 8 ? adc_int<NCHUNK, uint8_t>(smem_raw, qoff, w) : adc_int<NCHUNK, uint16_t>(smem_raw, qoff / 2, w);
         d = dequant(S, sc);
       }
       if (v < n_l) {

@@ -79,8 +79,8 @@ struct Pipe {
   static constexpr int Mp = NCHUNK * 16;
   const PArgs& a;
   unsigned char* sm;
-  float y[NROW][8][DSUB];   // this thread's codebook entries
-  float tq[NROW][8];        // LUT values of the pair between build and quantise
+  float2 y[NROW][4][DSUB];  // this thread's codebook entries, (c, c+32) paired
+  float2 tq[NROW][4];       // LUT values of the pair between build and quantise
   uint4 pf[NCHUNK];         // prefetched code tile
   int warp, lane;
 
@@ -91,10 +91,13 @@ struct Pipe {
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
+      for (int h = 0; h < 4; ++h)
 #pragma unroll
-        for (int j = 0; j < DSUB; ++j)
-          y[i][e][j] = m < a.M ? __ldg(a.codebooks + ((size_t)(m * kKsub + lane + 32 * e)) * DSUB + j) : 0.f;
+        for (int j = 0; j < DSUB; ++j) {
+          const size_t e0 = (size_t)(m * kKsub + lane + 64 * h), e1 = e0 + 32;
+          y[i][h][j] = m < a.M ? make_float2(__ldg(a.codebooks + e0 * DSUB + j), __ldg(a.codebooks + e1 * DSUB + j))
+                               : make_float2(0.f, 0.f);
+        }
     }
   }
 
@@ -135,8 +138,10 @@ struct Pipe {
     }
   }
 
-  // T for this warp's rows of pair p (FP32 rule). Plain pairs write the FP32
-  // table now; quantised pairs keep T in registers and publish row min/range.
+  // T for this warp's rows of pair p (FP32 rule, two entries per packed
+  // operation). Plain pairs write the FP32 table now; quantised pairs keep T
+  // in registers and publish row min/range. Rows M..Mp-1 are zero rows, so the
+  // scan needs no bound on m.
   __device__ void build_rows(int p) {
     const PairInfo pi = *info(p);
     if (pi.n_l == 0) return;
@@ -144,32 +149,43 @@ struct Pipe {
 #pragma unroll
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
-      if (m >= a.M) continue;
-      float rv[DSUB];
+      if (m >= Mp) continue;
+      if (m >= a.M) {   // padding row
+        if (pi.b == 0) {
+          float* T = (float*)table(p);
 #pragma unroll
-      for (int j = 0; j < DSUB; ++j) rv[j] = r[m * DSUB + j];
+          for (int e = 0; e < 8; ++e) T[m * kKsub + lane + 32 * e] = 0.f;
+        }
+        continue;
+      }
+      float2 rv[DSUB];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float acc = 0.f;
+      for (int j = 0; j < DSUB; ++j) { const float v = r[m * DSUB + j]; rv[j] = make_float2(v, v); }
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < DSUB; ++j) {
-          const float x = sub_rn(rv[j], y[i][e][j]);
-          acc = add_rn(acc, mul_rn(x, x));
+          const float2 x = sub2_rn(rv[j], y[i][h][j]);
+          acc = add2_rn(acc, mul2_rn(x, x));
         }
-        tq[i][e] = acc;
+        tq[i][h] = acc;
       }
       if (pi.b == 0) {
         float* T = (float*)table(p);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) T[m * kKsub + lane + 32 * e] = tq[i][e];
+        for (int h = 0; h < 4; ++h) {
+          T[m * kKsub + lane + 64 * h] = tq[i][h].x;
+          T[m * kKsub + lane + 64 * h + 32] = tq[i][h].y;
+        }
       } else {
-        float mn = tq[i][0];
+        float mn = fminf(tq[i][0].x, tq[i][0].y);
 #pragma unroll
-        for (int e = 1; e < 8; ++e) mn = fminf(mn, tq[i][e]);
+        for (int h = 1; h < 4; ++h) mn = fminf(mn, fminf(tq[i][h].x, tq[i][h].y));
         mn = warp_min(mn);
         float mx = 0.f;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) mx = fmaxf(mx, sub_rn(tq[i][e], mn));
+        for (int h = 0; h < 4; ++h) mx = fmaxf(mx, fmaxf(sub_rn(tq[i][h].x, mn), sub_rn(tq[i][h].y, mn)));
         mx = warp_max(mx);
         if (lane == 0) { rowmin(p)[m] = mn; rowmax(p)[m] = mx; }
       }
@@ -199,21 +215,39 @@ struct Pipe {
         *scal(p) = sc;
       }
     }
+    const float2 s2 = make_float2(s32, s32);
 #pragma unroll
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
-      if (m >= a.M) continue;
-      const float mn = rowmin(p)[m];
+      if (m >= Mp) continue;
+      int t[8];
+      if (m < a.M) {
+        const float mn = rowmin(p)[m];
+        const float2 mn2 = make_float2(mn, mn);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float2 yq = mul2_rn(sub2_rn(tq[i][h], mn2), s2);
+          t[2 * h] = min(__float2int_rn(yq.x), L);
+          t[2 * h + 1] = min(__float2int_rn(yq.y), L);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) t[e] = 0;   // padding row
+      }
       if (pi.b <= 8) {
         uint8_t* t8 = table(p);
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          t8[m * kKsub + lane + 32 * e] = (uint8_t)min(__float2int_rn(mul_rn(sub_rn(tq[i][e], mn), s32)), L);
+        for (int h = 0; h < 4; ++h) {
+          t8[m * kKsub + lane + 64 * h] = (uint8_t)t[2 * h];
+          t8[m * kKsub + lane + 64 * h + 32] = (uint8_t)t[2 * h + 1];
+        }
       } else {
         uint16_t* t16 = (uint16_t*)table(p);
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          t16[m * kKsub + lane + 32 * e] = (uint16_t)min(__float2int_rn(mul_rn(sub_rn(tq[i][e], mn), s32)), L);
+        for (int h = 0; h < 4; ++h) {
+          t16[m * kKsub + lane + 64 * h] = (uint16_t)t[2 * h];
+          t16[m * kKsub + lane + 64 * h + 32] = (uint16_t)t[2 * h + 1];
+        }
       }
     }
   }
@@ -230,35 +264,35 @@ struct Pipe {
     if (warp < pi.ntile) load_tile(pi, warp, pf);
   }
 
+  // Integer ADC over all Mp sub-tables (padding rows are zero): exact sum.
   template <typename LT>
-  __device__ __forceinline__ int adc_int(const LT* __restrict__ t, const uint4 (&w)[NCHUNK]) const {
-    int acc = 0;
+  __device__ __forceinline__ int adc_int(unsigned base, const uint4 (&w)[NCHUNK]) const {
+    int acc0 = 0, acc1 = 0;
 #pragma unroll
     for (int c = 0; c < NCHUNK; ++c)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const unsigned x = word_of(w[c], i);
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb) {
-          const int m = c * 16 + i * 4 + bb;
-          if (m < a.M) acc += (int)t[m * kKsub + ((x >> (8 * bb)) & 255u)];
-        }
+        const int m = c * 16 + i * 4;
+        acc0 += (int)lut_at<LT, 0>(sm, base, x, m) + (int)lut_at<LT, 1>(sm, base, x, m + 1);
+        acc1 += (int)lut_at<LT, 2>(sm, base, x, m + 2) + (int)lut_at<LT, 3>(sm, base, x, m + 3);
       }
-    return acc;
+    return acc0 + acc1;
   }
 
-  __device__ __forceinline__ float adc_f32(const float* __restrict__ T, const uint4 (&w)[NCHUNK]) const {
+  // FP32 ADC: acc = fl32(acc + T[m][code_m]) for m ascending (padding rows add 0).
+  __device__ __forceinline__ float adc_f32(unsigned base, const uint4 (&w)[NCHUNK]) const {
     float acc = 0.f;
 #pragma unroll
     for (int c = 0; c < NCHUNK; ++c)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const unsigned x = word_of(w[c], i);
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb) {
-          const int m = c * 16 + i * 4 + bb;
-          if (m < a.M) acc = add_rn(acc, T[m * kKsub + ((x >> (8 * bb)) & 255u)]);
-        }
+        const int m = c * 16 + i * 4;
+        acc = add_rn(acc, lut_at<float, 0>(sm, base, x, m));
+        acc = add_rn(acc, lut_at<float, 1>(sm, base, x, m + 1));
+        acc = add_rn(acc, lut_at<float, 2>(sm, base, x, m + 2));
+        acc = add_rn(acc, lut_at<float, 3>(sm, base, x, m + 3));
       }
     return acc;
   }
@@ -268,7 +302,7 @@ struct Pipe {
   __device__ void scan(int p, bool has_next, int kq, WarpTopK<R, int64_t>& top, float& thd,
                        int64_t& thi) {
     const PairInfo pi = *info(p);
-    const unsigned char* tab = table(p);
+    const unsigned slot_bytes = (unsigned)((p % kTabSlots) * table_bytes<NCHUNK>());
     PairScalP sc{};
     if (pi.b) sc = *scal(p);
     if (warp >= pi.ntile) {
@@ -282,9 +316,9 @@ struct Pipe {
       if (t + kNW < pi.ntile) load_tile(pi, t + kNW, pf);
       else if (has_next) prefetch_first(p + 1);
       float d;
-      if (pi.b == 0) d = adc_f32((const float*)tab, w);
-      else if (pi.b <= 8) d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int((const uint8_t*)tab, w))), sc.B32);
-      else d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int((const uint16_t*)tab, w))), sc.B32);
+      if (pi.b == 0) d = adc_f32(slot_bytes / 4, w);
+      else if (pi.b <= 8) d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint8_t>(slot_bytes, w))), sc.B32);
+      else d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint16_t>(slot_bytes / 2, w))), sc.B32);
       const int v = t * kTileVecs + lane;
       const bool pre = v < pi.n_l && d <= thd;
       const int64_t id = pre ? __ldg(a.ids + pi.vbase + v) : INT64_MAX;
