@@ -166,8 +166,9 @@ struct Pipe {
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < DSUB; ++j) {
-          const float2 x = sub2_rn(rv[j], y[i][h][j]);
-          acc = add2_rn(acc, mul2_rn(x, x));
+          const float x0 = sub_rn(rv[j].x, y[i][h][j].x), x1 = sub_rn(rv[j].y, y[i][h][j].y);
+          acc.x = add_rn(acc.x, mul_rn(x0, x0));
+          acc.y = add_rn(acc.y, mul_rn(x1, x1));
         }
         tq[i][h] = acc;
       }
@@ -215,7 +216,6 @@ struct Pipe {
         *scal(p) = sc;
       }
     }
-    const float2 s2 = make_float2(s32, s32);
 #pragma unroll
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
@@ -223,10 +223,9 @@ struct Pipe {
       int t[8];
       if (m < a.M) {
         const float mn = rowmin(p)[m];
-        const float2 mn2 = make_float2(mn, mn);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          const float2 yq = mul2_rn(sub2_rn(tq[i][h], mn2), s2);
+          const float2 yq = make_float2(mul_rn(sub_rn(tq[i][h].x, mn), s32), mul_rn(sub_rn(tq[i][h].y, mn), s32));
           t[2 * h] = min(__float2int_rn(yq.x), L);
           t[2 * h + 1] = min(__float2int_rn(yq.y), L);
         }
