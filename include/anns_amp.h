@@ -179,11 +179,11 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
 
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
- *    ANNS_KERNEL_AUTO (default): the persistent kernel when the codebook fits
- *      in registers (M * 256 * dsub floats over 512 threads, at most 64 each),
- *      else the one-block-per-query kernel.
+ *    ANNS_KERNEL_AUTO (default): the persistent kernel when k <= 32 and the
+ *      codebook (M * 256 * dsub floats) plus two LUTs fit in one block's
+ *      shared memory, else the one-block-per-query kernel.
  *    ANNS_KERNEL_BASIC: one block per query; codebook read through L1/L2.
- *    ANNS_KERNEL_PERSISTENT: one block per SM, codebook in registers;
+ *    ANNS_KERNEL_PERSISTENT: one block per SM, codebook in shared memory;
  *      UNSUPPORTED at search time if it does not fit.
  * Both kernels return identical results. Errors: INVALID_ARG. */
 enum { ANNS_OPT_KERNEL = 0 };

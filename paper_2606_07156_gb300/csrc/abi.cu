@@ -215,10 +215,12 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
                           ix->ws_bits, want_feat ? ix->ws_feat : nullptr, s)))
     return rc;
   if (ev) cudaEventRecord(ev[3], s);
+  const bool fits = persistent_supported(*ix, k);
   const bool persistent = ix->opt_kernel == ANNS_KERNEL_PERSISTENT ||
-                          (ix->opt_kernel == ANNS_KERNEL_AUTO && persistent_supported(*ix));
-  if (ix->opt_kernel == ANNS_KERNEL_PERSISTENT && !persistent_supported(*ix))
-    return fail(ANNS_ERR_UNSUPPORTED, "persistent kernel needs M*256*dsub to fit the register codebook");
+                          (ix->opt_kernel == ANNS_KERNEL_AUTO && fits);
+  if (ix->opt_kernel == ANNS_KERNEL_PERSISTENT && !fits)
+    return fail(ANNS_ERR_UNSUPPORTED,
+                "persistent kernel needs k <= 32 and the codebook plus two LUTs in shared memory");
   if (persistent)
     e = launch_search_persistent(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
                                  ix->ws_bits, ids_out, dists_out, ix->ws_counter, s);

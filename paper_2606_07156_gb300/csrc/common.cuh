@@ -7,6 +7,9 @@
 #include <climits>
 #include <cmath>
 
+// The block's dynamic shared memory; every kernel carves its own layout from it.
+extern __shared__ __align__(16) unsigned char anns_dyn_smem[];
+
 namespace anns {
 
 constexpr unsigned kFull = 0xffffffffu;

@@ -88,7 +88,7 @@ cudaError_t launch_search(const Index& ix, const float* Q, int64_t nq, int nprob
                           const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
                           float* dists_out, cudaStream_t s);
 // Persistent variant (codebook in registers); see search_persistent.cu.
-bool persistent_supported(const Index& ix);
+bool persistent_supported(const Index& ix, int k);
 cudaError_t launch_search_persistent(const Index& ix, const float* Q, int64_t nq, int nprobe,
                                      const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                                      const int32_t* probes, const uint8_t* bits, int64_t* ids_out,

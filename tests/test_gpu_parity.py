@@ -35,8 +35,18 @@ def case_a(amp, small_a, request):
     d, ix = small_a
     g, o = _pair(amp, ix)
     g.set_kernel(request.param)
+    g.kernel_name = request.param
     yield d, ix, g, o
     g.close()
+
+
+def forced_persistent_rejects(amp, g, k, call):
+    """The persistent kernel serves k <= 32; forced beyond that it must refuse."""
+    if getattr(g, "kernel_name", "") == "persistent" and k > 32:
+        with pytest.raises(amp.AnnsError, match="persistent"):
+            call()
+        return True
+    return False
 
 
 def cuda(a):
@@ -127,6 +137,8 @@ def test_search_bit_exact(amp, case_a, bits, k):
     d, ix, g, o = case_a
     Q = d["queries"]
     pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
+    if forced_persistent_rejects(amp, g, k, lambda: g.search(cuda(Q), 6, k, pol)):
+        return
     ids, dists = g.search(cuda(Q), 6, k, pol)
     ri, rd = ivfpq.search(o, Q, 6, k, bits=bits)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
@@ -184,9 +196,11 @@ def test_per_query_nprobe_and_k(amp, case_a):
     r = np.random.Generator(np.random.PCG64(8))
     npq = r.integers(0, 9, size=len(Q)).astype(np.int32)
     kpq = r.choice(np.array([0, 1, 10, 33], dtype=np.int32), size=len(Q))
-    ids, dists = g.search(cuda(Q), 8, 33, amp.policy("fixed", bits=6), nprobe_per_q=cuda(npq),
+    kmax = 32 if getattr(g, "kernel_name", "") == "persistent" else 33
+    kpq = np.minimum(kpq, kmax).astype(np.int32)
+    ids, dists = g.search(cuda(Q), 8, kmax, amp.policy("fixed", bits=6), nprobe_per_q=cuda(npq),
                           k_per_q=cuda(kpq))
-    ri, rd = ivfpq.search(o, Q, 8, 33, bits=6, nprobe_per_q=npq, k_per_q=kpq)
+    ri, rd = ivfpq.search(o, Q, 8, kmax, bits=6, nprobe_per_q=npq, k_per_q=kpq)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
     np.testing.assert_array_equal(dists.cpu().numpy(), rd)
 
@@ -218,7 +232,7 @@ def test_ties_broken_by_user_id_and_padding(amp):
     g, o = _pair(amp, ix, ids=uids)
     Q = r.integers(0, 4, size=(30, 8)).astype(np.float32)
     for kern, npb, k, bits in ((kn, *c) for kn in ("basic", "persistent")
-                               for c in ((4, 20, 0), (1, 128, 0), (2, 50, 4), (4, 7, 16))):
+                               for c in ((4, 20, 0), (1, 32, 0), (2, 30, 4), (4, 7, 16))):
         g.set_kernel(kern)
         pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
         ids, dists = g.search(cuda(Q), npb, k, pol)
@@ -244,7 +258,9 @@ def test_odd_subspace_counts(amp, M, dim):
     ix["list_of"][ix["list_of"] == 5] = 6                     # list 5 becomes empty
     g, o = _pair(amp, ix)
     Q = r.standard_normal((12, dim)).astype(np.float32)
-    fits = (M + 15) // 16 * 256 * (dim // M) <= 64 * 32 and M <= 64
+    dsub = dim // M
+    fits = (M <= 64 and (M + 15) // 16 <= 4 and
+            ((dsub in (1, 2) and M <= 64) or (dsub in (4, 8) and M <= 32)))
     for kern in ("basic", "persistent"):
         g.set_kernel(kern)
         for bits in (0, 8, 12):
