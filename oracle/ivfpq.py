@@ -25,6 +25,14 @@ Two families of functions:
   per operation, no fused multiply-add and a fixed summation order, so the
   library must reproduce it bit for bit.
 
+The FP32 LUT is evaluated in the decomposed form: with r = q - c_l,
+  ||r_m - y||^2 = ||r_m||^2 + [||y||^2 + 2 <c_{l,m}, y>] - 2 <q_m, y>,
+and sum_m ||r_m||^2 = ||q - c_l||^2 = D2 is the coarse distance CL already
+has. So the FP32 table of a pair is T'[m][c] = P_l[m][c] - 2 Q_q[m][c] with a
+per-list table P (fixed at index build) and a per-query table Q (shared by
+all probes of the query), and the ADC distance is D2 + sum_m T'[m][code_m].
+The FP64 definitions keep the direct form.
+
 Readings where the paper is silent (the paper states no quantiser, bit-width
 set, tie rule or feature normalisation):
 
@@ -105,29 +113,56 @@ def lut_fp64(q: np.ndarray, c: np.ndarray, books: np.ndarray) -> np.ndarray:
     return T
 
 
-def lut_fp32(q: np.ndarray, c: np.ndarray, books: np.ndarray) -> np.ndarray:
-    """FP32 rule for the LUT: r_d = fl32(q_d - c_d); then per entry, over
-    j = 0..dsub-1 ascending: e = fl32(r_{m*dsub+j} - y_{m,c',j});
-    acc = fl32(acc + fl32(e * e)), starting from acc = 0."""
+def lut_shift_fp64(q: np.ndarray, c: np.ndarray, books: np.ndarray) -> np.ndarray:
+    """The shifted table T'[m][c'] = ||r_m - y_{m,c'}||^2 - ||r_m||^2 in FP64."""
     M, ksub, dsub = books.shape
-    r = (np.asarray(q, dtype=F32) - np.asarray(c, dtype=F32)).astype(F32)
+    r = np.asarray(q, dtype=F64) - np.asarray(c, dtype=F64)
+    rn = np.array([np.dot(r[m * dsub:(m + 1) * dsub], r[m * dsub:(m + 1) * dsub]) for m in range(M)])
+    return lut_fp64(q, c, books) - rn[:, None]
+
+
+def _dot_rule(a: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """acc = 0; for j ascending: acc = fl32(acc + fl32(a_j * y_j)); a is [M, dsub], y [M, 256, dsub]."""
+    acc = np.zeros(y.shape[:2], dtype=F32)
+    for j in range(y.shape[2]):
+        acc = (acc + (a[:, j][:, None] * y[:, :, j]).astype(F32)).astype(F32)
+    return acc
+
+
+def query_table_fp32(q: np.ndarray, books: np.ndarray) -> np.ndarray:
+    """FP32 rule for Q_q[m][c] = <q_m, y_{m,c}> (dot rule, j ascending)."""
+    M, _, dsub = books.shape
+    return _dot_rule(np.asarray(q, dtype=F32).reshape(M, dsub), np.asarray(books, dtype=F32))
+
+
+def list_table_fp32(c: np.ndarray, books: np.ndarray) -> np.ndarray:
+    """FP32 rule for P_l[m][c'] = fl32(||y||^2 + fl32(2 <c_{l,m}, y>)), both
+    inner products by the dot rule."""
+    M, _, dsub = books.shape
     y = np.asarray(books, dtype=F32)
-    T = np.zeros((M, ksub), dtype=F32)
+    yn = np.zeros(y.shape[:2], dtype=F32)
     for j in range(dsub):
-        rj = r[np.arange(M) * dsub + j][:, None]          # [M, 1]
-        e = (rj - y[:, :, j]).astype(F32)                   # [M, 256]
-        T = (T + (e * e).astype(F32)).astype(F32)
-    return T
+        yn = (yn + (y[:, :, j] * y[:, :, j]).astype(F32)).astype(F32)
+    cy = _dot_rule(np.asarray(c, dtype=F32).reshape(M, dsub), y)
+    return (yn + (F32(2.0) * cy).astype(F32)).astype(F32)
+
+
+def lut_fp32(q: np.ndarray, c: np.ndarray, books: np.ndarray) -> np.ndarray:
+    """FP32 rule for the shifted table: T' = fl32(P_l - fl32(2 Q_q))."""
+    P = list_table_fp32(c, books)
+    Qt = query_table_fp32(q, books)
+    return (P - (F32(2.0) * Qt).astype(F32)).astype(F32)
 
 
 # ----------------------------------------------- precision: the LUT quantiser
 
-def quantize_lut(T32: np.ndarray, b: int) -> dict:
+def quantize_lut(T32: np.ndarray, b: int, d2=0.0) -> dict:
     """Quantise one (query, list) FP32 LUT to b bits (rule in the module docstring).
 
-    Returns the integer table ``t`` [M, 256] (int64), the FP32 biases, the FP32
-    range, FP64 step ``delta64`` and offset ``B64``, their FP32 roundings, and
-    the FP32 multiplier ``s32``.
+    ``d2`` is the pair's FP32 coarse distance, folded into the offset:
+    B = fl64(d2) + (tree sum of the biases). Returns the integer table ``t``
+    [M, 256] (int64), the FP32 biases, the FP32 range, FP64 step ``delta64``
+    and offset ``B64``, their FP32 roundings, and the FP32 multiplier ``s32``.
     """
     assert b in BITS
     T32 = np.asarray(T32, dtype=F32)
@@ -143,7 +178,7 @@ def quantize_lut(T32: np.ndarray, b: int) -> dict:
         s32 = F32(0.0)
     y = (Tp * s32).astype(F32)
     t = np.minimum(np.rint(y), L).astype(np.int64)          # rint: half to even
-    B64 = tree_sum64(bias)
+    B64 = F64(F64(F32(d2)) + tree_sum64(bias))
     return dict(t=t, bias=bias, range=rng, delta64=delta64, s32=s32, B64=B64,
                 delta32=F32(delta64), B32=F32(B64), L=L)
 
@@ -169,13 +204,14 @@ def adc_fp64(T: np.ndarray, codes: np.ndarray) -> np.ndarray:
     return np.asarray(T, dtype=F64)[np.arange(M)[None, :], codes.astype(np.int64)].sum(axis=1)
 
 
-def adc_fp32(T32: np.ndarray, codes: np.ndarray) -> np.ndarray:
-    """FP32 rule: acc = 0; for m = 0..M-1 ascending: acc = fl32(acc + T[m][code_m])."""
+def adc_fp32(T32: np.ndarray, codes: np.ndarray, d2=0.0) -> np.ndarray:
+    """FP32 rule: acc = 0; for m = 0..M-1 ascending: acc = fl32(acc + T'[m][code_m]);
+    the distance is fl32(d2 + acc) with d2 the pair's FP32 coarse distance."""
     codes = np.asarray(codes).astype(np.int64)
     acc = np.zeros(codes.shape[0], dtype=F32)
     for m in range(codes.shape[1]):
         acc = (acc + T32[m][codes[:, m]]).astype(F32)
-    return acc
+    return (F32(d2) + acc).astype(F32)
 
 
 def adc_int(t: np.ndarray, codes: np.ndarray) -> np.ndarray:
@@ -284,10 +320,11 @@ def search(index: Index, Q: np.ndarray, nprobe: int, k: int, bits=0,
                 d = adc_fp64(lut_fp64(Q[i], index.centroids[l], index.books), cd)
             else:
                 T32 = lut_fp32(Q[i], index.centroids[l], index.books)
+                d2 = pd[i, j]
                 if b == 0:
-                    d = adc_fp32(T32, cd)
+                    d = adc_fp32(T32, cd, d2)
                 else:
-                    qz = quantize_lut(T32, b)
+                    qz = quantize_lut(T32, b, d2)
                     d = dequant32(adc_int(qz["t"], cd), qz["delta32"], qz["B32"])
             ds.append(d)
             idl.append(index.ids[mem])

@@ -109,12 +109,13 @@ def labels_for_query(index: ivfpq.Index, q: np.ndarray, probes_q: np.ndarray, k:
     """
     T = []
     dl = []
-    for l in probes_q:
+    d2s = ivfpq.coarse_d2_fp32(np.asarray(q)[None], index.centroids[np.asarray(probes_q)])[0]
+    for j, l in enumerate(probes_q):
         l = int(l)
         T32 = ivfpq.lut_fp32(q, index.centroids[l], index.books)
         T.append(T32)
         mem = index.members[l]
-        dl.append(ivfpq.adc_fp32(T32, index.codes[mem]) if len(mem) else np.zeros(0, F32))
+        dl.append(ivfpq.adc_fp32(T32, index.codes[mem], d2s[j]) if len(mem) else np.zeros(0, F32))
     alld = np.concatenate(dl) if dl else np.zeros(0, F32)
     allid = np.concatenate([index.ids[index.members[int(l)]] for l in probes_q]) if dl else np.zeros(0, np.int64)
     if alld.size > k:
@@ -137,7 +138,7 @@ def labels_for_query(index: ivfpq.Index, q: np.ndarray, probes_q: np.ndarray, k:
         cd = index.codes[mem]
         lab = 0
         for bi, b in enumerate(BITS):
-            qz = ivfpq.quantize_lut(T[j], b)
+            qz = ivfpq.quantize_lut(T[j], b, d2s[j])
             dh = ivfpq.dequant32(ivfpq.adc_int(qz["t"], cd), qz["delta32"], qz["B32"]).astype(F64)
             errs[j, bi] = np.max(np.abs(dh - d))
             if lab == 0 and errs[j, bi] < margin:

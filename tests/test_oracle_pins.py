@@ -38,6 +38,21 @@ def test_adc_equals_distance_to_reconstruction(small_a):
             np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
 
 
+def test_decomposed_table_identity(small_a):
+    """D2 + sum_m T'[m][code_m] = ||q - x_hat||^2 in FP64, where T' is the
+    table shifted by ||r_m||^2 (the form the FP32 rule evaluates)."""
+    d, ix = small_a
+    I = _index(ix)
+    for qi in range(3):
+        q = d["queries"][qi]
+        for l in range(0, I.nlist, 4):
+            mem = I.members[l]
+            D2 = float(((q.astype(np.float64) - I.centroids[l].astype(np.float64)) ** 2).sum())
+            got = D2 + ivfpq.adc_fp64(ivfpq.lut_shift_fp64(q, I.centroids[l], I.books), I.codes[mem])
+            want = ((I.reconstruct(mem) - q.astype(np.float64)) ** 2).sum(1)
+            np.testing.assert_allclose(got, want, rtol=1e-10)
+
+
 # ------------------------------------------------------- P2: brute-force equivalence
 
 @pytest.mark.parametrize("fp64", [True, False])
@@ -62,14 +77,15 @@ def test_exact_operand_mode_fp32_rules_equal_fp64():
     I = _index(ix)
     r = np.random.Generator(np.random.PCG64(3))
     Q = r.integers(0, 16, size=(10, 16)).astype(np.float32)
-    np.testing.assert_array_equal(ivfpq.coarse_d2_fp32(Q, I.centroids),
-                                  ivfpq.coarse_d2_fp64(Q, I.centroids))
+    D32 = ivfpq.coarse_d2_fp32(Q, I.centroids)
+    np.testing.assert_array_equal(D32, ivfpq.coarse_d2_fp64(Q, I.centroids))
     for l in range(I.nlist):
         T32 = ivfpq.lut_fp32(Q[0], I.centroids[l], I.books)
+        np.testing.assert_array_equal(T32.astype(np.float64),
+                                      ivfpq.lut_shift_fp64(Q[0], I.centroids[l], I.books))
         T64 = ivfpq.lut_fp64(Q[0], I.centroids[l], I.books)
-        np.testing.assert_array_equal(T32.astype(np.float64), T64)
         cd = I.codes[I.members[l]]
-        np.testing.assert_array_equal(ivfpq.adc_fp32(T32, cd).astype(np.float64),
+        np.testing.assert_array_equal(ivfpq.adc_fp32(T32, cd, D32[0, l]).astype(np.float64),
                                       ivfpq.adc_fp64(T64, cd))
 
 
@@ -84,10 +100,16 @@ def test_fp32_rules_within_rounding_bound(small_a):
     D32 = ivfpq.coarse_d2_fp32(Q, I.centroids).astype(np.float64)
     D64 = ivfpq.coarse_d2_fp64(Q, I.centroids)
     assert np.all(np.abs(D32 - D64) <= (I.dim + 2) * u * D64 * 1.01)
-    T32 = ivfpq.lut_fp32(Q[0], I.centroids[0], I.books).astype(np.float64)
-    T64 = ivfpq.lut_fp64(Q[0], I.centroids[0], I.books)
-    # r = fl32(q - c) perturbs each difference by <= u |r|, squared terms by ~2u
-    assert np.all(np.abs(T32 - T64) <= (I.dsub + 4) * u * T64 + 1e-30)
+    for qi in range(3):
+        q, c = Q[qi].astype(np.float64), I.centroids[qi].astype(np.float64)
+        T32 = ivfpq.lut_fp32(Q[qi], I.centroids[qi], I.books).astype(np.float64)
+        T64 = ivfpq.lut_shift_fp64(Q[qi], I.centroids[qi], I.books)
+        # each inner product of the decomposed rule is within (dsub+1) u of its
+        # absolute sum; the final sum and subtraction add two more roundings
+        y = I.books.astype(np.float64)
+        qm, cm = q.reshape(I.M, 1, I.dsub), c.reshape(I.M, 1, I.dsub)
+        s_abs = (y * y).sum(-1) + 2 * np.abs(cm * y).sum(-1) + 2 * np.abs(qm * y).sum(-1)
+        assert np.all(np.abs(T32 - T64) <= (I.dsub + 3) * u * s_abs * 1.01)
 
 
 # ------------------------------------------------------------ P3: integer exactness
