@@ -149,6 +149,10 @@ int anns_debug_tap(anns_index* index, int32_t what, void* out, size_t bytes);
 
 /* LUT construction + quantisation for explicit pairs (RC + LC of Section 2.1
  * and the per-pair precision), with the same device code the search uses.
+ * The FP32 LUT is the one the search evaluates: T'[m][c] = ||r_m - y_mc||^2
+ * - ||r_m||^2 (the ADC distance is the coarse distance D2 plus sum_m T'),
+ * formed as fl32(P_l - 2 Q_q) from a per-list and a per-query table; the
+ * offset B of a quantised pair includes D2.
  *  queries  device float32 [nq * dim]; pair_q, pair_l device int32 [npairs];
  *  pair_bits device uint8 [npairs] (0 = FP32 only).
  *  T_out     device float32 [npairs * M * 256] FP32 LUT, or NULL.
@@ -169,8 +173,8 @@ int anns_scan_pairs(anns_index* index, const float* queries, int64_t nq,
                     void* cuda_stream);
 
 /* Stage timing with CUDA events recorded on the search stream around each
- * kernel of anns_search: CL distances, CL selection, precision choice, and the
- * fused LUT + scan + top-k kernel.
+ * stage of anns_search: CL distances, CL selection, precision choice plus the
+ * per-query tables, and the fused LUT + scan + top-k kernel.
  *  enable  1 = start recording (and clear the totals), 0 = stop, -1 = leave as is.
  *  out_ms  host double [4] or NULL: accumulated milliseconds per stage since
  *          recording started (waits for the recorded searches to finish).
@@ -179,12 +183,12 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
 
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
- *    ANNS_KERNEL_AUTO (default): the persistent kernel when k <= 32 and the
- *      codebook (M * 256 * dsub floats) plus two LUTs fit in one block's
- *      shared memory, else the one-block-per-query kernel.
- *    ANNS_KERNEL_BASIC: one block per query; codebook read through L1/L2.
- *    ANNS_KERNEL_PERSISTENT: one block per SM, codebook in shared memory;
- *      UNSUPPORTED at search time if it does not fit.
+ *    ANNS_KERNEL_AUTO (default): the persistent kernel when k <= 32 and
+ *      M <= 64 (two LUT slots and the query table fit in shared memory), else
+ *      the one-block-per-query kernel.
+ *    ANNS_KERNEL_BASIC: one block per query.
+ *    ANNS_KERNEL_PERSISTENT: one 1024-thread block per SM walking the queries
+ *      with a pipelined LUT build; UNSUPPORTED at search time if it does not fit.
  * Both kernels return identical results. Errors: INVALID_ARG. */
 enum { ANNS_OPT_KERNEL = 0 };
 enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_PERSISTENT = 2 };

@@ -100,6 +100,8 @@ int ensure_workspace(Index& ix, int64_t nq, int nprobe) {
   ix.ws_bits = (uint8_t*)((char*)blk + 28 * P);
   ix.ws_nq = nq;
   ix.ws_nprobe = nprobe;
+  rc = grow((void**)&ix.ws_qt, &ix.ws_qt_cap, (size_t)nq * ix.Mp * kKsub * 4);
+  if (rc) return rc;
   return grow((void**)&ix.ws_counter, &ix.ws_counter_cap, 64);
 }
 
@@ -214,6 +216,8 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
   if ((rc = launch_policy(*ix, P, nq, nprobe, nprobe_per_q, ix->ws_probes, ix->ws_probe_d2,
                           ix->ws_bits, want_feat ? ix->ws_feat : nullptr, s)))
     return rc;
+  e = launch_query_tables(*ix, Q, nq, ix->ws_qt, s);
+  if (e != cudaSuccess) return cuda_fail(e, "query tables");
   if (ev) cudaEventRecord(ev[3], s);
   const bool fits = persistent_supported(*ix, k);
   const bool persistent = ix->opt_kernel == ANNS_KERNEL_PERSISTENT ||
@@ -222,11 +226,11 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
     return fail(ANNS_ERR_UNSUPPORTED,
                 "persistent kernel needs k <= 32 and the codebook plus two LUTs in shared memory");
   if (persistent)
-    e = launch_search_persistent(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
-                                 ix->ws_bits, ids_out, dists_out, ix->ws_counter, s);
+    e = launch_search_persistent(*ix, ix->ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
+                                 ix->ws_probe_d2, ix->ws_bits, ids_out, dists_out, ix->ws_counter, s);
   else
-    e = launch_search(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes, ix->ws_bits,
-                      ids_out, dists_out, s);
+    e = launch_search(*ix, ix->ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
+                      ix->ws_probe_d2, ix->ws_bits, ids_out, dists_out, s);
   if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   if (ev) cudaEventRecord(ev[4], s);
   return ANNS_OK;
@@ -277,8 +281,11 @@ extern "C" int anns_compute_luts(anns_index* ix, const float* Q, int64_t nq, con
   if (rc) return rc;
   if (npairs == 0) return ANNS_OK;
   DeviceGuard g(ix->device);
-  cudaError_t e = launch_compute_luts(*ix, Q, nq, pq, pl, pb, npairs, T_out, t_out, scale_out,
-                                      (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = grow((void**)&ix->ws_qt, &ix->ws_qt_cap, (size_t)nq * ix->Mp * kKsub * 4))) return rc;
+  cudaError_t e = launch_query_tables(*ix, Q, nq, ix->ws_qt, s);
+  if (e == cudaSuccess)
+    e = launch_compute_luts(*ix, Q, ix->ws_qt, nq, pq, pl, pb, npairs, T_out, t_out, scale_out, s);
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "LUT kernel");
 }
 
@@ -290,8 +297,11 @@ extern "C" int anns_scan_pairs(anns_index* ix, const float* Q, int64_t nq, const
   if (npairs == 0) return ANNS_OK;
   if (!off || !dist_out) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
   DeviceGuard g(ix->device);
-  cudaError_t e = launch_scan_pairs(*ix, Q, nq, pq, pl, pb, npairs, off, dist_out, S_out,
-                                    (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = grow((void**)&ix->ws_qt, &ix->ws_qt_cap, (size_t)nq * ix->Mp * kKsub * 4))) return rc;
+  cudaError_t e = launch_query_tables(*ix, Q, nq, ix->ws_qt, s);
+  if (e == cudaSuccess)
+    e = launch_scan_pairs(*ix, Q, ix->ws_qt, nq, pq, pl, pb, npairs, off, dist_out, S_out, s);
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "scan kernel");
 }
 

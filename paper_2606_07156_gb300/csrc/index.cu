@@ -1,8 +1,10 @@
 // Index construction and facts (Section 2.1: IVF lists, PQ codes on residuals
 // with one codebook shared by every cluster; covering radius r of Eq. 1).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -42,7 +44,7 @@ static void free_index(anns_index* ix) {
   cudaGetDevice(&prev);
   cudaSetDevice(ix->device);
   void* ptrs[] = {ix->centroids, ix->codebooks, ix->codes, ix->ids, ix->list_len,
-                  ix->vec_off, ix->tile_off, ix->radius, ix->ws_d2,
+                  ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->ws_qt, ix->ws_d2,
                   ix->ws_probes /* base of the pair block; the other ws_* alias it */,
                   ix->st_q, ix->st_out, ix->st_pq, ix->mlp_dev, ix->ws_counter};
   for (void* p : ptrs)
@@ -85,6 +87,41 @@ int upload(T** dst, const T* src, size_t count, const char* what) {
     if (e != cudaSuccess) return cuda_fail(e, what);
   }
   return ANNS_OK;
+}
+
+// P_l[m][c] = fl32(yn[m][c] + fl32(2 * <c_lm, y_mc>)) with both inner products
+// accumulated in FP32, j ascending, one rounding per operation; rows M..Mp-1 zero.
+void list_tables(const std::vector<float>& cent, const std::vector<float>& books, int64_t nlist,
+                 int64_t dim, int64_t M, int64_t Mp, std::vector<float>& out) {
+  const int64_t dsub = dim / M;
+  std::vector<float> yn((size_t)M * ANNS_KSUB);
+  for (int64_t e = 0; e < M * ANNS_KSUB; ++e) {
+    float acc = 0.f;
+    for (int64_t j = 0; j < dsub; ++j) {
+      const float y = books[(size_t)e * dsub + j];
+      const float sq = y * y;
+      acc = acc + sq;
+    }
+    yn[e] = acc;
+  }
+  out.assign((size_t)nlist * Mp * ANNS_KSUB, 0.f);
+  auto work = [&](int64_t l0, int64_t l1) {
+    for (int64_t l = l0; l < l1; ++l)
+      for (int64_t m = 0; m < M; ++m)
+        for (int c = 0; c < ANNS_KSUB; ++c) {
+          float acc = 0.f;
+          for (int64_t j = 0; j < dsub; ++j) {
+            const float pr = cent[(size_t)l * dim + m * dsub + j] * books[((size_t)m * ANNS_KSUB + c) * dsub + j];
+            acc = acc + pr;
+          }
+          const float two = 2.f * acc;
+          out[((size_t)l * Mp + m) * ANNS_KSUB + c] = yn[(size_t)m * ANNS_KSUB + c] + two;
+        }
+  };
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), nlist));
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back(work, nlist * t / nt, nlist * (t + 1) / nt);
+  for (auto& x : th) x.join();
 }
 
 }  // namespace
@@ -188,7 +225,10 @@ extern "C" int anns_build_index_from_arrays(const anns_build_desc* d, anns_index
     len32[l] = (int32_t)cnt[l];
     ix->h_radius[l] = (float)std::sqrt(rmax2[l]);
   }
-  if ((rc = upload(&ix->centroids, cent.data(), cent.size(), "upload centroids")) ||
+  std::vector<float> ltab;
+  list_tables(cent, books, nlist, dim, M, Mp, ltab);
+  if ((rc = upload(&ix->ltab, ltab.data(), ltab.size(), "upload list tables")) ||
+      (rc = upload(&ix->centroids, cent.data(), cent.size(), "upload centroids")) ||
       (rc = upload(&ix->codebooks, books.data(), books.size(), "upload codebooks")) ||
       (rc = upload(&ix->codes, packed.data(), packed.size(), "upload codes")) ||
       (rc = upload(&ix->ids, pids.data(), pids.size(), "upload ids")) ||

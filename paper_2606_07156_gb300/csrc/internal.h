@@ -35,6 +35,10 @@ struct Index {
   int64_t* vec_off = nullptr;   // [nlist+1]
   int64_t* tile_off = nullptr;  // [nlist+1]
   float* radius = nullptr;      // [nlist] covering radius, FP64-derived
+  // Per-list table P_l[m][c] = fl32(||y_mc||^2 + fl32(2 <c_lm, y_mc>)), rows
+  // M..Mp-1 zero: [nlist * Mp * 256]. With the per-query table Q it gives the
+  // pair's LUT T' = P_l - 2 Q_q (the LUT shifted by ||r_m||^2, Section 2.1).
+  float* ltab = nullptr;
   // host copies of the small per-list tables
   std::string err;
   int64_t* h_list_len64 = nullptr;
@@ -46,6 +50,8 @@ struct Index {
   float* ws_probe_d2 = nullptr;  // [nq*nprobe]
   uint8_t* ws_bits = nullptr;    // [nq*nprobe]
   float* ws_feat = nullptr;      // [nq*nprobe*5]
+  float* ws_qt = nullptr;        // [nq*Mp*256] per-query tables 2 Q_q
+  size_t ws_qt_cap = 0;
   size_t ws_d2_cap = 0, ws_pair_cap = 0;
   int* ws_counter = nullptr;     // work counter of the persistent kernel
   size_t ws_counter_cap = 0;
@@ -78,28 +84,32 @@ int grow(void** p, size_t* cap, size_t bytes);
 cudaError_t launch_coarse(const Index& ix, const float* Q, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, float* d2, int32_t* probes,
                           float* probe_d2, cudaStream_t s, cudaEvent_t between = nullptr);
+// Per-query tables 2*Q_q[m][c] = 2 <q_m, y_mc> (FP32 dot rule), rows M..Mp-1 zero.
+cudaError_t launch_query_tables(const Index& ix, const float* Q, int64_t nq, float* qt, cudaStream_t s);
 // Precision choice per (query, probe rank).
 int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq, int nprobe,
                   const int32_t* nprobe_per_q, const int32_t* probes, const float* probe_d2,
                   uint8_t* bits, float* feat, cudaStream_t s);
 // RC + LC + quantise + DC + TS for every query.
-cudaError_t launch_search(const Index& ix, const float* Q, int64_t nq, int nprobe,
+cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
-                          const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
-                          float* dists_out, cudaStream_t s);
+                          const int32_t* probes, const float* probe_d2, const uint8_t* bits,
+                          int64_t* ids_out, float* dists_out, cudaStream_t s);
 // Persistent variant (codebook in registers); see search_persistent.cu.
 bool persistent_supported(const Index& ix, int k);
-cudaError_t launch_search_persistent(const Index& ix, const float* Q, int64_t nq, int nprobe,
+cudaError_t launch_search_persistent(const Index& ix, const float* qt, int64_t nq, int nprobe,
                                      const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
-                                     const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
-                                     float* dists_out, int* counter, cudaStream_t s);
-cudaError_t launch_compute_luts(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
-                                const int32_t* pl, const uint8_t* pb, int64_t npairs,
-                                float* T_out, uint16_t* t_out, double* scale_out,
+                                     const int32_t* probes, const float* probe_d2,
+                                     const uint8_t* bits, int64_t* ids_out, float* dists_out,
+                                     int* counter, cudaStream_t s);
+// Pair-level debug paths; qt are the queries' tables from launch_query_tables.
+cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt, int64_t nq,
+                                const int32_t* pq, const int32_t* pl, const uint8_t* pb,
+                                int64_t npairs, float* T_out, uint16_t* t_out, double* scale_out,
                                 cudaStream_t s);
-cudaError_t launch_scan_pairs(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
-                              const int32_t* pl, const uint8_t* pb, int64_t npairs,
-                              const int64_t* off, float* dist_out, int32_t* S_out,
+cudaError_t launch_scan_pairs(const Index& ix, const float* Q, const float* qt, int64_t nq,
+                              const int32_t* pq, const int32_t* pl, const uint8_t* pb,
+                              int64_t npairs, const int64_t* off, float* dist_out, int32_t* S_out,
                               cudaStream_t s);
 
 }  // namespace anns

@@ -1,18 +1,20 @@
-// RC + LC + precision + DC + TS (Section 2.1) for one query per thread block.
+// RC + LC + precision + DC + TS (Section 2.1) for one query per thread block;
+// the general kernel (any M, dsub, k) and the one behind the pair-level taps.
 //
 // Per probed list l of query q, the block
-//   1. forms the residual r = fl32(q - c_l) in shared memory (RC),
-//   2. builds the FP32 LUT T[m][c] = sum_j fl32((r_{m,j} - y_{m,c,j})^2),
-//      j ascending, explicitly rounded (LC), into shared memory,
-//   3. if the pair's precision is b bits, quantises T with one shared step
-//      Delta = range/(2^b-1) and per-sub-table biases (scale/offset in FP64),
-//      into a uint8 (b <= 8) or uint16 table in shared memory,
-//   4. scans the list's packed codes tile by tile, one vector per lane,
-//      accumulating LUT entries in ascending m — FP32 sums for the plain LUT,
-//      exact int32 sums S for quantised LUTs, whose estimate is
-//      fl32(fl32(Delta32 * S) + B32) (DC),
-//   5. offers each distance to a per-warp sorted top-k list (TS).
+//   1. forms the FP32 LUT shifted by ||r_m||^2, T'[m][c] = fl32(P_l - 2 Q_q),
+//      from the list's table P_l and the query's table 2 Q_q (LC),
+//   2. if the pair's precision is b bits, quantises T' with one shared step
+//      Delta = range/(2^b-1) and per-sub-table biases into a uint8 (b <= 8) or
+//      uint16 table in shared memory, the offset B = D2 + sum of biases in FP64,
+//   3. scans the list's packed codes tile by tile, one vector per lane,
+//      summing LUT entries in ascending m — FP32 sums for the plain LUT
+//      (distance fl32(D2 + sum)), exact int32 sums S for quantised LUTs
+//      (distance fl32(fl32(Delta32 * S) + B32)) (DC),
+//   4. offers each distance to a per-warp sorted top-k list (TS).
 // The LUT never leaves shared memory. At the end the warps' lists are merged.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -29,14 +31,13 @@ struct PairScal {
 };
 
 struct SmemLayout {
-  size_t r = 0, T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, md = 0, mi = 0, total = 0;
+  size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, md = 0, mi = 0, total = 0;
   static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   SmemLayout() = default;
-  SmemLayout(int64_t dim, int64_t Mp, int R) {
+  SmemLayout(int64_t Mp, int R) {
     size_t o = 0;   // the tables first: their element offsets have a zero low byte
     T = o; o += al(Mp * kKsub * 4);
     q = o; o += al(Mp * kKsub * 2);
-    r = o; o += al(dim * 4);
     bias = o; o += al(Mp * 4);
     rowmax = o; o += al(Mp * 4);
     scal = o; o += al(sizeof(PairScal));
@@ -47,34 +48,21 @@ struct SmemLayout {
 };
 
 struct Smem {
-  float* r; float* T; void* q; float* bias; float* rowmax; PairScal* sc; float* md; int64_t* mi;
-  __device__ Smem(unsigned char* base, const SmemLayout& L)
-      : r((float*)(base + L.r)), T((float*)(base + L.T)), q(base + L.q),
-        bias((float*)(base + L.bias)), rowmax((float*)(base + L.rowmax)),
-        sc((PairScal*)(base + L.scal)), md((float*)(base + L.md)), mi((int64_t*)(base + L.mi)) {}
+  float* T; void* q; float* bias; float* rowmax; PairScal* sc; float* md; int64_t* mi;
+  __device__ explicit Smem(const SmemLayout& L)
+      : T((float*)(anns_dyn_smem + L.T)), q(anns_dyn_smem + L.q),
+        bias((float*)(anns_dyn_smem + L.bias)), rowmax((float*)(anns_dyn_smem + L.rowmax)),
+        sc((PairScal*)(anns_dyn_smem + L.scal)), md((float*)(anns_dyn_smem + L.md)),
+        mi((int64_t*)(anns_dyn_smem + L.mi)) {}
 };
 
-// Steps 1-3 for pair (q, c): all threads of the block take part.
-__device__ void build_lut(const float* __restrict__ qv, const float* __restrict__ cv,
-                          const float* __restrict__ cb, int dim, int M, int Mp, int dsub, int b,
-                          Smem& s) {
+// Steps 1-2 for one pair: all threads of the block take part. P and qt2 are
+// the pair's list table and query table ([Mp * 256], rows M..Mp-1 zero).
+__device__ void build_lut(const float* __restrict__ P, const float* __restrict__ qt2, int M, int Mp,
+                          int b, float d2, Smem& s) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int d = tid; d < dim; d += blockDim.x) s.r[d] = sub_rn(qv[d], cv[d]);
-  __syncthreads();
   const int nent = Mp * kKsub;
-  for (int e = tid; e < nent; e += blockDim.x) {
-    const int m = e >> 8;
-    float acc = 0.f;
-    if (m < M) {
-      const float* y = cb + (size_t)e * dsub;
-      const float* rr = s.r + m * dsub;
-      for (int j = 0; j < dsub; ++j) {
-        const float x = sub_rn(rr[j], __ldg(y + j));
-        acc = add_rn(acc, mul_rn(x, x));
-      }
-    }
-    s.T[e] = acc;
-  }
+  for (int e = tid; e < nent; e += blockDim.x) s.T[e] = sub_rn(__ldg(P + e), __ldg(qt2 + e));
   __syncthreads();
   if (b == 0) return;
   for (int m = warp; m < M; m += blockDim.x / 32) {
@@ -91,7 +79,7 @@ __device__ void build_lut(const float* __restrict__ qv, const float* __restrict_
   }
   __syncthreads();
   if (warp == 0) {
-    // B: FP64 sum of the row minima in the fixed 32-lane tree order
+    // B: FP64 sum of the row minima in the fixed 32-lane tree order, plus D2
     double B = 0.0;
     float range = 0.f;
     for (int m = lane; m < M; m += 32) {
@@ -108,8 +96,8 @@ __device__ void build_lut(const float* __restrict__ qv, const float* __restrict_
       sc.delta64 = range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
       sc.s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
       sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
-      sc.B64 = B;
-      sc.B32 = __double2float_rn(B);
+      sc.B64 = __dadd_rn((double)d2, B);
+      sc.B32 = __double2float_rn(sc.B64);
       sc.range = range;
       sc.L = L;
       *s.sc = sc;
@@ -149,10 +137,10 @@ __device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// FP32 ADC over all Mp sub-tables: acc = fl32(acc + T[m][code_m]), m ascending
-// (padding rows are zero). The FP32 table sits at shared offset 0.
+// FP32 ADC over all Mp sub-tables: acc = fl32(acc + T'[m][code_m]), m
+// ascending (padding rows are zero). The FP32 table sits at shared offset 0.
 template <int NCHUNK>
-__device__ __forceinline__ float adc_f32(const unsigned char* sm, const uint4 (&w)[NCHUNK]) {
+__device__ __forceinline__ float adc_f32(const uint4 (&w)[NCHUNK]) {
   float acc = 0.f;
 #pragma unroll
   for (int c = 0; c < NCHUNK; ++c)
@@ -160,17 +148,17 @@ __device__ __forceinline__ float adc_f32(const unsigned char* sm, const uint4 (&
     for (int i = 0; i < 4; ++i) {
       const unsigned x = word_of(w[c], i);
       const int m = c * 16 + i * 4;
-      acc = add_rn(acc, lut_at<float, 0>(sm, 0u, x, m));
-      acc = add_rn(acc, lut_at<float, 1>(sm, 0u, x, m + 1));
-      acc = add_rn(acc, lut_at<float, 2>(sm, 0u, x, m + 2));
-      acc = add_rn(acc, lut_at<float, 3>(sm, 0u, x, m + 3));
+      acc = add_rn(acc, lut_at<float, 0>(anns_dyn_smem, 0u, x, m));
+      acc = add_rn(acc, lut_at<float, 1>(anns_dyn_smem, 0u, x, m + 1));
+      acc = add_rn(acc, lut_at<float, 2>(anns_dyn_smem, 0u, x, m + 2));
+      acc = add_rn(acc, lut_at<float, 3>(anns_dyn_smem, 0u, x, m + 3));
     }
   return acc;
 }
 
 // Integer ADC: S = sum_m t[m][code_m], exact; `base` is the table's element offset.
 template <int NCHUNK, typename LT>
-__device__ __forceinline__ int adc_int(const unsigned char* sm, unsigned base, const uint4 (&w)[NCHUNK]) {
+__device__ __forceinline__ int adc_int(unsigned base, const uint4 (&w)[NCHUNK]) {
   int acc0 = 0, acc1 = 0;
 #pragma unroll
   for (int c = 0; c < NCHUNK; ++c)
@@ -178,8 +166,8 @@ __device__ __forceinline__ int adc_int(const unsigned char* sm, unsigned base, c
     for (int i = 0; i < 4; ++i) {
       const unsigned x = word_of(w[c], i);
       const int m = c * 16 + i * 4;
-      acc0 += (int)lut_at<LT, 0>(sm, base, x, m) + (int)lut_at<LT, 1>(sm, base, x, m + 1);
-      acc1 += (int)lut_at<LT, 2>(sm, base, x, m + 2) + (int)lut_at<LT, 3>(sm, base, x, m + 3);
+      acc0 += (int)lut_at<LT, 0>(anns_dyn_smem, base, x, m) + (int)lut_at<LT, 1>(anns_dyn_smem, base, x, m + 1);
+      acc1 += (int)lut_at<LT, 2>(anns_dyn_smem, base, x, m + 2) + (int)lut_at<LT, 3>(anns_dyn_smem, base, x, m + 3);
     }
   return acc0 + acc1;
 }
@@ -188,41 +176,34 @@ __device__ __forceinline__ float dequant(int S, const PairScal& sc) {
   return add_rn(mul_rn(sc.delta32, __int2float_rn(S)), sc.B32);
 }
 
+// Distance of the vector whose code tile words are w, for a pair whose table
+// was built with `b` bits (0 = FP32) and coarse distance d2.
+template <int NCHUNK>
+__device__ __forceinline__ float pair_distance(int b, float d2, unsigned qoff, const PairScal& sc,
+                                               const uint4 (&w)[NCHUNK], int* S_out = nullptr) {
+  if (b == 0) return add_rn(d2, adc_f32<NCHUNK>(w));
+  const int S = b <= 8 ? adc_int<NCHUNK, uint8_t>(qoff, w) : adc_int<NCHUNK, uint16_t>(qoff / 2, w);
+  if (S_out) *S_out = S;
+  return dequant(S, sc);
+}
+
 struct SearchArgs {
-  const float* Q; int64_t nq, dim, nlist;
-  const float* centroids; const float* codebooks;
+  const float* Q; const float* qt; int64_t nq, dim, nlist;
+  const float* centroids; const float* ltab;
   const uint8_t* codes; const int64_t* ids;
   const int32_t* list_len; const int64_t* vec_off; const int64_t* tile_off;
-  int M, Mp, dsub, nprobe, k;
+  int M, Mp, nprobe, k;
   const int32_t* npq; const int32_t* kpq;
-  const int32_t* probes; const uint8_t* bits;
+  const int32_t* probes; const float* probe_d2; const uint8_t* bits;
   int64_t* ids_out; float* dists_out;
   SmemLayout lay;
 };
 
-template <int NCHUNK, int R, typename Fd>
-__device__ __forceinline__ void scan_list(const SearchArgs& a, int l, int n_l, int kq, Fd dist,
-                                          WarpTopK<R, int64_t>& top, float& thd, int64_t& thi) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
-  const uint8_t* base = a.codes + (size_t)a.tile_off[l] * NCHUNK * kTileChunkBytes;
-  const int64_t vbase = a.vec_off[l];
-  for (int t = warp; t < ntile; t += kWarps) {
-    uint4 w[NCHUNK];
-    load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
-    const float d = dist(w);
-    const int v = t * kTileVecs + lane;
-    const bool pre = v < n_l && d <= thd;
-    const int64_t id = pre ? __ldg(a.ids + vbase + v) : INT64_MAX;
-    top.offer(pre, d, id, kq, thd, thi);
-  }
-}
-
 template <int NCHUNK, int R>
 __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem s(smem_raw, a.lay);
+  Smem s(a.lay);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tstride = (int64_t)a.Mp * kKsub;
   for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
     const int np = a.npq ? min(max(a.npq[q], 0), a.nprobe) : a.nprobe;
     const int kq = a.kpq ? min(max(a.kpq[q], 0), a.k) : a.k;
@@ -230,29 +211,27 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
     top.init();
     float thd = INFINITY;
     int64_t thi = INT64_MAX;
-    const float* qv = a.Q + q * a.dim;
     for (int j = 0; kq > 0 && j < np; ++j) {
       const int l = a.probes[q * a.nprobe + j];
       if (l < 0) continue;
       const int n_l = a.list_len[l];
       if (n_l == 0) continue;
       const int b = a.bits[q * a.nprobe + j];
-      build_lut(qv, a.centroids + (size_t)l * a.dim, a.codebooks, (int)a.dim, a.M, a.Mp, a.dsub, b, s);
-      const unsigned qoff = (unsigned)a.lay.q;   // bytes; a multiple of 256 elements of either width
-      if (b == 0) {
-        scan_list<NCHUNK, R>(a, l, n_l, kq, [&](const uint4 (&w)[NCHUNK]) { return adc_f32<NCHUNK>(smem_raw, w); },
-                             top, thd, thi);
-      } else {
-        const PairScal sc = *s.sc;
-        if (b <= 8) {
-          scan_list<NCHUNK, R>(a, l, n_l, kq,
-                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK, uint8_t>(smem_raw, qoff, w), sc); },
-                               top, thd, thi);
-        } else {
-          scan_list<NCHUNK, R>(a, l, n_l, kq,
-                               [&](const uint4 (&w)[NCHUNK]) { return dequant(adc_int<NCHUNK, uint16_t>(smem_raw, qoff / 2, w), sc); },
-                               top, thd, thi);
-        }
+      const float d2 = a.probe_d2[q * a.nprobe + j];
+      build_lut(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
+      const PairScal sc = *s.sc;
+      const unsigned qoff = (unsigned)a.lay.q;
+      const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
+      const uint8_t* base = a.codes + (size_t)a.tile_off[l] * NCHUNK * kTileChunkBytes;
+      const int64_t vbase = a.vec_off[l];
+      for (int t = warp; t < ntile; t += kWarps) {
+        uint4 w[NCHUNK];
+        load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
+        const float d = pair_distance<NCHUNK>(b, d2, qoff, sc, w);
+        const int v = t * kTileVecs + lane;
+        const bool pre = v < n_l && d <= thd;
+        const int64_t id = pre ? __ldg(a.ids + vbase + v) : INT64_MAX;
+        top.offer(pre, d, id, kq, thd, thi);
       }
       __syncthreads();  // the next pair overwrites the LUT
     }
@@ -285,18 +264,36 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
   }
 }
 
+// FP32-rule coarse distance of one (query, list) pair, computed by one thread
+// (same operation order as the CL kernel).
+__device__ float pair_d2(const float* qv, const float* cv, int dim) {
+  float acc = 0.f;
+  for (int d = 0; d < dim; ++d) {
+    const float e = sub_rn(qv[d], cv[d]);
+    acc = add_rn(acc, mul_rn(e, e));
+  }
+  return acc;
+}
+
+__device__ float block_pair_d2(const SearchArgs& a, int q, int l) {
+  __shared__ float d2s;
+  if (threadIdx.x == 0) d2s = pair_d2(a.Q + (size_t)q * a.dim, a.centroids + (size_t)l * a.dim, (int)a.dim);
+  __syncthreads();
+  return d2s;
+}
+
 // One block per pair: LUT build + quantisation, written out (anns_compute_luts).
 __global__ void __launch_bounds__(kThreads) luts_kernel(const SearchArgs a, const int32_t* pq,
                                                         const int32_t* pl, const uint8_t* pb,
                                                         int64_t npairs, float* T_out,
                                                         uint16_t* t_out, double* scale_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem s(smem_raw, a.lay);
+  Smem s(a.lay);
+  const int64_t tstride = (int64_t)a.Mp * kKsub;
   for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
     const int q = pq[p], l = pl[p], b = pb[p] <= 16 ? pb[p] : 0;
     if (q < 0 || q >= a.nq || l < 0 || l >= a.nlist) continue;  // out-of-range pair: skipped
-    build_lut(a.Q + (size_t)q * a.dim, a.centroids + (size_t)l * a.dim, a.codebooks, (int)a.dim,
-              a.M, a.Mp, a.dsub, b, s);
+    const float d2 = block_pair_d2(a, q, l);
+    build_lut(a.ltab + (size_t)l * tstride, a.qt + (size_t)q * tstride, a.M, a.Mp, b, d2, s);
     const int nent = a.M * kKsub;
     for (int e = threadIdx.x; e < nent; e += blockDim.x) {
       if (T_out) T_out[p * nent + e] = s.T[e];
@@ -304,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) luts_kernel(const SearchArgs a, cons
     }
     if (scale_out && threadIdx.x == 0) {
       scale_out[p * 4 + 0] = b ? s.sc->delta64 : 0.0;
-      scale_out[p * 4 + 1] = b ? s.sc->B64 : 0.0;
+      scale_out[p * 4 + 1] = b ? s.sc->B64 : (double)d2;
       scale_out[p * 4 + 2] = b ? (double)s.sc->range : 0.0;
       scale_out[p * 4 + 3] = b ? (double)s.sc->s32 : 0.0;
     }
@@ -318,30 +315,25 @@ __global__ void __launch_bounds__(kThreads) scan_pairs_kernel(const SearchArgs a
                                                               const int32_t* pl, const uint8_t* pb,
                                                               int64_t npairs, const int64_t* off,
                                                               float* dist_out, int32_t* S_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem s(smem_raw, a.lay);
+  Smem s(a.lay);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tstride = (int64_t)a.Mp * kKsub;
   for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
     const int q = pq[p], l = pl[p], b = pb[p] <= 16 ? pb[p] : 0;
     if (q < 0 || q >= a.nq || l < 0 || l >= a.nlist) continue;  // out-of-range pair: skipped
-    build_lut(a.Q + (size_t)q * a.dim, a.centroids + (size_t)l * a.dim, a.codebooks, (int)a.dim,
-              a.M, a.Mp, a.dsub, b, s);
+    const float d2 = block_pair_d2(a, q, l);
+    build_lut(a.ltab + (size_t)l * tstride, a.qt + (size_t)q * tstride, a.M, a.Mp, b, d2, s);
     const int n_l = a.list_len[l];
     const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
     const uint8_t* base = a.codes + (size_t)a.tile_off[l] * NCHUNK * kTileChunkBytes;
     const PairScal sc = *s.sc;
+    const unsigned qoff = (unsigned)a.lay.q;
     for (int t = warp; t < ntile; t += kWarps) {
       uint4 w[NCHUNK];
       load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
       const int v = t * kTileVecs + lane;
-      float d;
       int S = 0;
-      const unsigned qoff = (unsigned)a.lay.q;
-      if (b == 0) d = adc_f32<NCHUNK>(smem_raw, w);
-      else {
-        S = b <= 8 ? adc_int<NCHUNK, uint8_t>(smem_raw, qoff, w) : adc_int<NCHUNK, uint16_t>(smem_raw, qoff / 2, w);
-        d = dequant(S, sc);
-      }
+      const float d = pair_distance<NCHUNK>(b, d2, qoff, sc, w, &S);
       if (v < n_l) {
         dist_out[off[p] + v] = d;
         if (S_out) S_out[off[p] + v] = S;
@@ -351,13 +343,13 @@ __global__ void __launch_bounds__(kThreads) scan_pairs_kernel(const SearchArgs a
   }
 }
 
-SearchArgs make_args(const Index& ix, const float* Q, int R) {
+SearchArgs make_args(const Index& ix, const float* Q, const float* qt, int R) {
   SearchArgs a{};
-  a.Q = Q; a.dim = ix.dim; a.nlist = ix.nlist;
-  a.centroids = ix.centroids; a.codebooks = ix.codebooks; a.codes = ix.codes; a.ids = ix.ids;
+  a.Q = Q; a.qt = qt; a.dim = ix.dim; a.nlist = ix.nlist;
+  a.centroids = ix.centroids; a.ltab = ix.ltab; a.codes = ix.codes; a.ids = ix.ids;
   a.list_len = ix.list_len; a.vec_off = ix.vec_off; a.tile_off = ix.tile_off;
-  a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.dsub = (int)ix.dsub;
-  a.lay = SmemLayout(ix.dim, ix.Mp, R);
+  a.M = (int)ix.M; a.Mp = (int)ix.Mp;
+  a.lay = SmemLayout(ix.Mp, R);
   return a;
 }
 
@@ -399,14 +391,14 @@ cudaError_t run_scan_pairs(const SearchArgs& a, const int32_t* pq, const int32_t
 
 }  // namespace
 
-cudaError_t launch_search(const Index& ix, const float* Q, int64_t nq, int nprobe,
+cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
-                          const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
-                          float* dists_out, cudaStream_t s) {
+                          const int32_t* probes, const float* probe_d2, const uint8_t* bits,
+                          int64_t* ids_out, float* dists_out, cudaStream_t s) {
   const int R = k <= 32 ? 1 : 4;
-  SearchArgs a = make_args(ix, Q, R);
+  SearchArgs a = make_args(ix, nullptr, qt, R);
   a.nq = nq; a.nprobe = nprobe; a.k = k; a.npq = nprobe_per_q; a.kpq = k_per_q;
-  a.probes = probes; a.bits = bits; a.ids_out = ids_out; a.dists_out = dists_out;
+  a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.ids_out = ids_out; a.dists_out = dists_out;
   switch (ix.nchunk) {
     case 1: return run_search_r<1>(a, R, s);
     case 2: return run_search_r<2>(a, R, s);
@@ -419,11 +411,11 @@ cudaError_t launch_search(const Index& ix, const float* Q, int64_t nq, int nprob
   }
 }
 
-cudaError_t launch_compute_luts(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
-                                const int32_t* pl, const uint8_t* pb, int64_t npairs,
-                                float* T_out, uint16_t* t_out, double* scale_out,
+cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt, int64_t nq,
+                                const int32_t* pq, const int32_t* pl, const uint8_t* pb,
+                                int64_t npairs, float* T_out, uint16_t* t_out, double* scale_out,
                                 cudaStream_t s) {
-  SearchArgs a = make_args(ix, Q, 1);
+  SearchArgs a = make_args(ix, Q, qt, 1);
   a.nq = nq;
   cudaError_t e = prep(luts_kernel, a.lay.total);
   if (e != cudaSuccess) return e;
@@ -432,11 +424,11 @@ cudaError_t launch_compute_luts(const Index& ix, const float* Q, int64_t nq, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_pairs(const Index& ix, const float* Q, int64_t nq, const int32_t* pq,
-                              const int32_t* pl, const uint8_t* pb, int64_t npairs,
-                              const int64_t* off, float* dist_out, int32_t* S_out,
+cudaError_t launch_scan_pairs(const Index& ix, const float* Q, const float* qt, int64_t nq,
+                              const int32_t* pq, const int32_t* pl, const uint8_t* pb,
+                              int64_t npairs, const int64_t* off, float* dist_out, int32_t* S_out,
                               cudaStream_t s) {
-  SearchArgs a = make_args(ix, Q, 1);
+  SearchArgs a = make_args(ix, Q, qt, 1);
   a.nq = nq;
   switch (ix.nchunk) {
     case 1: return run_scan_pairs<1>(a, pq, pl, pb, npairs, off, dist_out, S_out, s);

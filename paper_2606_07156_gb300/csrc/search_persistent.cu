@@ -1,19 +1,20 @@
-// Persistent search kernel for indexes whose codebook fits in shared memory
-// next to two LUT slots (M * 256 * dsub * 4 bytes + 2 * Mp KB <= 227 KB;
-// dim <= 128 for the usual shapes).
+// Persistent search kernel for indexes with Mp <= 64 and k <= 32.
 //
-// Same arithmetic as search.cu (RC, LC, quantiser, ADC, top-k of Section 2.1,
-// FP32 rule with explicit rounding), organised for the SM:
-//  - one 1024-thread block per SM walks the queries (atomic counter); the
-//    codebook is copied into shared memory once per block, so building a LUT
-//    costs no L2 traffic;
-//  - warp w builds the rows m = w, w+32, ... of a LUT, lane i owning entries
-//    c = i + 32e (e < 8); the values stay in registers between the build and
-//    the table write, which lets the row minima/maxima cross the block first;
+// Same arithmetic as search.cu (decomposed FP32 LUT T' = P_l - 2 Q_q, the
+// quantiser, ADC and top-k of Section 2.1, explicit rounding), organised for
+// the SM:
+//  - one 1024-thread block per SM walks the queries (atomic counter) and copies
+//    each query's table 2 Q_q into shared memory once;
+//  - warp w builds LUT rows m = w, w+32, ...; lane i owns entries
+//    c = 8i .. 8i+7 of those rows, so list-table loads, query-table loads and
+//    table stores are 16-byte vectors; values stay in registers between the
+//    build and the table write, which lets the row minima/maxima cross the
+//    block first;
 //  - the probed lists of a query flow through a pipeline with one block
-//    barrier per stage: in stage s the block scans pair s, writes the table
-//    of pair s+1, builds pair s+2 and loads the inputs of pair s+3, and every
-//    warp prefetches its first code tile of the next stage's pair.
+//    barrier per stage: in stage s the block issues the list-table loads of
+//    pair s+2, scans pair s, writes the table of pair s+1, builds pair s+2 and
+//    loads the inputs of pair s+3; every warp prefetches its first code tile
+//    of the next stage's pair.
 #include <algorithm>
 
 #include "common.cuh"
@@ -33,11 +34,12 @@ struct PairScalP {
 struct PairInfo {
   int l, n_l, b, ntile;
   int64_t tile0, vbase;
+  float d2;
 };
 
 struct PArgs {
-  const float* Q; int64_t nq, dim;
-  const float* centroids; const float* codebooks;
+  const float* qt; int64_t nq;
+  const float* ltab; const float* probe_d2;
   const uint8_t* codes; const int64_t* ids;
   const int32_t* list_len; const int64_t* vec_off; const int64_t* tile_off;
   int M, dsub, nprobe, k;
@@ -45,7 +47,7 @@ struct PArgs {
   const int32_t* probes; const uint8_t* bits;
   int64_t* ids_out; float* dists_out;
   int* counter;
-  size_t off_cb, off_r, off_rowmin, off_rowmax, off_scal, off_info, off_md, off_mi, off_q, total;
+  size_t off_qt, off_rowmin, off_rowmax, off_scal, off_info, off_md, off_mi, off_q, total;
 };
 
 template <int NCHUNK>
@@ -55,8 +57,7 @@ template <int NCHUNK>
 size_t layout(PArgs& a) {
   auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
   size_t o = 2 * table_bytes<NCHUNK>();   // two table slots at offset 0
-  a.off_cb = o; o += al((size_t)a.M * kKsub * a.dsub * 4);
-  a.off_r = o; o += al(2 * a.dim * 4);
+  a.off_qt = o; o += al((size_t)NCHUNK * 16 * kKsub * 4);
   a.off_rowmin = o; o += al(2 * NCHUNK * 16 * 4);
   a.off_rowmax = o; o += al(2 * NCHUNK * 16 * 4);
   a.off_scal = o; o += al(2 * sizeof(PairScalP));
@@ -72,32 +73,16 @@ __device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-template <int DSUB>
-__device__ __forceinline__ void load_y(const float* p, float (&y)[DSUB]) {
-  if constexpr (DSUB % 4 == 0) {
-#pragma unroll
-    for (int j = 0; j < DSUB; j += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(p + j);
-      y[j] = v.x; y[j + 1] = v.y; y[j + 2] = v.z; y[j + 3] = v.w;
-    }
-  } else if constexpr (DSUB == 2) {
-    const float2 v = *reinterpret_cast<const float2*>(p);
-    y[0] = v.x; y[1] = v.y;
-  } else {
-#pragma unroll
-    for (int j = 0; j < DSUB; ++j) y[j] = p[j];
-  }
-}
-
 // Pair p (probe rank p of the current query) moves through the stages
 //   load inputs (stage p-3) -> build (p-2) -> write table (p-1) -> scan (p).
-// Slots: tables, residuals, row statistics and scales p%2, list facts p%4;
-// each is rewritten only after the barrier that ends its last use.
-template <int NCHUNK, int NROW, int DSUB>
+// Slots: tables, row statistics and scales p%2, list facts p%4; each is
+// rewritten only after the barrier that ends its last use.
+template <int NCHUNK, int NROW>
 struct Pipe {
   static constexpr int Mp = NCHUNK * 16;
   const PArgs& a;
   float tq[NROW][8];        // LUT values between build and table write
+  float pp[NROW][8];        // list-table values loaded for the next build
   uint4 pf[NCHUNK];         // prefetched code tile
   int warp, lane;
 
@@ -108,68 +93,73 @@ struct Pipe {
 
   __device__ static unsigned char* sm() { return anns_dyn_smem; }
   __device__ unsigned table_off(int p) const { return (unsigned)((p & 1) * table_bytes<NCHUNK>()); }
-  __device__ const float* cb() const { return (const float*)(sm() + a.off_cb); }
-  __device__ float* resid(int p) const { return (float*)(sm() + a.off_r) + (p & 1) * a.dim; }
+  __device__ float* qtab() const { return (float*)(sm() + a.off_qt); }
   __device__ float* rowmin(int p) const { return (float*)(sm() + a.off_rowmin) + (p & 1) * Mp; }
   __device__ float* rowmax(int p) const { return (float*)(sm() + a.off_rowmax) + (p & 1) * Mp; }
   __device__ PairScalP* scal(int p) const { return (PairScalP*)(sm() + a.off_scal) + (p & 1); }
   __device__ PairInfo* info(int p) const { return (PairInfo*)(sm() + a.off_info) + (p % kInfoSlots); }
 
-  struct Staged { float qd, cd; int l, n_l, b; int64_t tile0, vbase; };
-  // Issued at the start of a stage; stored at its end (store_inputs).
+  // Copies the query's table 2 Q_q into shared memory (callers barrier after).
+  __device__ void load_query_table(int64_t q) const {
+    const float4* src = (const float4*)(a.qt + q * (int64_t)Mp * kKsub);
+    float4* dst = (float4*)qtab();
+    for (int i = threadIdx.x; i < Mp * kKsub / 4; i += kThreadsP) dst[i] = __ldg(src + i);
+  }
+
+  // List facts of pair p (thread 0), stored at the end of the stage.
+  struct Staged { int l, n_l, b; int64_t tile0, vbase; float d2; };
   __device__ void load_inputs(int64_t q, int p, Staged& st) const {
-    st.l = a.probes[q * a.nprobe + p];
-    const int d = threadIdx.x;
-    st.qd = 0.f; st.cd = 0.f;
-    if (st.l >= 0 && d < a.dim) {
-      st.qd = a.Q[q * a.dim + d];
-      st.cd = a.centroids[(size_t)st.l * a.dim + d];
-    }
-    st.n_l = 0; st.b = 0; st.tile0 = 0; st.vbase = 0;
-    if (threadIdx.x == 0 && st.l >= 0) {
+    if (threadIdx.x != 0) return;
+    const int64_t row = q * a.nprobe + p;
+    st.l = a.probes[row];
+    st.n_l = 0; st.b = 0; st.tile0 = 0; st.vbase = 0; st.d2 = 0.f;
+    if (st.l >= 0) {
       st.n_l = a.list_len[st.l];
-      st.b = a.bits[q * a.nprobe + p];
+      st.b = a.bits[row];
+      st.d2 = a.probe_d2[row];
       st.tile0 = a.tile_off[st.l];
       st.vbase = a.vec_off[st.l];
     }
   }
   __device__ void store_inputs(int p, const Staged& st) const {
-    if (threadIdx.x < a.dim && st.l >= 0) resid(p)[threadIdx.x] = sub_rn(st.qd, st.cd);
-    if (threadIdx.x == 0) {
-      PairInfo pi;
-      pi.l = st.l; pi.n_l = st.n_l; pi.b = st.b;
-      pi.ntile = (st.n_l + kTileVecs - 1) / kTileVecs;
-      pi.tile0 = st.tile0; pi.vbase = st.vbase;
-      *info(p) = pi;
-    }
+    if (threadIdx.x != 0) return;
+    PairInfo pi;
+    pi.l = st.l; pi.n_l = st.n_l; pi.b = st.b; pi.d2 = st.d2;
+    pi.ntile = (st.n_l + kTileVecs - 1) / kTileVecs;
+    pi.tile0 = st.tile0; pi.vbase = st.vbase;
+    *info(p) = pi;
   }
 
-  // T for this warp's rows of pair p by the FP32 rule; quantised pairs also
-  // publish each row's minimum and range.
-  __device__ void build(int p) {
+  // Issues this warp's list-table loads for pair p (used by build(p)).
+  __device__ void load_list_rows(int p) {
     const PairInfo pi = *info(p);
     if (pi.n_l == 0) return;
-    const float* r = resid(p);
-    const float* y = cb();
+    const float* P = a.ltab + (size_t)pi.l * Mp * kKsub;
 #pragma unroll
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
       if (m >= a.M) continue;
-      float rv[DSUB];
+      const float4* src = (const float4*)(P + m * kKsub + lane * 8);
+      const float4 u = __ldg(src), v = __ldg(src + 1);
+      pp[i][0] = u.x; pp[i][1] = u.y; pp[i][2] = u.z; pp[i][3] = u.w;
+      pp[i][4] = v.x; pp[i][5] = v.y; pp[i][6] = v.z; pp[i][7] = v.w;
+    }
+  }
+
+  // T' = fl32(P_l - 2 Q_q) for this warp's rows of pair p; quantised pairs
+  // also publish each row's minimum and range.
+  __device__ void build(int p) {
+    const PairInfo pi = *info(p);
+    if (pi.n_l == 0) return;
 #pragma unroll
-      for (int j = 0; j < DSUB; ++j) rv[j] = r[m * DSUB + j];
+    for (int i = 0; i < NROW; ++i) {
+      const int m = warp + kNW * i;
+      if (m >= a.M) continue;
+      const float4* qs = (const float4*)(qtab() + m * kKsub + lane * 8);
+      const float4 u = qs[0], v = qs[1];
+      const float qv[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float yv[DSUB];
-        load_y<DSUB>(y + ((size_t)(m * kKsub + lane + 32 * e)) * DSUB, yv);
-        float acc = 0.f;
-#pragma unroll
-        for (int j = 0; j < DSUB; ++j) {
-          const float x = sub_rn(rv[j], yv[j]);
-          acc = add_rn(acc, mul_rn(x, x));
-        }
-        tq[i][e] = acc;
-      }
+      for (int e = 0; e < 8; ++e) tq[i][e] = sub_rn(pp[i][e], qv[e]);
       if (pi.b != 0) {
         float mn = tq[i][0];
 #pragma unroll
@@ -186,20 +176,21 @@ struct Pipe {
 
   // Writes the table of pair p: FP32 values for plain pairs, else levels with
   // the shared step from the largest row range (warp 0 also forms Delta32 and
-  // B32, B summed in FP64 in the fixed 32-lane tree order). Rows M..Mp-1 are
-  // zero rows, so the scan needs no bound on m.
+  // B32 = fl32(D2 + B), B summed in FP64 in the fixed 32-lane tree order).
+  // Rows M..Mp-1 are zero rows, so the scan needs no bound on m.
   __device__ void write_table(int p) {
     const PairInfo pi = *info(p);
     if (pi.n_l == 0) return;
     unsigned char* tab = sm() + table_off(p);
     if (pi.b == 0) {
-      float* T = (float*)tab;
 #pragma unroll
       for (int i = 0; i < NROW; ++i) {
         const int m = warp + kNW * i;
         if (m >= Mp) continue;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) T[m * kKsub + lane + 32 * e] = m < a.M ? tq[i][e] : 0.f;
+        float4* T = (float4*)((float*)tab + m * kKsub + lane * 8);
+        const bool live = m < a.M;
+        T[0] = live ? make_float4(tq[i][0], tq[i][1], tq[i][2], tq[i][3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        T[1] = live ? make_float4(tq[i][4], tq[i][5], tq[i][6], tq[i][7]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       return;
     }
@@ -216,7 +207,7 @@ struct Pipe {
       if (lane == 0) {
         PairScalP sc;
         sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
-        sc.B32 = __double2float_rn(B);
+        sc.B32 = __double2float_rn(__dadd_rn((double)pi.d2, B));
         *scal(p) = sc;
       }
     }
@@ -224,22 +215,25 @@ struct Pipe {
     for (int i = 0; i < NROW; ++i) {
       const int m = warp + kNW * i;
       if (m >= Mp) continue;
-      int t[8];
+      unsigned t[8];
       if (m < a.M) {
         const float mn = rowmin(p)[m];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) t[e] = min(__float2int_rn(mul_rn(sub_rn(tq[i][e], mn), s32)), L);
+        for (int e = 0; e < 8; ++e) t[e] = (unsigned)min(__float2int_rn(mul_rn(sub_rn(tq[i][e], mn), s32)), L);
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) t[e] = 0;
+        for (int e = 0; e < 8; ++e) t[e] = 0u;
       }
       if (pi.b <= 8) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) tab[m * kKsub + lane + 32 * e] = (uint8_t)t[e];
+        uint2 v;
+        v.x = t[0] | (t[1] << 8) | (t[2] << 16) | (t[3] << 24);
+        v.y = t[4] | (t[5] << 8) | (t[6] << 16) | (t[7] << 24);
+        *(uint2*)(tab + m * kKsub + lane * 8) = v;
       } else {
-        uint16_t* t16 = (uint16_t*)tab;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) t16[m * kKsub + lane + 32 * e] = (uint16_t)t[e];
+        uint4 v;
+        v.x = t[0] | (t[1] << 16); v.y = t[2] | (t[3] << 16);
+        v.z = t[4] | (t[5] << 16); v.w = t[6] | (t[7] << 16);
+        *(uint4*)((uint16_t*)tab + m * kKsub + lane * 8) = v;
       }
     }
   }
@@ -307,7 +301,7 @@ struct Pipe {
       if (t + kNW < pi.ntile) load_tile(pi, t + kNW, pf);
       else if (has_next) prefetch_first(p + 1);
       float d;
-      if (pi.b == 0) d = adc_f32(tb / 4, w);
+      if (pi.b == 0) d = add_rn(pi.d2, adc_f32(tb / 4, w));
       else if (pi.b <= 8) d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint8_t>(tb, w))), sc.B32);
       else d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint16_t>(tb / 2, w))), sc.B32);
       const int v = t * kTileVecs + lane;
@@ -318,21 +312,15 @@ struct Pipe {
   }
 };
 
-template <int NCHUNK, int NROW, int DSUB>
+template <int NCHUNK, int NROW>
 __global__ void __launch_bounds__(kThreadsP, 1) search_persistent_kernel(const PArgs a) {
-  using PipeT = Pipe<NCHUNK, NROW, DSUB>;
+  using PipeT = Pipe<NCHUNK, NROW>;
   PipeT P(a);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* sm = anns_dyn_smem;
   float* md = (float*)(sm + a.off_md);
   int64_t* mi = (int64_t*)(sm + a.off_mi);
   int64_t* next_q = (int64_t*)(sm + a.off_q);
-  {  // the codebook, once per block
-    const int n4 = a.M * kKsub * a.dsub / 4;
-    float4* dst = (float4*)(sm + a.off_cb);
-    const float4* src = (const float4*)a.codebooks;
-    for (int i = threadIdx.x; i < n4; i += kThreadsP) dst[i] = __ldg(src + i);
-  }
   for (;;) {
     if (threadIdx.x == 0) *next_q = atomicAdd(a.counter, 1);
     __syncthreads();
@@ -344,15 +332,18 @@ __global__ void __launch_bounds__(kThreadsP, 1) search_persistent_kernel(const P
     top.init();
     float thd = INFINITY;
     int64_t thi = INT64_MAX;
-    if (kq > 0) {
+    if (kq > 0 && np > 0) {
+      P.load_query_table(q);
       for (int s = -3; s < np; ++s) {
         typename PipeT::Staged st;
         const bool stage_in = s + 3 < np;
         if (stage_in) P.load_inputs(q, s + 3, st);
+        const bool do_build = s + 2 >= 0 && s + 2 < np;
+        if (do_build) P.load_list_rows(s + 2);
         if (s >= 0) P.scan(s, s + 1 < np, kq, top, thd, thi);
         else if (s == -1) P.prefetch_first(0);
         if (s + 1 >= 0 && s + 1 < np) P.write_table(s + 1);
-        if (s + 2 >= 0 && s + 2 < np) P.build(s + 2);
+        if (do_build) P.build(s + 2);
         if (stage_in) P.store_inputs(s + 3, st);
         __syncthreads();
       }
@@ -377,10 +368,10 @@ __global__ void __launch_bounds__(kThreadsP, 1) search_persistent_kernel(const P
   }
 }
 
-template <int NCHUNK, int NROW, int DSUB>
+template <int NCHUNK, int NROW>
 cudaError_t run(PArgs& a, cudaStream_t s) {
   const size_t smem = layout<NCHUNK>(a);
-  auto kern = search_persistent_kernel<NCHUNK, NROW, DSUB>;
+  auto kern = search_persistent_kernel<NCHUNK, NROW>;
   int dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -395,61 +386,43 @@ cudaError_t run(PArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// NROW = ceil(M / 32) codebook rows per warp; the (NCHUNK, NROW, DSUB) shapes built.
-template <int NCHUNK>
-cudaError_t run_shape(PArgs& a, cudaStream_t s) {
-  const int nrow = (a.M + kNW - 1) / kNW;
-  switch (a.dsub) {
-    case 1: return nrow == 1 ? run<NCHUNK, 1, 1>(a, s) : nrow == 2 ? run<NCHUNK, 2, 1>(a, s) : cudaErrorNotSupported;
-    case 2: return nrow == 1 ? run<NCHUNK, 1, 2>(a, s) : nrow == 2 ? run<NCHUNK, 2, 2>(a, s) : cudaErrorNotSupported;
-    case 4: return nrow == 1 ? run<NCHUNK, 1, 4>(a, s) : cudaErrorNotSupported;
-    case 8: return nrow == 1 ? run<NCHUNK, 1, 8>(a, s) : cudaErrorNotSupported;
-    default: return cudaErrorNotSupported;
-  }
-}
-
-size_t smem_need(const Index& ix) {
-  PArgs a{};
-  a.M = (int)ix.M; a.dsub = (int)ix.dsub; a.dim = ix.dim;
-  switch (ix.nchunk) {
-    case 1: return layout<1>(a);
-    case 2: return layout<2>(a);
-    case 3: return layout<3>(a);
-    case 4: return layout<4>(a);
-    default: return SIZE_MAX;
-  }
-}
-
 }  // namespace
 
 bool persistent_supported(const Index& ix, int k) {
-  if (k > 32 || ix.dim > kThreadsP || ix.nchunk > 4) return false;
-  const int nrow = (int)((ix.M + kNW - 1) / kNW);
-  const int d = (int)ix.dsub;
-  const bool shape = ((d == 1 || d == 2) && nrow <= 2) || ((d == 4 || d == 8) && nrow == 1);
-  if (!shape || (ix.M * kKsub * ix.dsub) % 4) return false;
+  if (k > 32 || ix.nchunk > 4) return false;
+  PArgs a{};
+  a.M = (int)ix.M;
+  size_t need = 0;
+  switch (ix.nchunk) {
+    case 1: need = layout<1>(a); break;
+    case 2: need = layout<2>(a); break;
+    case 3: need = layout<3>(a); break;
+    default: need = layout<4>(a); break;
+  }
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return smem_need(ix) <= (size_t)optin;
+  return need <= (size_t)optin;
 }
 
-cudaError_t launch_search_persistent(const Index& ix, const float* Q, int64_t nq, int nprobe,
+cudaError_t launch_search_persistent(const Index& ix, const float* qt, int64_t nq, int nprobe,
                                      const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
-                                     const int32_t* probes, const uint8_t* bits, int64_t* ids_out,
-                                     float* dists_out, int* counter, cudaStream_t s) {
+                                     const int32_t* probes, const float* probe_d2,
+                                     const uint8_t* bits, int64_t* ids_out, float* dists_out,
+                                     int* counter, cudaStream_t s) {
   PArgs a{};
-  a.Q = Q; a.nq = nq; a.dim = ix.dim;
-  a.centroids = ix.centroids; a.codebooks = ix.codebooks; a.codes = ix.codes; a.ids = ix.ids;
+  a.qt = qt; a.nq = nq; a.ltab = ix.ltab; a.probe_d2 = probe_d2;
+  a.codes = ix.codes; a.ids = ix.ids;
   a.list_len = ix.list_len; a.vec_off = ix.vec_off; a.tile_off = ix.tile_off;
   a.M = (int)ix.M; a.dsub = (int)ix.dsub; a.nprobe = nprobe; a.k = k;
   a.npq = nprobe_per_q; a.kpq = k_per_q; a.probes = probes; a.bits = bits;
   a.ids_out = ids_out; a.dists_out = dists_out; a.counter = counter;
+  const bool two = ix.M > kNW;   // rows per warp
   switch (ix.nchunk) {
-    case 1: return run_shape<1>(a, s);
-    case 2: return run_shape<2>(a, s);
-    case 3: return run_shape<3>(a, s);
-    case 4: return run_shape<4>(a, s);
+    case 1: return run<1, 1>(a, s);
+    case 2: return run<2, 1>(a, s);
+    case 3: return two ? run<3, 2>(a, s) : run<3, 1>(a, s);
+    case 4: return two ? run<4, 2>(a, s) : run<4, 1>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
