@@ -112,16 +112,6 @@ __device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) { return add2_rn(a, make_float2(-b.x, -b.y)); }
 
-// Element `base + code_bb(x) + m*256` of a LUT of LT in shared memory, where
-// code_bb(x) is byte bb of the packed code word x and `base` (in elements)
-// has a zero low byte: one byte-permute forms the index, m*256 stays an
-// immediate offset.
-template <typename LT, int BB>
-__device__ __forceinline__ LT lut_at(const unsigned char* smem, unsigned base, unsigned x, int m) {
-  const unsigned idx = __byte_perm(x, base, 0x7650u + BB);
-  return reinterpret_cast<const LT*>(smem)[idx + (unsigned)m * 256u];
-}
-
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));

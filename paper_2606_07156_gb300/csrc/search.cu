@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "scan.cuh"
 
 namespace anns {
 namespace {
@@ -30,30 +31,41 @@ struct PairScal {
   int L;
 };
 
+// Offsets from a 256-byte aligned base inside the block's dynamic shared
+// memory (256 bytes of slack are allocated for the alignment).
 struct SmemLayout {
-  size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, md = 0, mi = 0, total = 0;
+  size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, d2 = 0, md = 0, mi = 0, total = 0;
   static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   SmemLayout() = default;
   SmemLayout(int64_t Mp, int R) {
-    size_t o = 0;   // the tables first: their element offsets have a zero low byte
+    size_t o = 0;   // the tables first, at multiples of 256 bytes
     T = o; o += al(Mp * kKsub * 4);
     q = o; o += al(Mp * kKsub * 2);
     bias = o; o += al(Mp * 4);
     rowmax = o; o += al(Mp * 4);
     scal = o; o += al(sizeof(PairScal));
+    d2 = o; o += 16;
     md = o; o += al((size_t)kWarps * R * 32 * 4);
     mi = o; o += al((size_t)kWarps * R * 32 * 8);
-    total = o;
+    total = o + 256;
   }
 };
 
+__device__ __forceinline__ unsigned char* aligned_smem() {
+  const uint32_t a = smem_addr(anns_dyn_smem);
+  return anns_dyn_smem + ((256u - (a & 255u)) & 255u);
+}
+
 struct Smem {
-  float* T; void* q; float* bias; float* rowmax; PairScal* sc; float* md; int64_t* mi;
-  __device__ explicit Smem(const SmemLayout& L)
-      : T((float*)(anns_dyn_smem + L.T)), q(anns_dyn_smem + L.q),
-        bias((float*)(anns_dyn_smem + L.bias)), rowmax((float*)(anns_dyn_smem + L.rowmax)),
-        sc((PairScal*)(anns_dyn_smem + L.scal)), md((float*)(anns_dyn_smem + L.md)),
-        mi((int64_t*)(anns_dyn_smem + L.mi)) {}
+  float* T; void* q; float* bias; float* rowmax; PairScal* sc; float* d2; float* md; int64_t* mi;
+  uint32_t T_addr, q_addr;  // shared-memory byte addresses of the two tables
+  __device__ explicit Smem(const SmemLayout& L) {
+    unsigned char* b = aligned_smem();
+    T = (float*)(b + L.T); q = b + L.q; bias = (float*)(b + L.bias); rowmax = (float*)(b + L.rowmax);
+    sc = (PairScal*)(b + L.scal); d2 = (float*)(b + L.d2); md = (float*)(b + L.md); mi = (int64_t*)(b + L.mi);
+    T_addr = smem_addr(T);
+    q_addr = smem_addr(q);
+  }
 };
 
 // Steps 1-2 for one pair: all threads of the block take part. P and qt2 are
@@ -133,45 +145,6 @@ __device__ __forceinline__ void load_tile(const uint8_t* __restrict__ tile, int 
     w[c] = __ldg(reinterpret_cast<const uint4*>(tile + c * kTileChunkBytes + lane * kChunkBytes));
 }
 
-__device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
-  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-}
-
-// FP32 ADC over all Mp sub-tables: acc = fl32(acc + T'[m][code_m]), m
-// ascending (padding rows are zero). The FP32 table sits at shared offset 0.
-template <int NCHUNK>
-__device__ __forceinline__ float adc_f32(const uint4 (&w)[NCHUNK]) {
-  float acc = 0.f;
-#pragma unroll
-  for (int c = 0; c < NCHUNK; ++c)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const unsigned x = word_of(w[c], i);
-      const int m = c * 16 + i * 4;
-      acc = add_rn(acc, lut_at<float, 0>(anns_dyn_smem, 0u, x, m));
-      acc = add_rn(acc, lut_at<float, 1>(anns_dyn_smem, 0u, x, m + 1));
-      acc = add_rn(acc, lut_at<float, 2>(anns_dyn_smem, 0u, x, m + 2));
-      acc = add_rn(acc, lut_at<float, 3>(anns_dyn_smem, 0u, x, m + 3));
-    }
-  return acc;
-}
-
-// Integer ADC: S = sum_m t[m][code_m], exact; `base` is the table's element offset.
-template <int NCHUNK, typename LT>
-__device__ __forceinline__ int adc_int(unsigned base, const uint4 (&w)[NCHUNK]) {
-  int acc0 = 0, acc1 = 0;
-#pragma unroll
-  for (int c = 0; c < NCHUNK; ++c)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const unsigned x = word_of(w[c], i);
-      const int m = c * 16 + i * 4;
-      acc0 += (int)lut_at<LT, 0>(anns_dyn_smem, base, x, m) + (int)lut_at<LT, 1>(anns_dyn_smem, base, x, m + 1);
-      acc1 += (int)lut_at<LT, 2>(anns_dyn_smem, base, x, m + 2) + (int)lut_at<LT, 3>(anns_dyn_smem, base, x, m + 3);
-    }
-  return acc0 + acc1;
-}
-
 __device__ __forceinline__ float dequant(int S, const PairScal& sc) {
   return add_rn(mul_rn(sc.delta32, __int2float_rn(S)), sc.B32);
 }
@@ -179,10 +152,10 @@ __device__ __forceinline__ float dequant(int S, const PairScal& sc) {
 // Distance of the vector whose code tile words are w, for a pair whose table
 // was built with `b` bits (0 = FP32) and coarse distance d2.
 template <int NCHUNK>
-__device__ __forceinline__ float pair_distance(int b, float d2, unsigned qoff, const PairScal& sc,
+__device__ __forceinline__ float pair_distance(int b, float d2, const Smem& s, const PairScal& sc,
                                                const uint4 (&w)[NCHUNK], int* S_out = nullptr) {
-  if (b == 0) return add_rn(d2, adc_f32<NCHUNK>(w));
-  const int S = b <= 8 ? adc_int<NCHUNK, uint8_t>(qoff, w) : adc_int<NCHUNK, uint16_t>(qoff / 2, w);
+  if (b == 0) return add_rn(d2, adc_f32<NCHUNK>(s.T_addr, w));
+  const int S = b <= 8 ? adc_int<uint8_t, NCHUNK>(s.q_addr, w) : adc_int<uint16_t, NCHUNK>(s.q_addr, w);
   if (S_out) *S_out = S;
   return dequant(S, sc);
 }
@@ -220,18 +193,20 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
       const float d2 = a.probe_d2[q * a.nprobe + j];
       build_lut(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
       const PairScal sc = *s.sc;
-      const unsigned qoff = (unsigned)a.lay.q;
       const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
-      const uint8_t* base = a.codes + (size_t)a.tile_off[l] * NCHUNK * kTileChunkBytes;
-      const int64_t vbase = a.vec_off[l];
-      for (int t = warp; t < ntile; t += kWarps) {
+      const uint8_t* tp = a.codes + ((size_t)a.tile_off[l] * NCHUNK + 0) * kTileChunkBytes +
+                          (size_t)warp * NCHUNK * kTileChunkBytes;
+      const int64_t* idp = a.ids + a.vec_off[l];
+      for (int t = warp; t < ntile; t += kWarps, tp += (size_t)kWarps * NCHUNK * kTileChunkBytes) {
         uint4 w[NCHUNK];
-        load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
-        const float d = pair_distance<NCHUNK>(b, d2, qoff, sc, w);
+        load_tile<NCHUNK>(tp, lane, w);
+        const float d = pair_distance<NCHUNK>(b, d2, s, sc, w);
         const int v = t * kTileVecs + lane;
         const bool pre = v < n_l && d <= thd;
-        const int64_t id = pre ? __ldg(a.ids + vbase + v) : INT64_MAX;
-        top.offer(pre, d, id, kq, thd, thi);
+        if (__any_sync(kFull, pre)) {
+          const int64_t id = pre ? __ldg(idp + v) : INT64_MAX;
+          top.offer(pre, d, id, kq, thd, thi);
+        }
       }
       __syncthreads();  // the next pair overwrites the LUT
     }
@@ -275,11 +250,10 @@ __device__ float pair_d2(const float* qv, const float* cv, int dim) {
   return acc;
 }
 
-__device__ float block_pair_d2(const SearchArgs& a, int q, int l) {
-  __shared__ float d2s;
-  if (threadIdx.x == 0) d2s = pair_d2(a.Q + (size_t)q * a.dim, a.centroids + (size_t)l * a.dim, (int)a.dim);
+__device__ float block_pair_d2(const SearchArgs& a, int q, int l, Smem& s) {
+  if (threadIdx.x == 0) *s.d2 = pair_d2(a.Q + (size_t)q * a.dim, a.centroids + (size_t)l * a.dim, (int)a.dim);
   __syncthreads();
-  return d2s;
+  return *s.d2;
 }
 
 // One block per pair: LUT build + quantisation, written out (anns_compute_luts).
@@ -292,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) luts_kernel(const SearchArgs a, cons
   for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
     const int q = pq[p], l = pl[p], b = pb[p] <= 16 ? pb[p] : 0;
     if (q < 0 || q >= a.nq || l < 0 || l >= a.nlist) continue;  // out-of-range pair: skipped
-    const float d2 = block_pair_d2(a, q, l);
+    const float d2 = block_pair_d2(a, q, l, s);
     build_lut(a.ltab + (size_t)l * tstride, a.qt + (size_t)q * tstride, a.M, a.Mp, b, d2, s);
     const int nent = a.M * kKsub;
     for (int e = threadIdx.x; e < nent; e += blockDim.x) {
@@ -321,19 +295,18 @@ __global__ void __launch_bounds__(kThreads) scan_pairs_kernel(const SearchArgs a
   for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
     const int q = pq[p], l = pl[p], b = pb[p] <= 16 ? pb[p] : 0;
     if (q < 0 || q >= a.nq || l < 0 || l >= a.nlist) continue;  // out-of-range pair: skipped
-    const float d2 = block_pair_d2(a, q, l);
+    const float d2 = block_pair_d2(a, q, l, s);
     build_lut(a.ltab + (size_t)l * tstride, a.qt + (size_t)q * tstride, a.M, a.Mp, b, d2, s);
     const int n_l = a.list_len[l];
     const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
     const uint8_t* base = a.codes + (size_t)a.tile_off[l] * NCHUNK * kTileChunkBytes;
     const PairScal sc = *s.sc;
-    const unsigned qoff = (unsigned)a.lay.q;
     for (int t = warp; t < ntile; t += kWarps) {
       uint4 w[NCHUNK];
       load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
       const int v = t * kTileVecs + lane;
       int S = 0;
-      const float d = pair_distance<NCHUNK>(b, d2, qoff, sc, w, &S);
+      const float d = pair_distance<NCHUNK>(b, d2, s, sc, w, &S);
       if (v < n_l) {
         dist_out[off[p] + v] = d;
         if (S_out) S_out[off[p] + v] = S;

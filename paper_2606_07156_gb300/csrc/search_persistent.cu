@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "scan.cuh"
 
 namespace anns {
 namespace {
@@ -65,12 +66,8 @@ size_t layout(PArgs& a) {
   a.off_md = o; o += al((size_t)kNW * 32 * 4);
   a.off_mi = o; o += al((size_t)kNW * 32 * 8);
   a.off_q = o; o += 16;
-  a.total = o;
-  return o;
-}
-
-__device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
-  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+  a.total = o + 256;   // slack for the 256-byte alignment of the base
+  return a.total;
 }
 
 // Pair p (probe rank p of the current query) moves through the stages
@@ -89,9 +86,16 @@ struct Pipe {
   __device__ explicit Pipe(const PArgs& args) : a(args) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
+    const uint32_t raw = smem_addr(anns_dyn_smem);
+    const uint32_t pad = (256u - (raw & 255u)) & 255u;
+    base = anns_dyn_smem + pad;
+    base_addr = raw + pad;
   }
 
-  __device__ static unsigned char* sm() { return anns_dyn_smem; }
+  unsigned char* base;       // 256-byte aligned start of the layout
+  uint32_t base_addr;        // its shared-memory byte address
+
+  __device__ unsigned char* sm() const { return base; }
   __device__ unsigned table_off(int p) const { return (unsigned)((p & 1) * table_bytes<NCHUNK>()); }
   __device__ float* qtab() const { return (float*)(sm() + a.off_qt); }
   __device__ float* rowmin(int p) const { return (float*)(sm() + a.off_rowmin) + (p & 1) * Mp; }
@@ -249,51 +253,19 @@ struct Pipe {
     if (warp < pi.ntile) load_tile(pi, warp, pf);
   }
 
-  // Integer ADC over all Mp sub-tables: exact sum.
-  template <typename LT>
-  __device__ __forceinline__ int adc_int(unsigned base, const uint4 (&w)[NCHUNK]) const {
-    int acc0 = 0, acc1 = 0;
-#pragma unroll
-    for (int c = 0; c < NCHUNK; ++c)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const unsigned x = word_of(w[c], i);
-        const int m = c * 16 + i * 4;
-        acc0 += (int)lut_at<LT, 0>(anns_dyn_smem, base, x, m) + (int)lut_at<LT, 1>(anns_dyn_smem, base, x, m + 1);
-        acc1 += (int)lut_at<LT, 2>(anns_dyn_smem, base, x, m + 2) + (int)lut_at<LT, 3>(anns_dyn_smem, base, x, m + 3);
-      }
-    return acc0 + acc1;
-  }
-
-  // FP32 ADC: acc = fl32(acc + T[m][code_m]) for m ascending.
-  __device__ __forceinline__ float adc_f32(unsigned base, const uint4 (&w)[NCHUNK]) const {
-    float acc = 0.f;
-#pragma unroll
-    for (int c = 0; c < NCHUNK; ++c)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const unsigned x = word_of(w[c], i);
-        const int m = c * 16 + i * 4;
-        acc = add_rn(acc, lut_at<float, 0>(anns_dyn_smem, base, x, m));
-        acc = add_rn(acc, lut_at<float, 1>(anns_dyn_smem, base, x, m + 1));
-        acc = add_rn(acc, lut_at<float, 2>(anns_dyn_smem, base, x, m + 2));
-        acc = add_rn(acc, lut_at<float, 3>(anns_dyn_smem, base, x, m + 3));
-      }
-    return acc;
-  }
-
   // Scans this warp's tiles of pair p (the first is already in pf) and
   // leaves the first tile of pair p+1 (if has_next) prefetched in pf.
   __device__ void scan(int p, bool has_next, int kq, WarpTopK<1, int64_t>& top, float& thd,
                        int64_t& thi) {
     const PairInfo pi = *info(p);
-    const unsigned tb = table_off(p);
+    const uint32_t tb = base_addr + table_off(p);
     PairScalP sc{};
     if (pi.b) sc = *scal(p);
     if (warp >= pi.ntile) {
       if (has_next) prefetch_first(p + 1);
       return;
     }
+    const int64_t* idp = a.ids + pi.vbase;
     for (int t = warp; t < pi.ntile; t += kNW) {
       uint4 w[NCHUNK];
 #pragma unroll
@@ -301,13 +273,15 @@ struct Pipe {
       if (t + kNW < pi.ntile) load_tile(pi, t + kNW, pf);
       else if (has_next) prefetch_first(p + 1);
       float d;
-      if (pi.b == 0) d = add_rn(pi.d2, adc_f32(tb / 4, w));
-      else if (pi.b <= 8) d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint8_t>(tb, w))), sc.B32);
-      else d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint16_t>(tb / 2, w))), sc.B32);
+      if (pi.b == 0) d = add_rn(pi.d2, adc_f32<NCHUNK>(tb, w));
+      else if (pi.b <= 8) d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint8_t, NCHUNK>(tb, w))), sc.B32);
+      else d = add_rn(mul_rn(sc.delta32, __int2float_rn(adc_int<uint16_t, NCHUNK>(tb, w))), sc.B32);
       const int v = t * kTileVecs + lane;
       const bool pre = v < pi.n_l && d <= thd;
-      const int64_t id = pre ? __ldg(a.ids + pi.vbase + v) : INT64_MAX;
-      top.offer(pre, d, id, kq, thd, thi);
+      if (__any_sync(kFull, pre)) {
+        const int64_t id = pre ? __ldg(idp + v) : INT64_MAX;
+        top.offer(pre, d, id, kq, thd, thi);
+      }
     }
   }
 };
@@ -317,7 +291,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) search_persistent_kernel(const P
   using PipeT = Pipe<NCHUNK, NROW>;
   PipeT P(a);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* sm = anns_dyn_smem;
+  unsigned char* sm = P.base;
   float* md = (float*)(sm + a.off_md);
   int64_t* mi = (int64_t*)(sm + a.off_mi);
   int64_t* next_q = (int64_t*)(sm + a.off_q);
