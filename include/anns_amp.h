@@ -183,15 +183,17 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
 
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
- *    ANNS_KERNEL_AUTO (default): the persistent kernel when k <= 32 and
- *      M <= 64 (two LUT slots and the query table fit in shared memory), else
- *      the one-block-per-query kernel.
- *    ANNS_KERNEL_BASIC: one block per query.
- *    ANNS_KERNEL_PERSISTENT: one 1024-thread block per SM walking the queries
- *      with a pipelined LUT build; UNSUPPORTED at search time if it does not fit.
+ *    ANNS_KERNEL_AUTO (default): list-major when at least four LUTs of the
+ *      policy's widest table fit in one block's shared memory, else
+ *      query-major.
+ *    ANNS_KERNEL_BASIC: query-major, one block per query walking its probes.
+ *    ANNS_KERNEL_LIST_MAJOR: the probed pairs regrouped by list; one warp per
+ *      (query, list) pair, blocks of pairs sharing a list, work items taken
+ *      largest list first; then a per-query merge of the pairs' top-k.
+ *      UNSUPPORTED at search time if one table does not fit.
  * Both kernels return identical results. Errors: INVALID_ARG. */
 enum { ANNS_OPT_KERNEL = 0 };
-enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_PERSISTENT = 2 };
+enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);
 
 /* Message of the last failure on the calling thread ("" if none). */

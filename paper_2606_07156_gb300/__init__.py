@@ -99,8 +99,8 @@ class Index:
         return ids, dists
 
     def set_kernel(self, which: str):
-        """'auto', 'basic' (one block per query) or 'persistent' (codebook in registers)."""
-        v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "persistent": abi.KERNEL_PERSISTENT}[which]
+        """'auto', 'basic' (query-major) or 'lists' (list-major, one warp per pair)."""
+        v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "lists": abi.KERNEL_LIST_MAJOR}[which]
         abi.anns_set_option(self.handle, abi.OPT_KERNEL, v)
 
     def tap(self, what: int, shape, dtype):

@@ -20,7 +20,7 @@ PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS = 10, 11, 12
 OPT_KERNEL = 0
-KERNEL_AUTO, KERNEL_BASIC, KERNEL_PERSISTENT = 0, 1, 2
+KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR = 0, 1, 2
 
 SYMBOLS = (
     "anns_build_index_from_arrays", "anns_free", "anns_search", "anns_search_host",

@@ -105,6 +105,32 @@ int ensure_workspace(Index& ix, int64_t nq, int nprobe) {
   return grow((void**)&ix.ws_counter, &ix.ws_counter_cap, 64);
 }
 
+int table_bytes_for(const anns_precision_policy& P) {
+  switch (P.lut_mode) {
+    case ANNS_LUT_FIXED_BITS: return P.fixed_bits <= 8 ? 1 : 2;
+    case ANNS_LUT_HEURISTIC_EQ2: return 2;   // 4..16 bits, never the FP32 table
+    default: return 4;                       // plain, explicit, MLP (with FP32 fallback)
+  }
+}
+
+int list_workspace(Index& ix, int64_t nq, int nprobe, int k, ListWork& w) {
+  const size_t L = (size_t)(ix.nlist + 1) * 4, P = (size_t)nq * nprobe;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t bytes = 4 * al(L) + al(P * 4) + al(P * k * 4) + al(P * k * 8);
+  int rc = grow(&ix.ws_lists, &ix.ws_lists_cap, bytes);
+  if (rc) return rc;
+  char* b = (char*)ix.ws_lists;
+  w.cnt = (int*)b; b += al(L);
+  w.off = (int*)b; b += al(L);
+  w.ioff = (int*)b; b += al(L);
+  w.fill = (int*)b; b += al(L);
+  w.pairs = (int32_t*)b; b += al(P * 4);
+  w.part_d = (float*)b; b += al(P * k * 4);
+  w.part_i = (int64_t*)b;
+  w.counter = ix.ws_counter;
+  return ANNS_OK;
+}
+
 // Folds finished event sets into the totals; with `all`, waits for every set.
 int drain_profile(Index& ix, bool all) {
   int keep = 0;
@@ -219,18 +245,22 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
   e = launch_query_tables(*ix, Q, nq, ix->ws_qt, s);
   if (e != cudaSuccess) return cuda_fail(e, "query tables");
   if (ev) cudaEventRecord(ev[3], s);
-  const bool fits = persistent_supported(*ix, k);
-  const bool persistent = ix->opt_kernel == ANNS_KERNEL_PERSISTENT ||
-                          (ix->opt_kernel == ANNS_KERNEL_AUTO && fits);
-  if (ix->opt_kernel == ANNS_KERNEL_PERSISTENT && !fits)
-    return fail(ANNS_ERR_UNSUPPORTED,
-                "persistent kernel needs k <= 32 and the codebook plus two LUTs in shared memory");
-  if (persistent)
-    e = launch_search_persistent(*ix, ix->ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
-                                 ix->ws_probe_d2, ix->ws_bits, ids_out, dists_out, ix->ws_counter, s);
-  else
+  // table width the policy may need: FP32 (4 bytes), 16-bit or 8-bit levels
+  const int tbytes = table_bytes_for(P);
+  const int nw = list_major_warps(*ix, tbytes);
+  const bool lists = ix->opt_kernel == ANNS_KERNEL_LIST_MAJOR ||
+                     (ix->opt_kernel == ANNS_KERNEL_AUTO && nw >= 4);
+  if (ix->opt_kernel == ANNS_KERNEL_LIST_MAJOR && nw < 1)
+    return fail(ANNS_ERR_UNSUPPORTED, "list-major kernel: one table does not fit in shared memory");
+  if (lists) {
+    ListWork w{};
+    if ((rc = list_workspace(*ix, nq, nprobe, k, w))) return rc;
+    e = launch_search_lists(*ix, ix->ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
+                            ix->ws_probe_d2, ix->ws_bits, tbytes, w, ids_out, dists_out, s);
+  } else {
     e = launch_search(*ix, ix->ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
                       ix->ws_probe_d2, ix->ws_bits, ids_out, dists_out, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   if (ev) cudaEventRecord(ev[4], s);
   return ANNS_OK;
@@ -327,7 +357,7 @@ extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
   if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
   switch (option) {
     case ANNS_OPT_KERNEL:
-      if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_PERSISTENT)
+      if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_LIST_MAJOR)
         return fail(ANNS_ERR_INVALID_ARG, "unknown kernel choice");
       ix->opt_kernel = (int)value;
       return ANNS_OK;

@@ -44,7 +44,8 @@ static void free_index(anns_index* ix) {
   cudaGetDevice(&prev);
   cudaSetDevice(ix->device);
   void* ptrs[] = {ix->centroids, ix->codebooks, ix->codes, ix->ids, ix->list_len,
-                  ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->ws_qt, ix->ws_d2,
+                  ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->order, ix->ws_qt,
+                  ix->ws_lists, ix->ws_d2,
                   ix->ws_probes /* base of the pair block; the other ws_* alias it */,
                   ix->st_q, ix->st_out, ix->st_pq, ix->mlp_dev, ix->ws_counter};
   for (void* p : ptrs)
@@ -227,7 +228,11 @@ extern "C" int anns_build_index_from_arrays(const anns_build_desc* d, anns_index
   }
   std::vector<float> ltab;
   list_tables(cent, books, nlist, dim, M, Mp, ltab);
+  std::vector<int32_t> order(nlist);
+  for (int64_t l = 0; l < nlist; ++l) order[l] = (int32_t)l;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cnt[x] > cnt[y]; });
   if ((rc = upload(&ix->ltab, ltab.data(), ltab.size(), "upload list tables")) ||
+      (rc = upload(&ix->order, order.data(), order.size(), "upload list order")) ||
       (rc = upload(&ix->centroids, cent.data(), cent.size(), "upload centroids")) ||
       (rc = upload(&ix->codebooks, books.data(), books.size(), "upload codebooks")) ||
       (rc = upload(&ix->codes, packed.data(), packed.size(), "upload codes")) ||

@@ -39,6 +39,7 @@ struct Index {
   // M..Mp-1 zero: [nlist * Mp * 256]. With the per-query table Q it gives the
   // pair's LUT T' = P_l - 2 Q_q (the LUT shifted by ||r_m||^2, Section 2.1).
   float* ltab = nullptr;
+  int32_t* order = nullptr;     // [nlist] list ids by size, largest first (ties by id)
   // host copies of the small per-list tables
   std::string err;
   int64_t* h_list_len64 = nullptr;
@@ -53,8 +54,10 @@ struct Index {
   float* ws_qt = nullptr;        // [nq*Mp*256] per-query tables 2 Q_q
   size_t ws_qt_cap = 0;
   size_t ws_d2_cap = 0, ws_pair_cap = 0;
-  int* ws_counter = nullptr;     // work counter of the persistent kernel
+  int* ws_counter = nullptr;     // work counter of the list-major kernel
   size_t ws_counter_cap = 0;
+  void* ws_lists = nullptr;      // list-major work: per-list counts/offsets, pairs, partial top-k
+  size_t ws_lists_cap = 0;
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   // staging for anns_search_host
   void* st_q = nullptr; size_t st_q_cap = 0;
@@ -95,13 +98,24 @@ cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int npro
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                           int64_t* ids_out, float* dists_out, cudaStream_t s);
-// Persistent variant (codebook in registers); see search_persistent.cu.
-bool persistent_supported(const Index& ix, int k);
-cudaError_t launch_search_persistent(const Index& ix, const float* qt, int64_t nq, int nprobe,
-                                     const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
-                                     const int32_t* probes, const float* probe_d2,
-                                     const uint8_t* bits, int64_t* ids_out, float* dists_out,
-                                     int* counter, cudaStream_t s);
+// List-major search (search_lists.cu): work regrouped by list (invert.cu),
+// one warp per (query, list) pair, then a per-query merge.
+struct ListWork {
+  int* cnt; int* off; int* ioff; int* fill;  // [nlist + 1] each
+  int32_t* pairs;                           // [nq * nprobe]
+  float* part_d; int64_t* part_i;           // [nq * nprobe * k]
+  int* counter;
+};
+cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
+                          int nprobe, int batch, int* cnt, int* off, int* ioff, int* fill,
+                          int32_t* pairs, cudaStream_t s);
+// Warps per block the list-major kernel gets for tables of `table_bytes_per_entry`.
+int list_major_warps(const Index& ix, int table_bytes_per_entry);
+cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, int nprobe,
+                                const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
+                                const int32_t* probes, const float* probe_d2, const uint8_t* bits,
+                                int table_bytes_per_entry, const ListWork& w, int64_t* ids_out,
+                                float* dists_out, cudaStream_t s);
 // Pair-level debug paths; qt are the queries' tables from launch_query_tables.
 cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt, int64_t nq,
                                 const int32_t* pq, const int32_t* pl, const uint8_t* pb,

@@ -29,7 +29,7 @@ def _pair(amp, ix, ids=None):
     return g, o
 
 
-@pytest.fixture(scope="module", params=["basic", "persistent"])
+@pytest.fixture(scope="module", params=["basic", "lists"])
 def case_a(amp, small_a, request):
     """Config A shape, searched by each of the two search kernels."""
     d, ix = small_a
@@ -40,13 +40,6 @@ def case_a(amp, small_a, request):
     g.close()
 
 
-def forced_persistent_rejects(amp, g, k, call):
-    """The persistent kernel serves k <= 32; forced beyond that it must refuse."""
-    if getattr(g, "kernel_name", "") == "persistent" and k > 32:
-        with pytest.raises(amp.AnnsError, match="persistent"):
-            call()
-        return True
-    return False
 
 
 def cuda(a):
@@ -140,8 +133,6 @@ def test_search_bit_exact(amp, case_a, bits, k):
     d, ix, g, o = case_a
     Q = d["queries"]
     pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
-    if forced_persistent_rejects(amp, g, k, lambda: g.search(cuda(Q), 6, k, pol)):
-        return
     ids, dists = g.search(cuda(Q), 6, k, pol)
     ri, rd = ivfpq.search(o, Q, 6, k, bits=bits)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
@@ -199,8 +190,7 @@ def test_per_query_nprobe_and_k(amp, case_a):
     r = np.random.Generator(np.random.PCG64(8))
     npq = r.integers(0, 9, size=len(Q)).astype(np.int32)
     kpq = r.choice(np.array([0, 1, 10, 33], dtype=np.int32), size=len(Q))
-    kmax = 32 if getattr(g, "kernel_name", "") == "persistent" else 33
-    kpq = np.minimum(kpq, kmax).astype(np.int32)
+    kmax = 33
     ids, dists = g.search(cuda(Q), 8, kmax, amp.policy("fixed", bits=6), nprobe_per_q=cuda(npq),
                           k_per_q=cuda(kpq))
     ri, rd = ivfpq.search(o, Q, 8, kmax, bits=6, nprobe_per_q=npq, k_per_q=kpq)
@@ -234,8 +224,8 @@ def test_ties_broken_by_user_id_and_padding(amp):
     uids = r.permutation(10_000_000)[:300].astype(np.int64) * 7 + 3
     g, o = _pair(amp, ix, ids=uids)
     Q = r.integers(0, 4, size=(30, 8)).astype(np.float32)
-    for kern, npb, k, bits in ((kn, *c) for kn in ("basic", "persistent")
-                               for c in ((4, 20, 0), (1, 32, 0), (2, 30, 4), (4, 7, 16))):
+    for kern, npb, k, bits in ((kn, *c) for kn in ("basic", "lists")
+                               for c in ((4, 20, 0), (1, 128, 0), (2, 50, 4), (4, 7, 16))):
         g.set_kernel(kern)
         pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
         ids, dists = g.search(cuda(Q), npb, k, pol)
@@ -261,15 +251,10 @@ def test_odd_subspace_counts(amp, M, dim):
     ix["list_of"][ix["list_of"] == 5] = 6                     # list 5 becomes empty
     g, o = _pair(amp, ix)
     Q = r.standard_normal((12, dim)).astype(np.float32)
-    fits = M <= 64
-    for kern in ("basic", "persistent"):
+    for kern in ("basic", "lists"):
         g.set_kernel(kern)
         for bits in (0, 8, 12):
             pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
-            if kern == "persistent" and not fits:
-                with pytest.raises(amp.AnnsError, match="persistent"):
-                    g.search(cuda(Q), 7, 12, pol)
-                continue
             ids, dists = g.search(cuda(Q), 7, 12, pol)
             ri, rd = ivfpq.search(o, Q, 7, 12, bits=bits)
             np.testing.assert_array_equal(ids.cpu().numpy(), ri)
