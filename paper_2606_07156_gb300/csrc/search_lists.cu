@@ -42,6 +42,15 @@ __device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
+// The same for data read once per warp (a query's table): not kept in L1, so
+// the list's code tiles and list table, shared by the block's warps, stay there.
+__device__ __forceinline__ void load8_stream(const float* p, float (&v)[8]) {
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]) : "l"(p + 4));
+}
+
 template <int NCHUNK>
 struct PairTable {
   static constexpr int Mp = NCHUNK * 16;
@@ -58,7 +67,7 @@ struct PairTable {
         if (m < M) {
           float p[8], q[8];
           load8(P + m * kKsub + lane * 8, p);
-          load8(Qt + m * kKsub + lane * 8, q);
+          load8_stream(Qt + m * kKsub + lane * 8, q);
           dst[0] = make_float4(sub_rn(p[0], q[0]), sub_rn(p[1], q[1]), sub_rn(p[2], q[2]), sub_rn(p[3], q[3]));
           dst[1] = make_float4(sub_rn(p[4], q[4]), sub_rn(p[5], q[5]), sub_rn(p[6], q[6]), sub_rn(p[7], q[7]));
         } else {
@@ -80,7 +89,7 @@ struct PairTable {
         if (m >= M) break;
         float p[8], q[8], t[8];
         load8(P + m * kKsub + lane * 8, p);
-        load8(Qt + m * kKsub + lane * 8, q);
+        load8_stream(Qt + m * kKsub + lane * 8, q);
 #pragma unroll
         for (int e = 0; e < 8; ++e) t[e] = sub_rn(p[e], q[e]);
         float mn = t[0];
@@ -115,7 +124,7 @@ struct PairTable {
           const float mn = __shfl_sync(kFull, rm[s], mm);
           float p[8], q[8];
           load8(P + m * kKsub + lane * 8, p);
-          load8(Qt + m * kKsub + lane * 8, q);
+          load8_stream(Qt + m * kKsub + lane * 8, q);
 #pragma unroll
           for (int e = 0; e < 8; ++e)
             t[e] = (unsigned)min(__float2int_rn(mul_rn(sub_rn(sub_rn(p[e], q[e]), mn), s32)), L);
@@ -145,8 +154,11 @@ __device__ __forceinline__ void load_tile(const uint8_t* __restrict__ tile, uint
   for (int c = 0; c < NCHUNK; ++c) w[c] = __ldg(reinterpret_cast<const uint4*>(tile + c * kTileChunkBytes));
 }
 
+// Wide codes (NCHUNK > 4) need more registers per thread: at most 16 warps.
+constexpr int max_warps(int nchunk) { return nchunk <= 4 ? 32 : 16; }
+
 template <int NCHUNK, int R>
-__global__ void __launch_bounds__(512) list_kernel(const LArgs a) {
+__global__ void __launch_bounds__(max_warps(NCHUNK) * 32) list_kernel(const LArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t raw = smem_addr(anns_dyn_smem);
   const uint32_t pad = (256u - (raw & 255u)) & 255u;
@@ -291,7 +303,7 @@ int list_major_warps(const Index& ix, int table_bytes_per_entry) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t region = (size_t)ix.Mp * kKsub * table_bytes_per_entry;
   const size_t avail = (size_t)optin > 1024 ? (size_t)optin - 1024 : 0;
-  return (int)std::min<size_t>(16, avail / region);
+  return (int)std::min<size_t>(max_warps((int)ix.nchunk), avail / region);
 }
 
 cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, int nprobe,
