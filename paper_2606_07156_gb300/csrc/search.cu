@@ -70,43 +70,58 @@ struct Smem {
 
 // Steps 1-2 for one pair: all threads of the block take part. P and qt2 are
 // the pair's list table and query table ([Mp * 256], rows M..Mp-1 zero).
+// Warp w builds rows m = w, w + nwarps, ...; lane i owns entries 8i..8i+7 of
+// a row, so each row's minimum and range come from warp shuffles during the
+// build, and each warp quantises the rows it built (two block barriers for a
+// b-bit pair, one for an FP32 pair).
 __device__ void build_lut(const float* __restrict__ P, const float* __restrict__ qt2, int M, int Mp,
                           int b, float d2, Smem& s) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nent = Mp * kKsub;
-  for (int e = tid; e < nent; e += blockDim.x) s.T[e] = sub_rn(__ldg(P + e), __ldg(qt2 + e));
-  __syncthreads();
-  if (b == 0) return;
-  for (int m = warp; m < M; m += blockDim.x / 32) {
-    const float* row = s.T + m * kKsub;
-    float mn = INFINITY;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int m = warp; m < Mp; m += nwarps) {
+    float4* dst = (float4*)(s.T + m * kKsub + lane * 8);
+    if (m >= M) {
+      dst[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float4* pr = (const float4*)(P + m * kKsub + lane * 8);
+    const float4* qr = (const float4*)(qt2 + m * kKsub + lane * 8);
+    const float4 p0 = __ldg(pr), p1 = __ldg(pr + 1), q0 = __ldg(qr), q1 = __ldg(qr + 1);
+    const float t[8] = {sub_rn(p0.x, q0.x), sub_rn(p0.y, q0.y), sub_rn(p0.z, q0.z), sub_rn(p0.w, q0.w),
+                        sub_rn(p1.x, q1.x), sub_rn(p1.y, q1.y), sub_rn(p1.z, q1.z), sub_rn(p1.w, q1.w)};
+    dst[0] = make_float4(t[0], t[1], t[2], t[3]);
+    dst[1] = make_float4(t[4], t[5], t[6], t[7]);
+    if (b != 0) {
+      float mn = t[0];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) mn = fminf(mn, row[lane + 32 * i]);
-    mn = warp_min(mn);
-    float mx = 0.f;
+      for (int e = 1; e < 8; ++e) mn = fminf(mn, t[e]);
+      mn = warp_min(mn);
+      float mx = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) mx = fmaxf(mx, sub_rn(row[lane + 32 * i], mn));
-    mx = warp_max(mx);
-    if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
+      for (int e = 0; e < 8; ++e) mx = fmaxf(mx, sub_rn(t[e], mn));
+      mx = warp_max(mx);
+      if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
+    }
   }
   __syncthreads();
+  if (b == 0) return;
+  // every warp derives the shared step; warp 0 also the offset B (FP64,
+  // row minima in the fixed 32-lane tree order, plus D2)
+  float range = 0.f;
+  for (int m = lane; m < M; m += 32) range = fmaxf(range, s.rowmax[m]);
+  range = warp_max(range);
+  const int L = (1 << b) - 1;
+  // fl32 of the FP64 quotient equals the correctly rounded FP32 quotient
+  const float s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
   if (warp == 0) {
-    // B: FP64 sum of the row minima in the fixed 32-lane tree order, plus D2
     double B = 0.0;
-    float range = 0.f;
-    for (int m = lane; m < M; m += 32) {
-      B = __dadd_rn(B, (double)s.bias[m]);
-      range = fmaxf(range, s.rowmax[m]);
-    }
+    for (int m = lane; m < M; m += 32) B = __dadd_rn(B, (double)s.bias[m]);
 #pragma unroll
     for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
-    range = warp_max(range);
     if (lane == 0) {
-      const int L = (1 << b) - 1;
       PairScal sc;
-      // fl32 of the FP64 quotient equals the correctly rounded FP32 quotient
       sc.delta64 = range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
-      sc.s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
+      sc.s32 = s32;
       sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
       sc.B64 = __dadd_rn((double)d2, B);
       sc.B32 = __double2float_rn(sc.B64);
@@ -115,24 +130,29 @@ __device__ void build_lut(const float* __restrict__ P, const float* __restrict__
       *s.sc = sc;
     }
   }
-  __syncthreads();
-  const float s32 = s.sc->s32;
-  const int L = s.sc->L;
-  if (b <= 8) {
-    uint8_t* t8 = (uint8_t*)s.q;
-    for (int e = tid; e < nent; e += blockDim.x) {
-      const int m = e >> 8;
-      int t = 0;
-      if (m < M) t = min(__float2int_rn(mul_rn(sub_rn(s.T[e], s.bias[m]), s32)), L);
-      t8[e] = (uint8_t)t;
+  for (int m = warp; m < Mp; m += nwarps) {
+    unsigned t[8];
+    if (m < M) {
+      const float mn = s.bias[m];
+      const float4* src = (const float4*)(s.T + m * kKsub + lane * 8);
+      const float4 u = src[0], v = src[1];
+      const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) t[e] = (unsigned)min(__float2int_rn(mul_rn(sub_rn(x[e], mn), s32)), L);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) t[e] = 0u;
     }
-  } else {
-    uint16_t* t16 = (uint16_t*)s.q;
-    for (int e = tid; e < nent; e += blockDim.x) {
-      const int m = e >> 8;
-      int t = 0;
-      if (m < M) t = min(__float2int_rn(mul_rn(sub_rn(s.T[e], s.bias[m]), s32)), L);
-      t16[e] = (uint16_t)t;
+    if (b <= 8) {
+      uint2 v;
+      v.x = t[0] | (t[1] << 8) | (t[2] << 16) | (t[3] << 24);
+      v.y = t[4] | (t[5] << 8) | (t[6] << 16) | (t[7] << 24);
+      *(uint2*)((uint8_t*)s.q + m * kKsub + lane * 8) = v;
+    } else {
+      uint4 v;
+      v.x = t[0] | (t[1] << 16); v.y = t[2] | (t[3] << 16);
+      v.z = t[4] | (t[5] << 16); v.w = t[6] | (t[7] << 16);
+      *(uint4*)((uint16_t*)s.q + m * kKsub + lane * 8) = v;
     }
   }
   __syncthreads();
