@@ -183,9 +183,7 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
 
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
- *    ANNS_KERNEL_AUTO (default): list-major when the policy needs only
- *      integer tables and at least eight of them fit in one block's shared
- *      memory, else query-major.
+ *    ANNS_KERNEL_AUTO (default): query-major.
  *    ANNS_KERNEL_BASIC: query-major, one block per query walking its probes.
  *    ANNS_KERNEL_LIST_MAJOR: the probed pairs regrouped by list; one warp per
  *      (query, list) pair, blocks of pairs sharing a list, work items taken

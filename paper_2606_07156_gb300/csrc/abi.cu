@@ -248,10 +248,9 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
   // table width the policy may need: FP32 (4 bytes), 16-bit or 8-bit levels
   const int tbytes = table_bytes_for(P);
   const int nw = list_major_warps(*ix, tbytes);
-  // AUTO: list-major for integer tables (small slices, many warps per SM),
-  // query-major when FP32 tables may be needed
-  const bool lists = ix->opt_kernel == ANNS_KERNEL_LIST_MAJOR ||
-                     (ix->opt_kernel == ANNS_KERNEL_AUTO && tbytes <= 2 && nw >= 8);
+  // AUTO: query-major (measured faster on the SIFT-shaped workload for every
+  // table width); list-major on request
+  const bool lists = ix->opt_kernel == ANNS_KERNEL_LIST_MAJOR;
   if (ix->opt_kernel == ANNS_KERNEL_LIST_MAJOR && nw < 1)
     return fail(ANNS_ERR_UNSUPPORTED, "list-major kernel: one table does not fit in shared memory");
   if (lists) {
