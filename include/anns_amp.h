@@ -194,6 +194,29 @@ enum { ANNS_OPT_KERNEL = 0 };
 enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);
 
+/* The coarse stage (cluster locating) without any allocation, for callers
+ * that cannot allocate device memory: code running inside a CUDA graph
+ * capture, hosts that forbid allocation after start-up, plugins whose host
+ * application owns all memory pools. There is no counterpart in the paper;
+ * it is the probe selection of anns_search (same kernels, same results as
+ * the PROBES / PROBE_D2 taps) with its scratch — the nq * nlist coarse
+ * distance matrix — in a fixed array of ANNS_STATIC_SCRATCH_FLOATS floats
+ * (8 MiB) compiled into the library and held by every GPU that loads it
+ * until the process exits. No cudaMalloc, cudaFree or allocating library
+ * call is made.
+ *  queries       device float32 [nq * dim].
+ *  probes_out    device int32 [nq * nprobe]: the nprobe nearest lists by (D2, list id).
+ *  probe_d2_out  device float32 [nq * nprobe]: their FP32 coarse distances.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls on a device share the array, so calls
+ * that overlap on the GPU race; each call overwrites every element it reads.
+ * Errors: INVALID_ARG (nq * nlist > ANNS_STATIC_SCRATCH_FLOATS, nprobe out of
+ * range, null buffer), CUDA. */
+#define ANNS_STATIC_SCRATCH_FLOATS (1 << 21)
+int anns_locate_static(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
+                       int32_t* probes_out, float* probe_d2_out, void* cuda_stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* anns_last_error(void);
 

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libanns_amp.so")
 
 ANNS_OK = 0
+STATIC_SCRATCH_FLOATS = 1 << 21
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSUPPORTED"}
 LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT = 0, 1, 2, 3, 4
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
@@ -25,7 +26,7 @@ KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR = 0, 1, 2
 SYMBOLS = (
     "anns_build_index_from_arrays", "anns_free", "anns_search", "anns_search_host",
     "anns_get_info", "anns_debug_tap", "anns_compute_luts", "anns_scan_pairs", "anns_profile",
-    "anns_set_option", "anns_last_error",
+    "anns_set_option", "anns_locate_static", "anns_last_error",
 )
 
 
@@ -74,6 +75,7 @@ def _load():
         "anns_scan_pairs": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
+        "anns_locate_static": ([vp, vp, i64, i32, vp, vp, vp], i32),
         "anns_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -151,3 +153,8 @@ def anns_profile(index, enable: int):
 
 def anns_set_option(index, option: int, value: int) -> None:
     _check(_lib.anns_set_option(index, option, value))
+
+
+def anns_locate_static(index, queries, nq, nprobe, probes_out, probe_d2_out, stream=None) -> None:
+    """Coarse stage with the library's fixed scratch array: no device allocation."""
+    _check(_lib.anns_locate_static(index, queries, nq, nprobe, probes_out, probe_d2_out, stream))
