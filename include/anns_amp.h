@@ -194,6 +194,59 @@ enum { ANNS_OPT_KERNEL = 0 };
 enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);
 
+/* Learned precision predictor: the regressor of Section 3.4 as a 5-32-32-5 MLP
+ * classifier over the bit widths {4, 6, 8, 12, 16}, on the features of
+ * Section 3.3 for probe rank j: (sqrt(D2_j) - sqrt(D2_0), r_0, r_j, sqrt(n_j),
+ * j / nprobe), normalised as fl32(fl32(x - mean) * inv_std). FP32 master
+ * weights, row-major [out][in]. Inference (policy ANNS_LUT_MLP) uses FP16
+ * operands with FP32 accumulation; a pair falls back to the FP32 LUT when its
+ * top-two logits differ by less than policy->fallback_margin. */
+typedef struct {
+  float W1[32 * 5], b1[32], W2[32 * 32], b2[32], W3[5 * 32], b3[5];
+  float mean[5], inv_std[5];
+} anns_predictor;
+typedef struct {
+  int32_t epochs, batch; /* passes over the samples, samples per Adam step */
+  float lr;              /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8) */
+  uint64_t seed;         /* initial weights and sample order */
+} anns_train_cfg;
+
+/* Installs / returns the index's predictor (host structs). */
+int anns_set_predictor(anns_index* index, const anns_predictor* p);
+int anns_get_predictor(const anns_index* index, anns_predictor* out);
+
+/* Training set from training queries (device float32 [nq * dim]), uniform
+ * nprobe and k (k + 1 <= 128). For every (query, probe rank) pair:
+ *  feat_out  device float32 [nq * nprobe * 5]: raw features,
+ *  label_out device uint8  [nq * nprobe]: the label (Section 3.3 / Fig. 6,
+ *            read as "the fewest bits that keep the FP32 top-k"):
+ *            tau = (d_k + d_{k+1}) / 2 of the FP32 search, margin = min over the
+ *            list of |d - tau|, E(b) = max over the list of |dhat_b - d|; the
+ *            fewest b in {4,6,8,12,16} with E(b) < margin, 0 if none (needs the
+ *            FP32 LUT), 255 for a rank the query does not probe.
+ * Synchronous. Reuses the index's search workspace. */
+int anns_make_training_set(anns_index* index, const float* train_q, int64_t nq, int32_t nprobe,
+                           int32_t k, float* feat_out, uint8_t* label_out, void* cuda_stream);
+
+/* Mean softmax cross-entropy and its gradient over n samples with the MLP
+ * in `w`: X device float32 [n * 5] raw features, cls device uint8 [n] classes
+ * 0..4 (255 = skipped). grad_out host float32 [1413] in the order W1 b1 W2 b2
+ * W3 b3; loss_out host (or NULL). FP16-operand forward, FP32 backward.
+ * Synchronous. */
+int anns_mlp_grad(anns_index* index, const anns_predictor* w, const float* X, const uint8_t* cls,
+                  int64_t n, float* grad_out, double* loss_out, void* cuda_stream);
+
+/* Adam training on given samples (as for anns_mlp_grad), starting from and
+ * returning the weights in *io (its normalisation is used as is). Synchronous. */
+int anns_mlp_train(anns_index* index, const float* X, const uint8_t* cls, int64_t n,
+                   const anns_train_cfg* cfg, anns_predictor* io, void* cuda_stream);
+
+/* Training set + normalisation statistics + seeded initial weights + Adam
+ * training on the GPU, then installs the predictor in the index (and copies
+ * it to *out if not NULL). Synchronous. */
+int anns_train_predictor(anns_index* index, const float* train_q, int64_t nq, int32_t nprobe,
+                         int32_t k, const anns_train_cfg* cfg, anns_predictor* out, void* cuda_stream);
+
 /* The coarse stage (cluster locating) without any allocation, for callers
  * that cannot allocate device memory: code running inside a CUDA graph
  * capture, hosts that forbid allocation after start-up, plugins whose host

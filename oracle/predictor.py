@@ -216,6 +216,35 @@ def loss_and_grad64(p: dict, X: np.ndarray, y: np.ndarray):
     return loss, mlp_backward64(p, fw, gz)
 
 
+def loss_and_grad16(p: dict, Xn: np.ndarray, y: np.ndarray):
+    """Mean softmax-CE loss and gradients of the network the GPU trains: FP16
+    weights, biases and normalised inputs, hidden activations rounded to FP16
+    after ReLU (the inference rule), evaluated in FP64 with those roundings."""
+    p16 = {k: np.asarray(v, dtype=F32).astype(F16).astype(F64) for k, v in p.items()}
+    X = np.asarray(Xn, dtype=F32).astype(F16).astype(F64)
+    a1 = X @ p16["W1"].T + p16["b1"]
+    h1 = np.maximum(a1, 0.0).astype(F16).astype(F64)
+    a2 = h1 @ p16["W2"].T + p16["b2"]
+    h2 = np.maximum(a2, 0.0).astype(F16).astype(F64)
+    z = h2 @ p16["W3"].T + p16["b3"]
+    loss, gz = softmax_ce64(z, y)
+    fw = dict(X=X, a1=a1, h1=h1, a2=a2, h2=h2, z=z)
+    return loss, mlp_backward64(p16, fw, gz)
+
+
+def adam_step(p: dict, g: dict, m: dict, v: dict, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (FP64) of every parameter; returns new (p, m, v)."""
+    out_p, out_m, out_v = {}, {}, {}
+    for k in p:
+        mk = b1 * m[k] + (1 - b1) * g[k]
+        vk = b2 * v[k] + (1 - b2) * g[k] ** 2
+        mh = mk / (1 - b1 ** t)
+        vh = vk / (1 - b2 ** t)
+        out_p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
+        out_m[k], out_v[k] = mk, vk
+    return out_p, out_m, out_v
+
+
 def to_fp16(p: dict) -> dict:
     return {k: np.asarray(v, dtype=F32).astype(F16) for k, v in p.items()}
 

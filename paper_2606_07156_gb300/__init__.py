@@ -33,6 +33,30 @@ def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), 
     return p
 
 
+_PRED_FIELDS = ("W1", "b1", "W2", "b2", "W3", "b3", "mean", "inv_std")
+_PRED_SHAPES = {"W1": (32, 5), "b1": (32,), "W2": (32, 32), "b2": (32,), "W3": (5, 32), "b3": (5,),
+                "mean": (5,), "inv_std": (5,)}
+
+
+def predictor_to_struct(p: dict) -> abi.anns_predictor:
+    """dict of numpy arrays (W1 [32,5] ... inv_std [5]) -> anns_predictor."""
+    s = abi.anns_predictor()
+    for f in _PRED_FIELDS:
+        arr = np.ascontiguousarray(np.asarray(p[f], dtype=np.float32).reshape(-1))
+        ctypes.memmove(getattr(s, f), arr.ctypes.data, arr.nbytes)
+    return s
+
+
+def predictor_to_dict(s: abi.anns_predictor) -> dict:
+    return {f: np.ctypeslib.as_array(getattr(s, f)).copy().reshape(_PRED_SHAPES[f]) for f in _PRED_FIELDS}
+
+
+def train_cfg(epochs: int = 10, batch: int = 1024, lr: float = 3e-3, seed: int = 0) -> abi.anns_train_cfg:
+    c = abi.anns_train_cfg()
+    c.epochs, c.batch, c.lr, c.seed = epochs, batch, lr, seed
+    return c
+
+
 def _ptr(a):
     if a is None:
         return None
@@ -102,6 +126,42 @@ class Index:
         """'auto', 'basic' (query-major) or 'lists' (list-major, one warp per pair)."""
         v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "lists": abi.KERNEL_LIST_MAJOR}[which]
         abi.anns_set_option(self.handle, abi.OPT_KERNEL, v)
+
+    def set_predictor(self, p: dict):
+        abi.anns_set_predictor(self.handle, predictor_to_struct(p))
+
+    def get_predictor(self) -> dict:
+        return predictor_to_dict(abi.anns_get_predictor(self.handle))
+
+    def make_training_set(self, train_q, nprobe: int, k: int, stream=None):
+        """Raw features [nq, nprobe, 5] and label bits [nq, nprobe] (CUDA tensors)."""
+        import torch
+        nq = train_q.shape[0]
+        feat = torch.empty((nq, nprobe, 5), dtype=torch.float32, device=train_q.device)
+        lab = torch.empty((nq, nprobe), dtype=torch.uint8, device=train_q.device)
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_make_training_set(self.handle, _ptr(train_q), nq, nprobe, k, _ptr(feat), _ptr(lab), s)
+        return feat, lab
+
+    def mlp_grad(self, p: dict, X, cls):
+        """Gradient (dict of numpy arrays) and mean loss over samples X [n, 5], cls [n] (CUDA tensors)."""
+        g = np.empty(1413, dtype=np.float32)
+        loss = abi.anns_mlp_grad(self.handle, predictor_to_struct(p), _ptr(X), _ptr(cls), X.shape[0], g.ctypes.data)
+        out, o = {}, 0
+        for f in _PRED_FIELDS[:6]:
+            n = int(np.prod(_PRED_SHAPES[f]))
+            out[f] = g[o:o + n].reshape(_PRED_SHAPES[f])
+            o += n
+        return out, loss
+
+    def mlp_train(self, p: dict, X, cls, cfg) -> dict:
+        s = predictor_to_struct(p)
+        abi.anns_mlp_train(self.handle, _ptr(X), _ptr(cls), X.shape[0], cfg, s)
+        return predictor_to_dict(s)
+
+    def train_predictor(self, train_q, nprobe: int, k: int, cfg) -> dict:
+        return predictor_to_dict(abi.anns_train_predictor(self.handle, _ptr(train_q), train_q.shape[0],
+                                                          nprobe, k, cfg))
 
     def tap(self, what: int, shape, dtype):
         out = np.empty(shape, dtype=dtype)

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libanns_amp.so")
 
 ANNS_OK = 0
 STATIC_SCRATCH_FLOATS = 1 << 21
+MAX_M, MAX_NPROBE, MAX_K = 128, 128, 128
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSUPPORTED"}
 LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT = 0, 1, 2, 3, 4
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
@@ -26,7 +27,8 @@ KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR = 0, 1, 2
 SYMBOLS = (
     "anns_build_index_from_arrays", "anns_free", "anns_search", "anns_search_host",
     "anns_get_info", "anns_debug_tap", "anns_compute_luts", "anns_scan_pairs", "anns_profile",
-    "anns_set_option", "anns_locate_static", "anns_last_error",
+    "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
+    "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor", "anns_last_error",
 )
 
 
@@ -58,6 +60,17 @@ class anns_index_info(ctypes.Structure):
                 ("device", ctypes.c_int32)]
 
 
+class anns_predictor(ctypes.Structure):
+    _fields_ = [("W1", ctypes.c_float * 160), ("b1", ctypes.c_float * 32), ("W2", ctypes.c_float * 1024),
+                ("b2", ctypes.c_float * 32), ("W3", ctypes.c_float * 160), ("b3", ctypes.c_float * 5),
+                ("mean", ctypes.c_float * 5), ("inv_std", ctypes.c_float * 5)]
+
+
+class anns_train_cfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: run paper_2606_07156_gb300.build.build() "
@@ -76,6 +89,12 @@ def _load():
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
         "anns_locate_static": ([vp, vp, i64, i32, vp, vp, vp], i32),
+        "anns_set_predictor": ([vp, ctypes.POINTER(anns_predictor)], i32),
+        "anns_get_predictor": ([vp, ctypes.POINTER(anns_predictor)], i32),
+        "anns_make_training_set": ([vp, vp, i64, i32, i32, vp, vp, vp], i32),
+        "anns_mlp_grad": ([vp, ctypes.POINTER(anns_predictor), vp, vp, i64, vp, ctypes.POINTER(ctypes.c_double), vp], i32),
+        "anns_mlp_train": ([vp, vp, vp, i64, ctypes.POINTER(anns_train_cfg), ctypes.POINTER(anns_predictor), vp], i32),
+        "anns_train_predictor": ([vp, vp, i64, i32, i32, ctypes.POINTER(anns_train_cfg), ctypes.POINTER(anns_predictor), vp], i32),
         "anns_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -158,3 +177,33 @@ def anns_set_option(index, option: int, value: int) -> None:
 def anns_locate_static(index, queries, nq, nprobe, probes_out, probe_d2_out, stream=None) -> None:
     """Coarse stage with the library's fixed scratch array: no device allocation."""
     _check(_lib.anns_locate_static(index, queries, nq, nprobe, probes_out, probe_d2_out, stream))
+
+
+def anns_set_predictor(index, pred: "anns_predictor") -> None:
+    _check(_lib.anns_set_predictor(index, ctypes.byref(pred)))
+
+
+def anns_get_predictor(index) -> "anns_predictor":
+    out = anns_predictor()
+    _check(_lib.anns_get_predictor(index, ctypes.byref(out)))
+    return out
+
+
+def anns_make_training_set(index, train_q, nq, nprobe, k, feat_out, label_out, stream=None) -> None:
+    _check(_lib.anns_make_training_set(index, train_q, nq, nprobe, k, feat_out, label_out, stream))
+
+
+def anns_mlp_grad(index, pred, X, cls, n, grad_out, stream=None) -> float:
+    loss = ctypes.c_double()
+    _check(_lib.anns_mlp_grad(index, ctypes.byref(pred), X, cls, n, grad_out, ctypes.byref(loss), stream))
+    return loss.value
+
+
+def anns_mlp_train(index, X, cls, n, cfg, pred, stream=None) -> None:
+    _check(_lib.anns_mlp_train(index, X, cls, n, ctypes.byref(cfg), ctypes.byref(pred), stream))
+
+
+def anns_train_predictor(index, train_q, nq, nprobe, k, cfg, out=None, stream=None) -> "anns_predictor":
+    out = out if out is not None else anns_predictor()
+    _check(_lib.anns_train_predictor(index, train_q, nq, nprobe, k, ctypes.byref(cfg), ctypes.byref(out), stream))
+    return out

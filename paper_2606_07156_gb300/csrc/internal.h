@@ -73,6 +73,7 @@ struct Index {
   // learned predictor (FP16 inference copy + normalisation), see predictor.cu
   bool has_mlp = false;
   void* mlp_dev = nullptr;       // device MlpParams16
+  anns_predictor mlp_host{};     // FP32 master copy of the installed predictor
 };
 
 void set_error(const std::string& msg);

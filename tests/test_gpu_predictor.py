@@ -1,0 +1,244 @@
+"""Learned precision predictor on the GPU vs the CPU oracle, through the C ABI.
+
+Labels are integers computed from FP32 values that follow the search's rules,
+so they must be identical. MLP inference (FP16 operands, FP32 accumulation in
+a fixed order) must choose identical bit widths. Gradients and Adam steps are
+FP32 reductions in a different order than the oracle's FP64 evaluation of the
+same FP16 network, so they are compared within a tolerance.
+"""
+import numpy as np
+import pytest
+
+from oracle import ivfpq, predictor
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_07156_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def pair(amp, small_a):
+    d, ix = small_a
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=0)
+    o = ivfpq.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"])
+    yield d, g, o
+    g.close()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _train_queries(d, n, seed):
+    """Training queries: base vectors plus small noise (queries of the same distribution)."""
+    r = np.random.Generator(np.random.PCG64(seed))
+    pick = r.choice(len(d["base"]), size=n, replace=False)
+    noise = r.normal(0.0, 0.05, size=(n, d["base"].shape[1])) * np.abs(d["base"][pick]).mean()
+    return (d["base"][pick] + noise).astype(np.float32)
+
+
+def _random_predictor(seed, F):
+    p = predictor.init_mlp(seed)
+    flat = F.reshape(-1, 5).astype(np.float64)
+    p["mean"] = flat.mean(axis=0).astype(np.float32)
+    sd = flat.std(axis=0)
+    p["inv_std"] = np.where(sd > 0, 1.0 / np.where(sd > 0, sd, 1.0), 1.0).astype(np.float32)
+    return p
+
+
+def _oracle_features(o, Q, nprobe):
+    D2 = ivfpq.coarse_d2_fp32(Q, o.centroids)
+    probes, pd = ivfpq.locate(D2, nprobe)
+    return predictor.features(pd, probes, o.radius, o.sizes)
+
+
+# ------------------------------------------------------------------ labels
+
+@pytest.mark.parametrize("nprobe,k", [(6, 10), (16, 1), (3, 40)])
+def test_training_set_bit_exact(pair, nprobe, k):
+    d, g, o = pair
+    Q = _train_queries(d, 20, seed=11 + k)
+    feat, lab = g.make_training_set(cuda(Q), nprobe, k)
+    feat, lab = feat.cpu().numpy(), lab.cpu().numpy()
+    np.testing.assert_array_equal(feat, _oracle_features(o, Q, nprobe))
+    want = predictor.labels(o, Q, nprobe, k)
+    np.testing.assert_array_equal(lab, want)
+    # every width occurs somewhere in a realistic mix, and 4 bits for the far lists
+    assert set(np.unique(lab)) <= {0, 4, 6, 8, 12, 16}
+
+
+def test_training_set_fewer_candidates_than_k(amp):
+    """k + 1 above the number of candidates: tau = +inf, every pair labelled 4 bits."""
+    from tests.conftest import int_dataset
+    base, ix = int_dataset(n=200, dim=8, nlist=4)
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=0)
+    try:
+        o = ivfpq.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"])
+        Q = base[:6] + 0.25
+        k = int(o.sizes.max()) + 1
+        assert k + 1 <= amp.abi.MAX_K
+        # two probed lists: some queries have k + 1 candidates, some not
+        feat, lab = g.make_training_set(cuda(Q), 2, k)
+        want = predictor.labels(o, Q, 2, k)
+        np.testing.assert_array_equal(lab.cpu().numpy(), want)
+        feat, lab = g.make_training_set(cuda(Q), 1, k)
+        np.testing.assert_array_equal(lab.cpu().numpy(), np.full((6, 1), 4, np.uint8))
+    finally:
+        g.close()
+
+
+# ------------------------------------------------------------------ inference
+
+@pytest.mark.parametrize("margin", [0.0, 0.5, 2.0])
+def test_mlp_policy_bit_exact(amp, pair, margin):
+    d, g, o = pair
+    Q = d["queries"]
+    nprobe = 7
+    F = _oracle_features(o, Q, nprobe)
+    p = _random_predictor(3, F)
+    # larger output weights spread the logits over the margins tested
+    p["W3"] = (p["W3"] * 4.0).astype(np.float32)
+    g.set_predictor(p)
+    back = g.get_predictor()
+    for key in p:
+        np.testing.assert_array_equal(back[key], np.asarray(p[key], np.float32))
+    ids, dists = g.search(cuda(Q), nprobe, 10, amp.policy("mlp", margin=margin))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(g.tap(amp.abi.TAP_FEATURES, (len(Q), nprobe, 5), np.float32), F)
+    Xn = predictor.normalise(F.reshape(-1, 5), p["mean"], p["inv_std"])
+    z = predictor.mlp_logits16(predictor.to_fp16({k: p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}), Xn)
+    bits = predictor.decide_bits(z, margin).reshape(len(Q), nprobe)
+    got = g.tap(amp.abi.TAP_BITS, (len(Q), nprobe), np.uint8)
+    np.testing.assert_array_equal(got, bits)
+    if margin == 0.5:
+        assert len(np.unique(bits)) >= 2
+    ri, rd = ivfpq.search(o, Q, nprobe, 10, bits=bits)
+    np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+    np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+
+
+def test_mlp_policy_needs_predictor(amp, small_a):
+    d, ix = small_a
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=0)
+    try:
+        with pytest.raises(amp.abi.AnnsError):
+            g.search(cuda(d["queries"]), 4, 10, amp.policy("mlp"))
+        with pytest.raises(amp.abi.AnnsError):
+            g.get_predictor()
+    finally:
+        g.close()
+
+
+# ------------------------------------------------------------------ training
+
+def _samples(n, seed, live_frac=1.0):
+    r = np.random.Generator(np.random.PCG64(seed))
+    X = np.stack([r.gamma(2.0, 3.0, n), r.gamma(3.0, 2.0, n), r.gamma(3.0, 2.0, n),
+                  np.sqrt(r.integers(0, 900, n)), r.integers(0, 32, n) / 32.0], axis=1).astype(np.float32)
+    y = r.integers(0, 5, n).astype(np.uint8)
+    if live_frac < 1.0:
+        y[r.random(n) > live_frac] = 255
+    return X, y
+
+
+def _grad_close(got, want, rtol):
+    for key in want:
+        w = np.asarray(want[key], np.float64)
+        scale = max(np.abs(w).max(), 1e-6)
+        err = np.abs(np.asarray(got[key], np.float64) - w).max()
+        assert err <= rtol * scale, (key, err, scale)
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 1000, 5000])
+def test_gradient_matches_fp16_network(pair, n):
+    d, g, o = pair
+    X, y = _samples(n, seed=n)
+    p = _random_predictor(5, X)
+    grad, loss = g.mlp_grad(p, cuda(X), cuda(y))
+    Xn = predictor.normalise(X, p["mean"], p["inv_std"])
+    wl, wg = predictor.loss_and_grad16({k: p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}, Xn,
+                                       y.astype(np.int64))
+    assert abs(loss - wl) <= 1e-5 * abs(wl) + 1e-7
+    _grad_close(grad, wg, 2e-3)
+
+
+def test_gradient_skips_unlabelled_samples(pair):
+    """Samples with class 255 add nothing (the mean is over all n samples)."""
+    d, g, o = pair
+    X, y = _samples(3000, seed=9, live_frac=0.6)
+    p = _random_predictor(6, X)
+    grad, loss = g.mlp_grad(p, cuda(X), cuda(y))
+    live = y < 5
+    g2, l2 = g.mlp_grad(p, cuda(X[live]), cuda(y[live]))
+    f = live.sum() / len(y)
+    assert abs(loss - l2 * f) <= 1e-5 * abs(loss)
+    _grad_close(grad, {k: v * f for k, v in g2.items()}, 1e-4)
+
+
+def test_adam_steps_match_oracle(amp, pair):
+    """Two full-batch Adam steps on the GPU vs the oracle's FP64 Adam on the
+    FP16 network's gradients."""
+    d, g, o = pair
+    X, y = _samples(2048, seed=21)
+    p0 = _random_predictor(7, X)
+    lr = 1e-2
+    cfg = amp.train_cfg(epochs=2, batch=len(X), lr=lr, seed=1)
+    got = g.mlp_train(p0, cuda(X), cuda(y), cfg)
+    Xn = predictor.normalise(X, p0["mean"], p0["inv_std"])
+    keys = ("W1", "b1", "W2", "b2", "W3", "b3")
+    w = {k: np.asarray(p0[k], np.float64) for k in keys}
+    m = {k: np.zeros_like(w[k]) for k in keys}
+    v = {k: np.zeros_like(w[k]) for k in keys}
+    small = {k: np.zeros(w[k].shape, bool) for k in keys}
+    for t in (1, 2):
+        _, gr = predictor.loss_and_grad16({k: w[k].astype(np.float32) for k in keys}, Xn, y.astype(np.int64))
+        for k in keys:
+            small[k] |= np.abs(gr[k]) < 1e-4 * max(np.abs(gr[k]).max(), 1e-12)
+        w, m, v = predictor.adam_step(w, gr, m, v, t, lr)
+    for k in keys:
+        diff = np.abs(got[k].astype(np.float64) - w[k])
+        # parameters with clear gradients follow the oracle closely; near-zero
+        # gradients make g / (|g| + eps) sensitive to rounding, but an Adam
+        # step never moves a parameter by more than lr
+        assert diff[~small[k]].max(initial=0) <= 2e-2 * lr, k
+        assert diff.max() <= 2.0 * lr * 1.001, k
+    for k in ("mean", "inv_std"):
+        np.testing.assert_array_equal(got[k], p0[k])
+
+
+def test_train_predictor_learns(amp, pair):
+    """End-to-end training on GPU-made labels beats the best constant
+    predictor, and the installed predictor drives the MLP policy."""
+    d, g, o = pair
+    Qt = _train_queries(d, 300, seed=5)
+    nprobe, k = 8, 10
+    cfg = amp.train_cfg(epochs=30, batch=256, lr=3e-3, seed=2)
+    feat, lab = g.make_training_set(cuda(Qt), nprobe, k)
+    cls = cuda(predictor.bits_to_class(lab.cpu().numpy()).astype(np.uint8))
+    p = g.train_predictor(cuda(Qt), nprobe, k, cfg)
+    _, l_after = g.mlp_grad(p, feat.reshape(-1, 5), cls.reshape(-1))
+    # the best constant predictor's loss is the entropy of the class mix
+    c = cls.cpu().numpy().reshape(-1)
+    f = np.bincount(c, minlength=5) / len(c)
+    entropy = -(f[f > 0] * np.log(f[f > 0])).sum()
+    assert l_after < 0.9 * entropy, (l_after, entropy, f)
+    # accuracy at least that of the majority class
+    Xn = predictor.normalise(feat.cpu().numpy().reshape(-1, 5), p["mean"], p["inv_std"])
+    z = predictor.mlp_logits16(predictor.to_fp16({k2: p[k2] for k2 in ("W1", "b1", "W2", "b2", "W3", "b3")}), Xn)
+    acc = (np.argmax(z, axis=1) == c).mean()
+    assert acc >= np.bincount(c, minlength=5).max() / len(c) - 0.02
+    np.testing.assert_array_equal(g.get_predictor()["W1"], p["W1"])
+    Q = d["queries"]
+    ids, dists = g.search(cuda(Q), nprobe, k, amp.policy("mlp", margin=0.0))
+    torch.cuda.synchronize()
+    bits = g.tap(amp.abi.TAP_BITS, (len(Q), nprobe), np.uint8)
+    ri, rd = ivfpq.search(o, Q, nprobe, k, bits=bits)
+    np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+    np.testing.assert_array_equal(dists.cpu().numpy(), rd)
