@@ -6,6 +6,12 @@ D = 128, nlist = 1024, M = 32, 10k queries, k = 10), queries resident in HBM.
 The index's codes (32 MB) fit in L2, so L2 is flushed (a 512 MB write)
 between timed steps.
 
+The headline policy is the learned predictor: trained on the GPU (labels,
+features, MLP training) from separate training queries, its fallback margin
+calibrated on held-out queries so that it keeps >= 99 % of the plain FP32
+search's top-10. Plain FP32, uniform widths and the Eq. 2 heuristic are timed
+beside it.
+
 Default: python bench.py [--gpus 1 --steps K --warmup W]
 Reference arm: python bench.py --impl reference (the CPU oracle, a bounded sample).
 Under torchrun each rank searches its own replica of the workload (weak
@@ -23,7 +29,11 @@ import tempfile
 import threading
 import time
 
-import numpy as np
+# the CPU oracle baseline is reported as single-threaded: keep BLAS on one thread
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -87,7 +97,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -131,6 +141,23 @@ def time_steps(fn, steps: int, warmup: int, stream, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def nvtx_push(name: str):
+    """Marks the timed region for profilers (a no-op where NVTX is unavailable)."""
+    import torch
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except (RuntimeError, AttributeError):
+        pass
+
+
+def nvtx_pop():
+    import torch
+    try:
+        torch.cuda.nvtx.range_pop()
+    except (RuntimeError, AttributeError):
+        pass
+
+
 def scan_bytes(index, probes: np.ndarray, M: int) -> int:
     """Algorithmic bytes of one scan launch: n_l * M code bytes per probed (query, list)."""
     sizes = index.list_sizes()
@@ -150,26 +177,71 @@ def traffic_from_profile(kernel_src: str, workload_name: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def overlap(a: np.ndarray, b: np.ndarray, k: int) -> float:
+    """Mean fraction of the first k ids of b also found in the first k of a."""
+    return float(np.mean([len(np.intersect1d(x[:k], y[:k])) / k for x, y in zip(a, b)]))
+
+
+def calibrate_margin(index, amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
+    """Smallest MLP fallback margin whose results keep >= target of the plain
+    FP32 top-k on held-out queries (the plain search as judge of the recall
+    loss: losing at most a fraction 1 - target of plain's results costs at most
+    that much recall)."""
+    ref = run(Qc, nprobe, amp.policy("plain"))
+    tried = {}
+    for m in (0.0, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0):
+        ov = overlap(run(Qc, nprobe, amp.policy("mlp", margin=m)), ref, k)
+        tried[m] = ov
+        if ov >= target:
+            return m, tried
+    return float("inf"), tried
+
+
+def calibrate_eq2(amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
+    """Most aggressive Eq. 2 threshold set (t*(4,3,2,1)) keeping >= target of plain."""
+    ref = run(Qc, nprobe, amp.policy("plain"))
+    best, tried = None, {}
+    for t in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0):
+        th = (4 * t, 3 * t, 2 * t, t)
+        ov = overlap(run(Qc, nprobe, amp.policy("eq2", thresholds=th)), ref, k)
+        tried[t] = ov
+        if ov >= target:
+            best = th
+            break
+    return best, tried
+
+
+def bits_mix(index, abi, nq: int, nprobe: int) -> dict:
+    b = index.tap(abi.TAP_BITS, (nq, nprobe), np.uint8).reshape(-1)
+    return {("fp32" if v == 0 else f"{v}bit"): round(float(np.mean(b == v)), 4) for v in (0, 4, 6, 8, 12, 16)}
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_2606_07156_gb300 as amp
     from paper_2606_07156_gb300 import abi
+    from workloads import make_queries
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     cfg, W = workload(args.config, device=dev)
+    if args.nq:
+        W = dict(W, queries=W["queries"][:args.nq], gt=W["gt"][:args.nq])
     index = amp.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"], device=local_rank)
     Q = torch.from_numpy(W["queries"]).to(dev)
     nq, k = Q.shape[0], cfg["k"]
     stream = torch.cuda.current_stream(dev)
     out = (torch.empty((nq, k), dtype=torch.int64, device=dev), torch.empty((nq, k), dtype=torch.float32, device=dev))
 
-    def run(nprobe, pol):
-        ids, _ = index.search(Q, nprobe, k, pol, stream=stream, out=out)
+    def run_q(Qd, nprobe, pol):
+        ids, _ = index.search(Qd, nprobe, k, pol, stream=stream)
         torch.cuda.synchronize()
         return ids.cpu().numpy()
+
+    def run(nprobe, pol):
+        return run_q(Q, nprobe, pol)
 
     # plain FP32 recall sweep; nprobe = smallest reaching recall@10 >= 0.9, else the largest
     sweep = cfg.get("nprobe_sweep", (cfg["nprobe"],)) if args.nprobe is None else (args.nprobe,)
@@ -177,15 +249,33 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     rec_plain = {npb: recall(run(npb, plain), W["gt"], 10) for npb in sweep}
     ok = [npb for npb in sweep if rec_plain[npb] >= 0.9]
     nprobe = ok[0] if ok else max(sweep)
-    # adaptive policy: the fewest uniform bits within 1 recall point of plain at this nprobe
-    chosen, rec_ad = 16, None
+    ref_ids = run(nprobe, plain)
+
+    # learned predictor: labels, features and training on the GPU from training queries
+    ntrain = cfg.get("ntrain", args.ntrain)
+    Qt = torch.from_numpy(make_queries(args.config, ntrain, stream=200)).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    index.train_predictor(Qt, nprobe, k, amp.train_cfg(epochs=args.epochs, batch=1024, lr=3e-3, seed=1))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del Qt
+    Qc = torch.from_numpy(make_queries(args.config, 2000, stream=300)).to(dev)
+    margin, tried = calibrate_margin(index, amp, Qc, nprobe, k, run_q)
+    eq2_th, eq2_tried = calibrate_eq2(amp, Qc, nprobe, k, run_q)
+    del Qc
+    adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38)
+    policies = {"mlp": adaptive, "plain": plain}
+    if eq2_th is not None:
+        policies["eq2"] = amp.policy("eq2", thresholds=eq2_th)
     for b in (4, 6, 8, 12, 16):
-        r = recall(run(nprobe, amp.policy("fixed", bits=b)), W["gt"], 10)
-        if r >= rec_plain[nprobe] - 0.01:
-            chosen, rec_ad = b, r
-            break
-    adaptive = amp.policy("fixed", bits=chosen)
-    log(f"recall@10 plain {rec_plain}, nprobe {nprobe}, fixed {chosen} bits -> {rec_ad}")
+        policies[f"fixed{b}"] = amp.policy("fixed", bits=b)
+    recs, mixes = {}, {}
+    for name, pol in policies.items():
+        ids = run(nprobe, pol)
+        recs[name] = (recall(ids, W["gt"], 10), overlap(ids, ref_ids, k))
+        mixes[name] = bits_mix(index, abi, nq, nprobe)
+    log(f"nprobe {nprobe}; margin {margin} {tried}; eq2 {eq2_th} {eq2_tried}; recalls {recs}")
 
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     if world > 1:
@@ -195,13 +285,18 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     abi.anns_profile(index.handle, 1)
     with ClockSampler(local_rank) as clk:
         t0 = time.perf_counter()
+        nvtx_push("anns_timed")
         ms_ad = time_steps(lambda: index.search(Q, nprobe, k, adaptive, stream=stream, out=out),
                            args.steps, args.warmup, stream, flush)
+        nvtx_pop()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     stage_ms, cnt = abi.anns_profile(index.handle, 0)
-    ms_plain = time_steps(lambda: index.search(Q, nprobe, k, plain, stream=stream, out=out),
-                          args.steps, args.warmup, stream, flush)
+    ms_pol = {"mlp": ms_ad}
+    for name, pol in policies.items():
+        if name != "mlp":
+            ms_pol[name] = time_steps(lambda: index.search(Q, nprobe, k, pol, stream=stream, out=out),
+                                      args.steps, args.warmup, stream, flush)
     # end to end through the host-buffer entry point (pinned in, pinned out)
     Qh = torch.from_numpy(W["queries"]).pin_memory()
     ih = torch.empty((nq, k), dtype=torch.int64).pin_memory()
@@ -218,18 +313,20 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     rec_e2e = recall(ih.numpy(), W["gt"], 10)
     nn10 = nn_in_top(ih.numpy(), W["gt"], 10)
 
-    total_ad = sum(ms_ad) / 1e3
+    totals = {name: sum(v) / 1e3 for name, v in ms_pol.items()}
+    total_e2e = sum(e2e_t)
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([total_ad, sum(ms_plain) / 1e3, sum(e2e_t)], dtype=torch.float64, device=dev)
+        names = sorted(totals)
+        tt = torch.tensor([totals[n] for n in names] + [total_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ad, total_plain, total_e2e = tt.tolist()
-    else:
-        total_plain, total_e2e = sum(ms_plain) / 1e3, sum(e2e_t)
+        vals = tt.tolist()
+        totals = dict(zip(names, vals[:-1]))
+        total_e2e = vals[-1]
     if rank != 0:
+        index.close()
         return None
-    qps = world * nq * args.steps / total_ad
-    qps_plain = world * nq * args.steps / total_plain
+    qps = {name: world * nq * args.steps / t for name, t in totals.items()}
     qps_e2e = world * nq * args.steps / total_e2e
     probes = index.tap(abi.TAP_PROBES, (nq, nprobe), np.int32)
     nbytes = scan_bytes(index, probes, cfg["M"])
@@ -241,33 +338,44 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     src = os.path.join(ROOT, "paper_2606_07156_gb300", "csrc", "search.cu")
     wl = f"{cfg['name']} nq={nq} nprobe={nprobe} k={k}"
     line = {
-        "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ad * 1e3 / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8-lut/i32-acc",
+        "metric": METRIC, "value": round(qps["mlp"], 1), "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(totals["mlp"] * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/u16-lut,i32-acc|f32",
         "data": "synthetic (seeded SIFT-shaped gamma mixture; no public dataset)",
         "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
-                   "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq, "policy": f"fixed-{chosen}bit",
+                   "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
+                   "policy": f"learned MLP per (query, list), fallback margin {margin}",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
-        "recall_at_10": round(rec_ad, 4) if rec_ad is not None else None,
+        "recall_at_10": round(recs["mlp"][0], 4),
+        "top10_kept_vs_plain": round(recs["mlp"][1], 4),
         "nn_in_top10": round(nn10, 4),
-        "plain_fp32": {"qps": round(qps_plain, 1), "recall_at_10": round(rec_plain[nprobe], 4),
-                       "ms_per_step": round(total_plain * 1e3 / args.steps, 4)},
-        "speedup_vs_plain_fp32": round(qps / qps_plain, 3),
+        "bits_mix": mixes["mlp"],
+        "plain_fp32": {"qps": round(qps["plain"], 1), "recall_at_10": round(recs["plain"][0], 4),
+                       "ms_per_step": round(totals["plain"] * 1e3 / args.steps, 4)},
+        "speedup_vs_plain_fp32": round(qps["mlp"] / qps["plain"], 3),
+        "policies": {name: {"qps": round(qps[name], 1), "recall_at_10": round(recs[name][0], 4),
+                            "top10_kept_vs_plain": round(recs[name][1], 4),
+                            "ms_per_step": round(totals[name] * 1e3 / args.steps, 4)} for name in qps},
+        "eq2_thresholds": list(eq2_th) if eq2_th is not None else None,
+        "predictor": {"train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
+                      "margin_calibration_kept": {str(a): round(b, 4) for a, b in tried.items()}},
         "recall_sweep_plain": {str(a): round(b, 4) for a, b in rec_plain.items()},
         "stage_ms_per_step": {n: round(v / max(cnt, 1), 4) for n, v in
-                              zip(("cl_distances", "cl_select", "precision_choice", "lut_scan_topk"), stage_ms)},
+                              zip(("cl_distances", "cl_select", "precision_choice+query_tables",
+                                   "lut_scan_topk"), stage_ms)},
         "roofline": {"bound": "hbm", "kernel": "search_kernel (LUT build + quantise + ADC scan + top-k)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
-                     "traffic": traffic_from_profile(src, wl), "algorithmic_bytes_per_launch": nbytes},
+                     "traffic": traffic_from_profile(src, wl), "algorithmic_bytes_per_launch": nbytes,
+                     "lookups_per_s": round(nbytes / (scan_ms / 1e3), 1)},
         "e2e": {"value": round(qps_e2e, 1), "unit": "queries/s", "h2d_bytes_per_step": int(Qh.numel() * 4),
                 "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4), "recall_at_10": round(rec_e2e, 4)},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(W, cfg, nprobe, chosen, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(W, cfg, nprobe, 8, args.cpu_seconds)
     index.close()
     return line
 
@@ -285,7 +393,8 @@ def cpu_baseline(W, cfg, nprobe: int, bits: int, seconds: float) -> dict:
         done += chunk
     el = time.perf_counter() - t0
     return {"value": round(done / el, 2), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of {len(Qs)} queries, nprobe={nprobe}, {bits}-bit LUTs, numpy single thread",
+            "sample": f"first {done} of {len(Qs)} queries, nprobe={nprobe}, {bits}-bit LUTs for every pair "
+                      "(the oracle's cost per pair is the same for every width), numpy single thread",
             "seconds": round(el, 2)}
 
 
@@ -322,7 +431,7 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
     ap.add_argument("--config", default="B")
@@ -330,6 +439,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
+    ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
+    ap.add_argument("--epochs", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
