@@ -183,14 +183,14 @@ def overlap(a: np.ndarray, b: np.ndarray, k: int) -> float:
 
 
 def calibrate_margin(index, amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
-    """Smallest MLP fallback margin whose results keep >= target of the plain
+    """Smallest MLP round-up margin whose results keep >= target of the plain
     FP32 top-k on held-out queries (the plain search as judge of the recall
     loss: losing at most a fraction 1 - target of plain's results costs at most
-    that much recall)."""
+    that much recall). Widths mapped to this GPU's tables."""
     ref = run(Qc, nprobe, amp.policy("plain"))
     tried = {}
     for m in (0.0, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0):
-        ov = overlap(run(Qc, nprobe, amp.policy("mlp", margin=m)), ref, k)
+        ov = overlap(run(Qc, nprobe, amp.policy("mlp", margin=m, width_map=True)), ref, k)
         tried[m] = ov
         if ov >= target:
             return m, tried
@@ -203,7 +203,7 @@ def calibrate_eq2(amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
     best, tried = None, {}
     for t in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0):
         th = (4 * t, 3 * t, 2 * t, t)
-        ov = overlap(run(Qc, nprobe, amp.policy("eq2", thresholds=th)), ref, k)
+        ov = overlap(run(Qc, nprobe, amp.policy("eq2", thresholds=th, width_map=True)), ref, k)
         tried[t] = ov
         if ov >= target:
             best = th
@@ -264,10 +264,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     margin, tried = calibrate_margin(index, amp, Qc, nprobe, k, run_q)
     eq2_th, eq2_tried = calibrate_eq2(amp, Qc, nprobe, k, run_q)
     del Qc
-    adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38)
+    adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True)
     policies = {"mlp": adaptive, "plain": plain}
     if eq2_th is not None:
-        policies["eq2"] = amp.policy("eq2", thresholds=eq2_th)
+        policies["eq2"] = amp.policy("eq2", thresholds=eq2_th, width_map=True)
     for b in (4, 6, 8, 12, 16):
         policies[f"fixed{b}"] = amp.policy("fixed", bits=b)
     recs, mixes = {}, {}
@@ -344,7 +344,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "data": "synthetic (seeded SIFT-shaped gamma mixture; no public dataset)",
         "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
-                   "policy": f"learned MLP per (query, list), fallback margin {margin}",
+                   "policy": f"learned MLP per (query, list), round-up margin {margin}, GB300 widths "
+                             "(6->8 bits, 12/16->FP32)",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "recall_at_10": round(recs["mlp"][0], 4),
         "top10_kept_vs_plain": round(recs["mlp"][1], 4),

@@ -93,8 +93,16 @@ typedef struct {
   int32_t cl_prec;         /* ANNS_PREC_* for the coarse distances; FP32 only for now */
   int32_t lc_prec;         /* ANNS_PREC_* for the LUT build; FP32 only for now */
   float eq2_thresholds[4]; /* HEURISTIC_EQ2: g thresholds for 4, 6, 8, 12 bits */
-  float fallback_margin;   /* MLP: FP32 LUT when top1 - top2 logit < margin */
+  float fallback_margin;   /* MLP round-up margin tau >= 0: the fewest bits b such that
+                              fl32(max logit over widths <= b - max logit over wider
+                              widths) >= tau (16 bits if none); tau = 0 is the argmax,
+                              ties to the narrower width. A larger tau rounds uncertain
+                              pairs up, towards full precision. */
   const uint8_t* pair_bits;/* EXPLICIT: device [nq * nprobe], 0 = FP32 */
+  int32_t width_map;       /* HEURISTIC_EQ2 / MLP: 0 = widths as chosen; 1 = widths
+                              mapped to this GPU's tables: 6 -> 8 bits (same table
+                              cost, finer levels), 12 and 16 -> FP32 (a 16-bit table
+                              gathers as slowly as FP32 and FP32 is exact) */
 } anns_precision_policy;
 
 /* Batched search (Section 2.1, stages CL -> RC -> LC -> DC -> TS).

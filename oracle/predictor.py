@@ -269,17 +269,29 @@ def mlp_logits16(p16: dict, Xn: np.ndarray) -> np.ndarray:
     return _layer16(p16["W3"], p16["b3"], h2, False)
 
 
-def decide_bits(z: np.ndarray, margin: float) -> np.ndarray:
-    """argmax (ties to the lower class) -> bits; FP32 (0) when top1 - top2 < margin."""
+def decide_bits(z: np.ndarray, tau: float) -> np.ndarray:
+    """Round-up rule on the FP32 logits of the widths 4, 6, 8, 12, 16: the
+    fewest bits c such that fl32(max_{i <= c} z_i - max_{i > c} z_i) >= tau,
+    16 bits when no narrower width qualifies. tau = 0 gives the argmax with
+    ties to the narrower width; a larger tau moves uncertain pairs to wider
+    tables (towards full precision)."""
     z = np.asarray(z, dtype=F32)
-    cls = np.argmax(z, axis=1)
-    top1 = z[np.arange(len(z)), cls]
-    zz = z.copy()
-    zz[np.arange(len(z)), cls] = -np.inf
-    top2 = zz.max(axis=1)
-    bits = np.asarray(BITS, dtype=np.uint8)[cls]
-    gap = (top1 - top2).astype(F32)
-    return np.where(gap < F32(margin), np.uint8(0), bits)
+    n = z.shape[0]
+    out = np.full(n, BITS[-1], dtype=np.uint8)
+    done = np.zeros(n, dtype=bool)
+    for c in range(len(BITS) - 1):
+        lo = z[:, :c + 1].max(axis=1)
+        hi = z[:, c + 1:].max(axis=1)
+        ok = ~done & ((lo - hi).astype(F32) >= F32(tau))
+        out[ok] = BITS[c]
+        done |= ok
+    return out
+
+
+def gpu_width(bits: np.ndarray) -> np.ndarray:
+    """Widths mapped to GB300 tables: 6 -> 8 bits, 12 and 16 -> FP32 (0)."""
+    b = np.asarray(bits, dtype=np.uint8)
+    return np.where(b == 6, np.uint8(8), np.where((b == 12) | (b == 16), np.uint8(0), b)).astype(np.uint8)
 
 
 def bits_to_class(bits: np.ndarray) -> np.ndarray:

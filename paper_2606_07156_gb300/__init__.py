@@ -19,8 +19,10 @@ _MODES = {"plain": abi.LUT_PLAIN_FP32, "fixed": abi.LUT_FIXED_BITS, "eq2": abi.L
 
 
 def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), margin: float = 0.0,
-           pair_bits=None) -> abi.anns_precision_policy:
-    """Builds an anns_precision_policy. ``pair_bits`` (EXPLICIT) is a uint8 CUDA tensor."""
+           pair_bits=None, width_map: bool = False) -> abi.anns_precision_policy:
+    """Builds an anns_precision_policy. ``pair_bits`` (EXPLICIT) is a uint8 CUDA tensor;
+    ``margin`` is the MLP round-up margin; ``width_map`` maps EQ2/MLP widths to this
+    GPU's tables (6 -> 8 bits, 12 and 16 -> FP32)."""
     p = abi.anns_precision_policy()
     p.lut_mode = _MODES[mode]
     p.fixed_bits = int(bits)
@@ -30,6 +32,7 @@ def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), 
         p.eq2_thresholds[i] = float(t)
     p.fallback_margin = float(margin)
     p.pair_bits = None if pair_bits is None else pair_bits.data_ptr()
+    p.width_map = 1 if width_map else 0
     return p
 
 

@@ -50,7 +50,7 @@ class anns_precision_policy(ctypes.Structure):
     _fields_ = [("lut_mode", ctypes.c_int32), ("fixed_bits", ctypes.c_int32),
                 ("cl_prec", ctypes.c_int32), ("lc_prec", ctypes.c_int32),
                 ("eq2_thresholds", ctypes.c_float * 4), ("fallback_margin", ctypes.c_float),
-                ("pair_bits", ctypes.c_void_p)]
+                ("pair_bits", ctypes.c_void_p), ("width_map", ctypes.c_int32)]
 
 
 class anns_index_info(ctypes.Structure):

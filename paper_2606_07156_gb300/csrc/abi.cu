@@ -14,7 +14,7 @@ struct PolicyArgs {
   int64_t nq; int nprobe; const int32_t* npq;
   const int32_t* probes; const float* probe_d2;
   const int32_t* list_len; const float* radius;
-  int mode, fixed_bits; float th[4]; float margin;
+  int mode, fixed_bits; float th[4]; float margin; int width_map;
   const uint8_t* pair_bits; const void* mlp;
   uint8_t* bits; float* feat;
 };
@@ -47,6 +47,10 @@ __device__ __forceinline__ uint8_t eq2_bits(const float f[5], const float th[4])
   return b;
 }
 
+// Widths on this GPU's tables: 6 -> 8 bits (byte tables either way, finer
+// levels), 12 and 16 -> FP32 (a 16-bit table gathers as slowly as FP32).
+__device__ __forceinline__ uint8_t gpu_width(uint8_t b) { return b == 6 ? 8 : (b == 12 || b == 16) ? 0 : b; }
+
 __global__ void policy_kernel(const PolicyArgs p) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= p.nq * p.nprobe) return;
@@ -64,10 +68,12 @@ __global__ void policy_kernel(const PolicyArgs p) {
       case ANNS_LUT_HEURISTIC_EQ2:
         features_of(p, q, j, np, f);
         b = eq2_bits(f, p.th);
+        if (p.width_map) b = gpu_width(b);
         break;
       case ANNS_LUT_MLP:
         features_of(p, q, j, np, f);
         b = mlp_decide(*(const MlpParams16*)p.mlp, f, p.margin);
+        if (p.width_map) b = gpu_width(b);
         break;
     }
   }
@@ -108,7 +114,7 @@ int ensure_workspace(Index& ix, int64_t nq, int nprobe) {
 int table_bytes_for(const anns_precision_policy& P) {
   switch (P.lut_mode) {
     case ANNS_LUT_FIXED_BITS: return P.fixed_bits <= 8 ? 1 : 2;
-    case ANNS_LUT_HEURISTIC_EQ2: return 2;   // 4..16 bits, never the FP32 table
+    case ANNS_LUT_HEURISTIC_EQ2: return P.width_map ? 4 : 2;  // 4..16 bits, or FP32 when mapped
     default: return 4;                       // plain, explicit, MLP (with FP32 fallback)
   }
 }
@@ -178,6 +184,7 @@ int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq,
   p.fixed_bits = pol.fixed_bits;
   for (int i = 0; i < 4; ++i) p.th[i] = pol.eq2_thresholds[i];
   p.margin = pol.fallback_margin; p.pair_bits = pol.pair_bits; p.mlp = ix.mlp_dev;
+  p.width_map = pol.width_map;
   p.bits = bits; p.feat = feat;
   const int64_t n = nq * nprobe;
   policy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
@@ -210,6 +217,7 @@ static int check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t
         break;
       case ANNS_LUT_MLP:
         if (!ix->has_mlp) return fail(ANNS_ERR_INVALID_ARG, "MLP policy needs a trained or loaded predictor");
+        if (!(pol->fallback_margin >= 0.f)) return fail(ANNS_ERR_INVALID_ARG, "MLP round-up margin must be >= 0");
         break;
       default: return fail(ANNS_ERR_INVALID_ARG, "unknown lut_mode");
     }

@@ -22,7 +22,7 @@ struct MlpParams16 {
   float mean[5], inv_std[5];
 };
 
-__device__ __forceinline__ uint8_t mlp_decide(const MlpParams16& P, const float f[5], float margin) {
+__device__ __forceinline__ uint8_t mlp_decide(const MlpParams16& P, const float f[5], float tau) {
   constexpr uint8_t kBits[5] = {4, 6, 8, 12, 16};
   float x[5];
 #pragma unroll
@@ -52,15 +52,18 @@ __device__ __forceinline__ uint8_t mlp_decide(const MlpParams16& P, const float 
     for (int i = 0; i < 32; ++i) acc = fmaf(__half2float(P.W3[o * 32 + i]), h2[i], acc);
     z[o] = acc;
   }
-  int c = 0;
+  // the fewest bits c whose best logit (widths <= c) beats every wider width by tau
+  int c = 4;
+  float lo = -INFINITY;
 #pragma unroll
-  for (int o = 1; o < 5; ++o)
-    if (z[o] > z[c]) c = o;
-  float t2 = -INFINITY;
+  for (int cc = 0; cc < 4; ++cc) {
+    lo = fmaxf(lo, z[cc]);
+    float hi = -INFINITY;
 #pragma unroll
-  for (int o = 0; o < 5; ++o)
-    if (o != c) t2 = fmaxf(t2, z[o]);
-  return sub_rn(z[c], t2) < margin ? (uint8_t)0 : kBits[c];
+    for (int o = cc + 1; o < 5; ++o) hi = fmaxf(hi, z[o]);
+    if (c == 4 && sub_rn(lo, hi) >= tau) c = cc;
+  }
+  return kBits[c];
 }
 
 }  // namespace anns

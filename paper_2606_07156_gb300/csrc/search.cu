@@ -32,7 +32,8 @@ struct PairScal {
 };
 
 // Offsets from a 256-byte aligned base inside the block's dynamic shared
-// memory (256 bytes of slack are allocated for the alignment).
+// memory (256 bytes of slack are allocated for the alignment): the FP32 table
+// T, the level table q (1 or 2 bytes an entry), row statistics and scales.
 struct SmemLayout {
   size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, d2 = 0, md = 0, mi = 0, total = 0;
   static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
@@ -68,12 +69,77 @@ struct Smem {
   }
 };
 
-// Steps 1-2 for one pair: all threads of the block take part. P and qt2 are
-// the pair's list table and query table ([Mp * 256], rows M..Mp-1 zero).
-// Warp w builds rows m = w, w + nwarps, ...; lane i owns entries 8i..8i+7 of
-// a row, so each row's minimum and range come from warp shuffles during the
-// build, and each warp quantises the rows it built (two block barriers for a
-// b-bit pair, one for an FP32 pair).
+// Round to nearest (ties to even) of y in [0, 2^22), read from the low bits of
+// fl32(y + 1.5 * 2^23): the sum lies in [2^23, 2^24), where consecutive FP32
+// values are 1 apart, so the IEEE addition itself rounds y to the nearest
+// integer n and the result's bit pattern is 0x4B400000 + n.
+__device__ __forceinline__ uint32_t rint_bits(float y) { return __float_as_uint(add_rn(y, 12582912.0f)); }
+
+// Per-pair step Delta and offset B from the row statistics `bias`, `rowmax`
+// (every warp derives the shared step; warp 0 also the offset B in FP64, row
+// minima summed in the fixed 32-lane tree order, plus D2, and writes *out).
+// The FP64 step delta64 (an FP64 division) is only computed for the taps.
+// Returns s32.
+template <bool WITH_D64>
+__device__ __forceinline__ float pair_scale(int M, int b, float d2, const float* bias, const float* rowmax,
+                                            PairScal* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float range = 0.f;
+  for (int m = lane; m < M; m += 32) range = fmaxf(range, rowmax[m]);
+  range = warp_max(range);
+  const int L = (1 << b) - 1;
+  // fl32 of the FP64 quotient equals the correctly rounded FP32 quotient
+  const float s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
+  if (warp == 0) {
+    double B = 0.0;
+    for (int m = lane; m < M; m += 32) B = __dadd_rn(B, (double)bias[m]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+    if (lane == 0) {
+      PairScal sc;
+      sc.delta64 = WITH_D64 && range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
+      sc.s32 = s32;
+      sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
+      sc.B64 = __dadd_rn((double)d2, B);
+      sc.B32 = __double2float_rn(sc.B64);
+      sc.range = range;
+      sc.L = L;
+      *out = sc;
+    }
+  }
+  return s32;
+}
+
+// Levels of 8 entries of one row: t = rint(fl32(fl32(T' - bias) * s32)).
+// min(t, L) of the rule never binds: T' - bias <= range and s32 <= (L / range)
+// (1 + 2^-24), so the product rounds to at most L + ulp(L) < L + 1/2.
+__device__ __forceinline__ void quantise8(const float (&x)[8], float mn, float s32, uint32_t (&n)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) n[e] = rint_bits(mul_rn(sub_rn(x[e], mn), s32));
+}
+
+// Packs 8 levels (low bits of n) into the table row at `dst`, 1 or 2 bytes each.
+__device__ __forceinline__ void store_levels(int b, const uint32_t (&n)[8], void* dst) {
+  if (b <= 8) {
+    uint2 v;
+    v.x = __byte_perm(__byte_perm(n[0], n[1], 0x0040), __byte_perm(n[2], n[3], 0x0040), 0x5410);
+    v.y = __byte_perm(__byte_perm(n[4], n[5], 0x0040), __byte_perm(n[6], n[7], 0x0040), 0x5410);
+    *(uint2*)dst = v;
+  } else {
+    uint4 v;
+    v.x = __byte_perm(n[0], n[1], 0x5410); v.y = __byte_perm(n[2], n[3], 0x5410);
+    v.z = __byte_perm(n[4], n[5], 0x5410); v.w = __byte_perm(n[6], n[7], 0x5410);
+    *(uint4*)dst = v;
+  }
+}
+
+// Steps 1-2 for one pair, T' staged in shared memory (any Mp): all threads of
+// the block take part. P and qt2 are the pair's list table and query table
+// ([Mp * 256], rows M..Mp-1 zero). Warp w builds rows m = w, w + nwarps, ...;
+// lane i owns entries 8i..8i+7 of a row, so each row's minimum and range come
+// from warp shuffles during the build, and each warp quantises the rows it
+// built (two block barriers for a b-bit pair, one for an FP32 pair). The FP32
+// T' stays in shared memory for every pair (the LUT taps read it).
 __device__ void build_lut(const float* __restrict__ P, const float* __restrict__ qt2, int M, int Mp,
                           int b, float d2, Smem& s) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -105,57 +171,86 @@ __device__ void build_lut(const float* __restrict__ P, const float* __restrict__
   }
   __syncthreads();
   if (b == 0) return;
-  // every warp derives the shared step; warp 0 also the offset B (FP64,
-  // row minima in the fixed 32-lane tree order, plus D2)
-  float range = 0.f;
-  for (int m = lane; m < M; m += 32) range = fmaxf(range, s.rowmax[m]);
-  range = warp_max(range);
-  const int L = (1 << b) - 1;
-  // fl32 of the FP64 quotient equals the correctly rounded FP32 quotient
-  const float s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
-  if (warp == 0) {
-    double B = 0.0;
-    for (int m = lane; m < M; m += 32) B = __dadd_rn(B, (double)s.bias[m]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
-    if (lane == 0) {
-      PairScal sc;
-      sc.delta64 = range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
-      sc.s32 = s32;
-      sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
-      sc.B64 = __dadd_rn((double)d2, B);
-      sc.B32 = __double2float_rn(sc.B64);
-      sc.range = range;
-      sc.L = L;
-      *s.sc = sc;
-    }
-  }
+  const float s32 = pair_scale<true>(M, b, d2, s.bias, s.rowmax, s.sc);
+  const size_t esz = b <= 8 ? 1 : 2;
   for (int m = warp; m < Mp; m += nwarps) {
-    unsigned t[8];
+    float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float mn = 0.f;
     if (m < M) {
-      const float mn = s.bias[m];
+      mn = s.bias[m];
       const float4* src = (const float4*)(s.T + m * kKsub + lane * 8);
       const float4 u = src[0], v = src[1];
-      const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int e = 0; e < 8; ++e) t[e] = (unsigned)min(__float2int_rn(mul_rn(sub_rn(x[e], mn), s32)), L);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) t[e] = 0u;
+      x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w; x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
     }
-    if (b <= 8) {
-      uint2 v;
-      v.x = t[0] | (t[1] << 8) | (t[2] << 16) | (t[3] << 24);
-      v.y = t[4] | (t[5] << 8) | (t[6] << 16) | (t[7] << 24);
-      *(uint2*)((uint8_t*)s.q + m * kKsub + lane * 8) = v;
+    uint32_t n[8];
+    quantise8(x, mn, s32, n);
+    store_levels(b, n, (uint8_t*)s.q + (m * kKsub + lane * 8) * esz);
+  }
+  __syncthreads();
+}
+
+// Steps 1-2 with T' kept in registers (Mp == RPW * warps of the block): warp w
+// owns rows w + r * nwarps, r < RPW. An FP32 pair stores T' into `T`; a
+// quantised pair never writes T', each warp quantising its rows from
+// registers into `lv` once the block-wide range is known (same values as
+// build_lut, one block barrier fewer and no FP32 round trip through shared
+// memory). One barrier between the row statistics and the scale; the caller
+// synchronises before reading the tables.
+template <int RPW>
+__device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, const float* __restrict__ qt2,
+                                               int M, int b, float d2, float* T, void* lv, float* bias,
+                                               float* rowmax, PairScal* sc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  float t[RPW][8];
+  float mn[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int m = warp + r * nwarps;
+    mn[r] = 0.f;
+    if (m < M) {
+      const float4* pr = (const float4*)(P + m * kKsub + lane * 8);
+      const float4* qr = (const float4*)(qt2 + m * kKsub + lane * 8);
+      const float4 p0 = __ldg(pr), p1 = __ldg(pr + 1), q0 = __ldg(qr), q1 = __ldg(qr + 1);
+      t[r][0] = sub_rn(p0.x, q0.x); t[r][1] = sub_rn(p0.y, q0.y);
+      t[r][2] = sub_rn(p0.z, q0.z); t[r][3] = sub_rn(p0.w, q0.w);
+      t[r][4] = sub_rn(p1.x, q1.x); t[r][5] = sub_rn(p1.y, q1.y);
+      t[r][6] = sub_rn(p1.z, q1.z); t[r][7] = sub_rn(p1.w, q1.w);
     } else {
-      uint4 v;
-      v.x = t[0] | (t[1] << 16); v.y = t[2] | (t[3] << 16);
-      v.z = t[4] | (t[5] << 16); v.w = t[6] | (t[7] << 16);
-      *(uint4*)((uint16_t*)s.q + m * kKsub + lane * 8) = v;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) t[r][e] = 0.f;
+    }
+  }
+  if (b == 0) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      float4* dst = (float4*)(T + (warp + r * nwarps) * kKsub + lane * 8);
+      dst[0] = make_float4(t[r][0], t[r][1], t[r][2], t[r][3]);
+      dst[1] = make_float4(t[r][4], t[r][5], t[r][6], t[r][7]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int m = warp + r * nwarps;
+    if (m < M) {
+      float lo = t[r][0], hi = t[r][0];
+#pragma unroll
+      for (int e = 1; e < 8; ++e) { lo = fminf(lo, t[r][e]); hi = fmaxf(hi, t[r][e]); }
+      mn[r] = warp_min(lo);
+      // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
+      const float mx = sub_rn(warp_max(hi), mn[r]);
+      if (lane == 0) { bias[m] = mn[r]; rowmax[m] = mx; }
     }
   }
   __syncthreads();
+  const float s32 = pair_scale<false>(M, b, d2, bias, rowmax, sc);
+  const size_t esz = b <= 8 ? 1 : 2;
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    uint32_t n[8];
+    quantise8(t[r], mn[r], s32, n);
+    store_levels(b, n, (uint8_t*)lv + ((warp + r * nwarps) * kKsub + lane * 8) * esz);
+  }
 }
 
 template <int NCHUNK>
@@ -170,12 +265,14 @@ __device__ __forceinline__ float dequant(int S, const PairScal& sc) {
 }
 
 // Distance of the vector whose code tile words are w, for a pair whose table
-// was built with `b` bits (0 = FP32) and coarse distance d2.
+// was built with `b` bits (0 = FP32, at T_addr; else levels at q_addr) and
+// coarse distance d2.
 template <int NCHUNK>
-__device__ __forceinline__ float pair_distance(int b, float d2, const Smem& s, const PairScal& sc,
-                                               const uint4 (&w)[NCHUNK], int* S_out = nullptr) {
-  if (b == 0) return add_rn(d2, adc_f32<NCHUNK>(s.T_addr, w));
-  const int S = b <= 8 ? adc_int<uint8_t, NCHUNK>(s.q_addr, w) : adc_int<uint16_t, NCHUNK>(s.q_addr, w);
+__device__ __forceinline__ float pair_distance(int b, float d2, uint32_t T_addr, uint32_t q_addr,
+                                               const PairScal& sc, const uint4 (&w)[NCHUNK],
+                                               int* S_out = nullptr) {
+  if (b == 0) return add_rn(d2, adc_f32<NCHUNK>(T_addr, w));
+  const int S = b <= 8 ? adc_int<uint8_t, NCHUNK>(q_addr, w) : adc_int<uint16_t, NCHUNK>(q_addr, w);
   if (S_out) *S_out = S;
   return dequant(S, sc);
 }
@@ -192,8 +289,44 @@ struct SearchArgs {
   SmemLayout lay;
 };
 
+// End of a query: the warps' lists are merged into warp 0, which writes the
+// query's k results (padding id -1, distance +inf). Ends with a barrier.
+template <int R>
+__device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, WarpTopK<R, int64_t>& top,
+                                                int64_t q, int kq, float& thd, int64_t& thi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    s.md[(warp * R + r) * 32 + lane] = top.d[r];
+    s.mi[(warp * R + r) * 32 + lane] = top.id[r];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int w2 = 1; w2 < kWarps && kq > 0; ++w2)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float cd = s.md[(w2 * R + r) * 32 + lane];
+        const int64_t ci = s.mi[(w2 * R + r) * 32 + lane];
+        top.offer(cd != INFINITY, cd, ci, kq, thd, thi);
+      }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = r * 32 + lane;
+      if (e < a.k) {
+        const bool ok = e < kq && top.d[r] != INFINITY;
+        a.ids_out[q * a.k + e] = ok ? top.id[r] : -1;
+        a.dists_out[q * a.k + e] = ok ? top.d[r] : INFINITY;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Query-major search: one query per block at a time. Per pair the block builds
+// the table (in registers for Mp <= 32, else staged in shared memory), then
+// every warp scans tiles of the list. Four blocks per SM for Mp <= 32.
 template <int NCHUNK, int R>
-__global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? 4 : 1) search_kernel(const SearchArgs a) {
   Smem s(a.lay);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tstride = (int64_t)a.Mp * kKsub;
@@ -211,7 +344,13 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
       if (n_l == 0) continue;
       const int b = a.bits[q * a.nprobe + j];
       const float d2 = a.probe_d2[q * a.nprobe + j];
-      build_lut(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
+      if constexpr (NCHUNK <= 2) {
+        build_lut_regs<NCHUNK * 16 / kWarps>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, b, d2,
+                                             s.T, s.q, s.bias, s.rowmax, s.sc);
+        __syncthreads();
+      } else {
+        build_lut(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
+      }
       const PairScal sc = *s.sc;
       const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
       const uint8_t* tp = a.codes + ((size_t)a.tile_off[l] * NCHUNK + 0) * kTileChunkBytes +
@@ -220,7 +359,7 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
       for (int t = warp; t < ntile; t += kWarps, tp += (size_t)kWarps * NCHUNK * kTileChunkBytes) {
         uint4 w[NCHUNK];
         load_tile<NCHUNK>(tp, lane, w);
-        const float d = pair_distance<NCHUNK>(b, d2, s, sc, w);
+        const float d = pair_distance<NCHUNK>(b, d2, s.T_addr, s.q_addr, sc, w);
         const int v = t * kTileVecs + lane;
         const bool pre = v < n_l && d <= thd;
         if (__any_sync(kFull, pre)) {
@@ -230,32 +369,7 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const SearchArgs a) {
       }
       __syncthreads();  // the next pair overwrites the LUT
     }
-    // merge the per-warp lists into warp 0
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      s.md[(warp * R + r) * 32 + lane] = top.d[r];
-      s.mi[(warp * R + r) * 32 + lane] = top.id[r];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int w2 = 1; w2 < kWarps && kq > 0; ++w2)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float cd = s.md[(w2 * R + r) * 32 + lane];
-          const int64_t ci = s.mi[(w2 * R + r) * 32 + lane];
-          top.offer(cd != INFINITY, cd, ci, kq, thd, thi);
-        }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int e = r * 32 + lane;
-        if (e < a.k) {
-          const bool ok = e < kq && top.d[r] != INFINITY;
-          a.ids_out[q * a.k + e] = ok ? top.id[r] : -1;
-          a.dists_out[q * a.k + e] = ok ? top.d[r] : INFINITY;
-        }
-      }
-    }
-    __syncthreads();
+    merge_and_write<R>(a, s, top, q, kq, thd, thi);
   }
 }
 
@@ -326,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) scan_pairs_kernel(const SearchArgs a
       load_tile<NCHUNK>(base + (size_t)t * NCHUNK * kTileChunkBytes, lane, w);
       const int v = t * kTileVecs + lane;
       int S = 0;
-      const float d = pair_distance<NCHUNK>(b, d2, s, sc, w, &S);
+      const float d = pair_distance<NCHUNK>(b, d2, s.T_addr, s.q_addr, sc, w, &S);
       if (v < n_l) {
         dist_out[off[p] + v] = d;
         if (S_out) S_out[off[p] + v] = S;
@@ -355,14 +469,18 @@ cudaError_t prep(K kernel, size_t smem) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int NCHUNK, int R>
-cudaError_t run_search(const SearchArgs& a, cudaStream_t s) {
-  auto kern = search_kernel<NCHUNK, R>;
+template <typename K>
+cudaError_t launch_query_major(K kern, const SearchArgs& a, cudaStream_t s) {
   cudaError_t e = prep(kern, a.lay.total);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::min<int64_t>(a.nq, 1 << 30);
   kern<<<grid, kThreads, a.lay.total, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int NCHUNK, int R>
+cudaError_t run_search(const SearchArgs& a, cudaStream_t s) {
+  return launch_query_major(search_kernel<NCHUNK, R>, a, s);
 }
 
 template <int NCHUNK>

@@ -40,8 +40,11 @@ def test_every_declared_symbol_is_exported(abi):
 
 def test_struct_layouts(abi):
     assert ctypes.sizeof(abi.anns_build_desc) == 5 * 8 + 5 * 8 + 2 * 4
-    assert ctypes.sizeof(abi.anns_precision_policy) == 4 * 4 + 4 * 4 + 4 + 4 + 8
+    assert ctypes.sizeof(abi.anns_precision_policy) == 4 * 4 + 4 * 4 + 4 + 4 + 8 + 8
     assert abi.anns_precision_policy.pair_bits.offset == 40
+    assert abi.anns_precision_policy.width_map.offset == 48
+    assert ctypes.sizeof(abi.anns_predictor) == 4 * (160 + 32 + 1024 + 32 + 160 + 5 + 5 + 5)
+    assert ctypes.sizeof(abi.anns_train_cfg) == 4 + 4 + 4 + 4 + 8
 
 
 def test_argument_errors_without_gpu(abi):

@@ -184,6 +184,21 @@ def test_search_eq2_policy(amp, case_a):
     np.testing.assert_array_equal(dists.cpu().numpy(), rd)
 
 
+def test_search_eq2_policy_width_map(amp, case_a):
+    d, ix, g, o = case_a
+    Q = d["queries"]
+    th = (2.0, 1.0, 0.0, -1.0)
+    ids, dists = g.search(cuda(Q), 6, 10, amp.policy("eq2", thresholds=th, width_map=True))
+    torch.cuda.synchronize()
+    D2 = ivfpq.coarse_d2_fp32(Q, o.centroids)
+    probes, pd = ivfpq.locate(D2, 6)
+    bits = predictor.gpu_width(predictor.eq2_bits(predictor.features(pd, probes, o.radius, o.sizes), th))
+    np.testing.assert_array_equal(g.tap(amp.abi.TAP_BITS, (len(Q), 6), np.uint8), bits)
+    ri, rd = ivfpq.search(o, Q, 6, 10, bits=bits)
+    np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+    np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+
+
 def test_per_query_nprobe_and_k(amp, case_a):
     d, ix, g, o = case_a
     Q = d["queries"]

@@ -96,8 +96,8 @@ def test_training_set_fewer_candidates_than_k(amp):
 
 # ------------------------------------------------------------------ inference
 
-@pytest.mark.parametrize("margin", [0.0, 0.5, 2.0])
-def test_mlp_policy_bit_exact(amp, pair, margin):
+@pytest.mark.parametrize("margin,wmap", [(0.0, False), (0.5, False), (2.0, False), (0.0, True), (1.0, True)])
+def test_mlp_policy_bit_exact(amp, pair, margin, wmap):
     d, g, o = pair
     Q = d["queries"]
     nprobe = 7
@@ -109,12 +109,14 @@ def test_mlp_policy_bit_exact(amp, pair, margin):
     back = g.get_predictor()
     for key in p:
         np.testing.assert_array_equal(back[key], np.asarray(p[key], np.float32))
-    ids, dists = g.search(cuda(Q), nprobe, 10, amp.policy("mlp", margin=margin))
+    ids, dists = g.search(cuda(Q), nprobe, 10, amp.policy("mlp", margin=margin, width_map=wmap))
     torch.cuda.synchronize()
     np.testing.assert_array_equal(g.tap(amp.abi.TAP_FEATURES, (len(Q), nprobe, 5), np.float32), F)
     Xn = predictor.normalise(F.reshape(-1, 5), p["mean"], p["inv_std"])
     z = predictor.mlp_logits16(predictor.to_fp16({k: p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}), Xn)
     bits = predictor.decide_bits(z, margin).reshape(len(Q), nprobe)
+    if wmap:
+        bits = predictor.gpu_width(bits)
     got = g.tap(amp.abi.TAP_BITS, (len(Q), nprobe), np.uint8)
     np.testing.assert_array_equal(got, bits)
     if margin == 0.5:

@@ -307,10 +307,41 @@ def test_fp16_inference_rule_close_to_fp64():
     assert np.max(np.abs(z16 - z64)) <= 4 * 2.0 ** -11 * (np.abs(z64).max() + 1)
 
 
-def test_decide_bits_margin_and_ties():
+def test_decide_bits_round_up_and_ties():
     z = np.array([[1, 3, 3, 0, 0], [5, 0, 0, 0, 0], [0, 0, 0, 2.0, 1.9]], dtype=np.float32)
     np.testing.assert_array_equal(predictor.decide_bits(z, 0.0), [6, 4, 12])
-    np.testing.assert_array_equal(predictor.decide_bits(z, 0.5), [0, 4, 0])
+    np.testing.assert_array_equal(predictor.decide_bits(z, 0.5), [8, 4, 16])
+    np.testing.assert_array_equal(predictor.gpu_width(predictor.decide_bits(z, 0.0)), [8, 4, 0])
+    np.testing.assert_array_equal(predictor.gpu_width([4, 6, 8, 12, 16, 0]), [4, 8, 8, 0, 0, 0])
+
+
+def test_decide_bits_against_brute_force():
+    """tau = 0 is the argmax (ties to the narrower width); in general the
+    chosen width is the fewest c such that every wider logit is beaten by
+    tau by some logit at or below c (checked pair by pair); the width never
+    shrinks as tau grows."""
+    r = np.random.Generator(np.random.PCG64(5))
+    z = r.integers(-3, 4, size=(400, 5)).astype(np.float32) * np.float32(0.5)
+    z[:200] += r.standard_normal((200, 5)).astype(np.float32)
+    am = np.argmax(z, axis=1)
+    np.testing.assert_array_equal(predictor.decide_bits(z, 0.0), np.asarray(predictor.BITS)[am])
+    prev = None
+    for tau in (0.0, 0.25, 0.5, 1.0, 3.0, np.inf):
+        got = predictor.decide_bits(z, tau)
+        want = []
+        for row in z:
+            pick = 16
+            for c in range(4):
+                if all(any(np.float32(row[i2] - row[i]) >= np.float32(tau) for i2 in range(c + 1))
+                       for i in range(c + 1, 5)):
+                    pick = predictor.BITS[c]
+                    break
+            want.append(pick)
+        np.testing.assert_array_equal(got, want)
+        if prev is not None:
+            assert np.all(got >= prev)
+        prev = got
+    assert np.all(prev == 16)
 
 
 # ------------------------------------------------------- P8: Eq. 1 / Eq. 2 features
