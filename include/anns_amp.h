@@ -197,18 +197,58 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
  *      (query, list) pair, blocks of pairs sharing a list, work items taken
  *      largest list first; then a per-query merge of the pairs' top-k.
  *      UNSUPPORTED at search time if one table does not fit.
- * Both kernels return identical results. Errors: INVALID_ARG. */
-enum { ANNS_OPT_KERNEL = 0 };
+ *  ANNS_OPT_SCHEDULE: the order in which the query-major kernel takes queries
+ *    (the greedy load scheduling of Section 4.3, applied to queries).
+ *    ANNS_SCHED_AUTO (default): longest first when nprobe_per_q is given (an
+ *      uneven batch), else in query order.
+ *    ANNS_SCHED_NATURAL: query order.
+ *    ANNS_SCHED_LPT: longest first by the estimated cost sum over the probed
+ *      lists of (list size + 768), bucketed within 12.5 %.
+ * Every kernel and schedule returns identical results. Errors: INVALID_ARG. */
+enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1 };
 enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2 };
+enum { ANNS_SCHED_AUTO = 0, ANNS_SCHED_NATURAL = 1, ANNS_SCHED_LPT = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);
+
+/* A whole search (the calls of anns_search) captured once as a CUDA graph on
+ * fixed device buffers and replayed with one launch. The graph owns its own
+ * workspace (allocated at capture), so searches on the index and other
+ * graphs do not disturb it; the index arrays, options and installed predictor
+ * are shared (the graph uses the kernel and schedule options set at capture,
+ * and the predictor's current weights at each replay). The caller keeps the
+ * buffers alive and may rewrite queries / nprobe_per_q / k_per_q / pair_bits
+ * between replays; the graph must be freed before the index. Capture runs the
+ * search once (outputs are written) and synchronises. Errors as anns_search. */
+typedef struct anns_graph anns_graph;
+int anns_graph_capture(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
+                       const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,
+                       const anns_precision_policy* policy, int64_t* ids_out, float* dists_out,
+                       anns_graph** out);
+int anns_graph_launch(anns_graph* graph, void* cuda_stream);
+void anns_graph_free(anns_graph* graph);
+
+/* Autotuner: times every available (kernel, schedule) configuration on the
+ * given batch (reps timed searches each, after one untimed), installs the
+ * fastest as the index's options and reports all of them (at most cap, in
+ * trial order) with their mean milliseconds. Uses temporary output buffers;
+ * synchronous. Errors as anns_search, plus INVALID_ARG for reps outside
+ * [1, 1000]. */
+typedef struct {
+  int32_t kernel, schedule; /* ANNS_KERNEL_*, ANNS_SCHED_* */
+  float ms;                 /* mean time of one search */
+} anns_tune_result;
+int anns_autotune(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
+                  const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,
+                  const anns_precision_policy* policy, int32_t reps, anns_tune_result* results,
+                  int32_t cap, int32_t* n_results, void* cuda_stream);
 
 /* Learned precision predictor: the regressor of Section 3.4 as a 5-32-32-5 MLP
  * classifier over the bit widths {4, 6, 8, 12, 16}, on the features of
  * Section 3.3 for probe rank j: (sqrt(D2_j) - sqrt(D2_0), r_0, r_j, sqrt(n_j),
  * j / nprobe), normalised as fl32(fl32(x - mean) * inv_std). FP32 master
  * weights, row-major [out][in]. Inference (policy ANNS_LUT_MLP) uses FP16
- * operands with FP32 accumulation; a pair falls back to the FP32 LUT when its
- * top-two logits differ by less than policy->fallback_margin. */
+ * operands with FP32 accumulation, then the round-up rule on the logits
+ * (policy->fallback_margin) and, if requested, the width map. */
 typedef struct {
   float W1[32 * 5], b1[32], W2[32 * 32], b2[32], W3[5 * 32], b3[5];
   float mean[5], inv_std[5];

@@ -68,6 +68,24 @@ def _ptr(a):
     return a.data_ptr()
 
 
+class Graph:
+    """A captured search (anns_graph); launch() replays it on a stream."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def launch(self, stream=None):
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_graph_launch(self.handle, s)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.anns_graph_free(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
 class Index:
     """An index owned by the library, built from host arrays (Section 2.1)."""
 
@@ -129,6 +147,28 @@ class Index:
         """'auto', 'basic' (query-major) or 'lists' (list-major, one warp per pair)."""
         v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "lists": abi.KERNEL_LIST_MAJOR}[which]
         abi.anns_set_option(self.handle, abi.OPT_KERNEL, v)
+
+    def set_schedule(self, which: str):
+        """'auto', 'natural' or 'lpt' (longest query first) for the query-major kernel."""
+        v = {"auto": abi.SCHED_AUTO, "natural": abi.SCHED_NATURAL, "lpt": abi.SCHED_LPT}[which]
+        abi.anns_set_option(self.handle, abi.OPT_SCHEDULE, v)
+
+    def capture_graph(self, queries, nprobe: int, k: int, pol=None, nprobe_per_q=None, k_per_q=None, out=None):
+        """CUDA graph of a whole search on fixed CUDA tensors; returns (Graph, ids, dists)."""
+        import torch
+        nq = queries.shape[0]
+        if out is None:
+            out = (torch.empty((nq, k), dtype=torch.int64, device=queries.device),
+                   torch.empty((nq, k), dtype=torch.float32, device=queries.device))
+        ids, dists = out
+        h = abi.anns_graph_capture(self.handle, _ptr(queries), nq, nprobe, _ptr(nprobe_per_q), k, _ptr(k_per_q),
+                                   pol, _ptr(ids), _ptr(dists))
+        return Graph(h), ids, dists
+
+    def autotune(self, queries, nprobe: int, k: int, pol=None, nprobe_per_q=None, k_per_q=None, reps: int = 3):
+        """Times every (kernel, schedule) choice, installs the fastest; returns [(kernel, schedule, ms)]."""
+        return abi.anns_autotune(self.handle, _ptr(queries), queries.shape[0], nprobe, _ptr(nprobe_per_q), k,
+                                 _ptr(k_per_q), pol, reps)
 
     def set_predictor(self, p: dict):
         abi.anns_set_predictor(self.handle, predictor_to_struct(p))

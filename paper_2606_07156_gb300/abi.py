@@ -21,14 +21,16 @@ LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT = 0, 1,
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS = 10, 11, 12
-OPT_KERNEL = 0
+OPT_KERNEL, OPT_SCHEDULE = 0, 1
 KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR = 0, 1, 2
+SCHED_AUTO, SCHED_NATURAL, SCHED_LPT = 0, 1, 2
 
 SYMBOLS = (
     "anns_build_index_from_arrays", "anns_free", "anns_search", "anns_search_host",
     "anns_get_info", "anns_debug_tap", "anns_compute_luts", "anns_scan_pairs", "anns_profile",
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
-    "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor", "anns_last_error",
+    "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
+    "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_last_error",
 )
 
 
@@ -66,6 +68,10 @@ class anns_predictor(ctypes.Structure):
                 ("mean", ctypes.c_float * 5), ("inv_std", ctypes.c_float * 5)]
 
 
+class anns_tune_result(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 class anns_train_cfg(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("seed", ctypes.c_uint64)]
@@ -89,6 +95,12 @@ def _load():
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
         "anns_locate_static": ([vp, vp, i64, i32, vp, vp, vp], i32),
+        "anns_graph_capture": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), vp, vp,
+                                ctypes.POINTER(vp)], i32),
+        "anns_graph_launch": ([vp, vp], i32),
+        "anns_graph_free": ([vp], None),
+        "anns_autotune": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), i32,
+                           ctypes.POINTER(anns_tune_result), i32, ctypes.POINTER(i32), vp], i32),
         "anns_set_predictor": ([vp, ctypes.POINTER(anns_predictor)], i32),
         "anns_get_predictor": ([vp, ctypes.POINTER(anns_predictor)], i32),
         "anns_make_training_set": ([vp, vp, i64, i32, i32, vp, vp, vp], i32),
@@ -207,3 +219,28 @@ def anns_train_predictor(index, train_q, nq, nprobe, k, cfg, out=None, stream=No
     out = out if out is not None else anns_predictor()
     _check(_lib.anns_train_predictor(index, train_q, nq, nprobe, k, ctypes.byref(cfg), ctypes.byref(out), stream))
     return out
+
+
+def anns_graph_capture(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, policy, ids_out, dists_out):
+    out = ctypes.c_void_p()
+    pol = ctypes.byref(policy) if policy is not None else None
+    _check(_lib.anns_graph_capture(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, pol, ids_out,
+                                   dists_out, ctypes.byref(out)))
+    return out.value
+
+
+def anns_graph_launch(graph, stream=None) -> None:
+    _check(_lib.anns_graph_launch(graph, stream))
+
+
+def anns_graph_free(graph) -> None:
+    _lib.anns_graph_free(graph)
+
+
+def anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, policy, reps, stream=None):
+    res = (anns_tune_result * 8)()
+    n = ctypes.c_int32()
+    pol = ctypes.byref(policy) if policy is not None else None
+    _check(_lib.anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, pol, reps, res, 8,
+                              ctypes.byref(n), stream))
+    return [(res[i].kernel, res[i].schedule, res[i].ms) for i in range(n.value)]

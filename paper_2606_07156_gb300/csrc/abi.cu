@@ -196,7 +196,7 @@ int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq,
 
 using namespace anns;
 
-static int check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe, int32_t k,
+int anns::check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe, int32_t k,
                              const anns_precision_policy* pol, const void* ids_out,
                              const void* dists_out) {
   if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
@@ -227,6 +227,86 @@ static int check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t
   return ANNS_OK;
 }
 
+namespace anns {
+
+static bool use_lpt(const Index& ix, const int32_t* nprobe_per_q) {
+  return ix.opt_schedule == ANNS_SCHED_LPT || (ix.opt_schedule == ANNS_SCHED_AUTO && nprobe_per_q);
+}
+
+int reserve_search(Index& ix, int64_t nq, int nprobe, int k, const anns_precision_policy& P,
+                   const int32_t* nprobe_per_q) {
+  int rc = ensure_workspace(ix, nq, nprobe);
+  if (rc) return rc;
+  if (ix.opt_kernel == ANNS_KERNEL_LIST_MAJOR) {
+    ListWork w{};
+    if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
+  } else if (use_lpt(ix, nprobe_per_q)) {
+    if ((rc = grow(&ix.ws_sched, &ix.ws_sched_cap, lpt_workspace_bytes(nq)))) return rc;
+  }
+  (void)P;
+  return ANNS_OK;
+}
+
+int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int32_t* nprobe_per_q, int k,
+                    const int32_t* k_per_q, const anns_precision_policy& P, int64_t* ids_out,
+                    float* dists_out, cudaStream_t s, bool profile) {
+  int rc = reserve_search(ix, nq, nprobe, k, P, nprobe_per_q);
+  if (rc) return rc;
+  cudaEvent_t* ev = profile ? next_profile_slot(ix) : nullptr;
+  if (ev) cudaEventRecord(ev[0], s);
+  cudaError_t e = launch_coarse(ix, Q, nq, nprobe, nprobe_per_q, ix.ws_d2, ix.ws_probes, ix.ws_probe_d2, s,
+                                ev ? ev[1] : nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "coarse kernels");
+  if (ev) cudaEventRecord(ev[2], s);
+  const bool want_feat = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2;
+  if ((rc = launch_policy(ix, P, nq, nprobe, nprobe_per_q, ix.ws_probes, ix.ws_probe_d2, ix.ws_bits,
+                          want_feat ? ix.ws_feat : nullptr, s)))
+    return rc;
+  e = launch_query_tables(ix, Q, nq, ix.ws_qt, s);
+  if (e != cudaSuccess) return cuda_fail(e, "query tables");
+  // table width the policy may need: FP32 (4 bytes), 16-bit or 8-bit levels
+  const int tbytes = table_bytes_for(P);
+  // AUTO: query-major (measured faster on the SIFT-shaped workload for every
+  // table width); list-major on request
+  if (ix.opt_kernel == ANNS_KERNEL_LIST_MAJOR) {
+    if (list_major_warps(ix, tbytes) < 1)
+      return fail(ANNS_ERR_UNSUPPORTED, "list-major kernel: one table does not fit in shared memory");
+    ListWork w{};
+    if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
+    if (ev) cudaEventRecord(ev[3], s);
+    e = launch_search_lists(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
+                            ix.ws_bits, tbytes, w, ids_out, dists_out, s);
+  } else {
+    const int32_t* order = nullptr;
+    if (use_lpt(ix, nprobe_per_q)) {
+      e = launch_lpt_order(ix, ix.ws_probes, nprobe_per_q, nq, nprobe, ix.ws_sched, s);
+      if (e != cudaSuccess) return cuda_fail(e, "schedule kernels");
+      order = lpt_order_ptr(ix.ws_sched, nq);
+    }
+    if (ev) cudaEventRecord(ev[3], s);
+    e = launch_search(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
+                      ix.ws_bits, order, ids_out, dists_out, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "search kernel");
+  if (ev) cudaEventRecord(ev[4], s);
+  return ANNS_OK;
+}
+
+void free_workspace(Index& ix) {
+  void* ptrs[] = {ix.ws_qt, ix.ws_lists, ix.ws_d2, ix.ws_probes /* base of the pair block */,
+                  ix.ws_counter, ix.ws_sched, ix.st_q, ix.st_out, ix.st_pq};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  ix.ws_qt = nullptr; ix.ws_lists = nullptr; ix.ws_d2 = nullptr; ix.ws_probes = nullptr;
+  ix.ws_probe_d2 = nullptr; ix.ws_bits = nullptr; ix.ws_feat = nullptr; ix.ws_counter = nullptr;
+  ix.ws_sched = nullptr; ix.st_q = nullptr; ix.st_out = nullptr; ix.st_pq = nullptr;
+  ix.ws_qt_cap = ix.ws_lists_cap = ix.ws_d2_cap = ix.ws_pair_cap = ix.ws_counter_cap = 0;
+  ix.ws_sched_cap = ix.st_q_cap = ix.st_out_cap = ix.st_pq_cap = 0;
+  ix.ws_nq = ix.ws_nprobe = 0;
+}
+
+}  // namespace anns
+
 extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe,
                            const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,
                            const anns_precision_policy* pol, int64_t* ids_out, float* dists_out,
@@ -235,44 +315,10 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
   if (rc) return rc;
   if (nq == 0) return ANNS_OK;
   DeviceGuard g(ix->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  if ((rc = ensure_workspace(*ix, nq, nprobe))) return rc;
   anns_precision_policy plain{};
   plain.lut_mode = ANNS_LUT_PLAIN_FP32;
-  const anns_precision_policy& P = pol ? *pol : plain;
-  cudaEvent_t* ev = next_profile_slot(*ix);
-  if (ev) cudaEventRecord(ev[0], s);
-  cudaError_t e = launch_coarse(*ix, Q, nq, nprobe, nprobe_per_q, ix->ws_d2, ix->ws_probes,
-                                ix->ws_probe_d2, s, ev ? ev[1] : nullptr);
-  if (e != cudaSuccess) return cuda_fail(e, "coarse kernels");
-  if (ev) cudaEventRecord(ev[2], s);
-  const bool want_feat = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2;
-  if ((rc = launch_policy(*ix, P, nq, nprobe, nprobe_per_q, ix->ws_probes, ix->ws_probe_d2,
-                          ix->ws_bits, want_feat ? ix->ws_feat : nullptr, s)))
-    return rc;
-  e = launch_query_tables(*ix, Q, nq, ix->ws_qt, s);
-  if (e != cudaSuccess) return cuda_fail(e, "query tables");
-  if (ev) cudaEventRecord(ev[3], s);
-  // table width the policy may need: FP32 (4 bytes), 16-bit or 8-bit levels
-  const int tbytes = table_bytes_for(P);
-  const int nw = list_major_warps(*ix, tbytes);
-  // AUTO: query-major (measured faster on the SIFT-shaped workload for every
-  // table width); list-major on request
-  const bool lists = ix->opt_kernel == ANNS_KERNEL_LIST_MAJOR;
-  if (ix->opt_kernel == ANNS_KERNEL_LIST_MAJOR && nw < 1)
-    return fail(ANNS_ERR_UNSUPPORTED, "list-major kernel: one table does not fit in shared memory");
-  if (lists) {
-    ListWork w{};
-    if ((rc = list_workspace(*ix, nq, nprobe, k, w))) return rc;
-    e = launch_search_lists(*ix, ix->ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
-                            ix->ws_probe_d2, ix->ws_bits, tbytes, w, ids_out, dists_out, s);
-  } else {
-    e = launch_search(*ix, ix->ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix->ws_probes,
-                      ix->ws_probe_d2, ix->ws_bits, ids_out, dists_out, s);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "search kernel");
-  if (ev) cudaEventRecord(ev[4], s);
-  return ANNS_OK;
+  return search_sequence(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, pol ? *pol : plain, ids_out, dists_out,
+                         (cudaStream_t)stream, true);
 }
 
 extern "C" int anns_search_host(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe,
@@ -369,6 +415,10 @@ extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
       if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_LIST_MAJOR)
         return fail(ANNS_ERR_INVALID_ARG, "unknown kernel choice");
       ix->opt_kernel = (int)value;
+      return ANNS_OK;
+    case ANNS_OPT_SCHEDULE:
+      if (value < ANNS_SCHED_AUTO || value > ANNS_SCHED_LPT) return fail(ANNS_ERR_INVALID_ARG, "unknown schedule");
+      ix->opt_schedule = (int)value;
       return ANNS_OK;
     default: return fail(ANNS_ERR_INVALID_ARG, "unknown option");
   }

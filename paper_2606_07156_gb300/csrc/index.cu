@@ -44,12 +44,10 @@ static void free_index(anns_index* ix) {
   cudaGetDevice(&prev);
   cudaSetDevice(ix->device);
   void* ptrs[] = {ix->centroids, ix->codebooks, ix->codes, ix->ids, ix->list_len,
-                  ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->order, ix->ws_qt,
-                  ix->ws_lists, ix->ws_d2,
-                  ix->ws_probes /* base of the pair block; the other ws_* alias it */,
-                  ix->st_q, ix->st_out, ix->st_pq, ix->mlp_dev, ix->ws_counter};
+                  ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->order, ix->mlp_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  free_workspace(*ix);
   for (auto& set : ix->prof_ev)
     for (cudaEvent_t e : set)
       if (e) cudaEventDestroy(e);

@@ -58,7 +58,10 @@ struct Index {
   size_t ws_counter_cap = 0;
   void* ws_lists = nullptr;      // list-major work: per-list counts/offsets, pairs, partial top-k
   size_t ws_lists_cap = 0;
+  void* ws_sched = nullptr;      // query order of the LPT schedule (schedule.cu)
+  size_t ws_sched_cap = 0;
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
+  int opt_schedule = 0;          // ANNS_SCHED_*
   // staging for anns_search_host
   void* st_q = nullptr; size_t st_q_cap = 0;
   void* st_out = nullptr; size_t st_out_cap = 0;
@@ -94,11 +97,29 @@ cudaError_t launch_query_tables(const Index& ix, const float* Q, int64_t nq, flo
 int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq, int nprobe,
                   const int32_t* nprobe_per_q, const int32_t* probes, const float* probe_d2,
                   uint8_t* bits, float* feat, cudaStream_t s);
-// RC + LC + quantise + DC + TS for every query.
+// RC + LC + quantise + DC + TS for every query; `order` (NULL = 0..nq-1) is
+// the order in which blocks take the queries.
 cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const float* probe_d2, const uint8_t* bits,
-                          int64_t* ids_out, float* dists_out, cudaStream_t s);
+                          const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s);
+// Longest-first query order (schedule.cu) into a workspace of
+// lpt_workspace_bytes(nq); the order is at lpt_order_ptr(ws, nq).
+size_t lpt_workspace_bytes(int64_t nq);
+int32_t* lpt_order_ptr(void* ws, int64_t nq);
+cudaError_t launch_lpt_order(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
+                             int nprobe, void* ws, cudaStream_t s);
+// The whole search sequence of anns_search on stream s (abi.cu), for an index
+// whose workspace is already large enough when `no_alloc` is set.
+int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int32_t* nprobe_per_q, int k,
+                    const int32_t* k_per_q, const anns_precision_policy& P, int64_t* ids_out,
+                    float* dists_out, cudaStream_t s, bool profile);
+// Grows every workspace buffer a search of this shape needs.
+int reserve_search(Index& ix, int64_t nq, int nprobe, int k, const anns_precision_policy& P,
+                   const int32_t* nprobe_per_q);
+// Frees the workspace buffers (not the index arrays).
+void free_workspace(Index& ix);
+
 // List-major search (search_lists.cu): work regrouped by list (invert.cu),
 // one warp per (query, list) pair, then a per-query merge.
 struct ListWork {
@@ -131,3 +152,8 @@ cudaError_t launch_scan_pairs(const Index& ix, const float* Q, const float* qt, 
 
 // The opaque handle of the C ABI is the internal index.
 struct anns_index : public anns::Index {};
+
+namespace anns {
+int check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe, int32_t k,
+                      const anns_precision_policy* pol, const void* ids_out, const void* dists_out);
+}

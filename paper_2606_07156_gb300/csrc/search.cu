@@ -285,6 +285,7 @@ struct SearchArgs {
   int M, Mp, nprobe, k;
   const int32_t* npq; const int32_t* kpq;
   const int32_t* probes; const float* probe_d2; const uint8_t* bits;
+  const int32_t* order;
   int64_t* ids_out; float* dists_out;
   SmemLayout lay;
 };
@@ -330,7 +331,8 @@ __global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? 4 : 1) search_kernel(c
   Smem s(a.lay);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tstride = (int64_t)a.Mp * kKsub;
-  for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+  for (int64_t qi = blockIdx.x; qi < a.nq; qi += gridDim.x) {
+    const int64_t q = a.order ? (int64_t)a.order[qi] : qi;
     const int np = a.npq ? min(max(a.npq[q], 0), a.nprobe) : a.nprobe;
     const int kq = a.kpq ? min(max(a.kpq[q], 0), a.k) : a.k;
     WarpTopK<R, int64_t> top;
@@ -505,11 +507,12 @@ cudaError_t run_scan_pairs(const SearchArgs& a, const int32_t* pq, const int32_t
 cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const float* probe_d2, const uint8_t* bits,
-                          int64_t* ids_out, float* dists_out, cudaStream_t s) {
+                          const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s) {
   const int R = k <= 32 ? 1 : 4;
   SearchArgs a = make_args(ix, nullptr, qt, R);
   a.nq = nq; a.nprobe = nprobe; a.k = k; a.npq = nprobe_per_q; a.kpq = k_per_q;
-  a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.ids_out = ids_out; a.dists_out = dists_out;
+  a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.order = order;
+  a.ids_out = ids_out; a.dists_out = dists_out;
   switch (ix.nchunk) {
     case 1: return run_search_r<1>(a, R, s);
     case 2: return run_search_r<2>(a, R, s);

@@ -1,0 +1,166 @@
+"""Scheduling and batching (LPT query order, CUDA graphs, autotuner) and the
+Deep-, GIST- and embedding-shaped index geometries, CUDA path vs the oracle.
+
+Every schedule, kernel and replay must return the oracle's results bit for
+bit: the order in which queries run never changes what a query returns.
+"""
+import numpy as np
+import pytest
+
+from oracle import ivfpq
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_07156_gb300 as m
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def pair_a(amp, small_a):
+    d, ix = small_a
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=0)
+    o = ivfpq.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"])
+    yield d, g, o
+    g.close()
+
+
+def _uneven(nq, seed, hi, kchoices):
+    from workloads import mixed_k, zipf_nprobe
+    return zipf_nprobe(nq, seed, lo=1, hi=hi), mixed_k(nq, seed, choices=kchoices)
+
+
+@pytest.mark.parametrize("sched", ["natural", "lpt", "auto"])
+def test_schedules_bit_exact(amp, pair_a, sched):
+    d, g, o = pair_a
+    Q = d["queries"]
+    npq, kpq = _uneven(len(Q), 3, 12, (1, 10, 40))
+    g.set_schedule(sched)
+    try:
+        for bits in (0, 8):
+            pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
+            ids, dists = g.search(cuda(Q), 12, 40, pol, nprobe_per_q=cuda(npq), k_per_q=cuda(kpq))
+            ri, rd = ivfpq.search(o, Q, 12, 40, bits=bits, nprobe_per_q=npq, k_per_q=kpq)
+            np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+            np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+    finally:
+        g.set_schedule("auto")
+
+
+def test_graph_replays_with_new_queries(amp, pair_a):
+    d, g, o = pair_a
+    Q = d["queries"]
+    nq = len(Q)
+    npq, kpq = _uneven(nq, 5, 10, (1, 10))
+    qbuf, nbuf, kbuf = cuda(Q), cuda(npq), cuda(kpq)
+    pol = amp.policy("fixed", bits=6)
+    g.set_schedule("lpt")
+    graph, ids, dists = g.capture_graph(qbuf, 10, 10, pol, nprobe_per_q=nbuf, k_per_q=kbuf)
+    try:
+        g.set_schedule("auto")
+        ri, rd = ivfpq.search(o, Q, 10, 10, bits=6, nprobe_per_q=npq, k_per_q=kpq)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+        # an unrelated search on the index (different shape) between replays
+        g.search(cuda(Q[:3]), 4, 7)
+        r = np.random.Generator(np.random.PCG64(9))
+        for rep in range(3):
+            Q2 = (Q[r.permutation(nq)] + r.normal(0, 0.01, Q.shape)).astype(np.float32)
+            np2 = r.integers(0, 11, nq).astype(np.int32)
+            qbuf.copy_(cuda(Q2))
+            nbuf.copy_(cuda(np2))
+            ids.fill_(-7)
+            graph.launch()
+            torch.cuda.synchronize()
+            ri, rd = ivfpq.search(o, Q2, 10, 10, bits=6, nprobe_per_q=np2, k_per_q=kpq)
+            np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+            np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+    finally:
+        graph.close()
+
+
+def test_graph_on_stream_and_list_major(amp, pair_a):
+    d, g, o = pair_a
+    Q = d["queries"]
+    g.set_kernel("lists")
+    try:
+        graph, ids, dists = g.capture_graph(cuda(Q), 5, 10, amp.policy("plain"))
+    finally:
+        g.set_kernel("auto")
+    try:
+        st = torch.cuda.Stream()
+        ids.zero_()
+        graph.launch(st)
+        st.synchronize()
+        ri, rd = ivfpq.search(o, Q, 5, 10, bits=0)
+        np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+        np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+    finally:
+        graph.close()
+
+
+def test_autotune_installs_a_configuration(amp, pair_a):
+    d, g, o = pair_a
+    Q = d["queries"]
+    res = g.autotune(cuda(Q), 8, 10, amp.policy("fixed", bits=8), reps=2)
+    kinds = {(kk, s) for kk, s, _ in res}
+    assert (amp.abi.KERNEL_BASIC, amp.abi.SCHED_NATURAL) in kinds
+    assert (amp.abi.KERNEL_BASIC, amp.abi.SCHED_LPT) in kinds
+    assert all(ms > 0 for _, _, ms in res)
+    ids, dists = g.search(cuda(Q), 8, 10, amp.policy("fixed", bits=8))
+    ri, rd = ivfpq.search(o, Q, 8, 10, bits=8)
+    np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+    g.set_kernel("auto")
+    g.set_schedule("auto")
+
+
+def test_option_and_argument_errors(amp, pair_a):
+    d, g, o = pair_a
+    with pytest.raises(amp.abi.AnnsError):
+        amp.abi.anns_set_option(g.handle, amp.abi.OPT_SCHEDULE, 7)
+    with pytest.raises(amp.abi.AnnsError):
+        g.autotune(cuda(d["queries"]), 4, 10, reps=0)
+    with pytest.raises(amp.abi.AnnsError):
+        g.capture_graph(cuda(d["queries"][:0]), 4, 10)
+
+
+# ------------------------------------------- index geometries of the workloads
+
+def _geometry_case(key, n, nlist, M, ncomp, nq):
+    from workloads import make_dataset, train_ivfpq
+    d = make_dataset(key, n=n, nq=nq, ncomp=ncomp)
+    ix = train_ivfpq(d["base"], nlist, M, iters=4, seed=1, device="cpu")
+    return d, ix
+
+
+@pytest.mark.parametrize("key,M,nlist,bits_set", [
+    ("C", 48, 24, (0, 8, 12)),       # Deep-shaped: D = 96, dsub = 2, Mp = 48
+    ("D", 120, 16, (0, 4, 16)),      # GIST-shaped: D = 960, dsub = 8, Mp = 128
+    ("E", 96, 16, (0, 6, 8)),        # embedding-shaped: D = 768, dsub = 8, Mp = 96
+])
+def test_workload_geometries_bit_exact(amp, key, M, nlist, bits_set):
+    d, ix = _geometry_case(key, 2500, nlist, M, 16, 10)
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=0)
+    o = ivfpq.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"])
+    Q = d["queries"]
+    npq, kpq = _uneven(len(Q), 7, 8, (1, 10, 100))
+    try:
+        for bits in bits_set:
+            pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
+            for kern in ("auto", "lists"):
+                g.set_kernel(kern)
+                ids, dists = g.search(cuda(Q), 8, 100, pol, nprobe_per_q=cuda(npq), k_per_q=cuda(kpq))
+                ri, rd = ivfpq.search(o, Q, 8, 100, bits=bits, nprobe_per_q=npq, k_per_q=kpq)
+                np.testing.assert_array_equal(ids.cpu().numpy(), ri, err_msg=f"{key} {bits} {kern}")
+                np.testing.assert_array_equal(dists.cpu().numpy(), rd, err_msg=f"{key} {bits} {kern}")
+    finally:
+        g.close()
