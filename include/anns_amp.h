@@ -90,8 +90,11 @@ enum { ANNS_PREC_FP32 = 0, ANNS_PREC_BF16 = 1, ANNS_PREC_FP8E4M3 = 2 };
 typedef struct {
   int32_t lut_mode;        /* ANNS_LUT_* */
   int32_t fixed_bits;      /* 4, 6, 8, 12 or 16 (FIXED_BITS) */
-  int32_t cl_prec;         /* ANNS_PREC_* for the coarse distances; FP32 only for now */
-  int32_t lc_prec;         /* ANNS_PREC_* for the LUT build; FP32 only for now */
+  int32_t cl_prec;         /* coarse distances: ANNS_PREC_FP32, or ANNS_PREC_BF16 = BF16
+                              tensor-core GEMM on centred operands, then every list
+                              within the GEMM's error bound of the nprobe-th re-ranked
+                              by the FP32 rule: same probes and distances as FP32 */
+  int32_t lc_prec;         /* ANNS_PREC_* for the LUT build; FP32 only */
   float eq2_thresholds[4]; /* HEURISTIC_EQ2: g thresholds for 4, 6, 8, 12 bits */
   float fallback_margin;   /* MLP round-up margin tau >= 0: the fewest bits b such that
                               fl32(max logit over widths <= b - max logit over wider
@@ -146,12 +149,18 @@ int anns_get_info(const anns_index* index, anns_index_info* out);
  *   PROBE_D2 float [nq * nprobe]  their FP32 coarse distances
  *   BITS     uint8 [nq * nprobe]  chosen bits per pair (0 = FP32 LUT)
  *   FEATURES float [nq * nprobe * 5] predictor features (MLP / EQ2 modes)
+ *   COARSE_APPROX     float [nq * nlist] BF16 tensor-core distances D~ (last
+ *                     search with cl_prec = BF16)
+ *   COARSE_CANDIDATES int32 [nq] lists re-ranked in FP32 per query (same)
  * Index taps:
  *   LIST_SIZES int64 [nlist], LIST_RADIUS float [nlist],
- *   PACKED_IDS int64 [n] (ids in list order, lists ascending). */
+ *   PACKED_IDS int64 [n] (ids in list order, lists ascending),
+ *   STATUS int32: the device status word (0 = ok, 1 = a bounded wait in a
+ *   kernel timed out), reset to 0 by the read. */
 enum {
   ANNS_TAP_PROBES = 0, ANNS_TAP_PROBE_D2 = 1, ANNS_TAP_BITS = 2, ANNS_TAP_FEATURES = 3,
-  ANNS_TAP_LIST_SIZES = 10, ANNS_TAP_LIST_RADIUS = 11, ANNS_TAP_PACKED_IDS = 12
+  ANNS_TAP_COARSE_APPROX = 4, ANNS_TAP_COARSE_CANDIDATES = 5,
+  ANNS_TAP_LIST_SIZES = 10, ANNS_TAP_LIST_RADIUS = 11, ANNS_TAP_PACKED_IDS = 12, ANNS_TAP_STATUS = 13
 };
 int anns_debug_tap(anns_index* index, int32_t what, void* out, size_t bytes);
 

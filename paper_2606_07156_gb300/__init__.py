@@ -19,14 +19,14 @@ _MODES = {"plain": abi.LUT_PLAIN_FP32, "fixed": abi.LUT_FIXED_BITS, "eq2": abi.L
 
 
 def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), margin: float = 0.0,
-           pair_bits=None, width_map: bool = False) -> abi.anns_precision_policy:
+           pair_bits=None, width_map: bool = False, cl: str = "fp32") -> abi.anns_precision_policy:
     """Builds an anns_precision_policy. ``pair_bits`` (EXPLICIT) is a uint8 CUDA tensor;
     ``margin`` is the MLP round-up margin; ``width_map`` maps EQ2/MLP widths to this
     GPU's tables (6 -> 8 bits, 12 and 16 -> FP32)."""
     p = abi.anns_precision_policy()
     p.lut_mode = _MODES[mode]
     p.fixed_bits = int(bits)
-    p.cl_prec = abi.PREC_FP32
+    p.cl_prec = {"fp32": abi.PREC_FP32, "bf16": abi.PREC_BF16}[cl]
     p.lc_prec = abi.PREC_FP32
     for i, t in enumerate(thresholds):
         p.eq2_thresholds[i] = float(t)

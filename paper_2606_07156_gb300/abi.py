@@ -20,7 +20,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSUPPOR
 LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT = 0, 1, 2, 3, 4
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
-TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS = 10, 11, 12
+TAP_COARSE_APPROX, TAP_COARSE_CANDIDATES = 4, 5
+TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS, TAP_STATUS = 10, 11, 12, 13
 OPT_KERNEL, OPT_SCHEDULE = 0, 1
 KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR = 0, 1, 2
 SCHED_AUTO, SCHED_NATURAL, SCHED_LPT = 0, 1, 2

@@ -221,8 +221,9 @@ int anns::check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t 
         break;
       default: return fail(ANNS_ERR_INVALID_ARG, "unknown lut_mode");
     }
-    if (pol->cl_prec != ANNS_PREC_FP32 || pol->lc_prec != ANNS_PREC_FP32)
-      return fail(ANNS_ERR_UNSUPPORTED, "only FP32 CL/LC operands are available");
+    if (pol->cl_prec != ANNS_PREC_FP32 && pol->cl_prec != ANNS_PREC_BF16)
+      return fail(ANNS_ERR_UNSUPPORTED, "CL operands: FP32 or BF16 (with exact re-rank)");
+    if (pol->lc_prec != ANNS_PREC_FP32) return fail(ANNS_ERR_UNSUPPORTED, "LC operands: FP32 only");
   }
   return ANNS_OK;
 }
@@ -243,7 +244,9 @@ int reserve_search(Index& ix, int64_t nq, int nprobe, int k, const anns_precisio
   } else if (use_lpt(ix, nprobe_per_q)) {
     if ((rc = grow(&ix.ws_sched, &ix.ws_sched_cap, lpt_workspace_bytes(nq)))) return rc;
   }
-  (void)P;
+  if (P.cl_prec == ANNS_PREC_BF16) {
+    if ((rc = grow(&ix.ws_tc, &ix.ws_tc_cap, coarse_tc_workspace_bytes(ix, nq)))) return rc;
+  }
   return ANNS_OK;
 }
 
@@ -254,8 +257,15 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
   if (rc) return rc;
   cudaEvent_t* ev = profile ? next_profile_slot(ix) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
-  cudaError_t e = launch_coarse(ix, Q, nq, nprobe, nprobe_per_q, ix.ws_d2, ix.ws_probes, ix.ws_probe_d2, s,
-                                ev ? ev[1] : nullptr);
+  cudaError_t e;
+  ix.ws_tc_valid = P.cl_prec == ANNS_PREC_BF16;
+  if (ix.ws_tc_valid) {
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_coarse_tc(ix, Q, nq, nprobe, nprobe_per_q, ix.ws_tc, ix.ws_d2, ix.ws_probes, ix.ws_probe_d2, s);
+  } else {
+    e = launch_coarse(ix, Q, nq, nprobe, nprobe_per_q, ix.ws_d2, ix.ws_probes, ix.ws_probe_d2, s,
+                      ev ? ev[1] : nullptr);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "coarse kernels");
   if (ev) cudaEventRecord(ev[2], s);
   const bool want_feat = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2;
@@ -294,12 +304,14 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
 
 void free_workspace(Index& ix) {
   void* ptrs[] = {ix.ws_qt, ix.ws_lists, ix.ws_d2, ix.ws_probes /* base of the pair block */,
-                  ix.ws_counter, ix.ws_sched, ix.st_q, ix.st_out, ix.st_pq};
+                  ix.ws_counter, ix.ws_sched, ix.ws_tc, ix.st_q, ix.st_out, ix.st_pq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix.ws_qt = nullptr; ix.ws_lists = nullptr; ix.ws_d2 = nullptr; ix.ws_probes = nullptr;
   ix.ws_probe_d2 = nullptr; ix.ws_bits = nullptr; ix.ws_feat = nullptr; ix.ws_counter = nullptr;
-  ix.ws_sched = nullptr; ix.st_q = nullptr; ix.st_out = nullptr; ix.st_pq = nullptr;
+  ix.ws_sched = nullptr; ix.ws_tc = nullptr; ix.st_q = nullptr; ix.st_out = nullptr; ix.st_pq = nullptr;
+  ix.ws_tc_cap = 0;
+  ix.ws_tc_valid = false;
   ix.ws_qt_cap = ix.ws_lists_cap = ix.ws_d2_cap = ix.ws_pair_cap = ix.ws_counter_cap = 0;
   ix.ws_sched_cap = ix.st_q_cap = ix.st_out_cap = ix.st_pq_cap = 0;
   ix.ws_nq = ix.ws_nprobe = 0;

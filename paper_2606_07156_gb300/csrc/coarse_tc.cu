@@ -1,0 +1,405 @@
+// Cluster locating on the tensor cores (the BF16 fast path of CL, Section 2.1),
+// with an exact re-rank so that the probed lists and their distances are the
+// ones of the FP32 rule.
+//
+// 1. Operands: q^ = fl32(q - mu), c^ = fl32(c - mu) with mu the centroids'
+//    mean (distances are translation invariant, and centring shrinks the
+//    norms the rounding error scales with), rounded to BF16 (nearest even)
+//    and zero-padded to Dp = dim rounded up to 64. Per row: qn = sum of the
+//    squared BF16 values (FP32), qh >= ||q^||_2.
+// 2. D~[q][l] = fl32(fl32(qn + cn) - fl32(2 <q~, c~>)): a 128 x 128 tile per
+//    CTA, tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulator in TMEM),
+//    operands staged in shared memory in the canonical no-swizzle K-major
+//    layout, one thread issuing the MMAs, completion through tcgen05.commit
+//    on an mbarrier, the accumulator read back with tcgen05.ld.
+// 3. Error bound per pair: |D~ - D2| <= eps(D~, norms), D2 the FP32-rule
+//    distance (derivation at rerank_bound). T = the nprobe-th smallest of
+//    D~ + eps; every list of the FP32 top-nprobe has D~ - eps <= T, so those
+//    candidates are re-ranked with the FP32 rule itself (same operation order
+//    as coarse.cu) and the nprobe smallest (D2, l) kept: identical output to
+//    the plain path.
+//
+// Every mbarrier wait is bounded (about a second); on a timeout the kernel
+// records ANNS_DEV_TIMEOUT in the index's device status word, waits once
+// more (bounded) for its MMAs, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "scan.cuh"
+
+namespace anns {
+namespace {
+
+constexpr int kTM = 128;             // queries per tile = TMEM lanes
+constexpr int kTN = 128;             // centroids per tile = FP32 TMEM columns
+constexpr int kKC = 64;              // K elements per staged chunk (4 MMAs of K = 16)
+constexpr int kGemmThreads = 128;    // one warpgroup: warp w reads TMEM lanes 32w..32w+31
+constexpr uint32_t kOpBytes = kTM * kKC * 2;  // 16 KB per operand chunk
+// Dynamic shared memory per CTA, padded so that at most four CTAs share an SM:
+// 4 x 128 columns never exceed the SM's 512 TMEM columns, so tcgen05.alloc
+// never waits.
+constexpr size_t kGemmSmem = 57 * 1024;
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits 7-9 =
+// 1), B BF16 (bits 10-12 = 1), A and B K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+// Byte offset of element (r, k) of a [128 x 64] BF16 chunk: core matrices of
+// 8 rows x 16 bytes, K-adjacent core matrices 128 bytes apart (LBO), 8-row
+// groups 1024 bytes apart (SBO).
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+  return (uint32_t)((((r >> 3) * (kKC / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+constexpr uint32_t kLBO = 128, kSBO = (kKC / 8) * 128;
+
+// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), LBO >> 4
+// (16-29), SBO >> 4 (32-45), descriptor version 1 (46-47), base offset 0,
+// no swizzle (61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait on phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// One warp per row: x^ = fl32(x - mu) in BF16 (zero past dim), xn = FP32 sum
+// of the squared BF16 values, xh = ||x^||_2 computed in FP64 and rounded up.
+__global__ void center_bf16_kernel(const float* __restrict__ X, int64_t n, int dim, int Dp,
+                                   const float* __restrict__ mu, __nv_bfloat16* __restrict__ Xb,
+                                   float* __restrict__ xn, float* __restrict__ xh) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float s = 0.f;
+  double h = 0.0;
+  for (int d = lane; d < Dp; d += 32) {
+    float v = 0.f;
+    if (d < dim) v = sub_rn(X[row * dim + d], mu[d]);
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    Xb[row * Dp + d] = b;
+    const float bf = __bfloat162float(b);
+    s = add_rn(s, mul_rn(bf, bf));
+    h += (double)v * (double)v;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    s = add_rn(s, __shfl_xor_sync(kFull, s, o));
+    h += __shfl_xor_sync(kFull, h, o);
+  }
+  if (lane == 0) {
+    xn[row] = s;
+    xh[row] = __double2float_ru(sqrt(h) * (1.0 + 1e-12));
+  }
+}
+
+// D~ for a 128 x 128 tile (grid: x over centroid tiles, y over query tiles).
+__global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
+    const __nv_bfloat16* __restrict__ Qb, const __nv_bfloat16* __restrict__ Cb, const float* __restrict__ qn,
+    const float* __restrict__ cn, int64_t nq, int64_t nlist, int Dp, float* __restrict__ dt,
+    int* __restrict__ status) {
+  unsigned char* base = anns_dyn_smem + ((1024u - (smem_addr(anns_dyn_smem) & 1023u)) & 1023u);
+  unsigned char* As = base;
+  unsigned char* Bs = base + kOpBytes;
+  uint64_t* bar = (uint64_t*)(base + 2 * kOpBytes);
+  uint32_t* slot = (uint32_t*)(base + 2 * kOpBytes + 16);
+  const uint32_t a_addr = smem_addr(As), b_addr = smem_addr(Bs), bar_addr = smem_addr(bar);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t q0 = (int64_t)blockIdx.y * kTM, l0 = (int64_t)blockIdx.x * kTN;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"((uint32_t)kTN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init(bar_addr, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  bool ok = true;
+  uint32_t parity = 0;
+  for (int k0 = 0; k0 < Dp && ok; k0 += kKC) {
+    // stage the chunk: 128 rows x 8 sixteen-byte units per operand
+    for (int u = tid; u < kTM * (kKC / 8); u += kGemmThreads) {
+      const int r = u >> 3, kg = u & 7;
+      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+      if (q0 + r < nq) va = __ldg((const uint4*)(Qb + (q0 + r) * Dp + k0 + kg * 8));
+      if (l0 + r < nlist) vb = __ldg((const uint4*)(Cb + (l0 + r) * Dp + k0 + kg * 8));
+      *(uint4*)(As + core_off(r, kg * 8)) = va;
+      *(uint4*)(Bs + core_off(r, kg * 8)) = vb;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < kKC / 16; ++ks)
+        tc_mma(tmem, smem_desc(a_addr + ks * 2 * kLBO), smem_desc(b_addr + ks * 2 * kLBO),
+               (k0 > 0 || ks > 0) ? 1u : 0u);
+      tc_commit(bar_addr);
+    }
+    // the chunk may be overwritten once the MMAs have read it
+    ok = mbar_wait(bar_addr, parity);
+    parity ^= 1u;
+    ok = __syncthreads_and(ok);
+  }
+  tc_fence_after();
+  if (ok) {
+    const int64_t q = q0 + warp * 32 + lane;
+    const float qv = q < nq ? qn[q] : 0.f;
+    for (int c0 = 0; c0 < kTN; c0 += 16) {
+      float acc[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+      if (q < nq) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t l = l0 + c0 + j;
+          if (l < nlist) dt[q * nlist + l] = sub_rn(add_rn(qv, cn[l]), mul_rn(2.f, acc[j]));
+        }
+      }
+    }
+  } else {
+    if (tid == 0) {
+      atomicExch(status, ANNS_DEV_TIMEOUT);
+      mbar_wait(bar_addr, parity);  // bounded: the MMAs of the last chunk
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTN)
+                 : "memory");
+}
+
+// eps >= |D~ - D2| for a pair, D2 the FP32-rule distance. With x^ the centred
+// FP32 vectors and x~ their BF16 roundings, delta = (q~ - c~) - (q - c) has
+// ||delta|| <= dn = 2^-8 (1 + 2^-15)(qh + ch) (BF16 relative rounding 2^-8,
+// plus the FP32 centring). S = ||q~ - c~||^2 differs from D~ by the FP32
+// evaluation error e_f <= (2 Dp + 8) 2^-24 (qn + cn) (norm sums, the FP32
+// accumulator of the products, the final combination), from the exact
+// distance by at most dn (2 sqrt(S) + dn), and the FP32 rule differs from the
+// exact distance by at most (dim + 2) 2^-24 of it. Constants padded by 1 %.
+__device__ __forceinline__ float rerank_bound(float dt, float qn, float cn, float qh, float ch, int dim, int Dp) {
+  const float ef = (float)(2 * Dp + 8) * 5.9604645e-8f * (qn + cn) * 1.01f;
+  const float dn = 3.90625e-3f * (1.0f + 3.0517578e-5f) * (qh + ch) * 1.01f;
+  const float sup = fmaxf(dt, 0.f) + ef;
+  const float E = dn * (2.f * sqrtf(sup) * 1.01f + dn);
+  return (ef + E + (float)(dim + 2) * 5.9604645e-8f * (sup + E)) * 1.01f + 1e-30f;
+}
+
+// FP32-rule distance (same operation order as coarse.cu).
+__device__ __forceinline__ float exact_d2(const float* __restrict__ qv, const float* __restrict__ cv, int dim) {
+  float acc = 0.f;
+  for (int d = 0; d < dim; ++d) {
+    const float e = sub_rn(qv[d], cv[d]);
+    acc = add_rn(acc, mul_rn(e, e));
+  }
+  return acc;
+}
+
+// One 256-thread block per query: T from the upper bounds, then the exact
+// top-np over the candidates. Writes nprobe entries (padding -1 / +inf) and
+// the number of candidates re-ranked.
+template <int R>
+__global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ Q, const float* __restrict__ C,
+                                                     const float* __restrict__ dt, const float* __restrict__ qn,
+                                                     const float* __restrict__ qh, const float* __restrict__ cn,
+                                                     const float* __restrict__ ch, int64_t nq, int64_t nlist,
+                                                     int dim, int Dp, int nprobe, const int32_t* __restrict__ npq,
+                                                     int32_t* __restrict__ probes, float* __restrict__ probe_d2,
+                                                     int* __restrict__ ncand) {
+  __shared__ float md[8][R * 32];
+  __shared__ int32_t mi[8][R * 32];
+  __shared__ float Tsh;
+  __shared__ int cnt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = blockIdx.x;
+  const int np = npq ? min(max(npq[q], 0), nprobe) : nprobe;
+  const float* row = dt + q * nlist;
+  const float qnv = qn[q], qhv = qh[q];
+  const float* qv = Q + q * dim;
+  if (threadIdx.x == 0) cnt = 0;
+  // pass 1: T = np-th smallest upper bound D~ + eps
+  WarpTopK<R, int32_t> top;
+  top.init();
+  float thd = INFINITY;
+  int32_t thi = INT32_MAX;
+  if (np > 0) {
+    for (int64_t b0 = (int64_t)warp * 32; b0 < nlist; b0 += 256) {
+      const int64_t l = b0 + lane;
+      const bool valid = l < nlist;
+      float u = INFINITY;
+      if (valid) u = row[l] + rerank_bound(row[l], qnv, cn[l], qhv, ch[l], dim, Dp);
+      top.offer(valid, u, (int32_t)l, np, thd, thi);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) { md[warp][r * 32 + lane] = top.d[r]; mi[warp][r * 32 + lane] = top.id[r]; }
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < 8 && np > 0; ++w)
+#pragma unroll
+      for (int r = 0; r < R; ++r) top.offer(md[w][r * 32 + lane] != INFINITY, md[w][r * 32 + lane],
+                                            mi[w][r * 32 + lane], np, thd, thi);
+    if (lane == 0) Tsh = thd;  // entry np - 1 (+inf if fewer lists)
+  }
+  __syncthreads();
+  const float T = Tsh;
+  // pass 2: exact distances of the candidates, top-np by (D2, l)
+  top.init();
+  thd = INFINITY;
+  thi = INT32_MAX;
+  if (np > 0) {
+    for (int64_t b0 = (int64_t)warp * 32; b0 < nlist; b0 += 256) {
+      const int64_t l = b0 + lane;
+      bool cand = false;
+      if (l < nlist) cand = row[l] - rerank_bound(row[l], qnv, cn[l], qhv, ch[l], dim, Dp) <= T;
+      float d = INFINITY;
+      if (cand) {
+        d = exact_d2(qv, C + l * dim, dim);
+        atomicAdd(&cnt, 1);
+      }
+      top.offer(cand, d, (int32_t)l, np, thd, thi);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < R; ++r) { md[warp][r * 32 + lane] = top.d[r]; mi[warp][r * 32 + lane] = top.id[r]; }
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < 8 && np > 0; ++w)
+#pragma unroll
+      for (int r = 0; r < R; ++r) top.offer(md[w][r * 32 + lane] != INFINITY, md[w][r * 32 + lane],
+                                            mi[w][r * 32 + lane], np, thd, thi);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = r * 32 + lane;
+      if (e < nprobe) {
+        const bool ok = e < np && top.d[r] != INFINITY;
+        probes[q * nprobe + e] = ok ? top.id[r] : -1;
+        probe_d2[q * nprobe + e] = ok ? top.d[r] : INFINITY;
+      }
+    }
+    if (lane == 0 && ncand) ncand[q] = cnt;
+  }
+}
+
+}  // namespace
+
+int coarse_tc_dp(const Index& ix) { return (int)((ix.dim + kKC - 1) / kKC * kKC); }
+
+// Centroid operands (once per index): mu, BF16 centred centroids and norms.
+int prepare_coarse_tc(Index& ix, const std::vector<float>& cent) {
+  const int Dp = coarse_tc_dp(ix);
+  std::vector<double> mu64(ix.dim, 0.0);
+  for (int64_t l = 0; l < ix.nlist; ++l)
+    for (int64_t d = 0; d < ix.dim; ++d) mu64[d] += cent[l * ix.dim + d];
+  std::vector<float> mu(ix.dim);
+  for (int64_t d = 0; d < ix.dim; ++d) mu[d] = (float)(mu64[d] / (double)ix.nlist);
+  cudaError_t e = cudaMalloc(&ix.tc_mu, ix.dim * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.tc_cb, (size_t)ix.nlist * Dp * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.tc_cn, (size_t)ix.nlist * 2 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.dev_status, 16);
+  if (e == cudaSuccess) e = cudaMemcpy(ix.tc_mu, mu.data(), ix.dim * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(ix.dev_status, 0, 16);
+  if (e != cudaSuccess) return cuda_fail(e, "coarse fast-path setup");
+  center_bf16_kernel<<<(unsigned)((ix.nlist + 7) / 8), 256>>>(ix.centroids, ix.nlist, (int)ix.dim, Dp, ix.tc_mu,
+                                                             (__nv_bfloat16*)ix.tc_cb, ix.tc_cn,
+                                                             ix.tc_cn + ix.nlist);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "coarse fast-path setup");
+}
+
+size_t coarse_tc_workspace_bytes(const Index& ix, int64_t nq) {
+  return (size_t)nq * coarse_tc_dp(ix) * 2 + (size_t)nq * 3 * 4 + 256;
+}
+
+cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int nprobe,
+                             const int32_t* nprobe_per_q, void* ws, float* dt, int32_t* probes,
+                             float* probe_d2, cudaStream_t s) {
+  const int Dp = coarse_tc_dp(ix);
+  __nv_bfloat16* Qb = (__nv_bfloat16*)ws;
+  float* qn = (float*)((char*)ws + (((size_t)nq * Dp * 2 + 255) & ~size_t(255)));
+  float* qh = qn + nq;
+  int* ncand = (int*)(qh + nq);
+  center_bf16_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, (int)ix.dim, Dp, ix.tc_mu, Qb, qn, qh);
+  cudaError_t e = cudaFuncSetAttribute(coarse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kGemmSmem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((ix.nlist + kTN - 1) / kTN), (unsigned)((nq + kTM - 1) / kTM));
+  coarse_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(Qb, (const __nv_bfloat16*)ix.tc_cb, qn, ix.tc_cn, nq,
+                                                         ix.nlist, Dp, dt, ix.dev_status);
+  const float* cn = ix.tc_cn;
+  const float* ch = ix.tc_cn + ix.nlist;
+  const int R = (nprobe + 31) / 32;
+  const unsigned g = (unsigned)nq;
+  switch (R) {
+    case 1: rerank_kernel<1><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
+    case 2: rerank_kernel<2><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
+    case 3: rerank_kernel<3><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
+    default: rerank_kernel<4><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace anns

@@ -31,7 +31,9 @@ void make_shadow(const Index& ix, Index& sh) {
   sh = ix;
   sh.ws_d2 = nullptr; sh.ws_probes = nullptr; sh.ws_probe_d2 = nullptr; sh.ws_bits = nullptr;
   sh.ws_feat = nullptr; sh.ws_qt = nullptr; sh.ws_counter = nullptr; sh.ws_lists = nullptr;
-  sh.ws_sched = nullptr; sh.st_q = nullptr; sh.st_out = nullptr; sh.st_pq = nullptr;
+  sh.ws_sched = nullptr; sh.ws_tc = nullptr; sh.st_q = nullptr; sh.st_out = nullptr; sh.st_pq = nullptr;
+  sh.ws_tc_cap = 0;
+  sh.ws_tc_valid = false;
   sh.ws_qt_cap = sh.ws_d2_cap = sh.ws_pair_cap = sh.ws_counter_cap = sh.ws_lists_cap = 0;
   sh.ws_sched_cap = sh.st_q_cap = sh.st_out_cap = sh.st_pq_cap = 0;
   sh.ws_nq = sh.ws_nprobe = 0;

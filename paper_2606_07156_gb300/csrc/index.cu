@@ -44,7 +44,8 @@ static void free_index(anns_index* ix) {
   cudaGetDevice(&prev);
   cudaSetDevice(ix->device);
   void* ptrs[] = {ix->centroids, ix->codebooks, ix->codes, ix->ids, ix->list_len,
-                  ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->order, ix->mlp_dev};
+                  ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->order, ix->mlp_dev,
+                  ix->tc_mu, ix->tc_cb, ix->tc_cn, ix->dev_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_workspace(*ix);
@@ -238,7 +239,8 @@ extern "C" int anns_build_index_from_arrays(const anns_build_desc* d, anns_index
       (rc = upload(&ix->list_len, len32.data(), len32.size(), "upload list_len")) ||
       (rc = upload(&ix->vec_off, voff.data(), voff.size(), "upload vec_off")) ||
       (rc = upload(&ix->tile_off, toff.data(), toff.size(), "upload tile_off")) ||
-      (rc = upload(&ix->radius, ix->h_radius, (size_t)nlist, "upload radius"))) {
+      (rc = upload(&ix->radius, ix->h_radius, (size_t)nlist, "upload radius")) ||
+      (rc = prepare_coarse_tc(*ix, cent))) {
     free_index(ix);
     cudaSetDevice(prev);
     return rc;
@@ -273,6 +275,25 @@ extern "C" int anns_debug_tap(anns_index* ix, int32_t what, void* out, size_t by
     case ANNS_TAP_LIST_SIZES: src = ix->h_list_len64; need = (size_t)ix->nlist * 8; host = true; break;
     case ANNS_TAP_LIST_RADIUS: src = ix->h_radius; need = (size_t)ix->nlist * 4; host = true; break;
     case ANNS_TAP_PACKED_IDS: src = ix->ids; need = (size_t)ix->n * 8; break;
+    case ANNS_TAP_COARSE_APPROX:
+      if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use BF16 CL");
+      src = ix->ws_d2; need = (size_t)ix->ws_nq * ix->nlist * 4; break;
+    case ANNS_TAP_COARSE_CANDIDATES: {
+      if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use BF16 CL");
+      const size_t qb = ((size_t)ix->ws_nq * coarse_tc_dp(*ix) * 2 + 255) & ~size_t(255);
+      src = (const char*)ix->ws_tc + qb + (size_t)ix->ws_nq * 8;
+      need = (size_t)ix->ws_nq * 4;
+      break;
+    }
+    case ANNS_TAP_STATUS: {
+      if (bytes < 4) return fail(ANNS_ERR_INVALID_ARG, "tap buffer too small");
+      int v = 0;
+      cudaError_t e = cudaMemcpy(&v, ix->dev_status, 4, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemset(ix->dev_status, 0, 4);
+      if (e != cudaSuccess) return cuda_fail(e, "status tap");
+      *(int32_t*)out = v;
+      return ANNS_OK;
+    }
     default: return fail(ANNS_ERR_INVALID_ARG, "unknown tap");
   }
   if (bytes < need) return fail(ANNS_ERR_INVALID_ARG, "tap buffer too small");

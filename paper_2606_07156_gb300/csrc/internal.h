@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "anns_amp.h"
 
@@ -15,6 +16,8 @@ constexpr int kTileVecs = 32;         // vectors per code tile (one per lane)
 constexpr int kChunkBytes = 16;       // code bytes a lane loads at once
 constexpr int kTileChunkBytes = 512;  // one 16-byte chunk for all 32 lanes
 constexpr int kNFeat = 5, kH1 = 32, kH2 = 32, kNCls = 5;
+// Device status word values (Index::dev_status, ANNS_TAP_STATUS).
+constexpr int ANNS_DEV_TIMEOUT = 1;   // a bounded wait in a kernel ran out
 
 // Device-resident index (Section 2.1: IVF lists + PQ codes, one shared codebook).
 //
@@ -40,6 +43,12 @@ struct Index {
   // pair's LUT T' = P_l - 2 Q_q (the LUT shifted by ||r_m||^2, Section 2.1).
   float* ltab = nullptr;
   int32_t* order = nullptr;     // [nlist] list ids by size, largest first (ties by id)
+  // CL fast path (coarse_tc.cu): centroid mean, BF16 centred centroids
+  // [nlist * Dp], their norms (cn [nlist] then ch [nlist]); device status word
+  float* tc_mu = nullptr;
+  void* tc_cb = nullptr;
+  float* tc_cn = nullptr;
+  int* dev_status = nullptr;
   // host copies of the small per-list tables
   std::string err;
   int64_t* h_list_len64 = nullptr;
@@ -60,6 +69,9 @@ struct Index {
   size_t ws_lists_cap = 0;
   void* ws_sched = nullptr;      // query order of the LPT schedule (schedule.cu)
   size_t ws_sched_cap = 0;
+  void* ws_tc = nullptr;         // BF16 centred queries, norms, candidate counts (coarse_tc.cu)
+  size_t ws_tc_cap = 0;
+  bool ws_tc_valid = false;      // the last search used the CL fast path
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   int opt_schedule = 0;          // ANNS_SCHED_*
   // staging for anns_search_host
@@ -91,6 +103,13 @@ int grow(void** p, size_t* cap, size_t bytes);
 cudaError_t launch_coarse(const Index& ix, const float* Q, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, float* d2, int32_t* probes,
                           float* probe_d2, cudaStream_t s, cudaEvent_t between = nullptr);
+// CL fast path: BF16 tensor-core distances, then the exact re-rank (coarse_tc.cu).
+int coarse_tc_dp(const Index& ix);
+int prepare_coarse_tc(Index& ix, const std::vector<float>& cent);
+size_t coarse_tc_workspace_bytes(const Index& ix, int64_t nq);
+cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int nprobe,
+                             const int32_t* nprobe_per_q, void* ws, float* dt, int32_t* probes,
+                             float* probe_d2, cudaStream_t s);
 // Per-query tables 2*Q_q[m][c] = 2 <q_m, y_mc> (FP32 dot rule), rows M..Mp-1 zero.
 cudaError_t launch_query_tables(const Index& ix, const float* Q, int64_t nq, float* qt, cudaStream_t s);
 // Precision choice per (query, probe rank).
