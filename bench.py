@@ -216,6 +216,40 @@ def bits_mix(index, abi, nq: int, nprobe: int) -> dict:
     return {("fp32" if v == 0 else f"{v}bit"): round(float(np.mean(b == v)), 4) for v in (0, 4, 6, 8, 12, 16)}
 
 
+def cl_tensor_bench(amp, dev, steps: int, warmup: int, flush) -> dict:
+    """The coarse stage alone at the embedding-shaped CL size (20000 queries x
+    8192 centroids x D = 768, nprobe 64): FP32 CUDA-core path vs the tcgen05
+    BF16 GEMM + exact re-rank. Centroids are draws of the same mixture as the
+    queries (stand-ins for trained centroids; the stage's cost does not depend
+    on the lists' contents)."""
+    import torch
+    from workloads import make_queries
+    nq, nlist, dim, M, nprobe = 20000, 8192, 768, 96, 64
+    C = make_queries("E", nlist, stream=500)
+    Q = torch.from_numpy(make_queries("E", nq, stream=100)).to(dev)
+    books = np.zeros((M, 256, dim // M), np.float32)
+    codes = np.zeros((nlist, M), np.uint8)
+    ix = amp.Index(C, books, codes, np.arange(nlist, dtype=np.int32), device=dev.index)
+    st = torch.cuda.current_stream(dev)
+    out = {}
+    res = {}
+    for cl in ("fp32", "bf16"):
+        res[cl] = ix.locate(Q, nprobe, cl=cl, stream=st)
+        ms = time_steps(lambda: ix.locate(Q, nprobe, cl=cl, stream=st), steps, warmup, st, flush)
+        out[cl] = float(np.median(ms))
+    torch.cuda.synchronize()
+    same = bool(torch.equal(res["fp32"][0], res["bf16"][0]) and torch.equal(res["fp32"][1], res["bf16"][1]))
+    ncand = ix.tap(amp.abi.TAP_COARSE_CANDIDATES, (nq,), np.int32)
+    ix.close()
+    Dp = (dim + 63) // 64 * 64
+    flops = 2.0 * nq * nlist * Dp
+    return {"workload": f"embedding-shaped CL: {nq} queries x {nlist} centroids x D={dim}, nprobe={nprobe}",
+            "fp32_ms": round(out["fp32"], 4), "bf16_tc_ms": round(out["bf16"], 4),
+            "speedup": round(out["fp32"] / out["bf16"], 2), "identical_probes": same,
+            "rerank_candidates_mean": round(float(ncand.mean()), 1),
+            "gemm_flop": flops, "bf16_effective_tflops": round(flops / (out["bf16"] / 1e3) / 1e12, 1)}
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     import __graft_entry__
@@ -375,6 +409,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
     }
+    # the same step replayed as one CUDA graph
+    graph, _, _ = index.capture_graph(Q, nprobe, k, adaptive, out=out)
+    ms_graph = time_steps(lambda: graph.launch(stream), args.steps, args.warmup, stream, flush)
+    graph.close()
+    line["graph_ms_per_step"] = round(float(np.mean(ms_graph)), 4)
+    if not args.no_cl_bench:
+        line["cl_fastpath"] = cl_tensor_bench(amp, dev, max(3, args.steps // 4), args.warmup, flush)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(W, cfg, nprobe, 8, args.cpu_seconds)
     index.close()
@@ -440,6 +481,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cl-bench", action="store_true", help="skip the coarse-stage comparison")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

@@ -304,6 +304,16 @@ int anns_mlp_train(anns_index* index, const float* X, const uint8_t* cls, int64_
 int anns_train_predictor(anns_index* index, const float* train_q, int64_t nq, int32_t nprobe,
                          int32_t k, const anns_train_cfg* cfg, anns_predictor* out, void* cuda_stream);
 
+/* The coarse stage (cluster locating, CL of Section 2.1) alone: the nprobe
+ * nearest lists of each query by the FP32 rule, ties by list id, computed
+ * with cl_prec = ANNS_PREC_FP32 (CUDA cores) or ANNS_PREC_BF16 (tensor-core
+ * GEMM + exact re-rank; same output). probes_out device int32 [nq * nprobe],
+ * probe_d2_out device float32 [nq * nprobe] (padding -1 / +inf past a query's
+ * nprobe_per_q). Uses the index workspace (asynchronous on cuda_stream). */
+int anns_locate(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
+                const int32_t* nprobe_per_q, int32_t cl_prec, int32_t* probes_out, float* probe_d2_out,
+                void* cuda_stream);
+
 /* The coarse stage (cluster locating) without any allocation, for callers
  * that cannot allocate device memory: code running inside a CUDA graph
  * capture, hosts that forbid allocation after start-up, plugins whose host

@@ -148,6 +148,17 @@ class Index:
         v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "lists": abi.KERNEL_LIST_MAJOR}[which]
         abi.anns_set_option(self.handle, abi.OPT_KERNEL, v)
 
+    def locate(self, queries, nprobe: int, cl: str = "fp32", nprobe_per_q=None, stream=None):
+        """Coarse stage alone: (probes int32, probe_d2 float32) CUDA tensors [nq, nprobe]."""
+        import torch
+        nq = queries.shape[0]
+        probes = torch.empty((nq, nprobe), dtype=torch.int32, device=queries.device)
+        pd = torch.empty((nq, nprobe), dtype=torch.float32, device=queries.device)
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_locate(self.handle, _ptr(queries), nq, nprobe, _ptr(nprobe_per_q),
+                        {"fp32": abi.PREC_FP32, "bf16": abi.PREC_BF16}[cl], _ptr(probes), _ptr(pd), s)
+        return probes, pd
+
     def set_schedule(self, which: str):
         """'auto', 'natural' or 'lpt' (longest query first) for the query-major kernel."""
         v = {"auto": abi.SCHED_AUTO, "natural": abi.SCHED_NATURAL, "lpt": abi.SCHED_LPT}[which]

@@ -31,7 +31,8 @@ SYMBOLS = (
     "anns_get_info", "anns_debug_tap", "anns_compute_luts", "anns_scan_pairs", "anns_profile",
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
-    "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_last_error",
+    "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
+    "anns_last_error",
 )
 
 
@@ -99,6 +100,7 @@ def _load():
         "anns_graph_capture": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), vp, vp,
                                 ctypes.POINTER(vp)], i32),
         "anns_graph_launch": ([vp, vp], i32),
+        "anns_locate": ([vp, vp, i64, i32, vp, i32, vp, vp, vp], i32),
         "anns_graph_free": ([vp], None),
         "anns_autotune": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), i32,
                            ctypes.POINTER(anns_tune_result), i32, ctypes.POINTER(i32), vp], i32),
@@ -245,3 +247,7 @@ def anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, policy, 
     _check(_lib.anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, pol, reps, res, 8,
                               ctypes.byref(n), stream))
     return [(res[i].kernel, res[i].schedule, res[i].ms) for i in range(n.value)]
+
+
+def anns_locate(index, queries, nq, nprobe, nprobe_per_q, cl_prec, probes_out, probe_d2_out, stream=None) -> None:
+    _check(_lib.anns_locate(index, queries, nq, nprobe, nprobe_per_q, cl_prec, probes_out, probe_d2_out, stream))

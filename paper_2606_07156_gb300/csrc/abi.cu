@@ -259,6 +259,7 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
   if (ev) cudaEventRecord(ev[0], s);
   cudaError_t e;
   ix.ws_tc_valid = P.cl_prec == ANNS_PREC_BF16;
+  ix.ws_tc_nq = nq;
   if (ix.ws_tc_valid) {
     if (ev) cudaEventRecord(ev[1], s);
     e = launch_coarse_tc(ix, Q, nq, nprobe, nprobe_per_q, ix.ws_tc, ix.ws_d2, ix.ws_probes, ix.ws_probe_d2, s);
@@ -331,6 +332,33 @@ extern "C" int anns_search(anns_index* ix, const float* Q, int64_t nq, int32_t n
   plain.lut_mode = ANNS_LUT_PLAIN_FP32;
   return search_sequence(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, pol ? *pol : plain, ids_out, dists_out,
                          (cudaStream_t)stream, true);
+}
+
+extern "C" int anns_locate(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe,
+                           const int32_t* nprobe_per_q, int32_t cl_prec, int32_t* probes_out,
+                           float* probe_d2_out, void* stream) {
+  if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
+  if (nq < 0) return fail(ANNS_ERR_INVALID_ARG, "nq must be >= 0");
+  if (nprobe < 1 || nprobe > ix->nlist || nprobe > ANNS_MAX_NPROBE)
+    return fail(ANNS_ERR_INVALID_ARG, "nprobe must be in [1, min(nlist, 128)]");
+  if (cl_prec != ANNS_PREC_FP32 && cl_prec != ANNS_PREC_BF16)
+    return fail(ANNS_ERR_UNSUPPORTED, "CL operands: FP32 or BF16 (with exact re-rank)");
+  if (nq == 0) return ANNS_OK;
+  if (!Q || !probes_out || !probe_d2_out) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
+  DeviceGuard g(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = grow((void**)&ix->ws_d2, &ix->ws_d2_cap, (size_t)nq * ix->nlist * 4);
+  if (rc) return rc;
+  cudaError_t e;
+  ix->ws_tc_valid = cl_prec == ANNS_PREC_BF16;
+  ix->ws_tc_nq = nq;
+  if (cl_prec == ANNS_PREC_BF16) {
+    if ((rc = grow(&ix->ws_tc, &ix->ws_tc_cap, coarse_tc_workspace_bytes(*ix, nq)))) return rc;
+    e = launch_coarse_tc(*ix, Q, nq, nprobe, nprobe_per_q, ix->ws_tc, ix->ws_d2, probes_out, probe_d2_out, s);
+  } else {
+    e = launch_coarse(*ix, Q, nq, nprobe, nprobe_per_q, ix->ws_d2, probes_out, probe_d2_out, s);
+  }
+  return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "coarse kernels");
 }
 
 extern "C" int anns_search_host(anns_index* ix, const float* Q, int64_t nq, int32_t nprobe,

@@ -13,7 +13,7 @@
 //    layout, one thread issuing the MMAs, completion through tcgen05.commit
 //    on an mbarrier, the accumulator read back with tcgen05.ld.
 // 3. Error bound per pair: |D~ - D2| <= eps(D~, norms), D2 the FP32-rule
-//    distance (derivation at rerank_bound). T = the nprobe-th smallest of
+//    distance (derivation at rerank_bound). T >= the nprobe-th smallest of
 //    D~ + eps; every list of the FP32 top-nprobe has D~ - eps <= T, so those
 //    candidates are re-ranked with the FP32 rule itself (same operation order
 //    as coarse.cu) and the nprobe smallest (D2, l) kept: identical output to
@@ -119,16 +119,17 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// One warp per row: x^ = fl32(x - mu) in BF16 (zero past dim), xn = FP32 sum
-// of the squared BF16 values, xh = ||x^||_2 computed in FP64 and rounded up.
+// One warp per row: x^ = fl32(x - mu) in BF16 (zero past dim); per row
+// xn = FP32 sum of the squared BF16 values, xh >= ||x^||_2 and
+// xe >= ||bf16(x^) - x^||_2 (both from FP64 sums, rounded up).
 __global__ void center_bf16_kernel(const float* __restrict__ X, int64_t n, int dim, int Dp,
                                    const float* __restrict__ mu, __nv_bfloat16* __restrict__ Xb,
-                                   float* __restrict__ xn, float* __restrict__ xh) {
+                                   float* __restrict__ xn, float* __restrict__ xh, float* __restrict__ xe) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   float s = 0.f;
-  double h = 0.0;
+  double h = 0.0, r = 0.0;
   for (int d = lane; d < Dp; d += 32) {
     float v = 0.f;
     if (d < dim) v = sub_rn(X[row * dim + d], mu[d]);
@@ -137,15 +138,19 @@ __global__ void center_bf16_kernel(const float* __restrict__ X, int64_t n, int d
     const float bf = __bfloat162float(b);
     s = add_rn(s, mul_rn(bf, bf));
     h += (double)v * (double)v;
+    const double dv = (double)bf - (double)v;
+    r += dv * dv;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     s = add_rn(s, __shfl_xor_sync(kFull, s, o));
     h += __shfl_xor_sync(kFull, h, o);
+    r += __shfl_xor_sync(kFull, r, o);
   }
   if (lane == 0) {
     xn[row] = s;
     xh[row] = __double2float_ru(sqrt(h) * (1.0 + 1e-12));
+    xe[row] = __double2float_ru(sqrt(r) * (1.0 + 1e-12));
   }
 }
 
@@ -232,101 +237,163 @@ __global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
 
 // eps >= |D~ - D2| for a pair, D2 the FP32-rule distance. With x^ the centred
 // FP32 vectors and x~ their BF16 roundings, delta = (q~ - c~) - (q - c) has
-// ||delta|| <= dn = 2^-8 (1 + 2^-15)(qh + ch) (BF16 relative rounding 2^-8,
+// ||delta|| <= dn = qe + ce + 2^-23 (qh + ch) (the rows' BF16 rounding errors
 // plus the FP32 centring). S = ||q~ - c~||^2 differs from D~ by the FP32
 // evaluation error e_f <= (2 Dp + 8) 2^-24 (qn + cn) (norm sums, the FP32
 // accumulator of the products, the final combination), from the exact
 // distance by at most dn (2 sqrt(S) + dn), and the FP32 rule differs from the
 // exact distance by at most (dim + 2) 2^-24 of it. Constants padded by 1 %.
-__device__ __forceinline__ float rerank_bound(float dt, float qn, float cn, float qh, float ch, int dim, int Dp) {
-  const float ef = (float)(2 * Dp + 8) * 5.9604645e-8f * (qn + cn) * 1.01f;
-  const float dn = 3.90625e-3f * (1.0f + 3.0517578e-5f) * (qh + ch) * 1.01f;
+struct RowNorms { float n, h, e; };
+__device__ __forceinline__ float rerank_bound(float dt, RowNorms q, RowNorms c, int dim, int Dp) {
+  const float ef = (float)(2 * Dp + 8) * 5.9604645e-8f * (q.n + c.n) * 1.01f;
+  const float dn = (q.e + c.e + 1.1920929e-7f * (q.h + c.h)) * 1.01f;
   const float sup = fmaxf(dt, 0.f) + ef;
   const float E = dn * (2.f * sqrtf(sup) * 1.01f + dn);
   return (ef + E + (float)(dim + 2) * 5.9604645e-8f * (sup + E)) * 1.01f + 1e-30f;
 }
 
-// FP32-rule distance (same operation order as coarse.cu).
-__device__ __forceinline__ float exact_d2(const float* __restrict__ qv, const float* __restrict__ cv, int dim) {
+constexpr int kRWarps = 8, kRThreads = kRWarps * 32;
+
+// Distances (FP32 rule) of up to 32 candidates, one per lane: the warp loads
+// the candidates' centroid rows 32 dimensions at a time into a transposed
+// tile (coalesced row segments) and each lane accumulates its own row in
+// ascending dimension order.
+__device__ __forceinline__ float batch_d2(const float* __restrict__ C, const float* qs, int dim, int32_t lc, int nc,
+                                          float (*tile)[33]) {
+  const int lane = threadIdx.x & 31;
   float acc = 0.f;
-  for (int d = 0; d < dim; ++d) {
-    const float e = sub_rn(qv[d], cv[d]);
-    acc = add_rn(acc, mul_rn(e, e));
+  for (int d0 = 0; d0 < dim; d0 += 32) {
+    for (int r = 0; r < 32; ++r) {
+      const int32_t lr = __shfl_sync(kFull, lc, r);
+      tile[r][lane] = (r < nc && d0 + lane < dim) ? __ldg(C + (int64_t)lr * dim + d0 + lane) : 0.f;
+    }
+    __syncwarp();
+    const int dd_end = min(32, dim - d0);
+    for (int dd = 0; dd < dd_end; ++dd) {
+      const float e = sub_rn(qs[d0 + dd], tile[lane][dd]);
+      acc = add_rn(acc, mul_rn(e, e));
+    }
+    __syncwarp();
   }
   return acc;
 }
 
-// One 256-thread block per query: T from the upper bounds, then the exact
-// top-np over the candidates. Writes nprobe entries (padding -1 / +inf) and
-// the number of candidates re-ranked.
+// One block per query.
+// Pass 1: T >= the np-th smallest upper bound u = D~ + eps, by a two-level
+//   256-bucket radix select on the bits of u (non-negative floats order like
+//   their bit patterns); T is the top of the bucket holding the np-th value.
+// Pass 2: each warp scans its lists (strided), queues the candidates with
+//   D~ - eps <= T (ballot compaction into a per-warp buffer), computes their
+//   FP32-rule distances 32 at a time and keeps its top-np by (D2, l); the
+//   warps' lists are merged at the end. Writes nprobe entries (padding -1 /
+//   +inf) and the number of candidates.
 template <int R>
-__global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ Q, const float* __restrict__ C,
-                                                     const float* __restrict__ dt, const float* __restrict__ qn,
-                                                     const float* __restrict__ qh, const float* __restrict__ cn,
-                                                     const float* __restrict__ ch, int64_t nq, int64_t nlist,
-                                                     int dim, int Dp, int nprobe, const int32_t* __restrict__ npq,
-                                                     int32_t* __restrict__ probes, float* __restrict__ probe_d2,
-                                                     int* __restrict__ ncand) {
-  __shared__ float md[8][R * 32];
-  __shared__ int32_t mi[8][R * 32];
-  __shared__ float Tsh;
-  __shared__ int cnt;
+__global__ void __launch_bounds__(kRThreads) rerank_kernel(
+    const float* __restrict__ Q, const float* __restrict__ C, const float* __restrict__ dt,
+    const float* __restrict__ qrows, const float* __restrict__ crows, int64_t nq, int64_t nlist, int dim, int Dp,
+    int nprobe, const int32_t* __restrict__ npq, int32_t* __restrict__ probes, float* __restrict__ probe_d2,
+    int* __restrict__ ncand) {
+  __shared__ float md[kRWarps][R * 32];
+  __shared__ int32_t mi[kRWarps][R * 32];
+  __shared__ float tile[kRWarps][32][33];
+  __shared__ int32_t qbuf[kRWarps][64];
+  __shared__ int hist[256];
+  __shared__ uint32_t sel_bucket, sel_before;
+  __shared__ int total;
+  float* qs = (float*)anns_dyn_smem;  // [dim]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q = blockIdx.x;
   const int np = npq ? min(max(npq[q], 0), nprobe) : nprobe;
   const float* row = dt + q * nlist;
-  const float qnv = qn[q], qhv = qh[q];
-  const float* qv = Q + q * dim;
-  if (threadIdx.x == 0) cnt = 0;
-  // pass 1: T = np-th smallest upper bound D~ + eps
+  const RowNorms qr = {qrows[q], qrows[nq + q], qrows[2 * nq + q]};
+  for (int d = threadIdx.x; d < dim; d += kRThreads) qs[d] = Q[q * dim + d];
+  if (threadIdx.x == 0) total = 0;
+  auto upper_key = [&](int64_t l) {
+    const RowNorms cr = {crows[l], crows[nlist + l], crows[2 * nlist + l]};
+    return __float_as_uint(fmaxf(row[l] + rerank_bound(row[l], qr, cr, dim, Dp), 0.f));
+  };
+  // pass 1: two radix levels of 8 bits
+  float T = INFINITY;
+  if (np > 0) {
+    uint32_t prefix = 0, before = 0;
+    for (int level = 0; level < 2; ++level) {
+      const int shift = 24 - 8 * level;
+      for (int i = threadIdx.x; i < 256; i += kRThreads) hist[i] = 0;
+      __syncthreads();
+      for (int64_t l = threadIdx.x; l < nlist; l += kRThreads) {
+        const uint32_t key = upper_key(l);
+        if (level == 0 || (key >> 24) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // bucket where the running count (after `before`) reaches np
+        int c[8], run = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { c[i] = hist[lane * 8 + i]; run += c[i]; }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int excl = incl - run;
+        const uint32_t need = (uint32_t)np - before;
+        if ((uint32_t)excl < need && need <= (uint32_t)incl) {
+          int acc = excl;
+          for (int i = 0; i < 8; ++i) {
+            if ((uint32_t)(acc + c[i]) >= need) { sel_bucket = (uint32_t)(lane * 8 + i); sel_before = (uint32_t)acc; break; }
+            acc += c[i];
+          }
+        }
+      }
+      __syncthreads();
+      prefix = level == 0 ? sel_bucket : prefix;
+      if (level == 0) before += sel_before;
+      else T = __uint_as_float((prefix << 24) | (sel_bucket << 16) | 0xFFFFu);
+    }
+  }
+  // pass 2
   WarpTopK<R, int32_t> top;
   top.init();
   float thd = INFINITY;
   int32_t thi = INT32_MAX;
-  if (np > 0) {
-    for (int64_t b0 = (int64_t)warp * 32; b0 < nlist; b0 += 256) {
-      const int64_t l = b0 + lane;
-      const bool valid = l < nlist;
-      float u = INFINITY;
-      if (valid) u = row[l] + rerank_bound(row[l], qnv, cn[l], qhv, ch[l], dim, Dp);
-      top.offer(valid, u, (int32_t)l, np, thd, thi);
+  int nq_w = 0, seen = 0;
+  for (int64_t b0 = (int64_t)warp * 32; np > 0 && b0 < nlist; b0 += kRThreads) {
+    const int64_t l = b0 + lane;
+    bool cand = false;
+    if (l < nlist) {
+      const RowNorms cr = {crows[l], crows[nlist + l], crows[2 * nlist + l]};
+      cand = row[l] - rerank_bound(row[l], qr, cr, dim, Dp) <= T;
+    }
+    const unsigned m = __ballot_sync(kFull, cand);
+    if (cand) qbuf[warp][nq_w + __popc(m & ((1u << lane) - 1u))] = (int32_t)l;
+    nq_w += __popc(m);
+    __syncwarp();
+    if (nq_w >= 32) {
+      const int32_t lc = qbuf[warp][lane];
+      const float d = batch_d2(C, qs, dim, lc, 32, tile[warp]);
+      top.offer(true, d, lc, np, thd, thi);
+      seen += 32;
+      const int rest = nq_w - 32;
+      const int32_t mv = lane < rest ? qbuf[warp][32 + lane] : 0;
+      __syncwarp();
+      if (lane < rest) qbuf[warp][lane] = mv;
+      nq_w = rest;
+      __syncwarp();
     }
   }
+  if (nq_w > 0) {
+    const int32_t lc = lane < nq_w ? qbuf[warp][lane] : 0;
+    const float d = batch_d2(C, qs, dim, lc, nq_w, tile[warp]);
+    top.offer(lane < nq_w, d, lc, np, thd, thi);
+    seen += nq_w;
+  }
+  if (lane == 0 && seen) atomicAdd(&total, seen);
 #pragma unroll
   for (int r = 0; r < R; ++r) { md[warp][r * 32 + lane] = top.d[r]; mi[warp][r * 32 + lane] = top.id[r]; }
   __syncthreads();
   if (warp == 0) {
-    for (int w = 1; w < 8 && np > 0; ++w)
-#pragma unroll
-      for (int r = 0; r < R; ++r) top.offer(md[w][r * 32 + lane] != INFINITY, md[w][r * 32 + lane],
-                                            mi[w][r * 32 + lane], np, thd, thi);
-    if (lane == 0) Tsh = thd;  // entry np - 1 (+inf if fewer lists)
-  }
-  __syncthreads();
-  const float T = Tsh;
-  // pass 2: exact distances of the candidates, top-np by (D2, l)
-  top.init();
-  thd = INFINITY;
-  thi = INT32_MAX;
-  if (np > 0) {
-    for (int64_t b0 = (int64_t)warp * 32; b0 < nlist; b0 += 256) {
-      const int64_t l = b0 + lane;
-      bool cand = false;
-      if (l < nlist) cand = row[l] - rerank_bound(row[l], qnv, cn[l], qhv, ch[l], dim, Dp) <= T;
-      float d = INFINITY;
-      if (cand) {
-        d = exact_d2(qv, C + l * dim, dim);
-        atomicAdd(&cnt, 1);
-      }
-      top.offer(cand, d, (int32_t)l, np, thd, thi);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < R; ++r) { md[warp][r * 32 + lane] = top.d[r]; mi[warp][r * 32 + lane] = top.id[r]; }
-  __syncthreads();
-  if (warp == 0) {
-    for (int w = 1; w < 8 && np > 0; ++w)
+    for (int w = 1; w < kRWarps && np > 0; ++w)
 #pragma unroll
       for (int r = 0; r < R; ++r) top.offer(md[w][r * 32 + lane] != INFINITY, md[w][r * 32 + lane],
                                             mi[w][r * 32 + lane], np, thd, thi);
@@ -339,7 +406,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ Q
         probe_d2[q * nprobe + e] = ok ? top.d[r] : INFINITY;
       }
     }
-    if (lane == 0 && ncand) ncand[q] = cnt;
+    if (lane == 0 && ncand) ncand[q] = total;
   }
 }
 
@@ -357,21 +424,21 @@ int prepare_coarse_tc(Index& ix, const std::vector<float>& cent) {
   for (int64_t d = 0; d < ix.dim; ++d) mu[d] = (float)(mu64[d] / (double)ix.nlist);
   cudaError_t e = cudaMalloc(&ix.tc_mu, ix.dim * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&ix.tc_cb, (size_t)ix.nlist * Dp * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&ix.tc_cn, (size_t)ix.nlist * 2 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&ix.tc_cn, (size_t)ix.nlist * 3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&ix.dev_status, 16);
   if (e == cudaSuccess) e = cudaMemcpy(ix.tc_mu, mu.data(), ix.dim * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ix.dev_status, 0, 16);
   if (e != cudaSuccess) return cuda_fail(e, "coarse fast-path setup");
   center_bf16_kernel<<<(unsigned)((ix.nlist + 7) / 8), 256>>>(ix.centroids, ix.nlist, (int)ix.dim, Dp, ix.tc_mu,
                                                              (__nv_bfloat16*)ix.tc_cb, ix.tc_cn,
-                                                             ix.tc_cn + ix.nlist);
+                                                             ix.tc_cn + ix.nlist, ix.tc_cn + 2 * ix.nlist);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "coarse fast-path setup");
 }
 
 size_t coarse_tc_workspace_bytes(const Index& ix, int64_t nq) {
-  return (size_t)nq * coarse_tc_dp(ix) * 2 + (size_t)nq * 3 * 4 + 256;
+  return (size_t)nq * coarse_tc_dp(ix) * 2 + (size_t)nq * 4 * 4 + 256;
 }
 
 cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int nprobe,
@@ -379,26 +446,33 @@ cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int np
                              float* probe_d2, cudaStream_t s) {
   const int Dp = coarse_tc_dp(ix);
   __nv_bfloat16* Qb = (__nv_bfloat16*)ws;
-  float* qn = (float*)((char*)ws + (((size_t)nq * Dp * 2 + 255) & ~size_t(255)));
-  float* qh = qn + nq;
-  int* ncand = (int*)(qh + nq);
-  center_bf16_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, (int)ix.dim, Dp, ix.tc_mu, Qb, qn, qh);
+  float* qrows = (float*)((char*)ws + (((size_t)nq * Dp * 2 + 255) & ~size_t(255)));  // qn | qh | qe
+  int* ncand = (int*)(qrows + 3 * nq);
+  center_bf16_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, (int)ix.dim, Dp, ix.tc_mu, Qb, qrows,
+                                                              qrows + nq, qrows + 2 * nq);
   cudaError_t e = cudaFuncSetAttribute(coarse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kGemmSmem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((ix.nlist + kTN - 1) / kTN), (unsigned)((nq + kTM - 1) / kTM));
-  coarse_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(Qb, (const __nv_bfloat16*)ix.tc_cb, qn, ix.tc_cn, nq,
+  coarse_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(Qb, (const __nv_bfloat16*)ix.tc_cb, qrows, ix.tc_cn, nq,
                                                          ix.nlist, Dp, dt, ix.dev_status);
-  const float* cn = ix.tc_cn;
-  const float* ch = ix.tc_cn + ix.nlist;
   const int R = (nprobe + 31) / 32;
   const unsigned g = (unsigned)nq;
+  const size_t qsm = (size_t)ix.dim * sizeof(float);
+  auto run = [&](auto kern) {
+    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
+    if (e2 != cudaSuccess) return e2;
+    kern<<<g, kRThreads, qsm, s>>>(Q, ix.centroids, dt, qrows, ix.tc_cn, nq, ix.nlist, (int)ix.dim, Dp, nprobe,
+                                   nprobe_per_q, probes, probe_d2, ncand);
+    return cudaGetLastError();
+  };
   switch (R) {
-    case 1: rerank_kernel<1><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
-    case 2: rerank_kernel<2><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
-    case 3: rerank_kernel<3><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
-    default: rerank_kernel<4><<<g, 256, 0, s>>>(Q, ix.centroids, dt, qn, qh, cn, ch, nq, ix.nlist, (int)ix.dim, Dp, nprobe, nprobe_per_q, probes, probe_d2, ncand); break;
+    case 1: e = run(rerank_kernel<1>); break;
+    case 2: e = run(rerank_kernel<2>); break;
+    case 3: e = run(rerank_kernel<3>); break;
+    default: e = run(rerank_kernel<4>); break;
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -277,12 +277,12 @@ extern "C" int anns_debug_tap(anns_index* ix, int32_t what, void* out, size_t by
     case ANNS_TAP_PACKED_IDS: src = ix->ids; need = (size_t)ix->n * 8; break;
     case ANNS_TAP_COARSE_APPROX:
       if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use BF16 CL");
-      src = ix->ws_d2; need = (size_t)ix->ws_nq * ix->nlist * 4; break;
+      src = ix->ws_d2; need = (size_t)ix->ws_tc_nq * ix->nlist * 4; break;
     case ANNS_TAP_COARSE_CANDIDATES: {
       if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use BF16 CL");
-      const size_t qb = ((size_t)ix->ws_nq * coarse_tc_dp(*ix) * 2 + 255) & ~size_t(255);
-      src = (const char*)ix->ws_tc + qb + (size_t)ix->ws_nq * 8;
-      need = (size_t)ix->ws_nq * 4;
+      const size_t qb = ((size_t)ix->ws_tc_nq * coarse_tc_dp(*ix) * 2 + 255) & ~size_t(255);
+      src = (const char*)ix->ws_tc + qb + (size_t)ix->ws_tc_nq * 12;
+      need = (size_t)ix->ws_tc_nq * 4;
       break;
     }
     case ANNS_TAP_STATUS: {

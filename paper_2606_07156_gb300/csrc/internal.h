@@ -44,7 +44,7 @@ struct Index {
   float* ltab = nullptr;
   int32_t* order = nullptr;     // [nlist] list ids by size, largest first (ties by id)
   // CL fast path (coarse_tc.cu): centroid mean, BF16 centred centroids
-  // [nlist * Dp], their norms (cn [nlist] then ch [nlist]); device status word
+  // [nlist * Dp], per-row norms (cn, ch, ce: [3 * nlist]); device status word
   float* tc_mu = nullptr;
   void* tc_cb = nullptr;
   float* tc_cn = nullptr;
@@ -71,7 +71,8 @@ struct Index {
   size_t ws_sched_cap = 0;
   void* ws_tc = nullptr;         // BF16 centred queries, norms, candidate counts (coarse_tc.cu)
   size_t ws_tc_cap = 0;
-  bool ws_tc_valid = false;      // the last search used the CL fast path
+  bool ws_tc_valid = false;      // the last search (or anns_locate) used the CL fast path
+  int64_t ws_tc_nq = 0;          // ... for this many queries
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   int opt_schedule = 0;          // ANNS_SCHED_*
   // staging for anns_search_host

@@ -53,10 +53,12 @@ def _bound(Q, C, dt):
     qn, cn = (qb ** 2).sum(1), (cb ** 2).sum(1)
     qh = np.linalg.norm(qh_.astype(np.float64), axis=1)
     ch = np.linalg.norm(ch_.astype(np.float64), axis=1)
+    qe = np.linalg.norm(qb - qh_, axis=1)
+    ce = np.linalg.norm(cb - ch_, axis=1)
     dim = Q.shape[1]
     Dp = (dim + 63) // 64 * 64
     ef = (2 * Dp + 8) * 2.0 ** -24 * (qn[:, None] + cn[None, :])
-    dn = 2.0 ** -8 * (1 + 2.0 ** -15) * (qh[:, None] + ch[None, :])
+    dn = qe[:, None] + ce[None, :] + 2.0 ** -23 * (qh[:, None] + ch[None, :])
     sup = np.maximum(dt, 0) + ef
     E = dn * (2 * np.sqrt(sup) + dn)
     return ef + E + (dim + 2) * 2.0 ** -24 * (sup + E)
@@ -121,3 +123,13 @@ def test_bf16_rejects_bf16_lut(amp, geo):
     p.lc_prec = amp.abi.PREC_BF16
     with pytest.raises(amp.abi.AnnsError):
         g.search(cuda(d["queries"][:4]), 4, 5, p)
+
+
+def test_locate_entry_point(amp, geo):
+    key, d, ix, g, o = geo
+    Q = d["queries"]
+    rp, rd = ivfpq.locate(ivfpq.coarse_d2_fp32(Q, o.centroids), 9)
+    for cl in ("fp32", "bf16"):
+        p, pd = g.locate(cuda(Q), 9, cl=cl)
+        np.testing.assert_array_equal(p.cpu().numpy(), rp)
+        np.testing.assert_array_equal(pd.cpu().numpy(), rd)
