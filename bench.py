@@ -198,11 +198,13 @@ def calibrate_margin(index, amp, Qc, nprobe: int, k: int, run, target: float = 0
 
 
 def calibrate_eq2(amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
-    """Most aggressive Eq. 2 threshold set (t*(4,3,2,1)) keeping >= target of plain."""
+    """Most aggressive Eq. 2 threshold set th = (t + 1.5, t + 1, t + 0.5, t) for
+    4, 6, 8, 12 bits (widths mapped to this GPU's tables) keeping >= target of
+    the plain top-k on held-out queries."""
     ref = run(Qc, nprobe, amp.policy("plain"))
     best, tried = None, {}
-    for t in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0):
-        th = (4 * t, 3 * t, 2 * t, t)
+    for t in (-3.0, -2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 1.0, 2.0, 4.0):
+        th = (t + 1.5, t + 1.0, t + 0.5, t)
         ov = overlap(run(Qc, nprobe, amp.policy("eq2", thresholds=th, width_map=True)), ref, k)
         tried[t] = ov
         if ov >= target:
@@ -485,9 +487,21 @@ def main():
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--only-cl", action="store_true",
+                    help="run only the coarse-stage comparison (for profiling its kernels)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.only_cl:
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2606_07156_gb300 as amp
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps({"cl_fastpath": cl_tensor_bench(amp, dev, args.steps, args.warmup, flush)}), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
