@@ -240,7 +240,11 @@ def test_train_predictor_learns(amp, pair):
     Q = d["queries"]
     ids, dists = g.search(cuda(Q), nprobe, k, amp.policy("mlp", margin=0.0))
     torch.cuda.synchronize()
-    bits = g.tap(amp.abi.TAP_BITS, (len(Q), nprobe), np.uint8)
+    F = _oracle_features(o, Q, nprobe).reshape(-1, 5)
+    z = predictor.mlp_logits16(predictor.to_fp16({k2: p[k2] for k2 in ("W1", "b1", "W2", "b2", "W3", "b3")}),
+                               predictor.normalise(F, p["mean"], p["inv_std"]))
+    bits = predictor.decide_bits(z, 0.0).reshape(len(Q), nprobe)
+    np.testing.assert_array_equal(g.tap(amp.abi.TAP_BITS, (len(Q), nprobe), np.uint8), bits)
     ri, rd = ivfpq.search(o, Q, nprobe, k, bits=bits)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
     np.testing.assert_array_equal(dists.cpu().numpy(), rd)
