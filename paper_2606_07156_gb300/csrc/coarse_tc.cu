@@ -7,11 +7,14 @@
 //    norms the rounding error scales with), rounded to BF16 (nearest even)
 //    and zero-padded to Dp = dim rounded up to 64. Per row: qn = sum of the
 //    squared BF16 values (FP32), qh >= ||q^||_2.
-// 2. D~[q][l] = fl32(fl32(qn + cn) - fl32(2 <q~, c~>)): a 128 x 128 tile per
-//    CTA, tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulator in TMEM),
-//    operands staged in shared memory in the canonical no-swizzle K-major
-//    layout, one thread issuing the MMAs, completion through tcgen05.commit
-//    on an mbarrier, the accumulator read back with tcgen05.ld.
+// 2. D~[q][l] = fl32(fl32(qn + cn) - fl32(2 <q~, c~>)): a 128 x 256 tile per
+//    CTA, tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulator in TMEM). One
+//    thread loads 64-wide K chunks of both operands with TMA (128-byte
+//    swizzle) into a 4-stage ring (full barriers: TMA transaction bytes);
+//    another issues the MMAs and releases each stage with tcgen05.commit
+//    (empty barriers); a final commit hands the accumulator to all four
+//    warps, which read it with tcgen05.ld, stage the tile in shared memory
+//    and write it out row by row.
 // 3. Error bound per pair: |D~ - D2| <= eps(D~, norms), D2 the FP32-rule
 //    distance (derivation at rerank_bound). T >= the nprobe-th smallest of
 //    D~ + eps; every list of the FP32 top-nprobe has D~ - eps <= T, so those
@@ -22,7 +25,9 @@
 // Every mbarrier wait is bounded (about a second); on a timeout the kernel
 // records ANNS_DEV_TIMEOUT in the index's device status word, waits once
 // more (bounded) for its MMAs, frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <vector>
@@ -35,14 +40,15 @@ namespace anns {
 namespace {
 
 constexpr int kTM = 128;             // queries per tile = TMEM lanes
-constexpr int kTN = 128;             // centroids per tile = FP32 TMEM columns
-constexpr int kKC = 64;              // K elements per staged chunk (4 MMAs of K = 16)
+constexpr int kTN = 256;             // centroids per tile = FP32 TMEM columns
+constexpr int kKC = 64;              // K elements per stage (4 MMAs of K = 16; one 128-byte swizzle row)
+constexpr int kStages = 4;
 constexpr int kGemmThreads = 128;    // one warpgroup: warp w reads TMEM lanes 32w..32w+31
-constexpr uint32_t kOpBytes = kTM * kKC * 2;  // 16 KB per operand chunk
-// Dynamic shared memory per CTA, padded so that at most four CTAs share an SM:
-// 4 x 128 columns never exceed the SM's 512 TMEM columns, so tcgen05.alloc
-// never waits.
-constexpr size_t kGemmSmem = 57 * 1024;
+constexpr uint32_t kABytes = kTM * kKC * 2;   // 16 KB
+constexpr uint32_t kBBytes = kTN * kKC * 2;   // 32 KB
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
+// ring + barriers + 1 KB alignment slack; one CTA per SM (256 of 512 TMEM columns)
+constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + 1024 + 256;
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 // Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits 7-9 =
@@ -51,25 +57,34 @@ constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
                             ((uint32_t)(kTM >> 4) << 24);
 
-// Byte offset of element (r, k) of a [128 x 64] BF16 chunk: core matrices of
-// 8 rows x 16 bytes, K-adjacent core matrices 128 bytes apart (LBO), 8-row
-// groups 1024 bytes apart (SBO).
-__device__ __forceinline__ uint32_t core_off(int r, int k) {
-  return (uint32_t)((((r >> 3) * (kKC / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
-}
-constexpr uint32_t kLBO = 128, kSBO = (kKC / 8) * 128;
-
-// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), LBO >> 4
-// (16-29), SBO >> 4 (32-45), descriptor version 1 (46-47), base offset 0,
-// no swizzle (61-63 = 0).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor of a K-major operand written by TMA with the
+// 128-byte swizzle: start address >> 4 (bits 0-13), leading offset unused for
+// swizzled K-major (encoded 1), stride between 8-row groups 1024 bytes >> 4
+// (bits 32-45), descriptor version 1 (46-47), base offset 0 (1024-byte
+// aligned atoms), layout 128-byte swizzle (61-63 = 2). Within the 128-byte
+// row, the k-th group of 16 elements starts 32 k bytes further.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 2-D tiled TMA load of box (x, y) of the tensor map into shared memory,
+// completing `bytes` on the mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 
 // Bounded wait on phase `parity` of the mbarrier; false on timeout.
@@ -154,19 +169,19 @@ __global__ void center_bf16_kernel(const float* __restrict__ X, int64_t n, int d
   }
 }
 
-// D~ for a 128 x 128 tile (grid: x over centroid tiles, y over query tiles).
+// D~ for a 128 x 256 tile (grid: x over centroid tiles, y over query tiles).
 __global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
-    const __nv_bfloat16* __restrict__ Qb, const __nv_bfloat16* __restrict__ Cb, const float* __restrict__ qn,
+    const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmC, const float* __restrict__ qn,
     const float* __restrict__ cn, int64_t nq, int64_t nlist, int Dp, float* __restrict__ dt,
     int* __restrict__ status) {
   unsigned char* base = anns_dyn_smem + ((1024u - (smem_addr(anns_dyn_smem) & 1023u)) & 1023u);
-  unsigned char* As = base;
-  unsigned char* Bs = base + kOpBytes;
-  uint64_t* bar = (uint64_t*)(base + 2 * kOpBytes);
-  uint32_t* slot = (uint32_t*)(base + 2 * kOpBytes + 16);
-  const uint32_t a_addr = smem_addr(As), b_addr = smem_addr(Bs), bar_addr = smem_addr(bar);
+  uint64_t* bars = (uint64_t*)(base + kStages * kStageBytes);  // full[S] | empty[S] | done
+  uint32_t* slot = (uint32_t*)(bars + 2 * kStages + 1);
+  const uint32_t ring = smem_addr(base);
+  const uint32_t full0 = smem_addr(bars), empty0 = full0 + 8 * kStages, done = full0 + 16 * kStages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t q0 = (int64_t)blockIdx.y * kTM, l0 = (int64_t)blockIdx.x * kTN;
+  const int q0 = (int)(blockIdx.y * kTM), l0 = (int)(blockIdx.x * kTN);
+  const int nK = Dp / kKC;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
@@ -174,59 +189,77 @@ __global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) mbar_init(bar_addr, 1);
+  if (tid == 32) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    mbar_init(done, 1);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
 
   bool ok = true;
-  uint32_t parity = 0;
-  for (int k0 = 0; k0 < Dp && ok; k0 += kKC) {
-    // stage the chunk: 128 rows x 8 sixteen-byte units per operand
-    for (int u = tid; u < kTM * (kKC / 8); u += kGemmThreads) {
-      const int r = u >> 3, kg = u & 7;
-      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-      if (q0 + r < nq) va = __ldg((const uint4*)(Qb + (q0 + r) * Dp + k0 + kg * 8));
-      if (l0 + r < nlist) vb = __ldg((const uint4*)(Cb + (l0 + r) * Dp + k0 + kg * 8));
-      *(uint4*)(As + core_off(r, kg * 8)) = va;
-      *(uint4*)(Bs + core_off(r, kg * 8)) = vb;
+  if (tid == 0) {
+    // TMA producer
+    for (int i = 0; i < nK && ok; ++i) {
+      const int st = i % kStages;
+      if (i >= kStages) ok = mbar_wait(empty0 + 8 * st, (uint32_t)((i / kStages - 1) & 1));
+      if (!ok) break;
+      const uint32_t a_dst = ring + st * kStageBytes, b_dst = a_dst + kABytes;
+      mbar_expect_tx(full0 + 8 * st, kStageBytes);
+      tma_load_2d(a_dst, &tmQ, i * kKC, q0, full0 + 8 * st);
+      tma_load_2d(b_dst, &tmC, i * kKC, l0, full0 + 8 * st);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == 32) {
+    // MMA issuer
+    for (int i = 0; i < nK && ok; ++i) {
+      const int st = i % kStages;
+      ok = mbar_wait(full0 + 8 * st, (uint32_t)((i / kStages) & 1));
+      if (!ok) break;
       tc_fence_after();
+      const uint32_t a_addr = ring + st * kStageBytes, b_addr = a_addr + kABytes;
 #pragma unroll
       for (int ks = 0; ks < kKC / 16; ++ks)
-        tc_mma(tmem, smem_desc(a_addr + ks * 2 * kLBO), smem_desc(b_addr + ks * 2 * kLBO),
-               (k0 > 0 || ks > 0) ? 1u : 0u);
-      tc_commit(bar_addr);
+        tc_mma(tmem, smem_desc_sw128(a_addr + ks * 32), smem_desc_sw128(b_addr + ks * 32),
+               (i > 0 || ks > 0) ? 1u : 0u);
+      tc_commit(empty0 + 8 * st);
     }
-    // the chunk may be overwritten once the MMAs have read it
-    ok = mbar_wait(bar_addr, parity);
-    parity ^= 1u;
-    ok = __syncthreads_and(ok);
+    tc_commit(done);  // arrives when every MMA issued above has completed
   }
+  // everyone: the accumulator is complete once `done` fires
+  const bool done_ok = mbar_wait(done, 0);
+  ok = __syncthreads_and(ok && done_ok);
   tc_fence_after();
   if (ok) {
-    const int64_t q = q0 + warp * 32 + lane;
-    const float qv = q < nq ? qn[q] : 0.f;
+    // TMEM -> registers -> shared tile [128][256] (the ring is free now) -> rows out
+    float* tileS = (float*)base;
+    const int r = warp * 32 + lane;
     for (int c0 = 0; c0 < kTN; c0 += 16) {
       float acc[16];
       tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
-      if (q < nq) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int64_t l = l0 + c0 + j;
-          if (l < nlist) dt[q * nlist + l] = sub_rn(add_rn(qv, cn[l]), mul_rn(2.f, acc[j]));
-        }
+      for (int j = 0; j < 16; ++j) tileS[r * (kTN + 1) + c0 + j] = acc[j];
+    }
+    __syncthreads();
+    for (int rr = warp; rr < kTM; rr += kGemmThreads / 32) {
+      const int64_t q = (int64_t)q0 + rr;
+      if (q >= nq) break;
+      const float qv = qn[q];
+      for (int c = lane; c < kTN; c += 32) {
+        const int64_t l = (int64_t)l0 + c;
+        if (l < nlist) dt[q * nlist + l] = sub_rn(add_rn(qv, cn[l]), mul_rn(2.f, tileS[rr * (kTN + 1) + c]));
       }
     }
-  } else {
-    if (tid == 0) {
-      atomicExch(status, ANNS_DEV_TIMEOUT);
-      mbar_wait(bar_addr, parity);  // bounded: the MMAs of the last chunk
-    }
+  } else if (tid == 0) {
+    atomicExch(status, ANNS_DEV_TIMEOUT);
+  }
+  if (!ok) {
+    // bounded: let in-flight TMA copies and MMAs finish before the CTA exits
+    for (int i = 0; i < kStages && tid == 0; ++i) mbar_wait(full0 + 8 * i, 0);
+    if (tid == 32) mbar_wait(done, 0);
   }
   tc_fence_before();
   __syncthreads();
@@ -437,6 +470,29 @@ int prepare_coarse_tc(Index& ix, const std::vector<float>& cent) {
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "coarse fast-path setup");
 }
 
+// Tensor map of a row-major BF16 matrix [rows x Dp]: boxes of 64 columns x
+// box_rows rows, 128-byte swizzle, zero fill past the last row. Built through
+// the driver entry point (no link to the driver library).
+static cudaError_t make_tmap(CUtensorMap* map, const void* base, int64_t rows, int Dp, int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+    if (e != cudaSuccess) return e;
+    if (qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Dp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 size_t coarse_tc_workspace_bytes(const Index& ix, int64_t nq) {
   return (size_t)nq * coarse_tc_dp(ix) * 2 + (size_t)nq * 4 * 4 + 256;
 }
@@ -450,12 +506,15 @@ cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int np
   int* ncand = (int*)(qrows + 3 * nq);
   center_bf16_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, (int)ix.dim, Dp, ix.tc_mu, Qb, qrows,
                                                               qrows + nq, qrows + 2 * nq);
-  cudaError_t e = cudaFuncSetAttribute(coarse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kGemmSmem);
+  CUtensorMap tmQ, tmC;
+  cudaError_t e = make_tmap(&tmQ, Qb, nq, Dp, kTM);
+  if (e == cudaSuccess) e = make_tmap(&tmC, ix.tc_cb, ix.nlist, Dp, kTN);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(coarse_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((ix.nlist + kTN - 1) / kTN), (unsigned)((nq + kTM - 1) / kTM));
-  coarse_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(Qb, (const __nv_bfloat16*)ix.tc_cb, qrows, ix.tc_cn, nq,
-                                                         ix.nlist, Dp, dt, ix.dev_status);
+  coarse_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(tmQ, tmC, qrows, ix.tc_cn, nq, ix.nlist, Dp, dt,
+                                                         ix.dev_status);
   const int R = (nprobe + 31) / 32;
   const unsigned g = (unsigned)nq;
   const size_t qsm = (size_t)ix.dim * sizeof(float);
