@@ -189,7 +189,7 @@ def calibrate_margin(index, amp, Qc, nprobe: int, k: int, run, target: float = 0
     that much recall). Widths mapped to this GPU's tables."""
     ref = run(Qc, nprobe, amp.policy("plain"))
     tried = {}
-    for m in (0.0, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0):
+    for m in (0.0, 0.1, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 8.0, 16.0):
         ov = overlap(run(Qc, nprobe, amp.policy("mlp", margin=m, width_map=True)), ref, k)
         tried[m] = ov
         if ov >= target:
@@ -292,7 +292,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     Qt = torch.from_numpy(make_queries(args.config, ntrain, stream=200)).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    index.train_predictor(Qt, nprobe, k, amp.train_cfg(epochs=args.epochs, batch=1024, lr=3e-3, seed=1))
+    # trained on the two tables of the GB300 width map, wide pairs weighted up
+    # (a wide pair put on a narrow table costs recall, the reverse only speed)
+    index.train_predictor(Qt, nprobe, k, amp.train_cfg(epochs=args.epochs, batch=1024, lr=3e-3, seed=1,
+                                                       gpu_classes=True, high_weight=args.high_weight))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del Qt
@@ -380,8 +383,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "data": "synthetic (seeded SIFT-shaped gamma mixture; no public dataset)",
         "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
-                   "policy": f"learned MLP per (query, list), round-up margin {margin}, GB300 widths "
-                             "(6->8 bits, 12/16->FP32)",
+                   "policy": f"learned MLP per (query, list) trained on GB300 table classes, round-up "
+                             f"margin {margin}, widths 6->8 bits and 12/16->FP32",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "recall_at_10": round(recs["mlp"][0], 4),
         "top10_kept_vs_plain": round(recs["mlp"][1], 4),
@@ -395,6 +398,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                             "ms_per_step": round(totals[name] * 1e3 / args.steps, 4)} for name in qps},
         "eq2_thresholds": list(eq2_th) if eq2_th is not None else None,
         "predictor": {"train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
+                      "classes": "GB300 tables (8-bit / wide)", "high_weight": args.high_weight,
                       "margin_calibration_kept": {str(a): round(b, 4) for a, b in tried.items()}},
         "recall_sweep_plain": {str(a): round(b, 4) for a, b in rec_plain.items()},
         "stage_ms_per_step": {n: round(v / max(cnt, 1), 4) for n, v in
@@ -487,6 +491,7 @@ def main():
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--high-weight", type=float, default=10.0, help="loss weight of wide-table training samples")
     ap.add_argument("--only-cl", action="store_true",
                     help="run only the coarse-stage comparison (for profiling its kernels)")
     args = ap.parse_args()

@@ -266,6 +266,13 @@ typedef struct {
   int32_t epochs, batch; /* passes over the samples, samples per Adam step */
   float lr;              /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8) */
   uint64_t seed;         /* initial weights and sample order */
+  int32_t label_map;     /* anns_train_predictor: 0 = classes of the label widths 4, 6, 8,
+                            12, 16 ("needs FP32" trains as 16); 1 = the two tables of
+                            the GB300 width map: labels 4, 6, 8 -> the 8-bit class,
+                            12, 16 and "needs FP32" -> the 16-bit class */
+  float high_weight;     /* loss weight of samples whose class is 12 or 16 bits (a
+                            missed wide pair costs recall, a missed narrow one only
+                            speed); 0 is read as 1 */
 } anns_train_cfg;
 
 /* Installs / returns the index's predictor (host structs). */
@@ -285,13 +292,14 @@ int anns_get_predictor(const anns_index* index, anns_predictor* out);
 int anns_make_training_set(anns_index* index, const float* train_q, int64_t nq, int32_t nprobe,
                            int32_t k, float* feat_out, uint8_t* label_out, void* cuda_stream);
 
-/* Mean softmax cross-entropy and its gradient over n samples with the MLP
- * in `w`: X device float32 [n * 5] raw features, cls device uint8 [n] classes
- * 0..4 (255 = skipped). grad_out host float32 [1413] in the order W1 b1 W2 b2
- * W3 b3; loss_out host (or NULL). FP16-operand forward, FP32 backward.
- * Synchronous. */
+/* Weighted softmax cross-entropy and its gradient over n samples with the
+ * MLP in `w`: (1/n) sum_i w_i CE_i with w_i = high_weight for classes 3 and 4
+ * (12 and 16 bits), else 1. X device float32 [n * 5] raw features, cls device
+ * uint8 [n] classes 0..4 (255 = skipped). grad_out host float32 [1413] in the
+ * order W1 b1 W2 b2 W3 b3; loss_out host (or NULL). FP16-operand forward,
+ * FP32 backward. Synchronous. */
 int anns_mlp_grad(anns_index* index, const anns_predictor* w, const float* X, const uint8_t* cls,
-                  int64_t n, float* grad_out, double* loss_out, void* cuda_stream);
+                  int64_t n, float high_weight, float* grad_out, double* loss_out, void* cuda_stream);
 
 /* Adam training on given samples (as for anns_mlp_grad), starting from and
  * returning the weights in *io (its normalisation is used as is). Synchronous. */

@@ -216,10 +216,12 @@ def loss_and_grad64(p: dict, X: np.ndarray, y: np.ndarray):
     return loss, mlp_backward64(p, fw, gz)
 
 
-def loss_and_grad16(p: dict, Xn: np.ndarray, y: np.ndarray):
-    """Mean softmax-CE loss and gradients of the network the GPU trains: FP16
+def loss_and_grad16(p: dict, Xn: np.ndarray, y: np.ndarray, high_weight: float = 1.0):
+    """Softmax-CE loss and gradients of the network the GPU trains: FP16
     weights, biases and normalised inputs, hidden activations rounded to FP16
-    after ReLU (the inference rule), evaluated in FP64 with those roundings."""
+    after ReLU (the inference rule), evaluated in FP64 with those roundings.
+    The loss is (1/n) sum_i w_i CE_i, w_i = high_weight for classes 3 and 4
+    (12 and 16 bits), else 1."""
     p16 = {k: np.asarray(v, dtype=F32).astype(F16).astype(F64) for k, v in p.items()}
     X = np.asarray(Xn, dtype=F32).astype(F16).astype(F64)
     a1 = X @ p16["W1"].T + p16["b1"]
@@ -227,7 +229,16 @@ def loss_and_grad16(p: dict, Xn: np.ndarray, y: np.ndarray):
     a2 = h1 @ p16["W2"].T + p16["b2"]
     h2 = np.maximum(a2, 0.0).astype(F16).astype(F64)
     z = h2 @ p16["W3"].T + p16["b3"]
-    loss, gz = softmax_ce64(z, y)
+    y = np.asarray(y)
+    w = np.where(y >= 3, float(high_weight), 1.0)
+    zm = z - z.max(axis=1, keepdims=True)
+    pr = np.exp(zm)
+    pr /= pr.sum(axis=1, keepdims=True)
+    n = z.shape[0]
+    loss = float(np.mean(-w * np.log(pr[np.arange(n), y])))
+    gz = pr.copy()
+    gz[np.arange(n), y] -= 1.0
+    gz *= (w / n)[:, None]
     fw = dict(X=X, a1=a1, h1=h1, a2=a2, h2=h2, z=z)
     return loss, mlp_backward64(p16, fw, gz)
 
@@ -294,8 +305,12 @@ def gpu_width(bits: np.ndarray) -> np.ndarray:
     return np.where(b == 6, np.uint8(8), np.where((b == 12) | (b == 16), np.uint8(0), b)).astype(np.uint8)
 
 
-def bits_to_class(bits: np.ndarray) -> np.ndarray:
-    """Training target: class of the label bits; "needs FP32" trains as 16 bits."""
+def bits_to_class(bits: np.ndarray, gpu: bool = False) -> np.ndarray:
+    """Training target: class of the label bits; "needs FP32" trains as 16 bits.
+    With `gpu`, the two tables of the GB300 width map: 4, 6, 8 -> class 2
+    (8 bits); 12, 16 and FP32 -> class 4 (16 bits)."""
     b = np.asarray(bits)
     lut = {4: 0, 6: 1, 8: 2, 12: 3, 16: 4, 0: 4}
+    if gpu:
+        lut = {4: 2, 6: 2, 8: 2, 12: 4, 16: 4, 0: 4}
     return np.vectorize(lambda v: lut[int(v)])(b).astype(np.int64)

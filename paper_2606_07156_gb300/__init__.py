@@ -54,9 +54,12 @@ def predictor_to_dict(s: abi.anns_predictor) -> dict:
     return {f: np.ctypeslib.as_array(getattr(s, f)).copy().reshape(_PRED_SHAPES[f]) for f in _PRED_FIELDS}
 
 
-def train_cfg(epochs: int = 10, batch: int = 1024, lr: float = 3e-3, seed: int = 0) -> abi.anns_train_cfg:
+def train_cfg(epochs: int = 10, batch: int = 1024, lr: float = 3e-3, seed: int = 0, gpu_classes: bool = False,
+              high_weight: float = 1.0) -> abi.anns_train_cfg:
     c = abi.anns_train_cfg()
     c.epochs, c.batch, c.lr, c.seed = epochs, batch, lr, seed
+    c.label_map = 1 if gpu_classes else 0
+    c.high_weight = high_weight
     return c
 
 
@@ -197,10 +200,11 @@ class Index:
         abi.anns_make_training_set(self.handle, _ptr(train_q), nq, nprobe, k, _ptr(feat), _ptr(lab), s)
         return feat, lab
 
-    def mlp_grad(self, p: dict, X, cls):
-        """Gradient (dict of numpy arrays) and mean loss over samples X [n, 5], cls [n] (CUDA tensors)."""
+    def mlp_grad(self, p: dict, X, cls, high_weight: float = 1.0):
+        """Gradient (dict of numpy arrays) and mean weighted loss over samples X [n, 5], cls [n] (CUDA tensors)."""
         g = np.empty(1413, dtype=np.float32)
-        loss = abi.anns_mlp_grad(self.handle, predictor_to_struct(p), _ptr(X), _ptr(cls), X.shape[0], g.ctypes.data)
+        loss = abi.anns_mlp_grad(self.handle, predictor_to_struct(p), _ptr(X), _ptr(cls), X.shape[0], g.ctypes.data,
+                                 high_weight)
         out, o = {}, 0
         for f in _PRED_FIELDS[:6]:
             n = int(np.prod(_PRED_SHAPES[f]))

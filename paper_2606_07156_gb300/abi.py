@@ -76,7 +76,7 @@ class anns_tune_result(ctypes.Structure):
 
 class anns_train_cfg(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("label_map", ctypes.c_int32), ("high_weight", ctypes.c_float)]
 
 
 def _load():
@@ -107,7 +107,8 @@ def _load():
         "anns_set_predictor": ([vp, ctypes.POINTER(anns_predictor)], i32),
         "anns_get_predictor": ([vp, ctypes.POINTER(anns_predictor)], i32),
         "anns_make_training_set": ([vp, vp, i64, i32, i32, vp, vp, vp], i32),
-        "anns_mlp_grad": ([vp, ctypes.POINTER(anns_predictor), vp, vp, i64, vp, ctypes.POINTER(ctypes.c_double), vp], i32),
+        "anns_mlp_grad": ([vp, ctypes.POINTER(anns_predictor), vp, vp, i64, ctypes.c_float, vp,
+                           ctypes.POINTER(ctypes.c_double), vp], i32),
         "anns_mlp_train": ([vp, vp, vp, i64, ctypes.POINTER(anns_train_cfg), ctypes.POINTER(anns_predictor), vp], i32),
         "anns_train_predictor": ([vp, vp, i64, i32, i32, ctypes.POINTER(anns_train_cfg), ctypes.POINTER(anns_predictor), vp], i32),
         "anns_last_error": ([], ctypes.c_char_p),
@@ -208,9 +209,10 @@ def anns_make_training_set(index, train_q, nq, nprobe, k, feat_out, label_out, s
     _check(_lib.anns_make_training_set(index, train_q, nq, nprobe, k, feat_out, label_out, stream))
 
 
-def anns_mlp_grad(index, pred, X, cls, n, grad_out, stream=None) -> float:
+def anns_mlp_grad(index, pred, X, cls, n, grad_out, high_weight=1.0, stream=None) -> float:
     loss = ctypes.c_double()
-    _check(_lib.anns_mlp_grad(index, ctypes.byref(pred), X, cls, n, grad_out, ctypes.byref(loss), stream))
+    _check(_lib.anns_mlp_grad(index, ctypes.byref(pred), X, cls, n, high_weight, grad_out, ctypes.byref(loss),
+                              stream))
     return loss.value
 
 

@@ -173,6 +173,7 @@ struct GradArgs {
   const float* w;                 // FP32 master weights [kNP]
   float mean[5], inv_std[5];
   float inv_count;                // 1 / number of samples in the batch
+  float high_w;                   // loss weight of classes 3 and 4
   float* grad; double* loss;
 };
 
@@ -233,8 +234,9 @@ __global__ void __launch_bounds__(kGT) mlp_grad_kernel(const GradArgs a) {
   float gz[5];
   double l = 0.0;
 #pragma unroll
-  for (int o = 0; o < 5; ++o) gz[o] = live ? (e[o] / se - (o == y ? 1.f : 0.f)) * a.inv_count : 0.f;
-  if (live) l = -(double)(z[y] - zmax - logf(se));
+  const float wy = y >= 3 ? a.high_w : 1.f;
+  for (int o = 0; o < 5; ++o) gz[o] = live ? (e[o] / se - (o == y ? 1.f : 0.f)) * (a.inv_count * wy) : 0.f;
+  if (live) l = -(double)wy * (double)(z[y] - zmax - logf(se));
   // backward to the hidden layers
   float g2[32];
 #pragma unroll
@@ -291,11 +293,14 @@ __global__ void adam_kernel(float* w, const float* g, float* m, float* v, float 
 }
 
 // Bits -> class (4, 6, 8, 12, 16 -> 0..4; "needs FP32" trains as 16 bits; 255 = no sample).
-__global__ void class_kernel(const uint8_t* bits, int64_t n, uint8_t* cls) {
+// With `gpu`, the two tables of the GB300 width map: 4, 6, 8 -> 2; 12, 16, FP32 -> 4.
+__global__ void class_kernel(const uint8_t* bits, int64_t n, int gpu, uint8_t* cls) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = bits[i];
-  cls[i] = b == 4 ? 0 : b == 6 ? 1 : b == 8 ? 2 : b == 12 ? 3 : (b == 16 || b == 0) ? 4 : 255;
+  uint8_t c = b == 4 ? 0 : b == 6 ? 1 : b == 8 ? 2 : b == 12 ? 3 : (b == 16 || b == 0) ? 4 : 255;
+  if (gpu && c < 5) c = c <= 2 ? 2 : 4;
+  cls[i] = c;
 }
 
 void pack(const anns_predictor& p, std::vector<float>& w) {
@@ -341,9 +346,10 @@ struct DeviceGuardP {
 // Gradient of the mean loss over samples idx[0..n) (or 0..n) into grad (device, zeroed here).
 cudaError_t launch_grad(const float* X, const uint8_t* cls, const int64_t* idx, int64_t n,
                         const float* w, const anns_predictor& norm, float* grad, double* loss,
-                        float inv_count, cudaStream_t s) {
+                        float inv_count, float high_w, cudaStream_t s) {
   GradArgs a{};
   a.X = X; a.cls = cls; a.idx = idx; a.n = n; a.w = w; a.inv_count = inv_count;
+  a.high_w = high_w > 0.f ? high_w : 1.f;
   for (int i = 0; i < 5; ++i) { a.mean[i] = norm.mean[i]; a.inv_std[i] = norm.inv_std[i]; }
   a.grad = grad; a.loss = loss;
   cudaError_t e = cudaMemsetAsync(grad, 0, kNP * sizeof(float), s);
@@ -379,7 +385,7 @@ int train_on(Index& ix, const float* X, const uint8_t* cls, int64_t n, const ann
     for (int64_t b0 = 0; b0 < n; b0 += B) {
       const int64_t cnt = std::min<int64_t>(B, n - b0);
       e = launch_grad(X, cls, (const int64_t*)didx.p + b0, cnt, (const float*)dw.p, io, (float*)dg.p,
-                      (double*)dl.p, 1.f / (float)cnt, s);
+                      (double*)dl.p, 1.f / (float)cnt, cfg.high_weight, s);
       if (e != cudaSuccess) return cuda_fail(e, "gradient kernel");
       ++step;
       const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
@@ -439,7 +445,7 @@ extern "C" int anns_get_predictor(const anns_index* ix, anns_predictor* out) {
 }
 
 extern "C" int anns_mlp_grad(anns_index* ix, const anns_predictor* w, const float* X, const uint8_t* cls,
-                             int64_t n, float* grad_out, double* loss_out, void* stream) {
+                             int64_t n, float high_weight, float* grad_out, double* loss_out, void* stream) {
   if (!ix || !w || !grad_out) return fail(ANNS_ERR_INVALID_ARG, "null argument");
   if (n <= 0 || !X || !cls) return fail(ANNS_ERR_INVALID_ARG, "need n > 0 samples");
   DeviceGuardP g(ix->device);
@@ -451,7 +457,8 @@ extern "C" int anns_mlp_grad(anns_index* ix, const anns_predictor* w, const floa
   if ((rc = dw.alloc(kNP * 4)) || (rc = dg.alloc(kNP * 4)) || (rc = dl.alloc(8))) return rc;
   cudaError_t e = cudaMemcpyAsync(dw.p, hw.data(), kNP * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = launch_grad(X, cls, nullptr, n, (const float*)dw.p, *w, (float*)dg.p, (double*)dl.p, 1.f / (float)n, s);
+    e = launch_grad(X, cls, nullptr, n, (const float*)dw.p, *w, (float*)dg.p, (double*)dl.p, 1.f / (float)n,
+                    high_weight, s);
   double loss = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(grad_out, dg.p, kNP * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, dl.p, 8, cudaMemcpyDeviceToHost, s);
@@ -490,7 +497,8 @@ extern "C" int anns_train_predictor(anns_index* ix, const float* Q, int64_t nq, 
   int rc;
   if ((rc = feat.alloc((size_t)n * 5 * 4)) || (rc = lab.alloc((size_t)n)) || (rc = cls.alloc((size_t)n))) return rc;
   if ((rc = make_training_set(*ix, Q, nq, nprobe, k, (float*)feat.p, (uint8_t*)lab.p, s))) return rc;
-  class_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const uint8_t*)lab.p, n, (uint8_t*)cls.p);
+  class_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const uint8_t*)lab.p, n, cfg->label_map,
+                                                           (uint8_t*)cls.p);
   // normalisation over the samples (host, FP64): a one-off set-up statistic
   std::vector<float> hf((size_t)n * 5);
   std::vector<uint8_t> hc((size_t)n);

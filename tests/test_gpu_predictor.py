@@ -171,6 +171,38 @@ def test_gradient_matches_fp16_network(pair, n):
     _grad_close(grad, wg, 2e-3)
 
 
+def test_weighted_gradient_matches_oracle(pair):
+    """Class-weighted loss: samples of 12 and 16 bits count high_weight times."""
+    d, g, o = pair
+    X, y = _samples(3000, seed=31)
+    p = _random_predictor(8, X)
+    grad, loss = g.mlp_grad(p, cuda(X), cuda(y), high_weight=4.0)
+    Xn = predictor.normalise(X, p["mean"], p["inv_std"])
+    wl, wg = predictor.loss_and_grad16({k: p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}, Xn,
+                                       y.astype(np.int64), high_weight=4.0)
+    assert abs(loss - wl) <= 1e-5 * abs(wl) + 1e-7
+    _grad_close(grad, wg, 2e-3)
+
+
+def test_gpu_class_map_training(amp, pair):
+    """label_map = GB300 tables: the training targets are the two classes of
+    the width map (checked through the oracle's class map)."""
+    d, g, o = pair
+    Qt = _train_queries(d, 200, seed=6)
+    feat, lab = g.make_training_set(cuda(Qt), 8, 10)
+    c = predictor.bits_to_class(lab.cpu().numpy(), gpu=True).reshape(-1)
+    assert set(np.unique(c)) <= {2, 4}
+    p = g.train_predictor(cuda(Qt), 8, 10, amp.train_cfg(epochs=20, batch=256, lr=3e-3, seed=2,
+                                                          gpu_classes=True, high_weight=3.0))
+    _, l_after = g.mlp_grad(p, feat.reshape(-1, 5), cuda(c.astype(np.uint8)).reshape(-1), high_weight=3.0)
+    f = np.bincount(c, minlength=5) / len(c)
+    w = np.where(np.arange(5) >= 3, 3.0, 1.0)
+    # weighted loss of the best constant predictor
+    pc = f * w / (f * w).sum()
+    const = -(f * w * np.log(np.where(pc > 0, pc, 1.0))).sum()
+    assert l_after < const, (l_after, const)
+
+
 def test_gradient_skips_unlabelled_samples(pair):
     """Samples with class 255 add nothing (the mean is over all n samples)."""
     d, g, o = pair
