@@ -203,7 +203,8 @@ def calibrate_eq2(amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
     the plain top-k on held-out queries."""
     ref = run(Qc, nprobe, amp.policy("plain"))
     best, tried = None, {}
-    for t in (-3.0, -2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 1.0, 2.0, 4.0):
+    for t in (-24.0, -16.0, -12.0, -10.0, -8.0, -7.0, -6.0, -5.0, -4.0, -3.5, -3.0, -2.5, -2.0, -1.5, -1.0,
+              -0.5, 0.0, 0.5, 1.0, 2.0, 4.0):
         th = (t + 1.5, t + 1.0, t + 0.5, t)
         ov = overlap(run(Qc, nprobe, amp.policy("eq2", thresholds=th, width_map=True)), ref, k)
         tried[t] = ov
