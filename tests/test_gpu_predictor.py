@@ -280,3 +280,63 @@ def test_train_predictor_learns(amp, pair):
     ri, rd = ivfpq.search(o, Q, nprobe, k, bits=bits)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
     np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+
+
+# ------------------------------------------------------------------ what the network gains
+
+def _kept(ids, ref, k):
+    return float(np.mean([len(np.intersect1d(a[:k], b[:k])) / k for a, b in zip(ids, ref)]))
+
+
+def test_mlp_gains_over_eq2(amp):
+    """The trained network against the method without it (the Eq. 2
+    heuristic), both calibrated on held-out queries to keep >= 99 % of the
+    plain FP32 search's top 10, both on the GB300 tables: on SIFT-shaped data
+    the network puts more (query, list) pairs on the cheap 8-bit tables, and
+    its calibrated accuracy holds on separate evaluation queries."""
+    from workloads import make_dataset, make_queries, train_ivfpq
+    d = make_dataset("B", n=30000, nq=300, ncomp=64)
+    ix = train_ivfpq(d["base"], 128, 32, iters=6, seed=3, device="cpu")
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=0)
+    try:
+        nprobe, k = 16, 10
+        Qt = cuda(make_queries("B", 3000, stream=200, ncomp=64))
+        Qc = cuda(make_queries("B", 400, stream=300, ncomp=64))
+        Qe = cuda(d["queries"])
+
+        def run(Q, pol):
+            ids, _ = g.search(Q, nprobe, k, pol)
+            torch.cuda.synchronize()
+            return ids.cpu().numpy()
+
+        def narrow_share(Q, pol):
+            run(Q, pol)
+            b = g.tap(amp.abi.TAP_BITS, (Q.shape[0], nprobe), np.uint8)
+            return float(np.mean(b == 8))
+
+        g.train_predictor(Qt, nprobe, k, amp.train_cfg(epochs=20, batch=512, lr=3e-3, seed=1, gpu_classes=True,
+                                                       high_weight=10.0))
+        ref_c, ref_e = run(Qc, amp.policy("plain")), run(Qe, amp.policy("plain"))
+        mlp = None
+        for tau in (0.0, 0.1, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 8.0):
+            pol = amp.policy("mlp", margin=tau, width_map=True)
+            if _kept(run(Qc, pol), ref_c, k) >= 0.99:
+                mlp = pol
+                break
+        eq2 = None
+        for t in (-24.0, -16.0, -12.0, -10.0, -8.0, -7.0, -6.0, -5.0, -4.0, -3.5, -3.0, -2.5, -2.0, -1.5, -1.0,
+                  -0.5, 0.0, 0.5, 1.0, 2.0, 4.0):
+            pol = amp.policy("eq2", thresholds=(t + 1.5, t + 1.0, t + 0.5, t), width_map=True)
+            if _kept(run(Qc, pol), ref_c, k) >= 0.99:
+                eq2 = pol
+                break
+        assert mlp is not None
+        share_mlp = narrow_share(Qe, mlp)
+        share_eq2 = narrow_share(Qe, eq2) if eq2 is not None else 0.0
+        kept_e = _kept(run(Qe, mlp), ref_e, k)
+        print(f"8-bit share: MLP {share_mlp:.3f} (tau {mlp.fallback_margin}), Eq. 2 {share_eq2:.3f}; "
+              f"MLP keeps {kept_e:.4f} of the plain top-10 on evaluation queries")
+        assert kept_e >= 0.98
+        assert share_mlp > share_eq2 + 0.05, (share_mlp, share_eq2)
+    finally:
+        g.close()
