@@ -141,6 +141,24 @@ def time_steps(fn, steps: int, warmup: int, stream, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def max_over_ranks(totals: dict, world: int, device) -> dict:
+    """Each timed total (seconds) replaced by its maximum over the ranks (the
+    job is as slow as its slowest replica). World 1: unchanged."""
+    if world <= 1:
+        return dict(totals)
+    import torch
+    import torch.distributed as dist
+    names = sorted(totals)
+    tt = torch.tensor([float(totals[n]) for n in names], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return dict(zip(names, tt.tolist()))
+
+
+def weak_scaling_qps(totals: dict, world: int, nq: int, steps: int) -> dict:
+    """Whole-job queries/s: every rank searched nq queries per step."""
+    return {name: world * nq * steps / t for name, t in totals.items()}
+
+
 def nvtx_push(name: str):
     """Marks the timed region for profilers (a no-op where NVTX is unavailable)."""
     import torch
@@ -354,19 +372,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     nn10 = nn_in_top(ih.numpy(), W["gt"], 10)
 
     totals = {name: sum(v) / 1e3 for name, v in ms_pol.items()}
-    total_e2e = sum(e2e_t)
-    if world > 1:
-        import torch.distributed as dist
-        names = sorted(totals)
-        tt = torch.tensor([totals[n] for n in names] + [total_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        vals = tt.tolist()
-        totals = dict(zip(names, vals[:-1]))
-        total_e2e = vals[-1]
+    totals["_e2e"] = sum(e2e_t)
+    totals = max_over_ranks(totals, world, dev)
+    total_e2e = totals.pop("_e2e")
     if rank != 0:
         index.close()
         return None
-    qps = {name: world * nq * args.steps / t for name, t in totals.items()}
+    qps = weak_scaling_qps(totals, world, nq, args.steps)
     qps_e2e = world * nq * args.steps / total_e2e
     probes = index.tap(abi.TAP_PROBES, (nq, nprobe), np.int32)
     nbytes = scan_bytes(index, probes, cfg["M"])
