@@ -200,8 +200,13 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
 
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
- *    ANNS_KERNEL_AUTO (default): query-major.
+ *    ANNS_KERNEL_AUTO (default): grouped when the policy can choose tables of
+ *      at most 8 bits and k <= 32, else query-major.
  *    ANNS_KERNEL_BASIC: query-major, one block per query walking its probes.
+ *    ANNS_KERNEL_GROUPED: the pairs on 1..8-bit tables taken four per list,
+ *      their byte tables interleaved so that one shared-memory gather serves
+ *      four queries; the other pairs query-major; then a per-query merge
+ *      (k <= 32, else query-major).
  *    ANNS_KERNEL_LIST_MAJOR: the probed pairs regrouped by list; one warp per
  *      (query, list) pair, blocks of pairs sharing a list, work items taken
  *      largest list first; then a per-query merge of the pairs' top-k.
@@ -215,7 +220,7 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
  *      lists of (list size + 768), bucketed within 12.5 %.
  * Every kernel and schedule returns identical results. Errors: INVALID_ARG. */
 enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1 };
-enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2 };
+enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2, ANNS_KERNEL_GROUPED = 3 };
 enum { ANNS_SCHED_AUTO = 0, ANNS_SCHED_NATURAL = 1, ANNS_SCHED_LPT = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);
 

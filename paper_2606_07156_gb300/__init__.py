@@ -147,8 +147,10 @@ class Index:
         return ids, dists
 
     def set_kernel(self, which: str):
-        """'auto', 'basic' (query-major) or 'lists' (list-major, one warp per pair)."""
-        v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "lists": abi.KERNEL_LIST_MAJOR}[which]
+        """'auto', 'basic' (query-major), 'lists' (list-major, one warp per pair) or
+        'grouped' (narrow pairs packed four queries to a gather)."""
+        v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "lists": abi.KERNEL_LIST_MAJOR,
+             "grouped": abi.KERNEL_GROUPED}[which]
         abi.anns_set_option(self.handle, abi.OPT_KERNEL, v)
 
     def locate(self, queries, nprobe: int, cl: str = "fp32", nprobe_per_q=None, stream=None):

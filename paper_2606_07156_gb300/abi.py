@@ -23,7 +23,7 @@ TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_COARSE_APPROX, TAP_COARSE_CANDIDATES = 4, 5
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS, TAP_STATUS = 10, 11, 12, 13
 OPT_KERNEL, OPT_SCHEDULE = 0, 1
-KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR = 0, 1, 2
+KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR, KERNEL_GROUPED = 0, 1, 2, 3
 SCHED_AUTO, SCHED_NATURAL, SCHED_LPT = 0, 1, 2
 
 SYMBOLS = (

@@ -230,6 +230,17 @@ int anns::check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t 
 
 namespace anns {
 
+// The grouped kernel (narrow pairs packed four to a word): on request, or by
+// default for a policy that can choose 1..8-bit tables, when k <= 32.
+static bool use_grouped(const Index& ix, const anns_precision_policy& P, int k) {
+  if (ix.opt_kernel == ANNS_KERNEL_GROUPED) return grouped_supported(ix, k);
+  if (ix.opt_kernel != ANNS_KERNEL_AUTO) return false;
+  const bool narrow_possible = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2 ||
+                               P.lut_mode == ANNS_LUT_EXPLICIT ||
+                               (P.lut_mode == ANNS_LUT_FIXED_BITS && P.fixed_bits <= 8);
+  return narrow_possible && grouped_supported(ix, k);
+}
+
 static bool use_lpt(const Index& ix, const int32_t* nprobe_per_q) {
   return ix.opt_schedule == ANNS_SCHED_LPT || (ix.opt_schedule == ANNS_SCHED_AUTO && nprobe_per_q);
 }
@@ -238,10 +249,14 @@ int reserve_search(Index& ix, int64_t nq, int nprobe, int k, const anns_precisio
                    const int32_t* nprobe_per_q) {
   int rc = ensure_workspace(ix, nq, nprobe);
   if (rc) return rc;
-  if (ix.opt_kernel == ANNS_KERNEL_LIST_MAJOR) {
+  if (ix.opt_kernel == ANNS_KERNEL_LIST_MAJOR || use_grouped(ix, P, k)) {
     ListWork w{};
     if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
-  } else if (use_lpt(ix, nprobe_per_q)) {
+  }
+  if (use_grouped(ix, P, k)) {
+    if ((rc = grow(&ix.ws_grp, &ix.ws_grp_cap, grouped_workspace_bytes(nq, k)))) return rc;
+  }
+  if (ix.opt_kernel != ANNS_KERNEL_LIST_MAJOR && use_lpt(ix, nprobe_per_q)) {
     if ((rc = grow(&ix.ws_sched, &ix.ws_sched_cap, lpt_workspace_bytes(nq)))) return rc;
   }
   if (P.cl_prec == ANNS_PREC_BF16) {
@@ -287,6 +302,12 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
     if (ev) cudaEventRecord(ev[3], s);
     e = launch_search_lists(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
                             ix.ws_bits, tbytes, w, ids_out, dists_out, s);
+  } else if (use_grouped(ix, P, k)) {
+    ListWork w{};
+    if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
+    if (ev) cudaEventRecord(ev[3], s);
+    e = launch_search_grouped(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
+                              ix.ws_bits, w, ix.ws_grp, ids_out, dists_out, s);
   } else {
     const int32_t* order = nullptr;
     if (use_lpt(ix, nprobe_per_q)) {
@@ -305,7 +326,7 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
 
 void free_workspace(Index& ix) {
   void* ptrs[] = {ix.ws_qt, ix.ws_lists, ix.ws_d2, ix.ws_probes /* base of the pair block */,
-                  ix.ws_counter, ix.ws_sched, ix.ws_tc, ix.st_q, ix.st_out, ix.st_pq};
+                  ix.ws_counter, ix.ws_sched, ix.ws_tc, ix.ws_grp, ix.st_q, ix.st_out, ix.st_pq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix.ws_qt = nullptr; ix.ws_lists = nullptr; ix.ws_d2 = nullptr; ix.ws_probes = nullptr;
@@ -313,6 +334,8 @@ void free_workspace(Index& ix) {
   ix.ws_sched = nullptr; ix.ws_tc = nullptr; ix.st_q = nullptr; ix.st_out = nullptr; ix.st_pq = nullptr;
   ix.ws_tc_cap = 0;
   ix.ws_tc_valid = false;
+  ix.ws_grp = nullptr;
+  ix.ws_grp_cap = 0;
   ix.ws_qt_cap = ix.ws_lists_cap = ix.ws_d2_cap = ix.ws_pair_cap = ix.ws_counter_cap = 0;
   ix.ws_sched_cap = ix.st_q_cap = ix.st_out_cap = ix.st_pq_cap = 0;
   ix.ws_nq = ix.ws_nprobe = 0;
@@ -452,7 +475,7 @@ extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
   if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
   switch (option) {
     case ANNS_OPT_KERNEL:
-      if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_LIST_MAJOR)
+      if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_GROUPED)
         return fail(ANNS_ERR_INVALID_ARG, "unknown kernel choice");
       ix->opt_kernel = (int)value;
       return ANNS_OK;

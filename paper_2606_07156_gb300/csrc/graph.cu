@@ -34,6 +34,8 @@ void make_shadow(const Index& ix, Index& sh) {
   sh.ws_sched = nullptr; sh.ws_tc = nullptr; sh.st_q = nullptr; sh.st_out = nullptr; sh.st_pq = nullptr;
   sh.ws_tc_cap = 0;
   sh.ws_tc_valid = false;
+  sh.ws_grp = nullptr;
+  sh.ws_grp_cap = 0;
   sh.ws_qt_cap = sh.ws_d2_cap = sh.ws_pair_cap = sh.ws_counter_cap = sh.ws_lists_cap = 0;
   sh.ws_sched_cap = sh.st_q_cap = sh.st_out_cap = sh.st_pq_cap = 0;
   sh.ws_nq = sh.ws_nprobe = 0;
@@ -142,7 +144,8 @@ extern "C" int anns_autotune(anns_index* ix, const float* Q, int64_t nq, int32_t
   const int kern0 = ix->opt_kernel, sched0 = ix->opt_schedule;
   struct Cand { int kernel, schedule; };
   std::vector<Cand> cands = {{ANNS_KERNEL_BASIC, ANNS_SCHED_NATURAL}, {ANNS_KERNEL_BASIC, ANNS_SCHED_LPT},
-                             {ANNS_KERNEL_LIST_MAJOR, ANNS_SCHED_NATURAL}};
+                             {ANNS_KERNEL_LIST_MAJOR, ANNS_SCHED_NATURAL}, {ANNS_KERNEL_GROUPED, ANNS_SCHED_NATURAL},
+                             {ANNS_KERNEL_GROUPED, ANNS_SCHED_LPT}};
   std::vector<anns_tune_result> got;
   for (const Cand& c : cands) {
     if (rc != ANNS_OK) break;

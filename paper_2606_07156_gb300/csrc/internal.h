@@ -69,6 +69,8 @@ struct Index {
   size_t ws_lists_cap = 0;
   void* ws_sched = nullptr;      // query order of the LPT schedule (schedule.cu)
   size_t ws_sched_cap = 0;
+  void* ws_grp = nullptr;        // query-major partial top-k of the grouped search
+  size_t ws_grp_cap = 0;
   void* ws_tc = nullptr;         // BF16 centred queries, norms, candidate counts (coarse_tc.cu)
   size_t ws_tc_cap = 0;
   bool ws_tc_valid = false;      // the last search (or anns_locate) used the CL fast path
@@ -122,7 +124,8 @@ int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq,
 cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const float* probe_d2, const uint8_t* bits,
-                          const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s);
+                          const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s,
+                          bool skip_narrow = false);
 // Longest-first query order (schedule.cu) into a workspace of
 // lpt_workspace_bytes(nq); the order is at lpt_order_ptr(ws, nq).
 size_t lpt_workspace_bytes(int64_t nq);
@@ -150,7 +153,7 @@ struct ListWork {
 };
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
                           int nprobe, int batch, int* cnt, int* off, int* ioff, int* fill,
-                          int32_t* pairs, cudaStream_t s);
+                          int32_t* pairs, cudaStream_t s, const uint8_t* narrow_bits = nullptr);
 // Warps per block the list-major kernel gets for tables of `table_bytes_per_entry`.
 int list_major_warps(const Index& ix, int table_bytes_per_entry);
 cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, int nprobe,
@@ -158,6 +161,16 @@ cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, in
                                 const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                 int table_bytes_per_entry, const ListWork& w, int64_t* ids_out,
                                 float* dists_out, cudaStream_t s);
+// Grouped search (search_grouped.cu): the pairs on 1..8-bit tables packed four
+// queries to a shared-memory word per list, the wide pairs query-major, then a
+// per-query merge. k <= 32.
+bool grouped_supported(const Index& ix, int k);
+size_t grouped_workspace_bytes(int64_t nq, int k);
+cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, int nprobe,
+                                  const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
+                                  const int32_t* probes, const float* probe_d2, const uint8_t* bits,
+                                  const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
+                                  cudaStream_t s);
 // Pair-level debug paths; qt are the queries' tables from launch_query_tables.
 cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt, int64_t nq,
                                 const int32_t* pq, const int32_t* pl, const uint8_t* pb,

@@ -5,7 +5,8 @@
 // longest-processing-time order, the analogue of the load scheduling of
 // Section 4.3), through the index's size ranking.
 //
-//   count:   cnt[l]  = number of valid pairs probing list l
+//   count:   cnt[l]  = number of valid pairs probing list l (with narrow_bits:
+//            only the pairs the grouped kernel packs: 1..8-bit tables, rank >= 1)
 //   offsets: off[l]  = exclusive prefix of cnt over lists;
 //            ioff[r] = exclusive prefix of ceil(cnt[order[r]] / batch) over
 //                      size ranks r (ioff[nlist] = number of items)
@@ -19,15 +20,26 @@
 namespace anns {
 namespace {
 
-__global__ void count_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
-                             int64_t nq, int nprobe, int* __restrict__ cnt) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nq * nprobe) return;
+// Pair i takes part: probed (rank below the query's nprobe, list >= 0) and,
+// with `bits`, one the grouped kernel packs: a table of 1..8 bits and probe
+// rank >= 1 (rank 0 goes through the query-major kernel, whose result bounds
+// the query's k-th distance for the grouped pairs).
+__device__ __forceinline__ bool pair_selected(const int32_t* probes, const int32_t* npq, const uint8_t* bits,
+                                              int64_t i, int nprobe) {
   const int64_t q = i / nprobe;
   const int j = (int)(i % nprobe);
   const int np = npq ? min(max(npq[q], 0), nprobe) : nprobe;
-  const int l = probes[i];
-  if (j < np && l >= 0) atomicAdd(cnt + l, 1);
+  if (j >= np || probes[i] < 0) return false;
+  if (!bits) return true;
+  const int b = bits[i];
+  return j >= 1 && b >= 1 && b <= 8;
+}
+
+__global__ void count_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
+                             const uint8_t* __restrict__ bits, int64_t nq, int nprobe, int* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * nprobe) return;
+  if (pair_selected(probes, npq, bits, i, nprobe)) atomicAdd(cnt + probes[i], 1);
 }
 
 // One block: exclusive scans over lists (pair offsets) and over size ranks
@@ -79,29 +91,27 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int* __restrict__ c
 }
 
 __global__ void scatter_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
-                               int64_t nq, int nprobe, const int* __restrict__ off,
-                               int* __restrict__ fill, int32_t* __restrict__ pairs) {
+                               const uint8_t* __restrict__ bits, int64_t nq, int nprobe,
+                               const int* __restrict__ off, int* __restrict__ fill, int32_t* __restrict__ pairs) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq * nprobe) return;
-  const int64_t q = i / nprobe;
-  const int j = (int)(i % nprobe);
-  const int np = npq ? min(max(npq[q], 0), nprobe) : nprobe;
+  if (!pair_selected(probes, npq, bits, i, nprobe)) return;
   const int l = probes[i];
-  if (j < np && l >= 0) pairs[off[l] + atomicAdd(fill + l, 1)] = (int32_t)i;
+  pairs[off[l] + atomicAdd(fill + l, 1)] = (int32_t)i;
 }
 
 }  // namespace
 
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
                           int nprobe, int batch, int* cnt, int* off, int* ioff, int* fill,
-                          int32_t* pairs, cudaStream_t s) {
+                          int32_t* pairs, cudaStream_t s, const uint8_t* narrow_bits) {
   const int64_t n = nq * nprobe;
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ix.nlist, s);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((n + 255) / 256);
-  count_kernel<<<g, 256, 0, s>>>(probes, npq, nq, nprobe, cnt);
+  count_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, cnt);
   offsets_kernel<<<1, 1024, 0, s>>>(cnt, ix.order, (int)ix.nlist, batch, off, ioff, fill);
-  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, nq, nprobe, off, fill, pairs);
+  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, off, fill, pairs);
   return cudaGetLastError();
 }
 

@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kGT) mlp_grad_kernel(const GradArgs a) {
   for (int o = 0; o < 5; ++o) { e[o] = expf(z[o] - zmax); se += e[o]; }
   float gz[5];
   double l = 0.0;
-#pragma unroll
   const float wy = y >= 3 ? a.high_w : 1.f;
+#pragma unroll
   for (int o = 0; o < 5; ++o) gz[o] = live ? (e[o] / se - (o == y ? 1.f : 0.f)) * (a.inv_count * wy) : 0.f;
   if (live) l = -(double)wy * (double)(z[y] - zmax - logf(se));
   // backward to the hidden layers

@@ -286,6 +286,7 @@ struct SearchArgs {
   const int32_t* npq; const int32_t* kpq;
   const int32_t* probes; const float* probe_d2; const uint8_t* bits;
   const int32_t* order;
+  int skip_narrow;   // leave out the pairs on 1..8-bit tables of rank >= 1 (the grouped kernel takes them)
   int64_t* ids_out; float* dists_out;
   SmemLayout lay;
 };
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? 4 : 1) search_kernel(c
       const int n_l = a.list_len[l];
       if (n_l == 0) continue;
       const int b = a.bits[q * a.nprobe + j];
+      if (a.skip_narrow && j >= 1 && b >= 1 && b <= 8) continue;
       const float d2 = a.probe_d2[q * a.nprobe + j];
       if constexpr (NCHUNK <= 2) {
         build_lut_regs<NCHUNK * 16 / kWarps>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, b, d2,
@@ -507,11 +509,12 @@ cudaError_t run_scan_pairs(const SearchArgs& a, const int32_t* pq, const int32_t
 cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const float* probe_d2, const uint8_t* bits,
-                          const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s) {
+                          const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s,
+                          bool skip_narrow) {
   const int R = k <= 32 ? 1 : 4;
   SearchArgs a = make_args(ix, nullptr, qt, R);
   a.nq = nq; a.nprobe = nprobe; a.k = k; a.npq = nprobe_per_q; a.kpq = k_per_q;
-  a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.order = order;
+  a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.order = order; a.skip_narrow = skip_narrow ? 1 : 0;
   a.ids_out = ids_out; a.dists_out = dists_out;
   switch (ix.nchunk) {
     case 1: return run_search_r<1>(a, R, s);

@@ -1,0 +1,442 @@
+// Grouped search of the narrow pairs (tables of 1..8 bits): the pairs probing
+// a list are taken four at a time, and their four byte tables are interleaved
+// into one table of 32-bit words, entry c of row m holding the levels of the
+// four queries in bytes 0..3 (each query's rank-0 pair and its wide pairs go
+// through the query-major kernel first; the k-th distance found there bounds
+// the query's final k-th distance and prunes the grouped pairs' candidates). One shared-memory gather per (vector,
+// sub-space) then serves four queries, and two 32-bit accumulators hold the
+// four integer sums as 16-bit lanes (bytes 0 and 2, bytes 1 and 3; a sum of
+// at most 128 levels of 255 stays below 2^16). The list's code tiles and list
+// table are read once per group instead of once per pair. This is the form
+// the paper's "throughput scales with lower precision" (Sections 1, 2.2)
+// takes for table gathers: 8-bit levels pack four queries per gather, where
+// FP32 entries pack one. The wide pairs (FP32, 12 and 16 bits) go through
+// the query-major kernel; a merge then takes each query's top-k over both
+// (TS). Results equal the other kernels' bit for bit: every table, integer
+// sum and distance follows the same rules (search.cu).
+//
+// Per group (one block of 8 warps, persistent grid, groups taken from an
+// atomic counter in descending list size):
+//   1. row statistics: for each (slot, row) the warps form T' = P_l - 2 Q_q
+//      and its row minimum and range;
+//   2. per slot: the shared step, its reciprocal scale and the FP64 offset
+//      (lane l adding rows l, l+32, ... then the butterfly, as elsewhere);
+//   3. levels: each warp recomputes T' for its rows of all four slots,
+//      quantises and interleaves the four levels of each entry;
+//   4. scan: warps take code tiles; per vector the four sums, distances and
+//      four warp top-k lists; the warps' lists are merged per slot and
+//      written to the pairs' partial results.
+#include <algorithm>
+#include <utility>
+
+#include "common.cuh"
+#include "internal.h"
+#include "scan.cuh"
+
+namespace anns {
+namespace {
+
+constexpr int kGThreads = 256, kGWarps = kGThreads / 32, kSlots = 4;
+
+struct GArgs {
+  const float* qt; const float* ltab; const float* probe_d2; const uint8_t* bits;
+  const uint8_t* codes; const int64_t* ids;
+  const int32_t* list_len; const int64_t* vec_off; const int64_t* tile_off;
+  const int32_t* order; const int* cnt; const int* off; const int* ioff; const int32_t* pairs;
+  int nlist, M, Mp, nprobe, k;
+  const int32_t* kpq;
+  float* part_d; int64_t* part_i;
+  const float* qm_d;  // [nq * k] query-major results (rank 0 and wide pairs): the bound
+  int* counter;
+};
+
+struct SlotScal { float s32, delta32, B32; int pad; };
+
+// Bytes of the block's shared memory (256-aligned offsets).
+struct GLayout {
+  size_t tab, bias, rowmax, scal, item, thr, md, mi, total;
+  __host__ __device__ GLayout(int Mp) {
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t o = 0;
+    tab = o; o += al((size_t)Mp * kKsub * 4);
+    bias = o; o += al((size_t)kSlots * Mp * 4);
+    rowmax = o; o += al((size_t)kSlots * Mp * 4);
+    scal = o; o += al(sizeof(SlotScal) * kSlots);
+    item = o; o += al(16 * 4);
+    thr = o; o += al(kSlots * 4);
+    md = o; o += al((size_t)kSlots * kGWarps * 32 * 4);
+    mi = o; o += al((size_t)kSlots * kGWarps * 32 * 8);
+    total = o + 256;
+  }
+};
+
+// Packed word of sub-space K for the vector whose codes are w.
+template <int K, int NCHUNK>
+__device__ __forceinline__ void packed_acc(uint32_t base, const uint4 (&w)[NCHUNK], uint32_t& a02, uint32_t& a13) {
+  const uint32_t x = code_word<K & ~3, NCHUNK>(w);
+  const uint32_t code = __byte_perm(x, 0u, 0x4440u + (K & 3));
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(base + code * 4u), "n"(K * 1024));
+  a02 += v & 0x00FF00FFu;
+  a13 += (v >> 8) & 0x00FF00FFu;
+}
+template <int NCHUNK, int... K>
+__device__ __forceinline__ void adc_packed_seq(uint32_t base, const uint4 (&w)[NCHUNK], uint32_t& a02, uint32_t& a13,
+                                               std::integer_sequence<int, K...>) {
+  (packed_acc<K, NCHUNK>(base, w, a02, a13), ...);
+}
+
+template <int NCHUNK>
+__device__ __forceinline__ void load_codes(const uint8_t* __restrict__ tile, uint4 (&w)[NCHUNK]) {
+#pragma unroll
+  for (int c = 0; c < NCHUNK; ++c) w[c] = __ldg(reinterpret_cast<const uint4*>(tile + c * kTileChunkBytes));
+}
+
+__device__ __forceinline__ void load8f(const float* p, float (&v)[8]) {
+  const float4 a = __ldg((const float4*)p), b = __ldg((const float4*)p + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+__device__ __forceinline__ uint32_t rint_bits_g(float y) { return __float_as_uint(add_rn(y, 12582912.0f)); }
+
+// Signed-int key with the order of the float (for atomicMin on distances).
+__device__ __forceinline__ int ord_key(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7FFFFFFF;
+}
+
+template <int NCHUNK>
+__global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 : 1)) packed_kernel(const GArgs a) {
+  constexpr int Mp = NCHUNK * 16;
+  const GLayout L(Mp);
+  const uint32_t raw = smem_addr(anns_dyn_smem);
+  const uint32_t pad = (256u - (raw & 255u)) & 255u;
+  unsigned char* base = anns_dyn_smem + pad;
+  uint32_t* tab = (uint32_t*)(base + L.tab);
+  float* bias = (float*)(base + L.bias);
+  float* rowmax = (float*)(base + L.rowmax);
+  SlotScal* scal = (SlotScal*)(base + L.scal);
+  int* item = (int*)(base + L.item);
+  int* thr = (int*)(base + L.thr);  // per slot: the best k-th distance any warp holds (ordered int)
+  float* md = (float*)(base + L.md);
+  int64_t* mi = (int64_t*)(base + L.mi);
+  const uint32_t tab_addr = raw + pad + (uint32_t)L.tab;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ngroups = a.ioff[a.nlist];
+  const size_t tstride = (size_t)Mp * kKsub;
+  for (;;) {
+    __syncthreads();  // the previous group is done with the shared tables
+    if (threadIdx.x < kSlots) thr[threadIdx.x] = 0x7F800000;  // +inf
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(a.counter, 1);
+      item[0] = it;
+      if (it < ngroups) {  // size rank r: the last with ioff[r] <= it
+        int lo = 0, hi = a.nlist - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.ioff[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const int l = a.order[lo];
+        const int i = it - a.ioff[lo];
+        const int ns = min(kSlots, a.cnt[l] - kSlots * i);
+        item[1] = l;
+        item[2] = ns;
+        for (int s = 0; s < kSlots; ++s) item[4 + s] = s < ns ? a.pairs[a.off[l] + kSlots * i + s] : -1;
+      }
+    }
+    __syncthreads();
+    if (item[0] >= ngroups) break;
+    const int l = item[1], ns = item[2];
+    int pid[kSlots], q[kSlots], bb[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      pid[s] = item[4 + s];
+      q[s] = pid[s] >= 0 ? pid[s] / a.nprobe : 0;
+      bb[s] = pid[s] >= 0 ? a.bits[pid[s]] : 8;
+    }
+    const float* P = a.ltab + (size_t)l * tstride;
+    // 1. row statistics of every (slot, row)
+    for (int t = warp; t < ns * a.M; t += kGWarps) {
+      const int s = t / a.M, m = t % a.M;
+      int qs = q[0];
+#pragma unroll
+      for (int u = 1; u < kSlots; ++u) if (s == u) qs = q[u];
+      float p[8], qq[8];
+      load8f(P + m * kKsub + lane * 8, p);
+      load8f(a.qt + (size_t)qs * tstride + m * kKsub + lane * 8, qq);
+      float lo_v = sub_rn(p[0], qq[0]), hi_v = lo_v;
+#pragma unroll
+      for (int e = 1; e < 8; ++e) {
+        const float tv = sub_rn(p[e], qq[e]);
+        lo_v = fminf(lo_v, tv);
+        hi_v = fmaxf(hi_v, tv);
+      }
+      const float mn = warp_min(lo_v);
+      // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
+      const float mx = sub_rn(warp_max(hi_v), mn);
+      if (lane == 0) { bias[s * Mp + m] = mn; rowmax[s * Mp + m] = mx; }
+    }
+    __syncthreads();
+    // 2. per slot: step, scale and offset
+    if (warp < ns) {
+      const int s = warp;
+      float range = 0.f;
+      for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
+      range = warp_max(range);
+      int bs = bb[0];
+      float d2 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kSlots; ++u) if (s == u) { bs = bb[u]; d2 = a.probe_d2[pid[u]]; }
+      const int Lv = (1 << bs) - 1;
+      double B = 0.0;
+      for (int m = lane; m < a.M; m += 32) B = __dadd_rn(B, (double)bias[s * Mp + m]);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+      if (lane == 0) {
+        SlotScal sc;
+        sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
+        sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
+        sc.B32 = __double2float_rn(__dadd_rn((double)d2, B));
+        sc.pad = 0;
+        scal[s] = sc;
+      }
+    }
+    __syncthreads();
+    // 3. interleaved levels, row by row
+    float s32[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) s32[s] = s < ns ? scal[s].s32 : 0.f;
+    for (int m = warp; m < Mp; m += kGWarps) {
+      uint32_t n[kSlots][8];
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) n[s][e] = 0u;
+      if (m < a.M) {
+        float p[8];
+        load8f(P + m * kKsub + lane * 8, p);
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          if (s < ns) {
+            float qq[8];
+            load8f(a.qt + (size_t)q[s] * tstride + m * kKsub + lane * 8, qq);
+            const float mn = bias[s * Mp + m];
+            // levels t = rint(fl32(fl32(T' - bias) * s32)) <= L, in the low byte
+#pragma unroll
+            for (int e = 0; e < 8; ++e) n[s][e] = rint_bits_g(mul_rn(sub_rn(sub_rn(p[e], qq[e]), mn), s32[s]));
+          }
+        }
+      }
+      uint32_t wv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        wv[e] = __byte_perm(__byte_perm(n[0][e], n[1][e], 0x0040), __byte_perm(n[2][e], n[3][e], 0x0040), 0x5410);
+      uint4* dst = (uint4*)(tab + m * kKsub + lane * 8);
+      dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      dst[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+    __syncthreads();
+    // 4. scan
+    float dl[kSlots], bo[kSlots];
+    int kq[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      dl[s] = s < ns ? scal[s].delta32 : 0.f;
+      bo[s] = s < ns ? scal[s].B32 : 0.f;
+      kq[s] = (s < ns) ? (a.kpq ? min(max(a.kpq[q[s]], 0), a.k) : a.k) : 0;
+    }
+    // each slot's threshold starts at its query's k-th distance over the
+    // query-major pairs (rank 0 and the wide pairs): no better candidate list
+    // can contain a vector farther than that; equal distances are kept
+    WarpTopK<1, int64_t> top[kSlots];
+    float thd[kSlots], bound[kSlots];
+    int64_t thi[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      top[s].init();
+      bound[s] = kq[s] > 0 ? a.qm_d[(size_t)q[s] * a.k + kq[s] - 1] : INFINITY;
+      thd[s] = bound[s];
+      thi[s] = INT64_MAX;
+      if (warp == 0 && lane == s && bound[s] != INFINITY) atomicMin(&thr[s], ord_key(bound[s]));
+    }
+    __syncwarp();
+    const int n_l = a.list_len[l];
+    const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
+    const size_t tile_bytes = (size_t)NCHUNK * kTileChunkBytes;
+    const uint8_t* tp = a.codes + (size_t)a.tile_off[l] * tile_bytes + (size_t)warp * tile_bytes + lane * kChunkBytes;
+    const int64_t* idp = a.ids + a.vec_off[l];
+    uint4 w[NCHUNK];
+    if (warp < ntile) load_codes<NCHUNK>(tp, w);
+    for (int t = warp; t < ntile; t += kGWarps) {
+      uint4 wn[NCHUNK];
+      const bool more = t + kGWarps < ntile;
+      if (more) load_codes<NCHUNK>(tp + kGWarps * tile_bytes, wn);
+      uint32_t a02 = 0u, a13 = 0u;
+      adc_packed_seq<NCHUNK>(tab_addr, w, a02, a13, std::make_integer_sequence<int, NCHUNK * 16>{});
+      const int S[kSlots] = {(int)(a02 & 0xFFFFu), (int)(a13 & 0xFFFFu), (int)(a02 >> 16), (int)(a13 >> 16)};
+      const int v = t * kTileVecs + lane;
+      float d[kSlots];
+      bool pre[kSlots];
+      bool any = false;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        d[s] = add_rn(mul_rn(dl[s], __int2float_rn(S[s])), bo[s]);
+        // a distance above another warp's k-th cannot enter the block's top-k
+        // (equal distances are kept: the id decides between them)
+        pre[s] = kq[s] > 0 && v < n_l && d[s] <= thd[s] && ord_key(d[s]) <= thr[s];
+        any |= pre[s];
+      }
+      if (__any_sync(kFull, any)) {
+        const int64_t id = any ? __ldg(idp + v) : INT64_MAX;
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s)
+          if (__any_sync(kFull, pre[s])) {
+            top[s].offer(pre[s], d[s], id, kq[s], thd[s], thi[s]);
+            if (bound[s] < thd[s]) { thd[s] = bound[s]; thi[s] = INT64_MAX; }
+            if (lane == 0 && thd[s] != INFINITY) atomicMin(&thr[s], ord_key(thd[s]));
+          }
+      }
+      if (more) {
+#pragma unroll
+        for (int c = 0; c < NCHUNK; ++c) w[c] = wn[c];
+      }
+      tp += kGWarps * tile_bytes;
+    }
+    // merge the warps' lists per slot; warp s writes slot s
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      md[(s * kGWarps + warp) * 32 + lane] = top[s].d[0];
+      mi[(s * kGWarps + warp) * 32 + lane] = top[s].id[0];
+    }
+    __syncthreads();
+    if (warp < ns) {
+      const int s = warp;
+      WarpTopK<1, int64_t> m;
+      m.init();
+      float th = INFINITY;
+      int64_t ti = INT64_MAX;
+      int ks = kq[0];
+      int p = pid[0];
+#pragma unroll
+      for (int u = 1; u < kSlots; ++u) if (s == u) { ks = kq[u]; p = pid[u]; }
+      for (int w2 = 0; w2 < kGWarps && ks > 0; ++w2) {
+        const float cd = md[(s * kGWarps + w2) * 32 + lane];
+        const int64_t ci = mi[(s * kGWarps + w2) * 32 + lane];
+        m.offer(cd != INFINITY, cd, ci, ks, th, ti);
+      }
+      if (lane < a.k) {
+        const bool ok = lane < ks && m.d[0] != INFINITY;
+        a.part_d[(size_t)p * a.k + lane] = ok ? m.d[0] : INFINITY;
+        a.part_i[(size_t)p * a.k + lane] = ok ? m.id[0] : -1;
+      }
+    }
+  }
+}
+
+// One warp per query: the k smallest (d, id) over the query-major partial
+// top-k (wide pairs) and the partial top-k of the query's narrow pairs.
+__global__ void __launch_bounds__(256) merge_grouped_kernel(
+    const float* __restrict__ qm_d, const int64_t* __restrict__ qm_i, const float* __restrict__ part_d,
+    const int64_t* __restrict__ part_i, const int32_t* __restrict__ probes, const uint8_t* __restrict__ bits,
+    const int32_t* __restrict__ npq, const int32_t* __restrict__ kpq, int64_t nq, int nprobe, int k,
+    int64_t* __restrict__ ids_out, float* __restrict__ dists_out) {
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  const int np = npq ? min(max(npq[q], 0), nprobe) : nprobe;
+  const int kq = kpq ? min(max(kpq[q], 0), k) : k;
+  WarpTopK<1, int64_t> top;
+  top.init();
+  float thd = INFINITY;
+  int64_t thi = INT64_MAX;
+  if (kq > 0) {
+    const bool in = lane < kq;
+    const float d = in ? qm_d[q * k + lane] : INFINITY;
+    const int64_t id = in ? qm_i[q * k + lane] : -1;
+    top.offer(in && id >= 0, d, id, kq, thd, thi);
+  }
+  for (int j = 0; kq > 0 && j < np; ++j) {
+    const int64_t pid = q * nprobe + j;
+    const int b = bits[pid];
+    if (j == 0 || probes[pid] < 0 || b < 1 || b > 8) continue;
+    const bool in = lane < kq;
+    const float d = in ? part_d[pid * k + lane] : INFINITY;
+    const int64_t id = in ? part_i[pid * k + lane] : -1;
+    top.offer(in && id >= 0, d, id, kq, thd, thi);
+  }
+  if (lane < k) {
+    const bool ok = lane < kq && top.d[0] != INFINITY;
+    ids_out[q * k + lane] = ok ? top.id[0] : -1;
+    dists_out[q * k + lane] = ok ? top.d[0] : INFINITY;
+  }
+}
+
+template <int NCHUNK>
+cudaError_t run_packed(const GArgs& a, cudaStream_t s) {
+  auto kern = packed_kernel<NCHUNK>;
+  const GLayout L(NCHUNK * 16);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGThreads, L.total);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  kern<<<sms * per_sm, kGThreads, L.total, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool grouped_supported(const Index& ix, int k) {
+  if (k > 32) return false;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return GLayout((int)ix.Mp).total <= (size_t)optin;
+}
+
+size_t grouped_workspace_bytes(int64_t nq, int k) { return (size_t)nq * k * 12 + 256; }
+
+cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, int nprobe,
+                                  const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
+                                  const int32_t* probes, const float* probe_d2, const uint8_t* bits,
+                                  const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
+                                  cudaStream_t s) {
+  // narrow pairs regrouped by list, groups of four, largest lists first
+  cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kSlots, w.cnt, w.off, w.ioff, w.fill,
+                                w.pairs, s, bits);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  // rank 0 and the wide pairs, query-major, into a partial top-k per query
+  float* qm_d = (float*)qm_ws;
+  int64_t* qm_i = (int64_t*)((char*)qm_ws + (((size_t)nq * k * 4 + 255) & ~size_t(255)));
+  e = launch_search(ix, qt, nq, nprobe, nprobe_per_q, k, k_per_q, probes, probe_d2, bits, nullptr, qm_i, qm_d, s,
+                    true);
+  if (e != cudaSuccess) return e;
+  GArgs a{};
+  a.qt = qt; a.ltab = ix.ltab; a.probe_d2 = probe_d2; a.bits = bits;
+  a.codes = ix.codes; a.ids = ix.ids; a.list_len = ix.list_len; a.vec_off = ix.vec_off;
+  a.tile_off = ix.tile_off; a.order = ix.order; a.cnt = w.cnt; a.off = w.off; a.ioff = w.ioff;
+  a.pairs = w.pairs; a.nlist = (int)ix.nlist; a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.nprobe = nprobe; a.k = k;
+  a.kpq = k_per_q; a.part_d = w.part_d; a.part_i = w.part_i; a.counter = w.counter; a.qm_d = qm_d;
+  switch (ix.nchunk) {
+    case 1: e = run_packed<1>(a, s); break;
+    case 2: e = run_packed<2>(a, s); break;
+    case 3: e = run_packed<3>(a, s); break;
+    case 4: e = run_packed<4>(a, s); break;
+    case 5: e = run_packed<5>(a, s); break;
+    case 6: e = run_packed<6>(a, s); break;
+    case 7: e = run_packed<7>(a, s); break;
+    default: e = run_packed<8>(a, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  merge_grouped_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(qm_d, qm_i, w.part_d, w.part_i, probes, bits,
+                                                                nprobe_per_q, k_per_q, nq, nprobe, k, ids_out,
+                                                                dists_out);
+  return cudaGetLastError();
+}
+
+}  // namespace anns

@@ -29,9 +29,9 @@ def _pair(amp, ix, ids=None):
     return g, o
 
 
-@pytest.fixture(scope="module", params=["basic", "lists"])
+@pytest.fixture(scope="module", params=["basic", "lists", "grouped"])
 def case_a(amp, small_a, request):
-    """Config A shape, searched by each of the two search kernels."""
+    """Config A shape, searched by each of the three search kernels."""
     d, ix = small_a
     g, o = _pair(amp, ix)
     g.set_kernel(request.param)

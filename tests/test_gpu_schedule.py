@@ -156,7 +156,7 @@ def test_workload_geometries_bit_exact(amp, key, M, nlist, bits_set):
     try:
         for bits in bits_set:
             pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
-            for kern in ("auto", "lists"):
+            for kern in ("auto", "lists", "grouped", "basic"):
                 g.set_kernel(kern)
                 ids, dists = g.search(cuda(Q), 8, 100, pol, nprobe_per_q=cuda(npq), k_per_q=cuda(kpq))
                 ri, rd = ivfpq.search(o, Q, 8, 100, bits=bits, nprobe_per_q=npq, k_per_q=kpq)
