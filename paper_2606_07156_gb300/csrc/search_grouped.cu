@@ -77,8 +77,8 @@ __device__ __forceinline__ void packed_acc(uint32_t base, const uint4 (&w)[NCHUN
   const uint32_t code = __byte_perm(x, 0u, 0x4440u + (K & 3));
   uint32_t v;
   asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(base + code * 4u), "n"(K * 1024));
-  a02 += v & 0x00FF00FFu;
-  a13 += (v >> 8) & 0x00FF00FFu;
+  a02 += __byte_perm(v, 0u, 0x4240u);  // bytes 0 and 2 as 16-bit lanes
+  a13 += __byte_perm(v, 0u, 0x4341u);  // bytes 1 and 3
 }
 template <int NCHUNK, int... K>
 __device__ __forceinline__ void adc_packed_seq(uint32_t base, const uint4 (&w)[NCHUNK], uint32_t& a02, uint32_t& a13,
@@ -155,26 +155,29 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
       bb[s] = pid[s] >= 0 ? a.bits[pid[s]] : 8;
     }
     const float* P = a.ltab + (size_t)l * tstride;
-    // 1. row statistics of every (slot, row)
-    for (int t = warp; t < ns * a.M; t += kGWarps) {
-      const int s = t / a.M, m = t % a.M;
-      int qs = q[0];
-#pragma unroll
-      for (int u = 1; u < kSlots; ++u) if (s == u) qs = q[u];
-      float p[8], qq[8];
+    // 1. row statistics: warp w takes rows m = w, w + 8, ...; the list-table
+    //    row is loaded once for the group's slots
+    for (int m = warp; m < a.M; m += kGWarps) {
+      float p[8];
       load8f(P + m * kKsub + lane * 8, p);
-      load8f(a.qt + (size_t)qs * tstride + m * kKsub + lane * 8, qq);
-      float lo_v = sub_rn(p[0], qq[0]), hi_v = lo_v;
 #pragma unroll
-      for (int e = 1; e < 8; ++e) {
-        const float tv = sub_rn(p[e], qq[e]);
-        lo_v = fminf(lo_v, tv);
-        hi_v = fmaxf(hi_v, tv);
+      for (int s = 0; s < kSlots; ++s) {
+        if (s < ns) {
+          float qq[8];
+          load8f(a.qt + (size_t)q[s] * tstride + m * kKsub + lane * 8, qq);
+          float lo_v = sub_rn(p[0], qq[0]), hi_v = lo_v;
+#pragma unroll
+          for (int e = 1; e < 8; ++e) {
+            const float tv = sub_rn(p[e], qq[e]);
+            lo_v = fminf(lo_v, tv);
+            hi_v = fmaxf(hi_v, tv);
+          }
+          const float mn = warp_min(lo_v);
+          // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
+          const float mx = sub_rn(warp_max(hi_v), mn);
+          if (lane == 0) { bias[s * Mp + m] = mn; rowmax[s * Mp + m] = mx; }
+        }
       }
-      const float mn = warp_min(lo_v);
-      // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
-      const float mx = sub_rn(warp_max(hi_v), mn);
-      if (lane == 0) { bias[s * Mp + m] = mn; rowmax[s * Mp + m] = mx; }
     }
     __syncthreads();
     // 2. per slot: step, scale and offset
