@@ -123,4 +123,23 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// The 8 entries of a 256-entry table row that lane i of a warp handles:
+// 4i..4i+3 (half 0) and 128+4i..128+4i+3 (half 1). Each of the warp's two
+// 16-byte accesses then covers 512 contiguous bytes: whole sectors from
+// global memory, no bank conflicts in shared memory.
+__device__ __forceinline__ int row_at(int lane, int h) { return h * 128 + lane * 4; }
+
+// Entries of row `row` (256 floats) for `lane` in the order above.
+__device__ __forceinline__ void ldg_row8(const float* __restrict__ row, int lane, float (&v)[8]) {
+  const float4 a = __ldg((const float4*)(row + row_at(lane, 0)));
+  const float4 b = __ldg((const float4*)(row + row_at(lane, 1)));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// Writes 8 floats of row `row` (shared or global) for `lane`, same order.
+__device__ __forceinline__ void st_row8(float* row, int lane, const float (&v)[8]) {
+  *(float4*)(row + row_at(lane, 0)) = make_float4(v[0], v[1], v[2], v[3]);
+  *(float4*)(row + row_at(lane, 1)) = make_float4(v[4], v[5], v[6], v[7]);
+}
+
 }  // namespace anns

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) label_kernel(const LabelArgs a) {
       float t[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const int c = lane * 8 + e;
+        const int c = e * 32 + lane;
         t[e] = sub_rn(__ldg(P + m * kKsub + c), __ldg(Qt + m * kKsub + c));
         T[m * kKsub + c] = t[e];
       }

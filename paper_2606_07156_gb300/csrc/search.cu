@@ -118,25 +118,26 @@ __device__ __forceinline__ void quantise8(const float (&x)[8], float mn, float s
   for (int e = 0; e < 8; ++e) n[e] = rint_bits(mul_rn(sub_rn(x[e], mn), s32));
 }
 
-// Packs 8 levels (low bits of n) into the table row at `dst`, 1 or 2 bytes each.
-__device__ __forceinline__ void store_levels(int b, const uint32_t (&n)[8], void* dst) {
+// Packs the 8 levels (low bits of n) of `lane` into table row `row`, 1 or 2
+// bytes each, at the entries row_at() gives.
+__device__ __forceinline__ void store_levels(int b, const uint32_t (&n)[8], void* row, int lane) {
   if (b <= 8) {
-    uint2 v;
-    v.x = __byte_perm(__byte_perm(n[0], n[1], 0x0040), __byte_perm(n[2], n[3], 0x0040), 0x5410);
-    v.y = __byte_perm(__byte_perm(n[4], n[5], 0x0040), __byte_perm(n[6], n[7], 0x0040), 0x5410);
-    *(uint2*)dst = v;
+    uint8_t* r = (uint8_t*)row;
+    *(uint32_t*)(r + row_at(lane, 0)) =
+        __byte_perm(__byte_perm(n[0], n[1], 0x0040), __byte_perm(n[2], n[3], 0x0040), 0x5410);
+    *(uint32_t*)(r + row_at(lane, 1)) =
+        __byte_perm(__byte_perm(n[4], n[5], 0x0040), __byte_perm(n[6], n[7], 0x0040), 0x5410);
   } else {
-    uint4 v;
-    v.x = __byte_perm(n[0], n[1], 0x5410); v.y = __byte_perm(n[2], n[3], 0x5410);
-    v.z = __byte_perm(n[4], n[5], 0x5410); v.w = __byte_perm(n[6], n[7], 0x5410);
-    *(uint4*)dst = v;
+    uint16_t* r = (uint16_t*)row;
+    *(uint2*)(r + row_at(lane, 0)) = make_uint2(__byte_perm(n[0], n[1], 0x5410), __byte_perm(n[2], n[3], 0x5410));
+    *(uint2*)(r + row_at(lane, 1)) = make_uint2(__byte_perm(n[4], n[5], 0x5410), __byte_perm(n[6], n[7], 0x5410));
   }
 }
 
 // Steps 1-2 for one pair, T' staged in shared memory (any Mp): all threads of
 // the block take part. P and qt2 are the pair's list table and query table
 // ([Mp * 256], rows M..Mp-1 zero). Warp w builds rows m = w, w + nwarps, ...;
-// lane i owns entries 8i..8i+7 of a row, so each row's minimum and range come
+// lane i owns the 8 entries row_at() gives, so each row's minimum and range come
 // from warp shuffles during the build, and each warp quantises the rows it
 // built (two block barriers for a b-bit pair, one for an FP32 pair). The FP32
 // T' stays in shared memory for every pair (the LUT taps read it).
@@ -144,19 +145,17 @@ __device__ void build_lut(const float* __restrict__ P, const float* __restrict__
                           int b, float d2, Smem& s) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int m = warp; m < Mp; m += nwarps) {
-    float4* dst = (float4*)(s.T + m * kKsub + lane * 8);
+    float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (m >= M) {
-      dst[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-      dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      st_row8(s.T + m * kKsub, lane, t);
       continue;
     }
-    const float4* pr = (const float4*)(P + m * kKsub + lane * 8);
-    const float4* qr = (const float4*)(qt2 + m * kKsub + lane * 8);
-    const float4 p0 = __ldg(pr), p1 = __ldg(pr + 1), q0 = __ldg(qr), q1 = __ldg(qr + 1);
-    const float t[8] = {sub_rn(p0.x, q0.x), sub_rn(p0.y, q0.y), sub_rn(p0.z, q0.z), sub_rn(p0.w, q0.w),
-                        sub_rn(p1.x, q1.x), sub_rn(p1.y, q1.y), sub_rn(p1.z, q1.z), sub_rn(p1.w, q1.w)};
-    dst[0] = make_float4(t[0], t[1], t[2], t[3]);
-    dst[1] = make_float4(t[4], t[5], t[6], t[7]);
+    float p[8], q[8];
+    ldg_row8(P + m * kKsub, lane, p);
+    ldg_row8(qt2 + m * kKsub, lane, q);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) t[e] = sub_rn(p[e], q[e]);
+    st_row8(s.T + m * kKsub, lane, t);
     if (b != 0) {
       float mn = t[0];
 #pragma unroll
@@ -178,13 +177,13 @@ __device__ void build_lut(const float* __restrict__ P, const float* __restrict__
     float mn = 0.f;
     if (m < M) {
       mn = s.bias[m];
-      const float4* src = (const float4*)(s.T + m * kKsub + lane * 8);
-      const float4 u = src[0], v = src[1];
+      const float* row = s.T + m * kKsub;
+      const float4 u = *(const float4*)(row + row_at(lane, 0)), v = *(const float4*)(row + row_at(lane, 1));
       x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w; x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
     }
     uint32_t n[8];
     quantise8(x, mn, s32, n);
-    store_levels(b, n, (uint8_t*)s.q + (m * kKsub + lane * 8) * esz);
+    store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub * esz, lane);
   }
   __syncthreads();
 }
@@ -208,13 +207,11 @@ __device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, cons
     const int m = warp + r * nwarps;
     mn[r] = 0.f;
     if (m < M) {
-      const float4* pr = (const float4*)(P + m * kKsub + lane * 8);
-      const float4* qr = (const float4*)(qt2 + m * kKsub + lane * 8);
-      const float4 p0 = __ldg(pr), p1 = __ldg(pr + 1), q0 = __ldg(qr), q1 = __ldg(qr + 1);
-      t[r][0] = sub_rn(p0.x, q0.x); t[r][1] = sub_rn(p0.y, q0.y);
-      t[r][2] = sub_rn(p0.z, q0.z); t[r][3] = sub_rn(p0.w, q0.w);
-      t[r][4] = sub_rn(p1.x, q1.x); t[r][5] = sub_rn(p1.y, q1.y);
-      t[r][6] = sub_rn(p1.z, q1.z); t[r][7] = sub_rn(p1.w, q1.w);
+      float p[8], q[8];
+      ldg_row8(P + m * kKsub, lane, p);
+      ldg_row8(qt2 + m * kKsub, lane, q);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) t[r][e] = sub_rn(p[e], q[e]);
     } else {
 #pragma unroll
       for (int e = 0; e < 8; ++e) t[r][e] = 0.f;
@@ -222,11 +219,7 @@ __device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, cons
   }
   if (b == 0) {
 #pragma unroll
-    for (int r = 0; r < RPW; ++r) {
-      float4* dst = (float4*)(T + (warp + r * nwarps) * kKsub + lane * 8);
-      dst[0] = make_float4(t[r][0], t[r][1], t[r][2], t[r][3]);
-      dst[1] = make_float4(t[r][4], t[r][5], t[r][6], t[r][7]);
-    }
+    for (int r = 0; r < RPW; ++r) st_row8(T + (warp + r * nwarps) * kKsub, lane, t[r]);
     return;
   }
 #pragma unroll
@@ -249,7 +242,7 @@ __device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, cons
   for (int r = 0; r < RPW; ++r) {
     uint32_t n[8];
     quantise8(t[r], mn[r], s32, n);
-    store_levels(b, n, (uint8_t*)lv + ((warp + r * nwarps) * kKsub + lane * 8) * esz);
+    store_levels(b, n, (uint8_t*)lv + (size_t)(warp + r * nwarps) * kKsub * esz, lane);
   }
 }
 

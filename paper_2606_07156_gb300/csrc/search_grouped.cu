@@ -7,10 +7,10 @@
 // sub-space) then serves four queries, and two 32-bit accumulators hold the
 // four integer sums as 16-bit lanes (bytes 0 and 2, bytes 1 and 3; a sum of
 // at most 128 levels of 255 stays below 2^16). The list's code tiles and list
-// table are read once per group instead of once per pair. This is the form
-// the paper's "throughput scales with lower precision" (Sections 1, 2.2)
-// takes for table gathers: 8-bit levels pack four queries per gather, where
-// FP32 entries pack one. The wide pairs (FP32, 12 and 16 bits) go through
+// table are read once per group instead of once per pair. For table gathers
+// this is how a narrower table becomes throughput (the gain the paper expects
+// of lower precision, Sections 1, 2.2): 8-bit levels pack four queries per
+// gather, where FP32 entries pack one. The wide pairs (FP32, 12 and 16 bits) go through
 // the query-major kernel; a merge then takes each query's top-k over both
 // (TS). Results equal the other kernels' bit for bit: every table, integer
 // sum and distance follows the same rules (search.cu).
@@ -23,9 +23,11 @@
 //      (lane l adding rows l, l+32, ... then the butterfly, as elsewhere);
 //   3. levels: each warp recomputes T' for its rows of all four slots,
 //      quantises and interleaves the four levels of each entry;
-//   4. scan: warps take code tiles; per vector the four sums, distances and
-//      four warp top-k lists; the warps' lists are merged per slot and
-//      written to the pairs' partial results.
+//   4. scan: warps take code tiles; per vector the four sums and one
+//      integer test of all four against the block's limits; the few vectors
+//      that pass get their distances and enter the warp's top-k lists (in
+//      shared memory); the warps' lists are merged per slot and written to
+//      the pairs' partial results.
 #include <algorithm>
 #include <utility>
 
@@ -50,11 +52,13 @@ struct GArgs {
   int* counter;
 };
 
-struct SlotScal { float s32, delta32, B32; int pad; };
+// Per slot: the scale, the step and offset of the distances, the bound from
+// the query-major pairs, the slot's k and its pair.
+struct SlotScal { float s32, delta32, B32, bound; int kq, pid, pad0, pad1; };
 
 // Bytes of the block's shared memory (256-aligned offsets).
 struct GLayout {
-  size_t tab, bias, rowmax, scal, item, thr, md, mi, total;
+  size_t tab, bias, rowmax, scal, item, lim, md, mi, total;
   __host__ __device__ GLayout(int Mp) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t o = 0;
@@ -63,7 +67,7 @@ struct GLayout {
     rowmax = o; o += al((size_t)kSlots * Mp * 4);
     scal = o; o += al(sizeof(SlotScal) * kSlots);
     item = o; o += al(16 * 4);
-    thr = o; o += al(kSlots * 4);
+    lim = o; o += al(2 * 4);
     md = o; o += al((size_t)kSlots * kGWarps * 32 * 4);
     mi = o; o += al((size_t)kSlots * kGWarps * 32 * 8);
     total = o + 256;
@@ -92,17 +96,32 @@ __device__ __forceinline__ void load_codes(const uint8_t* __restrict__ tile, uin
   for (int c = 0; c < NCHUNK; ++c) w[c] = __ldg(reinterpret_cast<const uint4*>(tile + c * kTileChunkBytes));
 }
 
-__device__ __forceinline__ void load8f(const float* p, float (&v)[8]) {
-  const float4 a = __ldg((const float4*)p), b = __ldg((const float4*)p + 1);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-
 __device__ __forceinline__ uint32_t rint_bits_g(float y) { return __float_as_uint(add_rn(y, 12582912.0f)); }
 
-// Signed-int key with the order of the float (for atomicMin on distances).
-__device__ __forceinline__ int ord_key(float f) {
-  const int b = __float_as_int(f);
-  return b >= 0 ? b : b ^ 0x7FFFFFFF;
+// Largest integer sum S in [0, 0x7FFF] whose distance fl32(fl32(delta * S) + B)
+// is <= x, or -1 when none is. The distance never falls as S rises (both
+// roundings are monotone), so d(S) <= x exactly when S <= smax_of(x).
+__device__ __noinline__ int smax_of(float x, float delta, float B) {
+  int lo = -1, hi = 0x7FFF;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (add_rn(mul_rn(delta, __int2float_rn(mid)), B) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Lowers slot s's 16-bit lane of the block's packed limits to v (if lower).
+// A retry lost to the cap leaves a larger limit, which only prunes less.
+__device__ __forceinline__ void lim_min(uint32_t* lim, int s, uint32_t v) {
+  uint32_t* w = lim + (s & 1);
+  const int sh = (s >> 1) * 16;
+  uint32_t old = *(volatile uint32_t*)w;
+  for (int it = 0; it < 256; ++it) {
+    if (((old >> sh) & 0xFFFFu) <= v) return;
+    const uint32_t seen = atomicCAS(w, old, (old & ~(0xFFFFu << sh)) | (v << sh));
+    if (seen == old) return;
+    old = seen;
+  }
 }
 
 template <int NCHUNK>
@@ -117,16 +136,17 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
   float* rowmax = (float*)(base + L.rowmax);
   SlotScal* scal = (SlotScal*)(base + L.scal);
   int* item = (int*)(base + L.item);
-  int* thr = (int*)(base + L.thr);  // per slot: the best k-th distance any warp holds (ordered int)
+  uint32_t* lim = (uint32_t*)(base + L.lim);  // 0x8000 + Smax per slot, 16-bit lanes (see the scan)
   float* md = (float*)(base + L.md);
   int64_t* mi = (int64_t*)(base + L.mi);
   const uint32_t tab_addr = raw + pad + (uint32_t)L.tab;
+  const uint32_t lim_addr = raw + pad + (uint32_t)L.lim;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngroups = a.ioff[a.nlist];
   const size_t tstride = (size_t)Mp * kKsub;
   for (;;) {
     __syncthreads();  // the previous group is done with the shared tables
-    if (threadIdx.x < kSlots) thr[threadIdx.x] = 0x7F800000;  // +inf
+    if (threadIdx.x < 2) lim[threadIdx.x] = 0xFFFFFFFFu;  // every sum passes until the seeds
     if (threadIdx.x == 0) {
       const int it = atomicAdd(a.counter, 1);
       item[0] = it;
@@ -147,62 +167,86 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
     __syncthreads();
     if (item[0] >= ngroups) break;
     const int l = item[1], ns = item[2];
-    int pid[kSlots], q[kSlots], bb[kSlots];
+    int q[kSlots];
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-      pid[s] = item[4 + s];
-      q[s] = pid[s] >= 0 ? pid[s] / a.nprobe : 0;
-      bb[s] = pid[s] >= 0 ? a.bits[pid[s]] : 8;
-    }
+    for (int s = 0; s < kSlots; ++s) q[s] = item[4 + s] >= 0 ? item[4 + s] / a.nprobe : 0;
     const float* P = a.ltab + (size_t)l * tstride;
     // 1. row statistics: warp w takes rows m = w, w + 8, ...; the list-table
-    //    row is loaded once for the group's slots
+    //    row is loaded once for the group's slots, the query-table rows two
+    //    slots at a time, and the eight reductions run side by side (an
+    //    absent slot reads its query 0 row and stores nothing)
     for (int m = warp; m < a.M; m += kGWarps) {
-      float p[8];
-      load8f(P + m * kKsub + lane * 8, p);
+      float p[8], lo_v[kSlots], hi_v[kSlots];
+      ldg_row8(P + m * kKsub, lane, p);
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-        if (s < ns) {
-          float qq[8];
-          load8f(a.qt + (size_t)q[s] * tstride + m * kKsub + lane * 8, qq);
-          float lo_v = sub_rn(p[0], qq[0]), hi_v = lo_v;
+      for (int s0 = 0; s0 < kSlots; s0 += 2) {
+        float qq[2][8];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) ldg_row8(a.qt + (size_t)q[s0 + u] * tstride + m * kKsub, lane, qq[u]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int s = s0 + u;
+          lo_v[s] = hi_v[s] = sub_rn(p[0], qq[u][0]);
 #pragma unroll
           for (int e = 1; e < 8; ++e) {
-            const float tv = sub_rn(p[e], qq[e]);
-            lo_v = fminf(lo_v, tv);
-            hi_v = fmaxf(hi_v, tv);
+            const float tv = sub_rn(p[e], qq[u][e]);
+            lo_v[s] = fminf(lo_v[s], tv);
+            hi_v[s] = fmaxf(hi_v[s], tv);
           }
-          const float mn = warp_min(lo_v);
-          // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
-          const float mx = sub_rn(warp_max(hi_v), mn);
-          if (lane == 0) { bias[s * Mp + m] = mn; rowmax[s * Mp + m] = mx; }
         }
       }
+#pragma unroll
+      for (int o = 16; o; o >>= 1)
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          lo_v[s] = fminf(lo_v[s], __shfl_xor_sync(kFull, lo_v[s], o));
+          hi_v[s] = fmaxf(hi_v[s], __shfl_xor_sync(kFull, hi_v[s], o));
+        }
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s)
+        // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
+        if (lane == 0 && s < ns) { bias[s * Mp + m] = lo_v[s]; rowmax[s * Mp + m] = sub_rn(hi_v[s], lo_v[s]); }
     }
     __syncthreads();
-    // 2. per slot: step, scale and offset
-    if (warp < ns) {
+    // 2. per slot: step, scale and offset; the slot's k and its bound, the
+    //    k-th distance of its query over the query-major pairs (rank 0 and
+    //    the wide pairs), which seeds the scan's limit (no better candidate
+    //    list holds a vector farther than that; equal distances are kept)
+    if (warp < kSlots) {
       const int s = warp;
       float range = 0.f;
-      for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
-      range = warp_max(range);
-      int bs = bb[0];
-      float d2 = 0.f;
-#pragma unroll
-      for (int u = 0; u < kSlots; ++u) if (s == u) { bs = bb[u]; d2 = a.probe_d2[pid[u]]; }
-      const int Lv = (1 << bs) - 1;
       double B = 0.0;
-      for (int m = lane; m < a.M; m += 32) B = __dadd_rn(B, (double)bias[s * Mp + m]);
+      const int p = item[4 + s];
+      const int qs = p >= 0 ? p / a.nprobe : 0, bs = p >= 0 ? a.bits[p] : 8;
+      float d2 = 0.f;
+      if (s < ns) {
+        for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
+        range = warp_max(range);
+        for (int m = lane; m < a.M; m += 32) B = __dadd_rn(B, (double)bias[s * Mp + m]);
 #pragma unroll
-      for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+        for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+        d2 = a.probe_d2[p];
+      }
       if (lane == 0) {
+        const int Lv = (1 << bs) - 1;
         SlotScal sc;
         sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
         sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
         sc.B32 = __double2float_rn(__dadd_rn((double)d2, B));
-        sc.pad = 0;
+        sc.kq = s < ns ? (a.kpq ? min(max(a.kpq[qs], 0), a.k) : a.k) : 0;
+        sc.bound = sc.kq > 0 ? a.qm_d[(size_t)qs * a.k + sc.kq - 1] : INFINITY;
+        sc.pid = p;
+        sc.pad0 = sc.pad1 = 0;
         scal[s] = sc;
+        const int seed = sc.kq == 0 ? -1 : (sc.bound == INFINITY ? 0x7FFF : smax_of(sc.bound, sc.delta32, sc.B32));
+        lim_min(lim, s, (uint32_t)(0x8000 + seed));
       }
+    }
+    // the warps' top-k lists start empty
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+      md[(s * kGWarps + warp) * 32 + lane] = INFINITY;
+      mi[(s * kGWarps + warp) * 32 + lane] = INT64_MAX;
     }
     __syncthreads();
     // 3. interleaved levels, row by row
@@ -210,59 +254,40 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) s32[s] = s < ns ? scal[s].s32 : 0.f;
     for (int m = warp; m < Mp; m += kGWarps) {
-      uint32_t n[kSlots][8];
+      // byte s of entry e's word holds slot s's level (absent slots and the
+      // padding rows m >= M hold 0)
+      uint32_t wv[8];
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) n[s][e] = 0u;
+      for (int e = 0; e < 8; ++e) wv[e] = 0u;
       if (m < a.M) {
         float p[8];
-        load8f(P + m * kKsub + lane * 8, p);
+        ldg_row8(P + m * kKsub, lane, p);
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) {
+          float qq[8];
+          ldg_row8(a.qt + (size_t)q[s] * tstride + m * kKsub, lane, qq);
           if (s < ns) {
-            float qq[8];
-            load8f(a.qt + (size_t)q[s] * tstride + m * kKsub + lane * 8, qq);
             const float mn = bias[s * Mp + m];
             // levels t = rint(fl32(fl32(T' - bias) * s32)) <= L, in the low byte
 #pragma unroll
-            for (int e = 0; e < 8; ++e) n[s][e] = rint_bits_g(mul_rn(sub_rn(sub_rn(p[e], qq[e]), mn), s32[s]));
+            for (int e = 0; e < 8; ++e)
+              wv[e] = __byte_perm(wv[e], rint_bits_g(mul_rn(sub_rn(sub_rn(p[e], qq[e]), mn), s32[s])),
+                                  0x3210u ^ (0x4u << (4 * s)) ^ ((uint32_t)s << (4 * s)));
           }
         }
       }
-      uint32_t wv[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        wv[e] = __byte_perm(__byte_perm(n[0][e], n[1][e], 0x0040), __byte_perm(n[2][e], n[3][e], 0x0040), 0x5410);
-      uint4* dst = (uint4*)(tab + m * kKsub + lane * 8);
-      dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-      dst[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+      *(uint4*)(tab + m * kKsub + row_at(lane, 0)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      *(uint4*)(tab + m * kKsub + row_at(lane, 1)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
     }
     __syncthreads();
-    // 4. scan
-    float dl[kSlots], bo[kSlots];
-    int kq[kSlots];
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-      dl[s] = s < ns ? scal[s].delta32 : 0.f;
-      bo[s] = s < ns ? scal[s].B32 : 0.f;
-      kq[s] = (s < ns) ? (a.kpq ? min(max(a.kpq[q[s]], 0), a.k) : a.k) : 0;
-    }
-    // each slot's threshold starts at its query's k-th distance over the
-    // query-major pairs (rank 0 and the wide pairs): no better candidate list
-    // can contain a vector farther than that; equal distances are kept
-    WarpTopK<1, int64_t> top[kSlots];
-    float thd[kSlots], bound[kSlots];
-    int64_t thi[kSlots];
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-      top[s].init();
-      bound[s] = kq[s] > 0 ? a.qm_d[(size_t)q[s] * a.k + kq[s] - 1] : INFINITY;
-      thd[s] = bound[s];
-      thi[s] = INT64_MAX;
-      if (warp == 0 && lane == s && bound[s] != INFINITY) atomicMin(&thr[s], ord_key(bound[s]));
-    }
-    __syncwarp();
+    // 4. scan. The test per vector is on the integer sums: lim holds
+    //    0x8000 + Smax per slot as 16-bit lanes laid out like the sums (slots
+    //    0 and 2 in lim[0], 1 and 3 in lim[1]), where Smax is the largest sum
+    //    whose distance is <= the smallest k-th distance any warp of the block
+    //    holds (or the bound). Sums stay <= 128 * 255 < 0x8000, so lane - S
+    //    borrows nothing and keeps bit 15 set exactly when S <= Smax. The
+    //    warps' lists live in shared memory (md, mi) and are touched only for
+    //    the vectors that pass.
     const int n_l = a.list_len[l];
     const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
     const size_t tile_bytes = (size_t)NCHUNK * kTileChunkBytes;
@@ -276,28 +301,38 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
       if (more) load_codes<NCHUNK>(tp + kGWarps * tile_bytes, wn);
       uint32_t a02 = 0u, a13 = 0u;
       adc_packed_seq<NCHUNK>(tab_addr, w, a02, a13, std::make_integer_sequence<int, NCHUNK * 16>{});
-      const int S[kSlots] = {(int)(a02 & 0xFFFFu), (int)(a13 & 0xFFFFu), (int)(a02 >> 16), (int)(a13 >> 16)};
+      uint32_t l02, l13;
+      asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(l02), "=r"(l13) : "r"(lim_addr));
+      const uint32_t p02 = (l02 - a02) & 0x80008000u, p13 = (l13 - a13) & 0x80008000u;
       const int v = t * kTileVecs + lane;
-      float d[kSlots];
-      bool pre[kSlots];
-      bool any = false;
-#pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-        d[s] = add_rn(mul_rn(dl[s], __int2float_rn(S[s])), bo[s]);
-        // a distance above another warp's k-th cannot enter the block's top-k
-        // (equal distances are kept: the id decides between them)
-        pre[s] = kq[s] > 0 && v < n_l && d[s] <= thd[s] && ord_key(d[s]) <= thr[s];
-        any |= pre[s];
-      }
+      const bool any = v < n_l && (p02 | p13) != 0u;
       if (__any_sync(kFull, any)) {
         const int64_t id = any ? __ldg(idp + v) : INT64_MAX;
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s)
-          if (__any_sync(kFull, pre[s])) {
-            top[s].offer(pre[s], d[s], id, kq[s], thd[s], thi[s]);
-            if (bound[s] < thd[s]) { thd[s] = bound[s]; thi[s] = INT64_MAX; }
-            if (lane == 0 && thd[s] != INFINITY) atomicMin(&thr[s], ord_key(thd[s]));
+        for (int s = 0; s < kSlots; ++s) {
+          const uint32_t acc = (s & 1) ? a13 : a02, pm = (s & 1) ? p13 : p02;
+          const bool ok = any && ((pm >> ((s >> 1) * 16 + 15)) & 1u);
+          if (__any_sync(kFull, ok)) {
+            const SlotScal sc = scal[s];
+            float* ld = md + (s * kGWarps + warp) * 32;
+            int64_t* li = mi + (s * kGWarps + warp) * 32;
+            WarpTopK<1, int64_t> top;
+            top.d[0] = ld[lane];
+            top.id[0] = li[lane];
+            // the warp's k-th entry, at most the bound (ties kept: the id decides)
+            float thd = ld[sc.kq - 1];
+            int64_t thi = li[sc.kq - 1];
+            if (sc.bound < thd) { thd = sc.bound; thi = INT64_MAX; }
+            const float d = add_rn(mul_rn(sc.delta32, __int2float_rn((int)((acc >> ((s >> 1) * 16)) & 0xFFFFu))),
+                                   sc.B32);
+            top.offer(ok, d, id, sc.kq, thd, thi);
+            if (sc.bound < thd) thd = sc.bound;
+            ld[lane] = top.d[0];
+            li[lane] = top.id[0];
+            if (lane == 0 && thd != INFINITY) lim_min(lim, s, (uint32_t)(0x8000 + smax_of(thd, sc.delta32, sc.B32)));
+            __syncwarp();
           }
+        }
       }
       if (more) {
 #pragma unroll
@@ -305,32 +340,24 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
       }
       tp += kGWarps * tile_bytes;
     }
-    // merge the warps' lists per slot; warp s writes slot s
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-      md[(s * kGWarps + warp) * 32 + lane] = top[s].d[0];
-      mi[(s * kGWarps + warp) * 32 + lane] = top[s].id[0];
-    }
     __syncthreads();
+    // merge the warps' lists per slot; warp s writes slot s
     if (warp < ns) {
       const int s = warp;
+      const SlotScal sc = scal[s];
       WarpTopK<1, int64_t> m;
       m.init();
       float th = INFINITY;
       int64_t ti = INT64_MAX;
-      int ks = kq[0];
-      int p = pid[0];
-#pragma unroll
-      for (int u = 1; u < kSlots; ++u) if (s == u) { ks = kq[u]; p = pid[u]; }
-      for (int w2 = 0; w2 < kGWarps && ks > 0; ++w2) {
+      for (int w2 = 0; w2 < kGWarps && sc.kq > 0; ++w2) {
         const float cd = md[(s * kGWarps + w2) * 32 + lane];
         const int64_t ci = mi[(s * kGWarps + w2) * 32 + lane];
-        m.offer(cd != INFINITY, cd, ci, ks, th, ti);
+        m.offer(cd != INFINITY, cd, ci, sc.kq, th, ti);
       }
       if (lane < a.k) {
-        const bool ok = lane < ks && m.d[0] != INFINITY;
-        a.part_d[(size_t)p * a.k + lane] = ok ? m.d[0] : INFINITY;
-        a.part_i[(size_t)p * a.k + lane] = ok ? m.id[0] : -1;
+        const bool ok = lane < sc.kq && m.d[0] != INFINITY;
+        a.part_d[(size_t)sc.pid * a.k + lane] = ok ? m.d[0] : INFINITY;
+        a.part_i[(size_t)sc.pid * a.k + lane] = ok ? m.id[0] : -1;
       }
     }
   }

@@ -37,18 +37,13 @@ struct LArgs {
   uint32_t region;   // bytes of one warp's table slice (a multiple of 256)
 };
 
-__device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
-  const float4 a = __ldg((const float4*)p), b = __ldg((const float4*)p + 1);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-
-// The same for data read once per warp (a query's table): not kept in L1, so
+// ldg_row8 for data read once per warp (a query's table): not kept in L1, so
 // the list's code tiles and list table, shared by the block's warps, stay there.
-__device__ __forceinline__ void load8_stream(const float* p, float (&v)[8]) {
+__device__ __forceinline__ void ldg_row8_stream(const float* row, int lane, float (&v)[8]) {
   asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(row + row_at(lane, 0)));
   asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]) : "l"(p + 4));
+               : "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]) : "l"(row + row_at(lane, 1)));
 }
 
 template <int NCHUNK>
@@ -63,17 +58,15 @@ struct PairTable {
                         unsigned char* tp, int lane) {
     if (b == 0) {
       for (int m = 0; m < Mp; ++m) {
-        float4* dst = (float4*)((float*)tp + m * kKsub + lane * 8);
+        float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (m < M) {
           float p[8], q[8];
-          load8(P + m * kKsub + lane * 8, p);
-          load8_stream(Qt + m * kKsub + lane * 8, q);
-          dst[0] = make_float4(sub_rn(p[0], q[0]), sub_rn(p[1], q[1]), sub_rn(p[2], q[2]), sub_rn(p[3], q[3]));
-          dst[1] = make_float4(sub_rn(p[4], q[4]), sub_rn(p[5], q[5]), sub_rn(p[6], q[6]), sub_rn(p[7], q[7]));
-        } else {
-          dst[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-          dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          ldg_row8(P + m * kKsub, lane, p);
+          ldg_row8_stream(Qt + m * kKsub, lane, q);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) t[e] = sub_rn(p[e], q[e]);
         }
+        st_row8((float*)tp + m * kKsub, lane, t);
       }
       return;
     }
@@ -88,8 +81,8 @@ struct PairTable {
         const int m = s * 32 + mm;
         if (m >= M) break;
         float p[8], q[8], t[8];
-        load8(P + m * kKsub + lane * 8, p);
-        load8_stream(Qt + m * kKsub + lane * 8, q);
+        ldg_row8(P + m * kKsub, lane, p);
+        ldg_row8_stream(Qt + m * kKsub, lane, q);
 #pragma unroll
         for (int e = 0; e < 8; ++e) t[e] = sub_rn(p[e], q[e]);
         float mn = t[0];
@@ -123,8 +116,8 @@ struct PairTable {
         if (m < M) {
           const float mn = __shfl_sync(kFull, rm[s], mm);
           float p[8], q[8];
-          load8(P + m * kKsub + lane * 8, p);
-          load8_stream(Qt + m * kKsub + lane * 8, q);
+          ldg_row8(P + m * kKsub, lane, p);
+          ldg_row8_stream(Qt + m * kKsub, lane, q);
 #pragma unroll
           for (int e = 0; e < 8; ++e)
             t[e] = (unsigned)min(__float2int_rn(mul_rn(sub_rn(sub_rn(p[e], q[e]), mn), s32)), L);
@@ -133,15 +126,12 @@ struct PairTable {
           for (int e = 0; e < 8; ++e) t[e] = 0u;
         }
         if (b <= 8) {
-          uint2 v;
-          v.x = t[0] | (t[1] << 8) | (t[2] << 16) | (t[3] << 24);
-          v.y = t[4] | (t[5] << 8) | (t[6] << 16) | (t[7] << 24);
-          *(uint2*)(tp + m * kKsub + lane * 8) = v;
+          *(uint32_t*)(tp + m * kKsub + row_at(lane, 0)) = t[0] | (t[1] << 8) | (t[2] << 16) | (t[3] << 24);
+          *(uint32_t*)(tp + m * kKsub + row_at(lane, 1)) = t[4] | (t[5] << 8) | (t[6] << 16) | (t[7] << 24);
         } else {
-          uint4 v;
-          v.x = t[0] | (t[1] << 16); v.y = t[2] | (t[3] << 16);
-          v.z = t[4] | (t[5] << 16); v.w = t[6] | (t[7] << 16);
-          *(uint4*)((uint16_t*)tp + m * kKsub + lane * 8) = v;
+          uint16_t* r = (uint16_t*)tp + m * kKsub;
+          *(uint2*)(r + row_at(lane, 0)) = make_uint2(t[0] | (t[1] << 16), t[2] | (t[3] << 16));
+          *(uint2*)(r + row_at(lane, 1)) = make_uint2(t[4] | (t[5] << 16), t[6] | (t[7] << 16));
         }
       }
     }
