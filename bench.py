@@ -7,10 +7,12 @@ The index's codes (32 MB) fit in L2, so L2 is flushed (a 512 MB write)
 between timed steps.
 
 The headline policy is the learned predictor: trained on the GPU (labels,
-features, MLP training) from separate training queries, its fallback margin
-calibrated on held-out queries so that it keeps >= 99 % of the plain FP32
-search's top-10. Plain FP32, uniform widths and the Eq. 2 heuristic are timed
-beside it.
+features, MLP training) from separate training queries, its round-up margin
+calibrated on 2000 held-out calibration queries (exact ground truth) as the
+most aggressive margin whose recall@10 stays within half the 1-point loss
+budget of plain FP32's. Plain FP32, uniform widths and the Eq. 2 heuristic
+(calibrated the same way) are timed beside it; the evaluation queries are
+used for neither training nor calibration.
 
 Default: python bench.py [--gpus 1 --steps K --warmup W]
 Reference arm: python bench.py --impl reference (the CPU oracle, a bounded sample).
@@ -48,13 +50,17 @@ def log(*a):
 
 # ------------------------------------------------------------------ workload
 
+NCAL = 2000  # calibration queries (seed offset 300), disjoint from the evaluation queries
+
+
 def workload(key: str, nq: int | None = None, device=None):
-    """Dataset, index arrays and exact ground truth (cached on disk)."""
-    from workloads import CONFIGS, exact_knn, make_dataset, train_ivfpq
+    """Dataset, index arrays, exact ground truth of the evaluation and the
+    calibration queries (cached on disk)."""
+    from workloads import CONFIGS, exact_knn, make_dataset, make_queries, train_ivfpq
     cfg = CONFIGS[key]
     nq = nq or cfg["nq"]
     os.makedirs(CACHE, exist_ok=True)
-    path = os.path.join(CACHE, f"{key}_{cfg['n']}_{nq}.npz")
+    path = os.path.join(CACHE, f"{key}_{cfg['n']}_{nq}_cal{NCAL}.npz")
     if os.path.exists(path):
         z = np.load(path)
         return cfg, {k: z[k] for k in z.files}
@@ -62,7 +68,9 @@ def workload(key: str, nq: int | None = None, device=None):
     d = make_dataset(key, nq=nq)
     ix = train_ivfpq(d["base"], cfg["nlist"], cfg["M"], seed=cfg["seed"], device=device)
     gt, _ = exact_knn(d["base"], d["queries"], 100, device=device)
-    out = dict(queries=d["queries"], gt=gt, **ix)
+    cal = make_queries(key, NCAL, stream=300)
+    cal_gt, _ = exact_knn(d["base"], cal, 100, device=device)
+    out = dict(queries=d["queries"], gt=gt, cal_queries=cal, cal_gt=cal_gt, **ix)
     np.savez(path, **out)
     log(f"workload {key}: generated in {time.time() - t:.1f}s")
     return cfg, out
@@ -176,11 +184,11 @@ def nvtx_pop():
         pass
 
 
-def scan_bytes(index, probes: np.ndarray, M: int) -> int:
-    """Algorithmic bytes of one scan launch: n_l * M code bytes per probed (query, list)."""
-    sizes = index.list_sizes()
-    p = probes[probes >= 0]
-    return int(sizes[p].sum()) * M
+def pair_bytes(index, probes: np.ndarray, M: int) -> np.ndarray:
+    """Algorithmic bytes per probed (query, list): n_l * M code bytes, one per
+    LUT lookup (0 for unused probe slots)."""
+    sizes = index.list_sizes().astype(np.int64)
+    return np.where(probes >= 0, sizes[np.maximum(probes, 0)], 0) * M
 
 
 def traffic_from_profile(kernel_src: str, workload_name: str):
@@ -200,33 +208,37 @@ def overlap(a: np.ndarray, b: np.ndarray, k: int) -> float:
     return float(np.mean([len(np.intersect1d(x[:k], y[:k])) / k for x, y in zip(a, b)]))
 
 
-def calibrate_margin(index, amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
-    """Smallest MLP round-up margin whose results keep >= target of the plain
-    FP32 top-k on held-out queries (the plain search as judge of the recall
-    loss: losing at most a fraction 1 - target of plain's results costs at most
-    that much recall). Widths mapped to this GPU's tables."""
-    ref = run(Qc, nprobe, amp.policy("plain"))
+LOSS_BUDGET = 0.5  # recall@10 points allowed on the calibration queries (half the 1-point target)
+
+
+def calibrate_margin(amp, Qc, gt_c, nprobe: int, k: int, run, budget: float = LOSS_BUDGET):
+    """Most aggressive MLP round-up margin (widths mapped to this GPU's
+    tables) whose recall@10 on the calibration queries is at most `budget`
+    points below plain FP32's: the plain search judges the recall loss, on
+    queries used neither for training nor for the timed evaluation. Margins
+    below 0 favour the narrower width; the grid ends at 16 (nearly all wide)."""
+    base = 100.0 * recall(run(Qc, nprobe, amp.policy("plain")), gt_c, 10)
     tried = {}
-    for m in (0.0, 0.1, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 8.0, 16.0):
-        ov = overlap(run(Qc, nprobe, amp.policy("mlp", margin=m, width_map=True)), ref, k)
-        tried[m] = ov
-        if ov >= target:
+    for m in (-2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.1, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 8.0, 16.0):
+        loss = base - 100.0 * recall(run(Qc, nprobe, amp.policy("mlp", margin=m, width_map=True)), gt_c, 10)
+        tried[m] = round(loss, 3)
+        if loss <= budget:
             return m, tried
     return float("inf"), tried
 
 
-def calibrate_eq2(amp, Qc, nprobe: int, k: int, run, target: float = 0.99):
+def calibrate_eq2(amp, Qc, gt_c, nprobe: int, k: int, run, budget: float = LOSS_BUDGET):
     """Most aggressive Eq. 2 threshold set th = (t + 1.5, t + 1, t + 0.5, t) for
-    4, 6, 8, 12 bits (widths mapped to this GPU's tables) keeping >= target of
-    the plain top-k on held-out queries."""
-    ref = run(Qc, nprobe, amp.policy("plain"))
+    4, 6, 8, 12 bits (widths mapped to this GPU's tables) within the same
+    recall budget on the calibration queries."""
+    base = 100.0 * recall(run(Qc, nprobe, amp.policy("plain")), gt_c, 10)
     best, tried = None, {}
     for t in (-24.0, -16.0, -12.0, -10.0, -8.0, -7.0, -6.0, -5.0, -4.0, -3.5, -3.0, -2.5, -2.0, -1.5, -1.0,
               -0.5, 0.0, 0.5, 1.0, 2.0, 4.0):
         th = (t + 1.5, t + 1.0, t + 0.5, t)
-        ov = overlap(run(Qc, nprobe, amp.policy("eq2", thresholds=th, width_map=True)), ref, k)
-        tried[t] = ov
-        if ov >= target:
+        loss = base - 100.0 * recall(run(Qc, nprobe, amp.policy("eq2", thresholds=th, width_map=True)), gt_c, 10)
+        tried[t] = round(loss, 3)
+        if loss <= budget:
             best = th
             break
     return best, tried
@@ -318,9 +330,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del Qt
-    Qc = torch.from_numpy(make_queries(args.config, 2000, stream=300)).to(dev)
-    margin, tried = calibrate_margin(index, amp, Qc, nprobe, k, run_q)
-    eq2_th, eq2_tried = calibrate_eq2(amp, Qc, nprobe, k, run_q)
+    Qc = torch.from_numpy(W["cal_queries"]).to(dev)
+    margin, tried = calibrate_margin(amp, Qc, W["cal_gt"], nprobe, k, run_q)
+    eq2_th, eq2_tried = calibrate_eq2(amp, Qc, W["cal_gt"], nprobe, k, run_q)
     del Qc
     adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True)
     policies = {"mlp": adaptive, "plain": plain}
@@ -341,6 +353,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         dist.barrier()
     torch.cuda.synchronize()
     abi.anns_profile(index.handle, 1)
+    launches0 = abi.anns_kernel_launches()
     with ClockSampler(local_rank) as clk:
         t0 = time.perf_counter()
         nvtx_push("anns_timed")
@@ -350,6 +363,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     stage_ms, cnt = abi.anns_profile(index.handle, 0)
+    launches_per_step = (abi.anns_kernel_launches() - launches0) / max(cnt, 1)
     ms_pol = {"mlp": ms_ad}
     for name, pol in policies.items():
         if name != "mlp":
@@ -380,14 +394,29 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         return None
     qps = weak_scaling_qps(totals, world, nq, args.steps)
     qps_e2e = world * nq * args.steps / total_e2e
+    # roofline of the dominant kernel of the adaptive step (the last search run
+    # was the adaptive one): the grouped kernel (stage 4) over the narrow pairs
+    # of probe rank >= 1, or the query-major kernel (stage 3) over the rest
     probes = index.tap(abi.TAP_PROBES, (nq, nprobe), np.int32)
-    nbytes = scan_bytes(index, probes, cfg["M"])
-    scan_ms = stage_ms[3] / max(cnt, 1)
+    bits = index.tap(abi.TAP_BITS, (nq, nprobe), np.uint8)
+    pb = pair_bytes(index, probes, cfg["M"])
+    narrow = (bits >= 1) & (bits <= 8)
+    narrow[:, 0] = False
+    st_ms = [v / max(cnt, 1) for v in stage_ms]
+    if st_ms[4] > 0.0 and st_ms[4] >= st_ms[3]:
+        kname, kfile, kms, nbytes = ("packed_kernel (grouped: four queries' 8-bit tables per gather; build + "
+                                     "scan + top-k)", "search_grouped.cu", st_ms[4], int(pb[narrow].sum()))
+    elif st_ms[4] > 0.0:
+        kname, kfile, kms, nbytes = ("search_kernel (query-major pass of the grouped search: rank 0 + wide "
+                                     "pairs)", "search.cu", st_ms[3], int(pb[~narrow].sum()))
+    else:
+        kname, kfile, kms, nbytes = ("search_kernel (LUT build + quantise + ADC scan + top-k)", "search.cu",
+                                     st_ms[3], int(pb.sum()))
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    achieved = nbytes / (scan_ms / 1e3) / 1e9
-    src = os.path.join(ROOT, "paper_2606_07156_gb300", "csrc", "search.cu")
+    achieved = nbytes / (kms / 1e3) / 1e9
+    src = os.path.join(ROOT, "paper_2606_07156_gb300", "csrc", kfile)
     wl = f"{cfg['name']} nq={nq} nprobe={nprobe} k={k}"
     line = {
         "metric": METRIC, "value": round(qps["mlp"], 1), "unit": "queries/s", "n_gpus": world,
@@ -397,7 +426,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
                    "policy": f"learned MLP per (query, list) trained on GB300 table classes, round-up "
-                             f"margin {margin}, widths 6->8 bits and 12/16->FP32",
+                             f"margin {margin} (recall-loss budget {LOSS_BUDGET} pt on calibration queries), widths 6->8 bits "
+                             f"and 12/16->FP32",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "recall_at_10": round(recs["mlp"][0], 4),
         "top10_kept_vs_plain": round(recs["mlp"][1], 4),
@@ -412,19 +442,23 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "eq2_thresholds": list(eq2_th) if eq2_th is not None else None,
         "predictor": {"train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
                       "classes": "GB300 tables (8-bit / wide)", "high_weight": args.high_weight,
-                      "margin_calibration_kept": {str(a): round(b, 4) for a, b in tried.items()}},
+                      "margin_calibration_recall_loss_pts": {str(a): b for a, b in tried.items()},
+                      "recall_loss_budget_pts": LOSS_BUDGET},
         "recall_sweep_plain": {str(a): round(b, 4) for a, b in rec_plain.items()},
-        "stage_ms_per_step": {n: round(v / max(cnt, 1), 4) for n, v in
+        "stage_ms_per_step": {n: round(v, 4) for n, v in
                               zip(("cl_distances", "cl_select", "precision_choice+query_tables",
-                                   "lut_scan_topk"), stage_ms)},
-        "roofline": {"bound": "hbm", "kernel": "search_kernel (LUT build + quantise + ADC scan + top-k)",
+                                   "search_before_grouped (invert + query-major)", "grouped_kernel",
+                                   "grouped_merge"), st_ms)},
+        "roofline": {"bound": "hbm", "kernel": kname,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
                      "traffic": traffic_from_profile(src, wl), "algorithmic_bytes_per_launch": nbytes,
-                     "lookups_per_s": round(nbytes / (scan_ms / 1e3), 1)},
+                     "kernel_ms": round(kms, 4), "lookups_per_s": round(nbytes / (kms / 1e3), 1),
+                     "note": "codes of this workload (32 MB) stay in L2: an as-if-HBM figure; the binding "
+                             "resource is the L1 / shared-memory data pipe"},
         "e2e": {"value": round(qps_e2e, 1), "unit": "queries/s", "h2d_bytes_per_step": int(Qh.numel() * 4),
                 "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4), "recall_at_10": round(rec_e2e, 4)},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk.summary(),
         "wall_s_timed": round(wall, 3),
     }

@@ -96,11 +96,13 @@ typedef struct {
                               by the FP32 rule: same probes and distances as FP32 */
   int32_t lc_prec;         /* ANNS_PREC_* for the LUT build; FP32 only */
   float eq2_thresholds[4]; /* HEURISTIC_EQ2: g thresholds for 4, 6, 8, 12 bits */
-  float fallback_margin;   /* MLP round-up margin tau >= 0: the fewest bits b such that
-                              fl32(max logit over widths <= b - max logit over wider
-                              widths) >= tau (16 bits if none); tau = 0 is the argmax,
-                              ties to the narrower width. A larger tau rounds uncertain
-                              pairs up, towards full precision. */
+  float fallback_margin;   /* MLP round-up margin tau (not NaN): the fewest bits b such
+                              that fl32(max logit over widths <= b - max logit over
+                              wider widths) >= tau (16 bits if none); tau = 0 is the
+                              argmax, ties to the narrower width. A larger tau rounds
+                              uncertain pairs up, towards full precision; a negative
+                              tau takes a narrower width while its best logit is
+                              within -tau of the wider ones'. */
   const uint8_t* pair_bits;/* EXPLICIT: device [nq * nprobe], 0 = FP32 */
   int32_t width_map;       /* HEURISTIC_EQ2 / MLP: 0 = widths as chosen; 1 = widths
                               mapped to this GPU's tables: 6 -> 8 bits (same table
@@ -190,13 +192,25 @@ int anns_scan_pairs(anns_index* index, const float* queries, int64_t nq,
                     void* cuda_stream);
 
 /* Stage timing with CUDA events recorded on the search stream around each
- * stage of anns_search: CL distances, CL selection, precision choice plus the
- * per-query tables, and the fused LUT + scan + top-k kernel.
+ * stage of anns_search:
+ *   0 CL distances, 1 CL selection, 2 precision choice plus the per-query
+ *   tables, 3 the search kernels up to the grouped kernel (the whole LUT +
+ *   scan + top-k for the query-major and list-major kernels; pair regrouping
+ *   plus the query-major pass for the grouped kernel), 4 the grouped kernel
+ *   itself, 5 the grouped kernel's per-query merge (4 and 5 are 0 on the other
+ *   kernels).
  *  enable  1 = start recording (and clear the totals), 0 = stop, -1 = leave as is.
- *  out_ms  host double [4] or NULL: accumulated milliseconds per stage since
- *          recording started (waits for the recorded searches to finish).
+ *  out_ms  host double [ANNS_PROFILE_STAGES] or NULL: accumulated
+ *          milliseconds per stage since recording started (waits for the
+ *          recorded searches to finish).
  *  count   host int64 or NULL: number of searches accumulated. */
+#define ANNS_PROFILE_STAGES 6
 int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* count);
+
+/* Number of CUDA kernels the library has enqueued since it was loaded, on
+ * every index and stream (host-side count: a launch into a stream being
+ * captured counts once, graph replays do not count). */
+int64_t anns_kernel_launches(void);
 
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.

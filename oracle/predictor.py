@@ -25,8 +25,8 @@ Readings (the paper fixes none of these):
   label = fewest b with E_l(b) < margin_l, else "needs FP32".
 * MLP inference: FP16 operands (weights, biases, inputs, hidden activations),
   FP32 accumulation in ascending input order starting from the bias, ReLU on
-  the hidden layers, FP32 logits, argmax with ties to the lower class; fall
-  back to the FP32 LUT when top1 - top2 logit < margin.
+  the hidden layers, FP32 logits; the width is the fewest bits c with
+  fl32(max_{i<=c} z_i - max_{i>c} z_i) >= tau, else 16 bits (decide_bits).
 """
 from __future__ import annotations
 

@@ -32,7 +32,7 @@ SYMBOLS = (
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
     "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
-    "anns_last_error",
+    "anns_kernel_launches", "anns_last_error",
 )
 
 
@@ -95,6 +95,7 @@ def _load():
         "anns_compute_luts": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
         "anns_scan_pairs": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
+        "anns_kernel_launches": ([], i64),
         "anns_set_option": ([vp, i32, i64], i32),
         "anns_locate_static": ([vp, vp, i64, i32, vp, vp, vp], i32),
         "anns_graph_capture": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), vp, vp,
@@ -178,12 +179,21 @@ def anns_scan_pairs(index, queries, nq, pair_q, pair_l, pair_bits, npairs, out_o
                                 out_off, dist_out, S_out, stream))
 
 
+PROFILE_STAGES = 6  # CL distances, CL selection, precision + query tables, search up to the
+# grouped kernel, the grouped kernel, the grouped merge
+
+
 def anns_profile(index, enable: int):
-    """Returns (ms per stage [4], number of searches) accumulated since recording started."""
-    ms = (ctypes.c_double * 4)()
+    """Returns (ms per stage [PROFILE_STAGES], number of searches) accumulated since recording started."""
+    ms = (ctypes.c_double * PROFILE_STAGES)()
     cnt = ctypes.c_int64()
     _check(_lib.anns_profile(index, enable, ms, ctypes.byref(cnt)))
     return list(ms), cnt.value
+
+
+def anns_kernel_launches() -> int:
+    """Kernels the library has enqueued since it was loaded (host-side count)."""
+    return int(_lib.anns_kernel_launches())
 
 
 def anns_set_option(index, option: int, value: int) -> None:

@@ -1,5 +1,6 @@
 // anns_search and friends: argument checks, workspace, and the launch sequence
 // CL -> precision choice -> (RC + LC + quantise + DC + TS) of Section 2.1.
+#include <cmath>
 #include <cstring>
 #include <utility>
 
@@ -187,7 +188,7 @@ int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq,
   p.width_map = pol.width_map;
   p.bits = bits; p.feat = feat;
   const int64_t n = nq * nprobe;
-  policy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
+  policy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p); note_launch();
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "policy kernel");
 }
@@ -217,7 +218,7 @@ int anns::check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t 
         break;
       case ANNS_LUT_MLP:
         if (!ix->has_mlp) return fail(ANNS_ERR_INVALID_ARG, "MLP policy needs a trained or loaded predictor");
-        if (!(pol->fallback_margin >= 0.f)) return fail(ANNS_ERR_INVALID_ARG, "MLP round-up margin must be >= 0");
+        if (std::isnan(pol->fallback_margin)) return fail(ANNS_ERR_INVALID_ARG, "MLP round-up margin is NaN");
         break;
       default: return fail(ANNS_ERR_INVALID_ARG, "unknown lut_mode");
     }
@@ -307,7 +308,10 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
     if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
     if (ev) cudaEventRecord(ev[3], s);
     e = launch_search_grouped(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
-                              ix.ws_bits, w, ix.ws_grp, ids_out, dists_out, s);
+                              ix.ws_bits, w, ix.ws_grp, ids_out, dists_out, s, ev ? ev[4] : nullptr,
+                              ev ? ev[5] : nullptr);
+    if (e == cudaSuccess && ev) cudaEventRecord(ev[6], s);
+    return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "search kernel");
   } else {
     const int32_t* order = nullptr;
     if (use_lpt(ix, nprobe_per_q)) {
@@ -320,7 +324,8 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
                       ix.ws_bits, order, ids_out, dists_out, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "search kernel");
-  if (ev) cudaEventRecord(ev[4], s);
+  if (ev)
+    for (int st = 4; st <= Index::kStages; ++st) cudaEventRecord(ev[st], s);
   return ANNS_OK;
 }
 

@@ -112,15 +112,15 @@ cudaError_t launch_coarse(const Index& ix, const float* Q, int64_t nq, int nprob
                           const int32_t* nprobe_per_q, float* d2, int32_t* probes,
                           float* probe_d2, cudaStream_t s, cudaEvent_t between) {
   dim3 g1((unsigned)((ix.nlist + kTL - 1) / kTL), (unsigned)std::min<int64_t>((nq + kTQ - 1) / kTQ, 65535));
-  coarse_d2_kernel<<<g1, 256, 0, s>>>(Q, ix.centroids, nq, ix.nlist, ix.dim, d2);
+  coarse_d2_kernel<<<g1, 256, 0, s>>>(Q, ix.centroids, nq, ix.nlist, ix.dim, d2); note_launch();
   if (between) cudaEventRecord(between, s);
   const unsigned g2 = (unsigned)((nq + 7) / 8);
   const int R = (nprobe + 31) / 32;
   switch (R) {
-    case 1: coarse_select_kernel<1><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
-    case 2: coarse_select_kernel<2><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
-    case 3: coarse_select_kernel<3><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
-    default: coarse_select_kernel<4><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
+    case 1: coarse_select_kernel<1><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
+    case 2: coarse_select_kernel<2><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
+    case 3: coarse_select_kernel<3><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
+    default: coarse_select_kernel<4><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
   }
   return cudaGetLastError();
 }

@@ -464,7 +464,7 @@ int prepare_coarse_tc(Index& ix, const std::vector<float>& cent) {
   if (e != cudaSuccess) return cuda_fail(e, "coarse fast-path setup");
   center_bf16_kernel<<<(unsigned)((ix.nlist + 7) / 8), 256>>>(ix.centroids, ix.nlist, (int)ix.dim, Dp, ix.tc_mu,
                                                              (__nv_bfloat16*)ix.tc_cb, ix.tc_cn,
-                                                             ix.tc_cn + ix.nlist, ix.tc_cn + 2 * ix.nlist);
+                                                             ix.tc_cn + ix.nlist, ix.tc_cn + 2 * ix.nlist); note_launch();
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "coarse fast-path setup");
@@ -505,7 +505,7 @@ cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int np
   float* qrows = (float*)((char*)ws + (((size_t)nq * Dp * 2 + 255) & ~size_t(255)));  // qn | qh | qe
   int* ncand = (int*)(qrows + 3 * nq);
   center_bf16_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, (int)ix.dim, Dp, ix.tc_mu, Qb, qrows,
-                                                              qrows + nq, qrows + 2 * nq);
+                                                              qrows + nq, qrows + 2 * nq); note_launch();
   CUtensorMap tmQ, tmC;
   cudaError_t e = make_tmap(&tmQ, Qb, nq, Dp, kTM);
   if (e == cudaSuccess) e = make_tmap(&tmC, ix.tc_cb, ix.nlist, Dp, kTN);
@@ -514,7 +514,7 @@ cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int np
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((ix.nlist + kTN - 1) / kTN), (unsigned)((nq + kTM - 1) / kTM));
   coarse_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(tmQ, tmC, qrows, ix.tc_cn, nq, ix.nlist, Dp, dt,
-                                                         ix.dev_status);
+                                                         ix.dev_status); note_launch();
   const int R = (nprobe + 31) / 32;
   const unsigned g = (unsigned)nq;
   const size_t qsm = (size_t)ix.dim * sizeof(float);
@@ -522,7 +522,7 @@ cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int np
     cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
     if (e2 != cudaSuccess) return e2;
     kern<<<g, kRThreads, qsm, s>>>(Q, ix.centroids, dt, qrows, ix.tc_cn, nq, ix.nlist, (int)ix.dim, Dp, nprobe,
-                                   nprobe_per_q, probes, probe_d2, ncand);
+                                   nprobe_per_q, probes, probe_d2, ncand); note_launch();
     return cudaGetLastError();
   };
   switch (R) {

@@ -1,6 +1,7 @@
 // Index construction and facts (Section 2.1: IVF lists, PQ codes on residuals
 // with one codebook shared by every cluster; covering radius r of Eq. 1).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -314,3 +315,13 @@ extern "C" int anns_debug_tap(anns_index* ix, int32_t what, void* out, size_t by
 }
 
 extern "C" const char* anns_last_error(void) { return anns::g_err.c_str(); }
+
+namespace anns {
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace anns
+
+extern "C" int64_t anns_kernel_launches(void) { return anns::launch_count(); }

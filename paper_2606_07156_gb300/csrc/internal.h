@@ -82,11 +82,11 @@ struct Index {
   void* st_out = nullptr; size_t st_out_cap = 0;
   void* st_pq = nullptr; size_t st_pq_cap = 0;
   // stage timing (anns_profile): pending event sets, accumulated ms
-  static constexpr int kProfSlots = 64, kStages = 4;
+  static constexpr int kProfSlots = 64, kStages = ANNS_PROFILE_STAGES;
   bool prof_on = false;
   cudaEvent_t prof_ev[kProfSlots][kStages + 1] = {};
   int prof_pending = 0;
-  double prof_ms[kStages] = {0, 0, 0, 0};
+  double prof_ms[kStages] = {};
   int64_t prof_count = 0;
   // learned predictor (FP16 inference copy + normalisation), see predictor.cu
   bool has_mlp = false;
@@ -95,6 +95,10 @@ struct Index {
 };
 
 void set_error(const std::string& msg);
+// Counts one kernel launch enqueued by the library (host side; a launch into a
+// stream being captured counts once, its replays not at all).
+void note_launch();
+int64_t launch_count();
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
@@ -170,7 +174,8 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
                                   const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                                   const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
-                                  cudaStream_t s);
+                                  cudaStream_t s, cudaEvent_t after_qm = nullptr,
+                                  cudaEvent_t after_packed = nullptr);
 // Pair-level debug paths; qt are the queries' tables from launch_query_tables.
 cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt, int64_t nq,
                                 const int32_t* pq, const int32_t* pl, const uint8_t* pb,

@@ -109,9 +109,9 @@ cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t*
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ix.nlist, s);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((n + 255) / 256);
-  count_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, cnt);
-  offsets_kernel<<<1, 1024, 0, s>>>(cnt, ix.order, (int)ix.nlist, batch, off, ioff, fill);
-  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, off, fill, pairs);
+  count_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, cnt); note_launch();
+  offsets_kernel<<<1, 1024, 0, s>>>(cnt, ix.order, (int)ix.nlist, batch, off, ioff, fill); note_launch();
+  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, off, fill, pairs); note_launch();
   return cudaGetLastError();
 }
 

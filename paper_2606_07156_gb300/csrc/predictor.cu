@@ -355,7 +355,7 @@ cudaError_t launch_grad(const float* X, const uint8_t* cls, const int64_t* idx, 
   cudaError_t e = cudaMemsetAsync(grad, 0, kNP * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
-  mlp_grad_kernel<<<(unsigned)((n + kGT - 1) / kGT), kGT, 0, s>>>(a);
+  mlp_grad_kernel<<<(unsigned)((n + kGT - 1) / kGT), kGT, 0, s>>>(a); note_launch();
   return cudaGetLastError();
 }
 
@@ -390,7 +390,7 @@ int train_on(Index& ix, const float* X, const uint8_t* cls, int64_t n, const ann
       ++step;
       const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
       adam_kernel<<<(kNP + 255) / 256, 256, 0, s>>>((float*)dw.p, (const float*)dg.p, (float*)dm.p,
-                                                     (float*)dv.p, cfg.lr, b1, b2, eps, c1, c2);
+                                                     (float*)dv.p, cfg.lr, b1, b2, eps, c1, c2); note_launch();
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "adam kernel");
     }
@@ -498,7 +498,7 @@ extern "C" int anns_train_predictor(anns_index* ix, const float* Q, int64_t nq, 
   if ((rc = feat.alloc((size_t)n * 5 * 4)) || (rc = lab.alloc((size_t)n)) || (rc = cls.alloc((size_t)n))) return rc;
   if ((rc = make_training_set(*ix, Q, nq, nprobe, k, (float*)feat.p, (uint8_t*)lab.p, s))) return rc;
   class_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const uint8_t*)lab.p, n, cfg->label_map,
-                                                           (uint8_t*)cls.p);
+                                                           (uint8_t*)cls.p); note_launch();
   // normalisation over the samples (host, FP64): a one-off set-up statistic
   std::vector<float> hf((size_t)n * 5);
   std::vector<uint8_t> hc((size_t)n);
@@ -549,7 +549,7 @@ int make_training_set(Index& ix, const float* Q, int64_t nq, int nprobe, int k, 
   if ((rc = anns_search(static_cast<anns_index*>(&ix), Q, nq, nprobe, nullptr, k + 1, nullptr, &plain,
                         (int64_t*)ids.p, (float*)dists.p, s)))
     return rc;
-  tau_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>((const float*)dists.p, nq, k, (double*)tau.p);
+  tau_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>((const float*)dists.p, nq, k, (double*)tau.p); note_launch();
   // the workspace now holds this batch's probes, probe D2 and query tables
   anns_precision_policy eq2{};
   eq2.lut_mode = ANNS_LUT_HEURISTIC_EQ2;
@@ -567,7 +567,7 @@ int make_training_set(Index& ix, const float* Q, int64_t nq, int nprobe, int k, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t np = nq * nprobe;
-  label_kernel<<<(unsigned)std::min<int64_t>(np, (int64_t)sms * 8), 256, smem, s>>>(a);
+  label_kernel<<<(unsigned)std::min<int64_t>(np, (int64_t)sms * 8), 256, smem, s>>>(a); note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "label kernel");
   // make sure the temporaries outlive the kernels that read them

@@ -6,8 +6,11 @@
 // FP32 accumulation: acc = b; for i ascending: acc = fma(W[o][i], x[i], acc).
 // The product of two FP16 values is exact in FP32, so the FMA rounds exactly
 // once, like fl32(acc + W*x). Hidden layers apply ReLU and round to FP16;
-// logits stay FP32. The class is the argmax (ties to the lower class); the
-// pair falls back to the FP32 LUT (bits 0) when top1 - top2 < margin.
+// logits stay FP32. The width is the fewest bits c whose best logit beats the
+// best logit of every wider width by at least the margin tau,
+// fl32(max_{i<=c} z_i - max_{i>c} z_i) >= tau, else 16 bits: tau = 0 is the
+// argmax with ties to the narrower width, tau > 0 rounds uncertain pairs up
+// and tau < 0 rounds them down.
 #pragma once
 
 #include <cuda_fp16.h>

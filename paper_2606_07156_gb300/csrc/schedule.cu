@@ -100,9 +100,9 @@ cudaError_t launch_lpt_order(const Index& ix, const int32_t* probes, const int32
   cudaError_t e = cudaMemsetAsync(hist, 0, kBuckets * sizeof(int), s);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((nq + 255) / 256);
-  cost_key_kernel<<<g, 256, 0, s>>>(probes, npq, ix.list_len, nq, nprobe, key, hist);
-  bucket_offsets_kernel<<<1, 1024, 0, s>>>(hist, off, cursor);
-  bucket_scatter_kernel<<<g, 256, 0, s>>>(key, off, cursor, nq, order_out);
+  cost_key_kernel<<<g, 256, 0, s>>>(probes, npq, ix.list_len, nq, nprobe, key, hist); note_launch();
+  bucket_offsets_kernel<<<1, 1024, 0, s>>>(hist, off, cursor); note_launch();
+  bucket_scatter_kernel<<<g, 256, 0, s>>>(key, off, cursor, nq, order_out); note_launch();
   return cudaGetLastError();
 }
 

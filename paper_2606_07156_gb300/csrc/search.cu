@@ -471,7 +471,7 @@ cudaError_t launch_query_major(K kern, const SearchArgs& a, cudaStream_t s) {
   cudaError_t e = prep(kern, a.lay.total);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::min<int64_t>(a.nq, 1 << 30);
-  kern<<<grid, kThreads, a.lay.total, s>>>(a);
+  kern<<<grid, kThreads, a.lay.total, s>>>(a); note_launch();
   return cudaGetLastError();
 }
 
@@ -493,7 +493,7 @@ cudaError_t run_scan_pairs(const SearchArgs& a, const int32_t* pq, const int32_t
   cudaError_t e = prep(kern, a.lay.total);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::min<int64_t>(npairs, 1 << 30);
-  kern<<<grid, kThreads, a.lay.total, s>>>(a, pq, pl, pb, npairs, off, dist_out, S_out);
+  kern<<<grid, kThreads, a.lay.total, s>>>(a, pq, pl, pb, npairs, off, dist_out, S_out); note_launch();
   return cudaGetLastError();
 }
 
@@ -530,7 +530,7 @@ cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt
   cudaError_t e = prep(luts_kernel, a.lay.total);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::min<int64_t>(npairs, 1 << 30);
-  luts_kernel<<<grid, kThreads, a.lay.total, s>>>(a, pq, pl, pb, npairs, T_out, t_out, scale_out);
+  luts_kernel<<<grid, kThreads, a.lay.total, s>>>(a, pq, pl, pb, npairs, T_out, t_out, scale_out); note_launch();
   return cudaGetLastError();
 }
 

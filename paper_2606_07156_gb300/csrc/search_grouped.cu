@@ -413,7 +413,7 @@ cudaError_t run_packed(const GArgs& a, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGThreads, L.total);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  kern<<<sms * per_sm, kGThreads, L.total, s>>>(a);
+  kern<<<sms * per_sm, kGThreads, L.total, s>>>(a); note_launch();
   return cudaGetLastError();
 }
 
@@ -433,7 +433,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
                                   const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                                   const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, cudaEvent_t after_qm, cudaEvent_t after_packed) {
   // narrow pairs regrouped by list, groups of four, largest lists first
   cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kSlots, w.cnt, w.off, w.ioff, w.fill,
                                 w.pairs, s, bits);
@@ -446,6 +446,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
   e = launch_search(ix, qt, nq, nprobe, nprobe_per_q, k, k_per_q, probes, probe_d2, bits, nullptr, qm_i, qm_d, s,
                     true);
   if (e != cudaSuccess) return e;
+  if (after_qm) cudaEventRecord(after_qm, s);
   GArgs a{};
   a.qt = qt; a.ltab = ix.ltab; a.probe_d2 = probe_d2; a.bits = bits;
   a.codes = ix.codes; a.ids = ix.ids; a.list_len = ix.list_len; a.vec_off = ix.vec_off;
@@ -463,9 +464,10 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
     default: e = run_packed<8>(a, s); break;
   }
   if (e != cudaSuccess) return e;
+  if (after_packed) cudaEventRecord(after_packed, s);
   merge_grouped_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(qm_d, qm_i, w.part_d, w.part_i, probes, bits,
                                                                 nprobe_per_q, k_per_q, nq, nprobe, k, ids_out,
-                                                                dists_out);
+                                                                dists_out); note_launch();
   return cudaGetLastError();
 }
 

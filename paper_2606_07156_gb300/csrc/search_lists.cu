@@ -276,7 +276,7 @@ cudaError_t run_lists(const LArgs& a, int nw, size_t smem, int sms, cudaStream_t
   auto kern = list_kernel<NCHUNK, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<sms, nw * 32, smem, s>>>(a);
+  kern<<<sms, nw * 32, smem, s>>>(a); note_launch();
   return cudaGetLastError();
 }
 
@@ -332,10 +332,11 @@ cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, in
   }
   if (e != cudaSuccess) return e;
   const unsigned gm = (unsigned)((nq + 7) / 8);
-  if (R == 1)
-    merge_kernel<1><<<gm, 256, 0, s>>>(w.part_d, w.part_i, probes, nprobe_per_q, k_per_q, nq, nprobe, k, ids_out, dists_out);
-  else
-    merge_kernel<4><<<gm, 256, 0, s>>>(w.part_d, w.part_i, probes, nprobe_per_q, k_per_q, nq, nprobe, k, ids_out, dists_out);
+  if (R == 1) {
+    merge_kernel<1><<<gm, 256, 0, s>>>(w.part_d, w.part_i, probes, nprobe_per_q, k_per_q, nq, nprobe, k, ids_out, dists_out); note_launch();
+  } else {
+    merge_kernel<4><<<gm, 256, 0, s>>>(w.part_d, w.part_i, probes, nprobe_per_q, k_per_q, nq, nprobe, k, ids_out, dists_out); note_launch();
+  }
   return cudaGetLastError();
 }
 

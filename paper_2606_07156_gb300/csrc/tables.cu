@@ -44,7 +44,7 @@ cudaError_t launch_query_tables(const Index& ix, const float* Q, int64_t nq, flo
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)sms * 16);
   query_table_kernel<<<(unsigned)grid, 256, 0, s>>>(Q, ix.codebooks, nq, (int)ix.dim, (int)ix.M,
-                                                    (int)ix.Mp, (int)ix.dsub, qt);
+                                                    (int)ix.Mp, (int)ix.dsub, qt); note_launch();
   return cudaGetLastError();
 }
 

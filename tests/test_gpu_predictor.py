@@ -96,7 +96,8 @@ def test_training_set_fewer_candidates_than_k(amp):
 
 # ------------------------------------------------------------------ inference
 
-@pytest.mark.parametrize("margin,wmap", [(0.0, False), (0.5, False), (2.0, False), (0.0, True), (1.0, True)])
+@pytest.mark.parametrize("margin,wmap", [(0.0, False), (0.5, False), (2.0, False), (-0.75, False), (0.0, True),
+                                         (1.0, True), (-0.5, True)])
 def test_mlp_policy_bit_exact(amp, pair, margin, wmap):
     d, g, o = pair
     Q = d["queries"]

@@ -164,3 +164,39 @@ def test_workload_geometries_bit_exact(amp, key, M, nlist, bits_set):
                 np.testing.assert_array_equal(dists.cpu().numpy(), rd, err_msg=f"{key} {bits} {kern}")
     finally:
         g.close()
+
+
+def test_stage_profile_and_launch_count(amp, pair_a):
+    """Stage timing splits the grouped search into its query-major pass, the
+    grouped kernel and the merge; the library's launch counter sees every
+    kernel of a search (5 query-major: CL distances, CL selection, precision
+    choice, query tables, search; 10 grouped: the same four, pair regrouping
+    (3), query-major pass, grouped kernel, merge)."""
+    d, g, o = pair_a
+    Q = cuda(d["queries"])
+    abi = amp.abi
+    cases = (("basic", "natural", amp.policy("plain"), 5, False),
+             ("grouped", "auto", amp.policy("fixed", bits=8), 10, True))
+    idle = {}
+    try:
+        for kern, sched, pol, n_launch, grouped in cases:
+            g.set_kernel(kern)
+            g.set_schedule(sched)
+            g.search(Q, 8, 10, pol)
+            torch.cuda.synchronize()
+            abi.anns_profile(g.handle, 1)
+            before = abi.anns_kernel_launches()
+            g.search(Q, 8, 10, pol)
+            g.search(Q, 8, 10, pol)
+            after = abi.anns_kernel_launches()
+            ms, cnt = abi.anns_profile(g.handle, 0)
+            assert cnt == 2
+            assert after - before == 2 * n_launch, (kern, after - before)
+            assert len(ms) == abi.PROFILE_STAGES and all(v >= 0.0 for v in ms)
+            assert ms[3] > 0.0
+            idle[grouped] = ms[4]
+        # stage 4 of the query-major search is two events recorded back to back
+        assert idle[True] > 2.0 * idle[False], idle
+    finally:
+        g.set_kernel("auto")
+        g.set_schedule("auto")

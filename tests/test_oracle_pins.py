@@ -311,6 +311,9 @@ def test_decide_bits_round_up_and_ties():
     z = np.array([[1, 3, 3, 0, 0], [5, 0, 0, 0, 0], [0, 0, 0, 2.0, 1.9]], dtype=np.float32)
     np.testing.assert_array_equal(predictor.decide_bits(z, 0.0), [6, 4, 12])
     np.testing.assert_array_equal(predictor.decide_bits(z, 0.5), [8, 4, 16])
+    # a negative tau rounds down: a width within -tau of the wider ones' best logit
+    np.testing.assert_array_equal(predictor.decide_bits(z, -1.5), [6, 4, 12])
+    np.testing.assert_array_equal(predictor.decide_bits(z, -2.0), [4, 4, 4])
     np.testing.assert_array_equal(predictor.gpu_width(predictor.decide_bits(z, 0.0)), [8, 4, 0])
     np.testing.assert_array_equal(predictor.gpu_width([4, 6, 8, 12, 16, 0]), [4, 8, 8, 0, 0, 0])
 
@@ -326,7 +329,7 @@ def test_decide_bits_against_brute_force():
     am = np.argmax(z, axis=1)
     np.testing.assert_array_equal(predictor.decide_bits(z, 0.0), np.asarray(predictor.BITS)[am])
     prev = None
-    for tau in (0.0, 0.25, 0.5, 1.0, 3.0, np.inf):
+    for tau in (-np.inf, -3.0, -1.0, -0.25, 0.0, 0.25, 0.5, 1.0, 3.0, np.inf):
         got = predictor.decide_bits(z, tau)
         want = []
         for row in z:
