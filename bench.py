@@ -219,7 +219,8 @@ def calibrate_margin(amp, Qc, gt_c, nprobe: int, k: int, run, budget: float = LO
     below 0 favour the narrower width; the grid ends at 16 (nearly all wide)."""
     base = 100.0 * recall(run(Qc, nprobe, amp.policy("plain")), gt_c, 10)
     tried = {}
-    for m in (-2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.1, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 8.0, 16.0):
+    for m in (-8.0, -6.0, -4.0, -3.0, -2.0, -1.5, -1.0, -0.75, -0.5, -0.25, 0.0, 0.1, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0,
+              3.0, 4.0, 8.0, 16.0):
         loss = base - 100.0 * recall(run(Qc, nprobe, amp.policy("mlp", margin=m, width_map=True)), gt_c, 10)
         tried[m] = round(loss, 3)
         if loss <= budget:
@@ -422,7 +423,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "metric": METRIC, "value": round(qps["mlp"], 1), "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(totals["mlp"] * 1e3 / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/u16-lut,i32-acc|f32",
-        "data": "synthetic (seeded SIFT-shaped gamma mixture; no public dataset)",
+        "data": f"synthetic (seeded {cfg['name']} mixture; no public dataset)",
         "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
                    "policy": f"learned MLP per (query, list) trained on GB300 table classes, round-up "

@@ -232,8 +232,15 @@ int64_t anns_kernel_launches(void);
  *    ANNS_SCHED_NATURAL: query order.
  *    ANNS_SCHED_LPT: longest first by the estimated cost sum over the probed
  *      lists of (list size + 768), bucketed within 12.5 %.
- * Every kernel and schedule returns identical results. Errors: INVALID_ARG. */
-enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1 };
+ *  ANNS_OPT_QCHUNK: queries per chunk of the grouped kernel's work order (its
+ *    groups run chunk by chunk, each chunk largest list first, so that one
+ *    chunk's query tables are in use at a time). 0 (default) = automatic:
+ *    chunks whose query tables take half of L2 (at least 256 queries) when
+ *    the list tables and codes fit in the other half, else one chunk.
+ *    Values >= 1 fix the chunk.
+ * Every kernel, schedule and chunk size returns identical results.
+ * Errors: INVALID_ARG. */
+enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1, ANNS_OPT_QCHUNK = 2 };
 enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2, ANNS_KERNEL_GROUPED = 3 };
 enum { ANNS_SCHED_AUTO = 0, ANNS_SCHED_NATURAL = 1, ANNS_SCHED_LPT = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);

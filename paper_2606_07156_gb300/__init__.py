@@ -20,9 +20,10 @@ _MODES = {"plain": abi.LUT_PLAIN_FP32, "fixed": abi.LUT_FIXED_BITS, "eq2": abi.L
 
 def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), margin: float = 0.0,
            pair_bits=None, width_map: bool = False, cl: str = "fp32") -> abi.anns_precision_policy:
-    """Builds an anns_precision_policy. ``pair_bits`` (EXPLICIT) is a uint8 CUDA tensor;
-    ``margin`` is the MLP round-up margin; ``width_map`` maps EQ2/MLP widths to this
-    GPU's tables (6 -> 8 bits, 12 and 16 -> FP32)."""
+    """Builds an anns_precision_policy. ``pair_bits`` (EXPLICIT) is a uint8 CUDA tensor
+    [nq * nprobe], kept alive by the returned policy (the struct holds its device
+    pointer); ``margin`` is the MLP round-up margin; ``width_map`` maps EQ2/MLP
+    widths to this GPU's tables (6 -> 8 bits, 12 and 16 -> FP32)."""
     p = abi.anns_precision_policy()
     p.lut_mode = _MODES[mode]
     p.fixed_bits = int(bits)
@@ -32,6 +33,7 @@ def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), 
         p.eq2_thresholds[i] = float(t)
     p.fallback_margin = float(margin)
     p.pair_bits = None if pair_bits is None else pair_bits.data_ptr()
+    p._pair_bits_ref = pair_bits  # the device memory the pointer refers to
     p.width_map = 1 if width_map else 0
     return p
 
@@ -163,6 +165,10 @@ class Index:
         abi.anns_locate(self.handle, _ptr(queries), nq, nprobe, _ptr(nprobe_per_q),
                         {"fp32": abi.PREC_FP32, "bf16": abi.PREC_BF16}[cl], _ptr(probes), _ptr(pd), s)
         return probes, pd
+
+    def set_qchunk(self, queries: int):
+        """Queries per chunk of the grouped kernel's work order (0 = automatic)."""
+        abi.anns_set_option(self.handle, abi.OPT_QCHUNK, int(queries))
 
     def set_schedule(self, which: str):
         """'auto', 'natural' or 'lpt' (longest query first) for the query-major kernel."""

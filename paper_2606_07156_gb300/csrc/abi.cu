@@ -120,8 +120,12 @@ int table_bytes_for(const anns_precision_policy& P) {
   }
 }
 
-int list_workspace(Index& ix, int64_t nq, int nprobe, int k, ListWork& w) {
-  const size_t L = (size_t)(ix.nlist + 1) * 4, P = (size_t)nq * nprobe;
+int list_workspace(Index& ix, int64_t nq, int nprobe, int k, ListWork& w, int64_t qchunk) {
+  w.qchunk = std::max<int64_t>(qchunk, 1);
+  const int64_t nchunks = std::max<int64_t>((nq + w.qchunk - 1) / w.qchunk, 1);
+  if (nchunks * ix.nlist > INT32_MAX / 2) return fail(ANNS_ERR_INVALID_ARG, "too many (query chunk, list) buckets");
+  w.nbuckets = (int)(nchunks * ix.nlist);
+  const size_t L = (size_t)(w.nbuckets + 1) * 4, P = (size_t)nq * nprobe;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t bytes = 4 * al(L) + al(P * 4) + al(P * k * 4) + al(P * k * 8);
   int rc = grow(&ix.ws_lists, &ix.ws_lists_cap, bytes);
@@ -252,7 +256,8 @@ int reserve_search(Index& ix, int64_t nq, int nprobe, int k, const anns_precisio
   if (rc) return rc;
   if (ix.opt_kernel == ANNS_KERNEL_LIST_MAJOR || use_grouped(ix, P, k)) {
     ListWork w{};
-    if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
+    const int64_t qchunk = ix.opt_kernel == ANNS_KERNEL_LIST_MAJOR ? nq : grouped_qchunk(ix, nq);
+    if ((rc = list_workspace(ix, nq, nprobe, k, w, qchunk))) return rc;
   }
   if (use_grouped(ix, P, k)) {
     if ((rc = grow(&ix.ws_grp, &ix.ws_grp_cap, grouped_workspace_bytes(nq, k)))) return rc;
@@ -299,13 +304,13 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
     if (list_major_warps(ix, tbytes) < 1)
       return fail(ANNS_ERR_UNSUPPORTED, "list-major kernel: one table does not fit in shared memory");
     ListWork w{};
-    if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
+    if ((rc = list_workspace(ix, nq, nprobe, k, w, nq))) return rc;
     if (ev) cudaEventRecord(ev[3], s);
     e = launch_search_lists(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
                             ix.ws_bits, tbytes, w, ids_out, dists_out, s);
   } else if (use_grouped(ix, P, k)) {
     ListWork w{};
-    if ((rc = list_workspace(ix, nq, nprobe, k, w))) return rc;
+    if ((rc = list_workspace(ix, nq, nprobe, k, w, grouped_qchunk(ix, nq)))) return rc;
     if (ev) cudaEventRecord(ev[3], s);
     e = launch_search_grouped(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
                               ix.ws_bits, w, ix.ws_grp, ids_out, dists_out, s, ev ? ev[4] : nullptr,
@@ -487,6 +492,10 @@ extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
     case ANNS_OPT_SCHEDULE:
       if (value < ANNS_SCHED_AUTO || value > ANNS_SCHED_LPT) return fail(ANNS_ERR_INVALID_ARG, "unknown schedule");
       ix->opt_schedule = (int)value;
+      return ANNS_OK;
+    case ANNS_OPT_QCHUNK:
+      if (value < 0) return fail(ANNS_ERR_INVALID_ARG, "query chunk must be >= 0");
+      ix->opt_qchunk = value;
       return ANNS_OK;
     default: return fail(ANNS_ERR_INVALID_ARG, "unknown option");
   }

@@ -77,6 +77,7 @@ struct Index {
   int64_t ws_tc_nq = 0;          // ... for this many queries
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   int opt_schedule = 0;          // ANNS_SCHED_*
+  int64_t opt_qchunk = 0;        // grouped kernel: queries per chunk (0 = automatic)
   // staging for anns_search_host
   void* st_q = nullptr; size_t st_q_cap = 0;
   void* st_out = nullptr; size_t st_out_cap = 0;
@@ -149,15 +150,19 @@ void free_workspace(Index& ix);
 
 // List-major search (search_lists.cu): work regrouped by list (invert.cu),
 // one warp per (query, list) pair, then a per-query merge.
+// Buckets are (query chunk, list) pairs, key c * nlist + l with c = q / qchunk
+// (one chunk unless the grouped kernel asks for more).
 struct ListWork {
-  int* cnt; int* off; int* ioff; int* fill;  // [nlist + 1] each
+  int* cnt; int* off; int* ioff; int* fill;  // [nbuckets + 1] each
   int32_t* pairs;                           // [nq * nprobe]
   float* part_d; int64_t* part_i;           // [nq * nprobe * k]
   int* counter;
+  int64_t qchunk;                           // queries per chunk
+  int nbuckets;                             // chunks * nlist
 };
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
-                          int nprobe, int batch, int* cnt, int* off, int* ioff, int* fill,
-                          int32_t* pairs, cudaStream_t s, const uint8_t* narrow_bits = nullptr);
+                          int nprobe, int batch, const ListWork& w, cudaStream_t s,
+                          const uint8_t* narrow_bits = nullptr);
 // Warps per block the list-major kernel gets for tables of `table_bytes_per_entry`.
 int list_major_warps(const Index& ix, int table_bytes_per_entry);
 cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, int nprobe,
@@ -169,6 +174,9 @@ cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, in
 // queries to a shared-memory word per list, the wide pairs query-major, then a
 // per-query merge. k <= 32.
 bool grouped_supported(const Index& ix, int k);
+// Queries per chunk of the grouped kernel's work order: chunks whose query
+// tables fit in L2 beside the list tables and codes, when those fit; else nq.
+int64_t grouped_qchunk(const Index& ix, int64_t nq);
 size_t grouped_workspace_bytes(int64_t nq, int k);
 cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, int nprobe,
                                   const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,

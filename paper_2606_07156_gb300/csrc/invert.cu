@@ -5,13 +5,19 @@
 // longest-processing-time order, the analogue of the load scheduling of
 // Section 4.3), through the index's size ranking.
 //
-//   count:   cnt[l]  = number of valid pairs probing list l (with narrow_bits:
+// The grouped kernel can split the queries into chunks of qchunk: a bucket is
+// then a (chunk c, list l) pair, key c * nlist + l, and the items run chunk by
+// chunk, so that only one chunk's query tables are in use at a time.
+//
+//   count:   cnt[key] = number of valid pairs of the bucket (with narrow_bits:
 //            only the pairs the grouped kernel packs: 1..8-bit tables, rank >= 1)
-//   offsets: off[l]  = exclusive prefix of cnt over lists;
-//            ioff[r] = exclusive prefix of ceil(cnt[order[r]] / batch) over
-//                      size ranks r (ioff[nlist] = number of items)
-//   scatter: pairs[off[l] + i] = q * nprobe + j for the pairs of list l (the
-//            order within a list is unspecified; results do not depend on it)
+//   offsets: off[key] = exclusive prefix of cnt over keys;
+//            ioff[c * nlist + r] = exclusive prefix of
+//                      ceil(cnt[c * nlist + order[r]] / batch) over chunks and
+//                      size ranks r (ioff[nbuckets] = number of items)
+//   scatter: pairs[off[key] + i] = q * nprobe + j for the pairs of the bucket
+//            (the order within a bucket is unspecified; results do not depend
+//            on it)
 #include <algorithm>
 
 #include "common.cuh"
@@ -35,17 +41,22 @@ __device__ __forceinline__ bool pair_selected(const int32_t* probes, const int32
   return j >= 1 && b >= 1 && b <= 8;
 }
 
-__global__ void count_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
-                             const uint8_t* __restrict__ bits, int64_t nq, int nprobe, int* __restrict__ cnt) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nq * nprobe) return;
-  if (pair_selected(probes, npq, bits, i, nprobe)) atomicAdd(cnt + probes[i], 1);
+__device__ __forceinline__ int bucket_of(const int32_t* probes, int64_t i, int nprobe, int64_t qchunk, int nlist) {
+  return (int)((i / nprobe) / qchunk) * nlist + probes[i];
 }
 
-// One block: exclusive scans over lists (pair offsets) and over size ranks
-// (item offsets). Also resets the scatter cursors.
+__global__ void count_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
+                             const uint8_t* __restrict__ bits, int64_t nq, int nprobe, int64_t qchunk, int nlist,
+                             int* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * nprobe) return;
+  if (pair_selected(probes, npq, bits, i, nprobe)) atomicAdd(cnt + bucket_of(probes, i, nprobe, qchunk, nlist), 1);
+}
+
+// One block: exclusive scans over bucket keys (pair offsets) and over
+// (chunk, size rank) (item offsets). Also resets the scatter cursors.
 __global__ void __launch_bounds__(1024) offsets_kernel(const int* __restrict__ cnt,
-                                                       const int32_t* __restrict__ order, int nlist,
+                                                       const int32_t* __restrict__ order, int nlist, int nb,
                                                        int batch, int* __restrict__ off,
                                                        int* __restrict__ ioff, int* __restrict__ fill) {
   __shared__ int part[32];
@@ -53,10 +64,10 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int* __restrict__ c
   if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < nlist; base += blockDim.x) {
+  for (int base = 0; base < nb; base += blockDim.x) {
     const int l = base + threadIdx.x;
-    const int v0 = l < nlist ? cnt[l] : 0;
-    const int v1 = l < nlist ? (cnt[order[l]] + batch - 1) / batch : 0;
+    const int v0 = l < nb ? cnt[l] : 0;
+    const int v1 = l < nb ? (cnt[(l / nlist) * nlist + order[l % nlist]] + batch - 1) / batch : 0;
     for (int which = 0; which < 2; ++which) {
       const int v = which ? v1 : v0;
       int x = v;
@@ -78,7 +89,7 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int* __restrict__ c
       }
       __syncthreads();
       const int excl = carry[which] + (warp ? part[warp - 1] : 0) + x - v;
-      if (l < nlist) {
+      if (l < nb) {
         if (which) ioff[l] = excl;
         else { off[l] = excl; fill[l] = 0; }
       }
@@ -87,31 +98,32 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int* __restrict__ c
       __syncthreads();
     }
   }
-  if (threadIdx.x == 0) { off[nlist] = carry[0]; ioff[nlist] = carry[1]; }
+  if (threadIdx.x == 0) { off[nb] = carry[0]; ioff[nb] = carry[1]; }
 }
 
 __global__ void scatter_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
-                               const uint8_t* __restrict__ bits, int64_t nq, int nprobe,
+                               const uint8_t* __restrict__ bits, int64_t nq, int nprobe, int64_t qchunk, int nlist,
                                const int* __restrict__ off, int* __restrict__ fill, int32_t* __restrict__ pairs) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq * nprobe) return;
   if (!pair_selected(probes, npq, bits, i, nprobe)) return;
-  const int l = probes[i];
-  pairs[off[l] + atomicAdd(fill + l, 1)] = (int32_t)i;
+  const int b = bucket_of(probes, i, nprobe, qchunk, nlist);
+  pairs[off[b] + atomicAdd(fill + b, 1)] = (int32_t)i;
 }
 
 }  // namespace
 
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
-                          int nprobe, int batch, int* cnt, int* off, int* ioff, int* fill,
-                          int32_t* pairs, cudaStream_t s, const uint8_t* narrow_bits) {
+                          int nprobe, int batch, const ListWork& w, cudaStream_t s, const uint8_t* narrow_bits) {
   const int64_t n = nq * nprobe;
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ix.nlist, s);
+  const int nlist = (int)ix.nlist;
+  cudaError_t e = cudaMemsetAsync(w.cnt, 0, sizeof(int) * w.nbuckets, s);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((n + 255) / 256);
-  count_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, cnt); note_launch();
-  offsets_kernel<<<1, 1024, 0, s>>>(cnt, ix.order, (int)ix.nlist, batch, off, ioff, fill); note_launch();
-  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, off, fill, pairs); note_launch();
+  count_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, w.qchunk, nlist, w.cnt); note_launch();
+  offsets_kernel<<<1, 1024, 0, s>>>(w.cnt, ix.order, nlist, w.nbuckets, batch, w.off, w.ioff, w.fill); note_launch();
+  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, w.qchunk, nlist, w.off, w.fill, w.pairs);
+  note_launch();
   return cudaGetLastError();
 }
 

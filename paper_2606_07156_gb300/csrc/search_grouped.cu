@@ -45,7 +45,7 @@ struct GArgs {
   const uint8_t* codes; const int64_t* ids;
   const int32_t* list_len; const int64_t* vec_off; const int64_t* tile_off;
   const int32_t* order; const int* cnt; const int* off; const int* ioff; const int32_t* pairs;
-  int nlist, M, Mp, nprobe, k;
+  int nlist, nb, M, Mp, nprobe, k;  // nb: (query chunk, list) buckets
   const int32_t* kpq;
   float* part_d; int64_t* part_i;
   const float* qm_d;  // [nq * k] query-major results (rank 0 and wide pairs): the bound
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
   const uint32_t tab_addr = raw + pad + (uint32_t)L.tab;
   const uint32_t lim_addr = raw + pad + (uint32_t)L.lim;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ngroups = a.ioff[a.nlist];
+  const int ngroups = a.ioff[a.nb];
   const size_t tstride = (size_t)Mp * kKsub;
   for (;;) {
     __syncthreads();  // the previous group is done with the shared tables
@@ -150,18 +150,19 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
     if (threadIdx.x == 0) {
       const int it = atomicAdd(a.counter, 1);
       item[0] = it;
-      if (it < ngroups) {  // size rank r: the last with ioff[r] <= it
-        int lo = 0, hi = a.nlist - 1;
+      if (it < ngroups) {  // (chunk, size rank) b: the last with ioff[b] <= it
+        int lo = 0, hi = a.nb - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
           if (a.ioff[mid] <= it) lo = mid; else hi = mid - 1;
         }
-        const int l = a.order[lo];
+        const int l = a.order[lo % a.nlist];
+        const int key = (lo / a.nlist) * a.nlist + l;
         const int i = it - a.ioff[lo];
-        const int ns = min(kSlots, a.cnt[l] - kSlots * i);
+        const int ns = min(kSlots, a.cnt[key] - kSlots * i);
         item[1] = l;
         item[2] = ns;
-        for (int s = 0; s < kSlots; ++s) item[4 + s] = s < ns ? a.pairs[a.off[l] + kSlots * i + s] : -1;
+        for (int s = 0; s < kSlots; ++s) item[4 + s] = s < ns ? a.pairs[a.off[key] + kSlots * i + s] : -1;
       }
     }
     __syncthreads();
@@ -429,14 +430,26 @@ bool grouped_supported(const Index& ix, int k) {
 
 size_t grouped_workspace_bytes(int64_t nq, int k) { return (size_t)nq * k * 12 + 256; }
 
+int64_t grouped_qchunk(const Index& ix, int64_t nq) {
+  if (ix.opt_qchunk > 0) return std::min<int64_t>(ix.opt_qchunk, std::max<int64_t>(nq, 1));
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  const int64_t qt_bytes = ix.Mp * kKsub * 4;  // one query's tables
+  const int64_t shared = ix.nlist * qt_bytes + ix.ntiles * ix.nchunk * kTileChunkBytes;  // list tables + codes
+  if (nq <= 0 || l2 <= 0 || shared > l2 / 2) return std::max<int64_t>(nq, 1);
+  // half of L2 for the current chunk's query tables (measured on the SIFT-shaped
+  // workload: a quarter and an eighth are slower)
+  return std::min<int64_t>(nq, std::max<int64_t>(256, (l2 / 2) / qt_bytes));
+}
+
 cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, int nprobe,
                                   const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                                   const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
                                   cudaStream_t s, cudaEvent_t after_qm, cudaEvent_t after_packed) {
   // narrow pairs regrouped by list, groups of four, largest lists first
-  cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kSlots, w.cnt, w.off, w.ioff, w.fill,
-                                w.pairs, s, bits);
+  cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kSlots, w, s, bits);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -451,7 +464,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
   a.qt = qt; a.ltab = ix.ltab; a.probe_d2 = probe_d2; a.bits = bits;
   a.codes = ix.codes; a.ids = ix.ids; a.list_len = ix.list_len; a.vec_off = ix.vec_off;
   a.tile_off = ix.tile_off; a.order = ix.order; a.cnt = w.cnt; a.off = w.off; a.ioff = w.ioff;
-  a.pairs = w.pairs; a.nlist = (int)ix.nlist; a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.nprobe = nprobe; a.k = k;
+  a.pairs = w.pairs; a.nlist = (int)ix.nlist; a.nb = w.nbuckets; a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.nprobe = nprobe; a.k = k;
   a.kpq = k_per_q; a.part_d = w.part_d; a.part_i = w.part_i; a.counter = w.counter; a.qm_d = qm_d;
   switch (ix.nchunk) {
     case 1: e = run_packed<1>(a, s); break;

@@ -303,8 +303,7 @@ cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, in
                                 float* dists_out, cudaStream_t s) {
   const int nw = list_major_warps(ix, table_bytes_per_entry);
   if (nw < 1) return cudaErrorInvalidValue;
-  cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, nw, w.cnt, w.off, w.ioff,
-                                w.fill, w.pairs, s);
+  cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, nw, w, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;

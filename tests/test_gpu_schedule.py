@@ -200,3 +200,42 @@ def test_stage_profile_and_launch_count(amp, pair_a):
     finally:
         g.set_kernel("auto")
         g.set_schedule("auto")
+
+
+@pytest.mark.parametrize("qchunk", [1, 7, 64, 0])
+def test_grouped_query_chunks_bit_exact(amp, pair_a, qchunk):
+    """The grouped kernel's work order by (query chunk, list): chunks of one
+    query, a ragged chunk size, a chunk larger than the batch and the automatic
+    choice all return the oracle's results, with uneven nprobe and k and a
+    mix of 8-bit, 6-bit and wide tables."""
+    d, g, o = pair_a
+    Q = d["queries"]
+    nq, nprobe = len(Q), 10
+    npq, kpq = _uneven(nq, 11, nprobe, (1, 10, 32))
+    r = np.random.Generator(np.random.PCG64(13))
+    bits = r.choice(np.array([8, 8, 8, 6, 4, 0, 16], np.uint8), size=(nq, nprobe))
+    g.set_kernel("grouped")
+    g.set_qchunk(qchunk)
+    try:
+        pol = amp.policy("explicit", pair_bits=cuda(bits))
+        ids, dists = g.search(cuda(Q), nprobe, 32, pol, nprobe_per_q=cuda(npq), k_per_q=cuda(kpq))
+        ri, rd = ivfpq.search(o, Q, nprobe, 32, bits=bits, nprobe_per_q=npq, k_per_q=kpq)
+        np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+        np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+        graph, gi, gd = g.capture_graph(cuda(Q), nprobe, 32, pol, nprobe_per_q=cuda(npq), k_per_q=cuda(kpq))
+        try:
+            gi.fill_(-3)
+            graph.launch()
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(gi.cpu().numpy(), ri)
+        finally:
+            graph.close()
+    finally:
+        g.set_kernel("auto")
+        g.set_qchunk(0)
+
+
+def test_qchunk_option_errors(amp, pair_a):
+    d, g, o = pair_a
+    with pytest.raises(amp.abi.AnnsError):
+        amp.abi.anns_set_option(g.handle, amp.abi.OPT_QCHUNK, -1)

@@ -93,7 +93,14 @@ class _Mixture:
             return np.clip(np.rint(x), 0, 255)
         if self.key == "C":
             z = r.standard_normal((n, d)) * (self.sig[lab, None] * self.decay[None, :])
-            x = self.mu[lab] + np.einsum("nij,nj->ni", self.rot[lab], z)
+            x = np.empty((n, d))
+            # x = mu_c + R_c z, one matrix product per component present
+            order = np.argsort(lab, kind="stable")
+            cut = np.flatnonzero(np.diff(lab[order])) + 1
+            for idx in np.split(order, cut):
+                if idx.size:
+                    c = lab[idx[0]]
+                    x[idx] = self.mu[c] + z[idx] @ self.rot[c].T
             return x / np.linalg.norm(x, axis=1, keepdims=True)
         if self.key == "D":
             return r.exponential(1.0 / self.lam[lab])
