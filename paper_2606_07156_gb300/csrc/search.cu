@@ -35,7 +35,7 @@ struct PairScal {
 // memory (256 bytes of slack are allocated for the alignment): the FP32 table
 // T, the level table q (1 or 2 bytes an entry), row statistics and scales.
 struct SmemLayout {
-  size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, d2 = 0, md = 0, mi = 0, total = 0;
+  size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, d2 = 0, plist = 0, md = 0, mi = 0, total = 0;
   static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   SmemLayout() = default;
   SmemLayout(int64_t Mp, int R) {
@@ -46,6 +46,7 @@ struct SmemLayout {
     rowmax = o; o += al(Mp * 4);
     scal = o; o += al(sizeof(PairScal));
     d2 = o; o += 16;
+    plist = o; o += al((size_t)ANNS_MAX_NPROBE * 16 + 16);  // + the count
     md = o; o += al((size_t)kWarps * R * 32 * 4);
     mi = o; o += al((size_t)kWarps * R * 32 * 8);
     total = o + 256;
@@ -59,11 +60,13 @@ __device__ __forceinline__ unsigned char* aligned_smem() {
 
 struct Smem {
   float* T; void* q; float* bias; float* rowmax; PairScal* sc; float* d2; float* md; int64_t* mi;
+  int4* plist; int* npairs;  // query-major kernel: the block's pairs (list, n_l, bits, D2 bits) and their count
   uint32_t T_addr, q_addr;  // shared-memory byte addresses of the two tables
   __device__ explicit Smem(const SmemLayout& L) {
     unsigned char* b = aligned_smem();
     T = (float*)(b + L.T); q = b + L.q; bias = (float*)(b + L.bias); rowmax = (float*)(b + L.rowmax);
     sc = (PairScal*)(b + L.scal); d2 = (float*)(b + L.d2); md = (float*)(b + L.md); mi = (int64_t*)(b + L.mi);
+    plist = (int4*)(b + L.plist); npairs = (int*)(b + L.plist + (size_t)ANNS_MAX_NPROBE * 16);
     T_addr = smem_addr(T);
     q_addr = smem_addr(q);
   }
@@ -333,14 +336,37 @@ __global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? 4 : 1) search_kernel(c
     top.init();
     float thd = INFINITY;
     int64_t thi = INT64_MAX;
-    for (int j = 0; kq > 0 && j < np; ++j) {
-      const int l = a.probes[q * a.nprobe + j];
-      if (l < 0) continue;
-      const int n_l = a.list_len[l];
-      if (n_l == 0) continue;
-      const int b = a.bits[q * a.nprobe + j];
-      if (a.skip_narrow && j >= 1 && b >= 1 && b <= 8) continue;
-      const float d2 = a.probe_d2[q * a.nprobe + j];
+    // the probe ranks this block scans, found by warp 0 in one parallel pass
+    // (lane i reads rank 32 r + i) and kept in shared memory: the pairs'
+    // metadata costs one round of loads per query instead of a dependent chain
+    // of loads per rank
+    if (warp == 0) {
+      int base = 0;
+      for (int j0 = 0; j0 < np && kq > 0; j0 += 32) {
+        const int j = j0 + lane;
+        int l = -1, n_l = 0, b = 0;
+        float d2 = 0.f;
+        if (j < np) {
+          const int64_t i = q * a.nprobe + j;
+          l = a.probes[i];
+          b = a.bits[i];
+          d2 = a.probe_d2[i];
+          if (l >= 0) n_l = a.list_len[l];
+        }
+        const bool use = l >= 0 && n_l > 0 && !(a.skip_narrow && j >= 1 && b >= 1 && b <= 8);
+        const unsigned m = __ballot_sync(kFull, use);
+        if (use) s.plist[base + __popc(m & ((1u << lane) - 1u))] = make_int4(l, n_l, b, __float_as_int(d2));
+        base += __popc(m);
+      }
+      if (lane == 0) *s.npairs = base;
+    }
+    __syncthreads();
+    const int npairs = *s.npairs;
+    for (int e = 0; e < npairs; ++e) {
+      const int4 pe = s.plist[e];
+      const int l = pe.x, n_l = pe.y, b = pe.z;
+      const float d2 = __int_as_float(pe.w);
+      const int64_t tile0 = a.tile_off[l], vec0 = a.vec_off[l];  // requested before the table build
       if constexpr (NCHUNK <= 2) {
         build_lut_regs<NCHUNK * 16 / kWarps>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, b, d2,
                                              s.T, s.q, s.bias, s.rowmax, s.sc);
@@ -350,9 +376,9 @@ __global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? 4 : 1) search_kernel(c
       }
       const PairScal sc = *s.sc;
       const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
-      const uint8_t* tp = a.codes + ((size_t)a.tile_off[l] * NCHUNK + 0) * kTileChunkBytes +
+      const uint8_t* tp = a.codes + ((size_t)tile0 * NCHUNK + 0) * kTileChunkBytes +
                           (size_t)warp * NCHUNK * kTileChunkBytes;
-      const int64_t* idp = a.ids + a.vec_off[l];
+      const int64_t* idp = a.ids + vec0;
       for (int t = warp; t < ntile; t += kWarps, tp += (size_t)kWarps * NCHUNK * kTileChunkBytes) {
         uint4 w[NCHUNK];
         load_tile<NCHUNK>(tp, lane, w);
