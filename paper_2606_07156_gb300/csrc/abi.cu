@@ -127,7 +127,8 @@ int list_workspace(Index& ix, int64_t nq, int nprobe, int k, ListWork& w, int64_
   w.nbuckets = (int)(nchunks * ix.nlist);
   const size_t L = (size_t)(w.nbuckets + 1) * 4, P = (size_t)nq * nprobe;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t bytes = 4 * al(L) + al(P * 4) + al(P * k * 4) + al(P * k * 8);
+  const size_t G = (P + (size_t)w.nbuckets + 1) * 4;  // groups: at most one per pair plus one per bucket
+  const size_t bytes = 4 * al(L) + al(P * 4) + al(P * k * 4) + al(P * k * 8) + al(G);
   int rc = grow(&ix.ws_lists, &ix.ws_lists_cap, bytes);
   if (rc) return rc;
   char* b = (char*)ix.ws_lists;
@@ -137,7 +138,8 @@ int list_workspace(Index& ix, int64_t nq, int nprobe, int k, ListWork& w, int64_
   w.fill = (int*)b; b += al(L);
   w.pairs = (int32_t*)b; b += al(P * 4);
   w.part_d = (float*)b; b += al(P * k * 4);
-  w.part_i = (int64_t*)b;
+  w.part_i = (int64_t*)b; b += al(P * k * 8);
+  w.gtab = (int*)b;
   w.counter = ix.ws_counter;
   return ANNS_OK;
 }

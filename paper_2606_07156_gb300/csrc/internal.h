@@ -159,6 +159,7 @@ struct ListWork {
   int* counter;
   int64_t qchunk;                           // queries per chunk
   int nbuckets;                             // chunks * nlist
+  int* gtab;                                // grouped kernel: bucket of each group [<= pairs + nbuckets]
 };
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
                           int nprobe, int batch, const ListWork& w, cudaStream_t s,

@@ -18,6 +18,7 @@
 //   scatter: pairs[off[key] + i] = q * nprobe + j for the pairs of the bucket
 //            (the order within a bucket is unspecified; results do not depend
 //            on it)
+//   groups:  (grouped kernel) gtab[g] = the (chunk, size rank) index of group g
 #include <algorithm>
 
 #include "common.cuh"
@@ -111,6 +112,13 @@ __global__ void scatter_kernel(const int32_t* __restrict__ probes, const int32_t
   pairs[off[b] + atomicAdd(fill + b, 1)] = (int32_t)i;
 }
 
+// gtab[g] = the bucket index (chunk * nlist + size rank) of group g.
+__global__ void group_table_kernel(const int* __restrict__ ioff, int nb, int* __restrict__ gtab) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  for (int g = ioff[b]; g < ioff[b + 1]; ++g) gtab[g] = b;
+}
+
 }  // namespace
 
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
@@ -124,6 +132,10 @@ cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t*
   offsets_kernel<<<1, 1024, 0, s>>>(w.cnt, ix.order, nlist, w.nbuckets, batch, w.off, w.ioff, w.fill); note_launch();
   scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, w.qchunk, nlist, w.off, w.fill, w.pairs);
   note_launch();
+  if (narrow_bits) {  // the grouped kernel looks its groups up in a table
+    group_table_kernel<<<(unsigned)((w.nbuckets + 255) / 256), 256, 0, s>>>(w.ioff, w.nbuckets, w.gtab);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -16,7 +16,8 @@
 // sum and distance follows the same rules (search.cu).
 //
 // Per group (one block of 8 warps, persistent grid, groups taken from an
-// atomic counter in descending list size):
+// atomic counter by (query chunk, descending list size); the last warp fetches
+// the next group's item while the block scans the current one):
 //   1. row statistics: for each (slot, row) the warps form T' = P_l - 2 Q_q
 //      and its row minimum and range;
 //   2. per slot: the shared step, its reciprocal scale and the FP64 offset
@@ -45,6 +46,7 @@ struct GArgs {
   const uint8_t* codes; const int64_t* ids;
   const int32_t* list_len; const int64_t* vec_off; const int64_t* tile_off;
   const int32_t* order; const int* cnt; const int* off; const int* ioff; const int32_t* pairs;
+  const int* gtab;  // bucket of each group
   int nlist, nb, M, Mp, nprobe, k;  // nb: (query chunk, list) buckets
   const int32_t* kpq;
   float* part_d; int64_t* part_i;
@@ -56,6 +58,16 @@ struct GArgs {
 // the query-major pairs, the slot's k and its pair.
 struct SlotScal { float s32, delta32, B32, bound; int kq, pid, pad0, pad1; };
 
+// One group's work item: its list, number of pairs and per slot the pair, its
+// query, table width, D2, k and bound (the query's k-th distance over its
+// query-major pairs). Fetched by one warp while the block scans the previous
+// group, so that the block never waits on this chain of dependent loads.
+struct GItem {
+  int it, l, ns, pad;
+  int pid[4], q[4], bits[4], kq[4];
+  float d2[4], bound[4];
+};
+
 // Bytes of the block's shared memory (256-aligned offsets).
 struct GLayout {
   size_t tab, bias, rowmax, scal, item, lim, md, mi, total;
@@ -66,7 +78,7 @@ struct GLayout {
     bias = o; o += al((size_t)kSlots * Mp * 4);
     rowmax = o; o += al((size_t)kSlots * Mp * 4);
     scal = o; o += al(sizeof(SlotScal) * kSlots);
-    item = o; o += al(16 * 4);
+    item = o; o += al(2 * sizeof(GItem));  // double buffer
     lim = o; o += al(2 * 4);
     md = o; o += al((size_t)kSlots * kGWarps * 32 * 4);
     mi = o; o += al((size_t)kSlots * kGWarps * 32 * 8);
@@ -124,6 +136,37 @@ __device__ __forceinline__ void lim_min(uint32_t* lim, int s, uint32_t v) {
   }
 }
 
+// The next group from the work queue (whole warp; lanes 0..3 take the slots).
+__device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItem* out, int lane) {
+  int it = 0;
+  if (lane == 0) it = atomicAdd(a.counter, 1);
+  it = __shfl_sync(kFull, it, 0);
+  if (it >= ngroups) {
+    if (lane == 0) out->it = it;
+    return;
+  }
+  const int b = a.gtab[it];
+  const int l = a.order[b % a.nlist];
+  const int key = (b / a.nlist) * a.nlist + l;
+  const int i = it - a.ioff[b];
+  const int ns = min(kSlots, a.cnt[key] - kSlots * i);
+  if (lane < kSlots) {
+    const int p = lane < ns ? a.pairs[a.off[key] + kSlots * i + lane] : -1;
+    int qs = 0, bs = 8, kq = 0;
+    float d2 = 0.f, bound = INFINITY;
+    if (p >= 0) {
+      qs = p / a.nprobe;
+      bs = a.bits[p];
+      d2 = a.probe_d2[p];
+      kq = a.kpq ? min(max(a.kpq[qs], 0), a.k) : a.k;
+      if (kq > 0) bound = a.qm_d[(size_t)qs * a.k + kq - 1];
+    }
+    out->pid[lane] = p; out->q[lane] = qs; out->bits[lane] = bs; out->kq[lane] = kq;
+    out->d2[lane] = d2; out->bound[lane] = bound;
+  }
+  if (lane == 0) { out->it = it; out->l = l; out->ns = ns; }
+}
+
 template <int NCHUNK>
 __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 : 1)) packed_kernel(const GArgs a) {
   constexpr int Mp = NCHUNK * 16;
@@ -135,7 +178,7 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
   float* bias = (float*)(base + L.bias);
   float* rowmax = (float*)(base + L.rowmax);
   SlotScal* scal = (SlotScal*)(base + L.scal);
-  int* item = (int*)(base + L.item);
+  GItem* items = (GItem*)(base + L.item);
   uint32_t* lim = (uint32_t*)(base + L.lim);  // 0x8000 + Smax per slot, 16-bit lanes (see the scan)
   float* md = (float*)(base + L.md);
   int64_t* mi = (int64_t*)(base + L.mi);
@@ -144,33 +187,17 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngroups = a.ioff[a.nb];
   const size_t tstride = (size_t)Mp * kKsub;
+  int cur = 0;
+  if (warp == kGWarps - 1) fetch_group(a, ngroups, items, lane);
   for (;;) {
-    __syncthreads();  // the previous group is done with the shared tables
+    __syncthreads();  // the previous group is done with the shared tables; items[cur] is complete
     if (threadIdx.x < 2) lim[threadIdx.x] = 0xFFFFFFFFu;  // every sum passes until the seeds
-    if (threadIdx.x == 0) {
-      const int it = atomicAdd(a.counter, 1);
-      item[0] = it;
-      if (it < ngroups) {  // (chunk, size rank) b: the last with ioff[b] <= it
-        int lo = 0, hi = a.nb - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.ioff[mid] <= it) lo = mid; else hi = mid - 1;
-        }
-        const int l = a.order[lo % a.nlist];
-        const int key = (lo / a.nlist) * a.nlist + l;
-        const int i = it - a.ioff[lo];
-        const int ns = min(kSlots, a.cnt[key] - kSlots * i);
-        item[1] = l;
-        item[2] = ns;
-        for (int s = 0; s < kSlots; ++s) item[4 + s] = s < ns ? a.pairs[a.off[key] + kSlots * i + s] : -1;
-      }
-    }
-    __syncthreads();
-    if (item[0] >= ngroups) break;
-    const int l = item[1], ns = item[2];
+    const GItem& G = items[cur];
+    if (G.it >= ngroups) break;
+    const int l = G.l, ns = G.ns;
     int q[kSlots];
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) q[s] = item[4 + s] >= 0 ? item[4 + s] / a.nprobe : 0;
+    for (int s = 0; s < kSlots; ++s) q[s] = G.q[s];
     const float* P = a.ltab + (size_t)l * tstride;
     // 1. row statistics: warp w takes rows m = w, w + 8, ...; the list-table
     //    row is loaded once for the group's slots, the query-table rows two
@@ -217,25 +244,23 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
       const int s = warp;
       float range = 0.f;
       double B = 0.0;
-      const int p = item[4 + s];
-      const int qs = p >= 0 ? p / a.nprobe : 0, bs = p >= 0 ? a.bits[p] : 8;
-      float d2 = 0.f;
+      const int p = G.pid[s], bs = G.bits[s];
       if (s < ns) {
         for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
         range = warp_max(range);
         for (int m = lane; m < a.M; m += 32) B = __dadd_rn(B, (double)bias[s * Mp + m]);
 #pragma unroll
         for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
-        d2 = a.probe_d2[p];
       }
+      const float d2 = G.d2[s];
       if (lane == 0) {
         const int Lv = (1 << bs) - 1;
         SlotScal sc;
         sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
         sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
         sc.B32 = __double2float_rn(__dadd_rn((double)d2, B));
-        sc.kq = s < ns ? (a.kpq ? min(max(a.kpq[qs], 0), a.k) : a.k) : 0;
-        sc.bound = sc.kq > 0 ? a.qm_d[(size_t)qs * a.k + sc.kq - 1] : INFINITY;
+        sc.kq = s < ns ? G.kq[s] : 0;
+        sc.bound = sc.kq > 0 ? G.bound[s] : INFINITY;
         sc.pid = p;
         sc.pad0 = sc.pad1 = 0;
         scal[s] = sc;
@@ -294,6 +319,8 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
     const size_t tile_bytes = (size_t)NCHUNK * kTileChunkBytes;
     const uint8_t* tp = a.codes + (size_t)a.tile_off[l] * tile_bytes + (size_t)warp * tile_bytes + lane * kChunkBytes;
     const int64_t* idp = a.ids + a.vec_off[l];
+    // the next group's item, fetched while the block scans this one
+    if (warp == kGWarps - 1) fetch_group(a, ngroups, items + (cur ^ 1), lane);
     uint4 w[NCHUNK];
     if (warp < ntile) load_codes<NCHUNK>(tp, w);
     for (int t = warp; t < ntile; t += kGWarps) {
@@ -361,6 +388,7 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
         a.part_i[(size_t)sc.pid * a.k + lane] = ok ? m.id[0] : -1;
       }
     }
+    cur ^= 1;
   }
 }
 
@@ -464,7 +492,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
   a.qt = qt; a.ltab = ix.ltab; a.probe_d2 = probe_d2; a.bits = bits;
   a.codes = ix.codes; a.ids = ix.ids; a.list_len = ix.list_len; a.vec_off = ix.vec_off;
   a.tile_off = ix.tile_off; a.order = ix.order; a.cnt = w.cnt; a.off = w.off; a.ioff = w.ioff;
-  a.pairs = w.pairs; a.nlist = (int)ix.nlist; a.nb = w.nbuckets; a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.nprobe = nprobe; a.k = k;
+  a.pairs = w.pairs; a.gtab = w.gtab; a.nlist = (int)ix.nlist; a.nb = w.nbuckets; a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.nprobe = nprobe; a.k = k;
   a.kpq = k_per_q; a.part_d = w.part_d; a.part_i = w.part_i; a.counter = w.counter; a.qm_d = qm_d;
   switch (ix.nchunk) {
     case 1: e = run_packed<1>(a, s); break;

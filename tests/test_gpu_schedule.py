@@ -170,13 +170,14 @@ def test_stage_profile_and_launch_count(amp, pair_a):
     """Stage timing splits the grouped search into its query-major pass, the
     grouped kernel and the merge; the library's launch counter sees every
     kernel of a search (5 query-major: CL distances, CL selection, precision
-    choice, query tables, search; 10 grouped: the same four, pair regrouping
-    (3), query-major pass, grouped kernel, merge)."""
+    choice, query tables, search; 11 grouped: the same four, pair regrouping
+    (count, offsets, scatter, group table), query-major pass, grouped kernel,
+    merge)."""
     d, g, o = pair_a
     Q = cuda(d["queries"])
     abi = amp.abi
     cases = (("basic", "natural", amp.policy("plain"), 5, False),
-             ("grouped", "auto", amp.policy("fixed", bits=8), 10, True))
+             ("grouped", "auto", amp.policy("fixed", bits=8), 11, True))
     idle = {}
     try:
         for kern, sched, pol, n_launch, grouped in cases:
