@@ -63,9 +63,10 @@ struct SlotScal { float s32, delta32, B32, bound; int kq, pid, pad0, pad1; };
 // query-major pairs). Fetched by one warp while the block scans the previous
 // group, so that the block never waits on this chain of dependent loads.
 struct GItem {
-  int it, l, ns, pad;
+  int it, l, ns, n_l;
   int pid[4], q[4], bits[4], kq[4];
   float d2[4], bound[4];
+  long long tile0, vec0;  // the list's first code tile and first id
 };
 
 // Bytes of the block's shared memory (256-aligned offsets).
@@ -111,13 +112,22 @@ __device__ __forceinline__ void load_codes(const uint8_t* __restrict__ tile, uin
 __device__ __forceinline__ uint32_t rint_bits_g(float y) { return __float_as_uint(add_rn(y, 12582912.0f)); }
 
 // Largest integer sum S in [0, 0x7FFF] whose distance fl32(fl32(delta * S) + B)
-// is <= x, or -1 when none is. The distance never falls as S rises (both
-// roundings are monotone), so d(S) <= x exactly when S <= smax_of(x).
-__device__ __noinline__ int smax_of(float x, float delta, float B) {
+// is <= x, or -1 when none is (whole warp, uniform arguments). The distance
+// never falls as S rises (both roundings are monotone), so d(S) <= x exactly
+// when S <= smax_warp(x). Each round tests 32 evenly spaced candidates of the
+// remaining interval [lo, hi] (d(lo) <= x); the passing ones form a prefix, so
+// their count places the answer in one gap: three rounds for 2^15 values.
+__device__ __forceinline__ int smax_warp(float x, float delta, float B) {
+  const int lane = threadIdx.x & 31;
   int lo = -1, hi = 0x7FFF;
   while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (add_rn(mul_rn(delta, __int2float_rn(mid)), B) <= x) lo = mid; else hi = mid - 1;
+    const int step = (hi - lo + 31) >> 5;  // 32 * step >= hi - lo: the candidates reach hi
+    const int c = lo + (lane + 1) * step;
+    const bool ok = c <= hi && add_rn(mul_rn(delta, __int2float_rn(c)), B) <= x;
+    const int t = __popc(__ballot_sync(kFull, ok));
+    const int nhi = min(hi, lo + (t + 1) * step - 1);
+    lo = t > 0 ? lo + t * step : lo;
+    hi = nhi;
   }
   return lo;
 }
@@ -164,7 +174,11 @@ __device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItem* 
     out->pid[lane] = p; out->q[lane] = qs; out->bits[lane] = bs; out->kq[lane] = kq;
     out->d2[lane] = d2; out->bound[lane] = bound;
   }
-  if (lane == 0) { out->it = it; out->l = l; out->ns = ns; }
+  if (lane == 0) {
+    out->it = it; out->l = l; out->ns = ns; out->n_l = a.list_len[l];
+    out->tile0 = a.tile_off[l];
+    out->vec0 = a.vec_off[l];
+  }
 }
 
 template <int NCHUNK>
@@ -253,18 +267,19 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
         for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
       }
       const float d2 = G.d2[s];
+      // every lane forms the same values (range and B are warp-uniform)
+      const int Lv = (1 << bs) - 1;
+      SlotScal sc;
+      sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
+      sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
+      sc.B32 = __double2float_rn(__dadd_rn((double)d2, B));
+      sc.kq = s < ns ? G.kq[s] : 0;
+      sc.bound = sc.kq > 0 ? G.bound[s] : INFINITY;
+      sc.pid = p;
+      sc.pad0 = sc.pad1 = 0;
+      const int seed = sc.kq == 0 ? -1 : (sc.bound == INFINITY ? 0x7FFF : smax_warp(sc.bound, sc.delta32, sc.B32));
       if (lane == 0) {
-        const int Lv = (1 << bs) - 1;
-        SlotScal sc;
-        sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
-        sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
-        sc.B32 = __double2float_rn(__dadd_rn((double)d2, B));
-        sc.kq = s < ns ? G.kq[s] : 0;
-        sc.bound = sc.kq > 0 ? G.bound[s] : INFINITY;
-        sc.pid = p;
-        sc.pad0 = sc.pad1 = 0;
         scal[s] = sc;
-        const int seed = sc.kq == 0 ? -1 : (sc.bound == INFINITY ? 0x7FFF : smax_of(sc.bound, sc.delta32, sc.B32));
         lim_min(lim, s, (uint32_t)(0x8000 + seed));
       }
     }
@@ -314,11 +329,11 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
     //    borrows nothing and keeps bit 15 set exactly when S <= Smax. The
     //    warps' lists live in shared memory (md, mi) and are touched only for
     //    the vectors that pass.
-    const int n_l = a.list_len[l];
+    const int n_l = G.n_l;
     const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
     const size_t tile_bytes = (size_t)NCHUNK * kTileChunkBytes;
-    const uint8_t* tp = a.codes + (size_t)a.tile_off[l] * tile_bytes + (size_t)warp * tile_bytes + lane * kChunkBytes;
-    const int64_t* idp = a.ids + a.vec_off[l];
+    const uint8_t* tp = a.codes + (size_t)G.tile0 * tile_bytes + (size_t)warp * tile_bytes + lane * kChunkBytes;
+    const int64_t* idp = a.ids + G.vec0;
     // the next group's item, fetched while the block scans this one
     if (warp == kGWarps - 1) fetch_group(a, ngroups, items + (cur ^ 1), lane);
     uint4 w[NCHUNK];
@@ -357,7 +372,10 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 
             if (sc.bound < thd) thd = sc.bound;
             ld[lane] = top.d[0];
             li[lane] = top.id[0];
-            if (lane == 0 && thd != INFINITY) lim_min(lim, s, (uint32_t)(0x8000 + smax_of(thd, sc.delta32, sc.B32)));
+            if (thd != INFINITY) {
+              const int sm = smax_warp(thd, sc.delta32, sc.B32);
+              if (lane == 0) lim_min(lim, s, (uint32_t)(0x8000 + sm));
+            }
             __syncwarp();
           }
         }
