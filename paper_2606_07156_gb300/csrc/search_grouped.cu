@@ -182,7 +182,7 @@ __device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItem* 
 }
 
 template <int NCHUNK>
-__global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 2 : 1)) packed_kernel(const GArgs a) {
+__global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 : (NCHUNK <= 6 ? 2 : 1))) packed_kernel(const GArgs a) {
   constexpr int Mp = NCHUNK * 16;
   const GLayout L(Mp);
   const uint32_t raw = smem_addr(anns_dyn_smem);
