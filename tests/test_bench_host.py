@@ -1,0 +1,96 @@
+"""Host logic of bench.py without a GPU: recall, the margin and Eq. 2
+calibrations on the recall budget, and the roofline's algorithmic bytes.
+
+The searches are fakes: each policy returns a fixed result table, so the test
+checks which policy the calibration picks, not the library.
+"""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class FakeAmp:
+    """Stands in for the package: policy() returns its arguments."""
+
+    @staticmethod
+    def policy(mode, **kw):
+        return (mode, tuple(sorted(kw.items())))
+
+
+def _gt(nq=40, k=10):
+    return np.arange(nq * k, dtype=np.int64).reshape(nq, k)
+
+
+def _with_hits(gt, hits):
+    """Result rows holding the first `hits` ground-truth ids (the rest misses)."""
+    out = np.full_like(gt, -5)
+    out[:, :hits] = gt[:, :hits]
+    return out
+
+
+def test_recall_counts_ground_truth_hits():
+    gt = _gt()
+    assert bench.recall(gt, gt, 10) == 1.0
+    assert bench.recall(_with_hits(gt, 7), gt, 10) == 0.7
+    assert bench.recall(np.full_like(gt, -1), gt, 10) == 0.0
+
+
+def test_margin_calibration_takes_the_most_aggressive_margin_within_budget():
+    gt = _gt()
+    # plain recall 1.0; the recall the fake search reaches at each margin
+    # (any other margin: 1.0)
+    table = {-8.0: 0.97, -6.0: 0.996, -4.0: 0.998}
+
+    def run(Qc, nprobe, pol):
+        mode, kw = pol
+        if mode == "plain":
+            return gt
+        keep = table.get(dict(kw)["margin"], 1.0)
+        # turn the first (1 - keep) of all result entries into misses
+        out = gt.copy()
+        nbad = int(round((1.0 - keep) * gt.size))
+        out.reshape(-1)[:nbad] = -5
+        return out
+
+    m, tried = bench.calibrate_margin(FakeAmp, None, gt, 64, 10, run, budget=0.5)
+    # -8 loses 3 points, -6 loses 0.4 (within 0.5): -6 is the most aggressive within budget
+    assert m == -6.0
+    assert tried[-8.0] > 0.5 >= tried[-6.0]
+    # with a budget no margin meets, the calibration gives up (infinite margin: all wide)
+    m2, _ = bench.calibrate_margin(FakeAmp, None, gt, 64, 10,
+                                   lambda Qc, n, pol: run(Qc, n, pol) if pol[0] == "plain"
+                                   else _with_hits(gt, 8), budget=0.5)
+    assert m2 == float("inf")
+
+
+def test_eq2_calibration_on_the_budget():
+    gt = _gt()
+
+    def run(Qc, nprobe, pol):
+        mode, kw = pol
+        if mode == "plain":
+            return gt
+        t = dict(kw)["thresholds"][3]
+        return gt if t >= -4.0 else _with_hits(gt, 5)
+
+    th, tried = bench.calibrate_eq2(FakeAmp, None, gt, 64, 10, run, budget=0.5)
+    assert th == (-2.5, -3.0, -3.5, -4.0)
+    assert tried[-5.0] == 50.0 and tried[-4.0] == 0.0
+
+
+def test_pair_bytes_counts_list_sizes_of_probed_pairs():
+    class FakeIndex:
+        @staticmethod
+        def list_sizes():
+            return np.array([10, 0, 7, 3], dtype=np.int32)
+
+    probes = np.array([[0, 2, -1], [3, 3, 1]], dtype=np.int32)
+    pb = bench.pair_bytes(FakeIndex, probes, 32)
+    np.testing.assert_array_equal(pb, [[320, 224, 0], [96, 96, 0]])
