@@ -70,29 +70,86 @@ __global__ void __launch_bounds__(256) coarse_d2_kernel(const float* __restrict_
   }
 }
 
-// One warp per query: the nprobe_q smallest (D2, list id).
+// One warp per query: the nprobe_q smallest (D2, list id). D2 >= 0, so the
+// float bits order like the values. One counting pass over a 256-bin
+// histogram (per warp, in shared memory) of (key - kmin) >> shift, the shift
+// chosen so that the row's key range fits, finds the bucket of the np-th
+// smallest key; its upper end T bounds the np-th value, and only the lists
+// with D2 bits <= T are offered to the sorted warp list (about np of them
+// instead of every list), which orders them by (D2, id) as before.
 template <int R>
 __global__ void __launch_bounds__(256) coarse_select_kernel(const float* __restrict__ d2,
                                                             int64_t nq, int64_t nlist, int nprobe,
                                                             const int32_t* __restrict__ npq,
                                                             int32_t* __restrict__ probes,
                                                             float* __restrict__ probe_d2) {
+  __shared__ int hist_all[8][256];
   const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
+  int* hist = hist_all[threadIdx.x >> 5];
   if (q >= nq) return;
   int np = nprobe;
   if (npq) np = min(max(npq[q], 0), nprobe);
   WarpTopK<R, int32_t> top;
   top.init();
   if (np > 0) {
+    const float* row = d2 + q * nlist;
+    uint32_t tkey = 0xFFFFFFFFu;
+    if (nlist > np) {
+      uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+      for (int64_t l = lane; l < nlist; l += 32) {
+        const uint32_t key = __float_as_uint(row[l]);
+        kmin = min(kmin, key);
+        kmax = max(kmax, key);
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(kFull, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+      }
+      int shift = 0;
+      while (((kmax - kmin) >> shift) > 255u) ++shift;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
+      __syncwarp();
+      for (int64_t l = lane; l < nlist; l += 32)
+        atomicAdd(&hist[(__float_as_uint(row[l]) - kmin) >> shift], 1);
+      __syncwarp();
+      // the bucket where the running count reaches np
+      int c[8], run = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { c[i] = hist[lane * 8 + i]; run += c[i]; }
+      int incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int excl = incl - run;
+      uint32_t pick = 0xFFFFFFFFu;
+      if (excl < np && np <= incl) {
+        int acc = excl;
+        for (int i = 0; i < 8; ++i) {
+          if (acc + c[i] >= np) { pick = (uint32_t)(lane * 8 + i); break; }
+          acc += c[i];
+        }
+      }
+      const unsigned who = __ballot_sync(kFull, pick != 0xFFFFFFFFu);
+      __syncwarp();
+      if (who) {  // always, as nlist > np keys were counted
+        pick = __shfl_sync(kFull, pick, __ffs(who) - 1);
+        const uint64_t top_key = (uint64_t)kmin + (((uint64_t)pick + 1) << shift) - 1;
+        tkey = top_key > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)top_key;
+      }
+    }
     float thd = INFINITY;
     int32_t thi = INT32_MAX;
-    const float* row = d2 + q * nlist;
     for (int64_t base = 0; base < nlist; base += 32) {
       const int64_t l = base + lane;
       const bool valid = l < nlist;
       const float v = valid ? row[l] : INFINITY;
-      top.offer(valid, v, (int32_t)l, np, thd, thi);
+      const bool cand = valid && __float_as_uint(v) <= tkey;
+      if (__any_sync(kFull, cand)) top.offer(cand, v, (int32_t)l, np, thd, thi);
     }
   }
 #pragma unroll
