@@ -312,9 +312,10 @@ __device__ __forceinline__ float batch_d2(const float* __restrict__ C, const flo
 }
 
 // One block per query.
-// Pass 1: T >= the np-th smallest upper bound u = D~ + eps, by a two-level
-//   256-bucket radix select on the bits of u (non-negative floats order like
-//   their bit patterns); T is the top of the bucket holding the np-th value.
+// Pass 1: T >= the np-th smallest upper bound u = D~ + eps: the keys (bits of
+//   u; non-negative floats order like their bit patterns) are counted into
+//   256 bins of (key - kmin) >> shift, the shift fitting the query's key range;
+//   T is the top of the bin holding the np-th value.
 // Pass 2: each warp scans its lists (strided), queues the candidates with
 //   D~ - eps <= T (ballot compaction into a per-warp buffer), computes their
 //   FP32-rule distances 32 at a time and keeps its top-np by (D2, l); the
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kRThreads) rerank_kernel(
   __shared__ float tile[kRWarps][32][33];
   __shared__ int32_t qbuf[kRWarps][64];
   __shared__ int hist[256];
-  __shared__ uint32_t sel_bucket, sel_before;
+  __shared__ uint32_t sel_bucket;
   __shared__ int total;
   float* qs = (float*)anns_dyn_smem;  // [dim]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -345,45 +346,63 @@ __global__ void __launch_bounds__(kRThreads) rerank_kernel(
     const RowNorms cr = {crows[l], crows[nlist + l], crows[2 * nlist + l]};
     return __float_as_uint(fmaxf(row[l] + rerank_bound(row[l], qr, cr, dim, Dp), 0.f));
   };
-  // pass 1: two radix levels of 8 bits
+  // pass 1: the key range of the upper bounds, then one count of
+  // (key - kmin) >> shift into 256 bins (the shift fits the range), and T = the
+  // top of the bin holding the np-th smallest key
   float T = INFINITY;
   if (np > 0) {
-    uint32_t prefix = 0, before = 0;
-    for (int level = 0; level < 2; ++level) {
-      const int shift = 24 - 8 * level;
-      for (int i = threadIdx.x; i < 256; i += kRThreads) hist[i] = 0;
-      __syncthreads();
-      for (int64_t l = threadIdx.x; l < nlist; l += kRThreads) {
-        const uint32_t key = upper_key(l);
-        if (level == 0 || (key >> 24) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
-      }
-      __syncthreads();
-      if (warp == 0) {
-        // bucket where the running count (after `before`) reaches np
-        int c[8], run = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) { c[i] = hist[lane * 8 + i]; run += c[i]; }
-        int incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int excl = incl - run;
-        const uint32_t need = (uint32_t)np - before;
-        if ((uint32_t)excl < need && need <= (uint32_t)incl) {
-          int acc = excl;
-          for (int i = 0; i < 8; ++i) {
-            if ((uint32_t)(acc + c[i]) >= need) { sel_bucket = (uint32_t)(lane * 8 + i); sel_before = (uint32_t)acc; break; }
-            acc += c[i];
-          }
-        }
-      }
-      __syncthreads();
-      prefix = level == 0 ? sel_bucket : prefix;
-      if (level == 0) before += sel_before;
-      else T = __uint_as_float((prefix << 24) | (sel_bucket << 16) | 0xFFFFu);
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+    for (int64_t l = threadIdx.x; l < nlist; l += kRThreads) {
+      const uint32_t key = upper_key(l);
+      kmin = min(kmin, key);
+      kmax = max(kmax, key);
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      kmin = min(kmin, __shfl_xor_sync(kFull, kmin, o));
+      kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+    }
+    if (lane == 0) { qbuf[warp][0] = (int32_t)kmin; qbuf[warp][1] = (int32_t)kmax; }
+    for (int i = threadIdx.x; i < 256; i += kRThreads) hist[i] = 0;
+    __syncthreads();
+    kmin = 0xFFFFFFFFu;
+    kmax = 0;
+    for (int w = 0; w < kRWarps; ++w) {
+      kmin = min(kmin, (uint32_t)qbuf[w][0]);
+      kmax = max(kmax, (uint32_t)qbuf[w][1]);
+    }
+    int shift = 0;
+    while (((kmax - kmin) >> shift) > 255u) ++shift;
+    for (int64_t l = threadIdx.x; l < nlist; l += kRThreads) atomicAdd(&hist[(upper_key(l) - kmin) >> shift], 1);
+    __syncthreads();
+    if (warp == 0) {
+      // bin where the running count reaches np
+      int c[8], run = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { c[i] = hist[lane * 8 + i]; run += c[i]; }
+      int incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int excl = incl - run;
+      uint32_t pick = 0xFFFFFFFFu;
+      if (excl < np && np <= incl) {
+        int acc = excl;
+        for (int i = 0; i < 8; ++i) {
+          if (acc + c[i] >= np) { pick = (uint32_t)(lane * 8 + i); break; }
+          acc += c[i];
+        }
+      }
+      const unsigned who = __ballot_sync(kFull, pick != 0xFFFFFFFFu);
+      pick = __shfl_sync(kFull, pick, who ? __ffs(who) - 1 : 0);
+      if (lane == 0) sel_bucket = who ? pick : 255u;  // (every list counted: np <= nlist keys, so found)
+    }
+    __syncthreads();
+    const uint64_t top_key = (uint64_t)kmin + (((uint64_t)sel_bucket + 1) << shift) - 1;
+    T = __uint_as_float(top_key > 0x7F800000ull ? 0x7F800000u : (uint32_t)top_key);
+    __syncthreads();  // qbuf is reused below
   }
   // pass 2
   WarpTopK<R, int32_t> top;
