@@ -174,11 +174,12 @@ cudaError_t launch_coarse(const Index& ix, const float* Q, int64_t nq, int nprob
   const unsigned g2 = (unsigned)((nq + 7) / 8);
   const int R = (nprobe + 31) / 32;
   switch (R) {
-    case 1: coarse_select_kernel<1><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
-    case 2: coarse_select_kernel<2><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
-    case 3: coarse_select_kernel<3><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
-    default: coarse_select_kernel<4><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); note_launch(); break;
+    case 1: coarse_select_kernel<1><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
+    case 2: coarse_select_kernel<2><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
+    case 3: coarse_select_kernel<3><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
+    default: coarse_select_kernel<4><<<g2, 256, 0, s>>>(d2, nq, ix.nlist, nprobe, nprobe_per_q, probes, probe_d2); break;
   }
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -483,7 +483,8 @@ int prepare_coarse_tc(Index& ix, const std::vector<float>& cent) {
   if (e != cudaSuccess) return cuda_fail(e, "coarse fast-path setup");
   center_bf16_kernel<<<(unsigned)((ix.nlist + 7) / 8), 256>>>(ix.centroids, ix.nlist, (int)ix.dim, Dp, ix.tc_mu,
                                                              (__nv_bfloat16*)ix.tc_cb, ix.tc_cn,
-                                                             ix.tc_cn + ix.nlist, ix.tc_cn + 2 * ix.nlist); note_launch();
+                                                             ix.tc_cn + ix.nlist, ix.tc_cn + 2 * ix.nlist);
+  note_launch();
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "coarse fast-path setup");

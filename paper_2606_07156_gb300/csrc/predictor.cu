@@ -549,7 +549,8 @@ int make_training_set(Index& ix, const float* Q, int64_t nq, int nprobe, int k, 
   if ((rc = anns_search(static_cast<anns_index*>(&ix), Q, nq, nprobe, nullptr, k + 1, nullptr, &plain,
                         (int64_t*)ids.p, (float*)dists.p, s)))
     return rc;
-  tau_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>((const float*)dists.p, nq, k, (double*)tau.p); note_launch();
+  tau_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>((const float*)dists.p, nq, k, (double*)tau.p);
+  note_launch();
   // the workspace now holds this batch's probes, probe D2 and query tables
   anns_precision_policy eq2{};
   eq2.lut_mode = ANNS_LUT_HEURISTIC_EQ2;

@@ -1,19 +1,21 @@
-// Grouped search of the narrow pairs (tables of 1..8 bits): the pairs probing
+// Grouped search of the narrow pairs (tables of 1..8 bits). The pairs probing
 // a list are taken four at a time, and their four byte tables are interleaved
-// into one table of 32-bit words, entry c of row m holding the levels of the
-// four queries in bytes 0..3 (each query's rank-0 pair and its wide pairs go
+// into one table of 32-bit words: entry c of row m holds the levels of the four
+// queries in bytes 0..3. One shared-memory gather per (vector, sub-space) then
+// serves four queries, and two 32-bit accumulators hold the four integer sums
+// as 16-bit lanes (bytes 0 and 2, bytes 1 and 3; a sum of at most 128 levels
+// of 255 stays below 2^16). The list's code tiles and list table are read once
+// per group instead of once per pair. For table gathers this is how a
+// narrower table becomes throughput (the gain the paper expects of lower
+// precision, Sections 1, 2.2): 8-bit levels pack four queries per gather,
+// where FP32 entries pack one.
+//
+// Each query's rank-0 pair and its wide pairs (FP32, 12 and 16 bits) go
 // through the query-major kernel first; the k-th distance found there bounds
-// the query's final k-th distance and prunes the grouped pairs' candidates). One shared-memory gather per (vector,
-// sub-space) then serves four queries, and two 32-bit accumulators hold the
-// four integer sums as 16-bit lanes (bytes 0 and 2, bytes 1 and 3; a sum of
-// at most 128 levels of 255 stays below 2^16). The list's code tiles and list
-// table are read once per group instead of once per pair. For table gathers
-// this is how a narrower table becomes throughput (the gain the paper expects
-// of lower precision, Sections 1, 2.2): 8-bit levels pack four queries per
-// gather, where FP32 entries pack one. The wide pairs (FP32, 12 and 16 bits) go through
-// the query-major kernel; a merge then takes each query's top-k over both
-// (TS). Results equal the other kernels' bit for bit: every table, integer
-// sum and distance follows the same rules (search.cu).
+// the query's final k-th distance and prunes the grouped pairs' candidates. A
+// merge then takes each query's top-k over both (TS). Results equal the other
+// kernels' bit for bit: every table, integer sum and distance follows the same
+// rules (search.cu).
 //
 // Per group (one block of 8 warps, persistent grid, groups taken from an
 // atomic counter by (query chunk, descending list size); the last warp fetches
@@ -182,7 +184,8 @@ __device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItem* 
 }
 
 template <int NCHUNK>
-__global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 : (NCHUNK <= 6 ? 2 : 1))) packed_kernel(const GArgs a) {
+__global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 : (NCHUNK <= 6 ? 2 : 1)))
+    packed_kernel(const GArgs a) {
   constexpr int Mp = NCHUNK * 16;
   const GLayout L(Mp);
   const uint32_t raw = smem_addr(anns_dyn_smem);
@@ -510,7 +513,8 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
   a.qt = qt; a.ltab = ix.ltab; a.probe_d2 = probe_d2; a.bits = bits;
   a.codes = ix.codes; a.ids = ix.ids; a.list_len = ix.list_len; a.vec_off = ix.vec_off;
   a.tile_off = ix.tile_off; a.order = ix.order; a.cnt = w.cnt; a.off = w.off; a.ioff = w.ioff;
-  a.pairs = w.pairs; a.gtab = w.gtab; a.nlist = (int)ix.nlist; a.nb = w.nbuckets; a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.nprobe = nprobe; a.k = k;
+  a.pairs = w.pairs; a.gtab = w.gtab; a.nlist = (int)ix.nlist; a.nb = w.nbuckets;
+  a.M = (int)ix.M; a.Mp = (int)ix.Mp; a.nprobe = nprobe; a.k = k;
   a.kpq = k_per_q; a.part_d = w.part_d; a.part_i = w.part_i; a.counter = w.counter; a.qm_d = qm_d;
   switch (ix.nchunk) {
     case 1: e = run_packed<1>(a, s); break;
