@@ -371,6 +371,26 @@ int anns_locate(anns_index* index, const float* queries, int64_t nq, int32_t npr
 int anns_locate_static(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
                        int32_t* probes_out, float* probe_d2_out, void* cuda_stream);
 
+/* SVR-RBF precision model (Section 3.4), training on the host (the paper's
+ * predictor, a comparator to the MLP; at most ANNS_SVR_MAX_SAMPLES samples).
+ * Model: f(x) = sum_i beta_i (exp(-gamma |x_i - x|^2) + 1), the constant 1
+ * being the bias. Training solves the dual of epsilon-insensitive regression
+ * over the box beta in [-C, C]^n,
+ *   minimise 1/2 beta^T K1 beta - y^T beta + eps |beta|_1,  K1 = K + 1,
+ * by exact coordinate descent: i ascending in sweeps, each step the
+ * coordinate's minimiser (soft threshold, then the clip to the box), until
+ * the largest change of a sweep is <= tol or max_sweeps sweeps ran. FP64.
+ *  X          host double [n x dim], row-major features
+ *  y          host double [n] targets
+ *  beta_out   host double [n] (written)
+ *  sweeps_out host int64 or NULL: sweeps run
+ * No GPU is used. Errors: INVALID_ARG (n < 1, n > ANNS_SVR_MAX_SAMPLES,
+ * dim < 1, C <= 0, gamma <= 0, eps < 0, tol < 0, max_sweeps < 1, null
+ * pointer), OOM. */
+#define ANNS_SVR_MAX_SAMPLES 4096
+int anns_svr_fit(const double* X, const double* y, int64_t n, int32_t dim, double C, double gamma,
+                 double eps, double tol, int64_t max_sweeps, double* beta_out, int64_t* sweeps_out);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* anns_last_error(void);
 

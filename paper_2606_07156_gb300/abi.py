@@ -32,7 +32,7 @@ SYMBOLS = (
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
     "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
-    "anns_kernel_launches", "anns_last_error",
+    "anns_kernel_launches", "anns_svr_fit", "anns_last_error",
 )
 
 
@@ -96,6 +96,8 @@ def _load():
         "anns_scan_pairs": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "anns_kernel_launches": ([], i64),
+        "anns_svr_fit": ([vp, vp, i64, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64,
+                          vp, ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
         "anns_locate_static": ([vp, vp, i64, i32, vp, vp, vp], i32),
         "anns_graph_capture": ([vp, vp, i64, i32, vp, i32, vp, ctypes.POINTER(anns_precision_policy), vp, vp,
@@ -189,6 +191,22 @@ def anns_profile(index, enable: int):
     cnt = ctypes.c_int64()
     _check(_lib.anns_profile(index, enable, ms, ctypes.byref(cnt)))
     return list(ms), cnt.value
+
+
+SVR_MAX_SAMPLES = 4096
+
+
+def anns_svr_fit(X, y, C: float, gamma: float, eps: float, tol: float = 1e-10, max_sweeps: int = 10000):
+    """SVR-RBF training on the host (numpy float64 X [n, dim], y [n]) -> (beta [n], sweeps)."""
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n, dim = X.shape
+    beta = np.zeros(n, dtype=np.float64)
+    sweeps = ctypes.c_int64()
+    _check(_lib.anns_svr_fit(X.ctypes.data, y.ctypes.data, n, dim, C, gamma, eps, tol, max_sweeps,
+                             beta.ctypes.data, ctypes.byref(sweeps)))
+    return beta, sweeps.value
 
 
 def anns_kernel_launches() -> int:
