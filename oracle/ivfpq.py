@@ -25,13 +25,17 @@ Two families of functions:
   per operation, no fused multiply-add and a fixed summation order, so the
   library must reproduce it bit for bit.
 
-The FP32 LUT is evaluated in the decomposed form: with r = q - c_l,
-  ||r_m - y||^2 = ||r_m||^2 + [||y||^2 + 2 <c_{l,m}, y>] - 2 <q_m, y>,
-and sum_m ||r_m||^2 = ||q - c_l||^2 = D2 is the coarse distance CL already
-has. So the FP32 table of a pair is T'[m][c] = P_l[m][c] - 2 Q_q[m][c] with a
-per-list table P (fixed at index build) and a per-query table Q (shared by
-all probes of the query), and the ADC distance is D2 + sum_m T'[m][code_m].
-The FP64 definitions keep the direct form.
+The FP32 LUT follows the published IVFADC look-up-table decomposition for
+residual PQ (Johnson, Douze and Jegou, "Billion-scale similarity search with
+GPUs", 2017): with r = q - c_l and y = y_{m,c},
+  ||r_m - y||^2 = ||q_m - c_{l,m}||^2 + (||y||^2 + 2 <c_{l,m}, y>) - 2 <q_m, y>
+                =      term 1       +          term 2             + term 3.
+Term 1 summed over m is the coarse distance D2 that CL already has; term 2
+depends only on the list (it is tabulated once per list when the index is
+built); term 3 depends only on the query (tabulated once per query and shared
+by all its probes). The FP32 table of a pair is T'[m][c] = fl32(term2 + term3)
+(the entry shifted by ||r_m||^2), and the ADC distance is D2 + sum_m T'. The
+FP64 definitions keep the direct form ||r_m - y||^2 of Section 2.1.
 
 Readings where the paper is silent (the paper states no quantiser, bit-width
 set, tie rule or feature normalisation):
@@ -41,12 +45,14 @@ set, tie rule or feature normalisation):
   one step Delta = range / (2^b - 1) shared by all sub-tables (so that integer
   sums over m are coherent), t = round-half-even((T - bias_m) * s) with
   s = fl32((2^b - 1) / range) clamped to [0, 2^b - 1]; the distance estimate is
-  fl32(fl32(Delta32 * S) + B32) with S the exact integer sum and B the sum of
-  the biases. The per-pair scale and offset are derived in FP64; B is summed
-  in a fixed 32-lane tree order (lane l adds the biases m = l, l+32, ...
-  ascending, then five butterfly steps with offsets 16, 8, 4, 2, 1).
+  fl32(fl32(Delta32 * S) + B32) with S the exact integer sum. The offset B32
+  is the exact (rational) sum of the pair's FP32 coarse distance and the M
+  biases, rounded once to the nearest FP32 value (ties to even): a value
+  that no summation order changes.
 """
 from __future__ import annotations
+
+from fractions import Fraction
 
 import numpy as np
 
@@ -130,14 +136,15 @@ def _dot_rule(a: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 
 def query_table_fp32(q: np.ndarray, books: np.ndarray) -> np.ndarray:
-    """FP32 rule for Q_q[m][c] = <q_m, y_{m,c}> (dot rule, j ascending)."""
+    """FP32 rule for <q_m, y_{m,c}> (dot rule, j ascending); term 3 of the
+    decomposition is -2 times this table."""
     M, _, dsub = books.shape
     return _dot_rule(np.asarray(q, dtype=F32).reshape(M, dsub), np.asarray(books, dtype=F32))
 
 
 def list_table_fp32(c: np.ndarray, books: np.ndarray) -> np.ndarray:
-    """FP32 rule for P_l[m][c'] = fl32(||y||^2 + fl32(2 <c_{l,m}, y>)), both
-    inner products by the dot rule."""
+    """FP32 rule for term 2 of the decomposition, fl32(||y||^2 + fl32(2 <c_{l,m}, y>)),
+    both inner products by the dot rule."""
     M, _, dsub = books.shape
     y = np.asarray(books, dtype=F32)
     yn = np.zeros(y.shape[:2], dtype=F32)
@@ -159,10 +166,12 @@ def lut_fp32(q: np.ndarray, c: np.ndarray, books: np.ndarray) -> np.ndarray:
 def quantize_lut(T32: np.ndarray, b: int, d2=0.0) -> dict:
     """Quantise one (query, list) FP32 LUT to b bits (rule in the module docstring).
 
-    ``d2`` is the pair's FP32 coarse distance, folded into the offset:
-    B = fl64(d2) + (tree sum of the biases). Returns the integer table ``t``
-    [M, 256] (int64), the FP32 biases, the FP32 range, FP64 step ``delta64``
-    and offset ``B64``, their FP32 roundings, and the FP32 multiplier ``s32``.
+    ``d2`` is the pair's FP32 coarse distance, folded into the offset. Returns
+    the integer table ``t`` [M, 256] (int64), the FP32 biases, the FP32 range,
+    the FP64 step ``delta64`` = fl64(range / L) and its FP32 rounding
+    ``delta32``, the FP32 multiplier ``s32``, and the offset: ``B_exact`` (the
+    exact rational d2 + sum of the biases), ``B64`` and ``B32`` (its nearest
+    FP64 and FP32 values).
     """
     assert b in BITS
     T32 = np.asarray(T32, dtype=F32)
@@ -178,21 +187,38 @@ def quantize_lut(T32: np.ndarray, b: int, d2=0.0) -> dict:
         s32 = F32(0.0)
     y = (Tp * s32).astype(F32)
     t = np.minimum(np.rint(y), L).astype(np.int64)          # rint: half to even
-    B64 = F64(F64(F32(d2)) + tree_sum64(bias))
-    return dict(t=t, bias=bias, range=rng, delta64=delta64, s32=s32, B64=B64,
-                delta32=F32(delta64), B32=F32(B64), L=L)
+    B_exact = exact_sum([F32(d2)] + list(bias))
+    return dict(t=t, bias=bias, range=rng, delta64=delta64, s32=s32, B_exact=B_exact,
+                B64=F64(float(B_exact)), delta32=F32(delta64), B32=nearest_f32(B_exact), L=L)
 
 
-def tree_sum64(v: np.ndarray) -> np.float64:
-    """FP64 sum in the 32-lane tree order: lane l accumulates v[l], v[l+32], ...
-    (ascending), then lanes combine by butterfly with offsets 16, 8, 4, 2, 1."""
-    lanes = np.zeros(32, dtype=F64)
-    for m in range(len(v)):
-        lanes[m % 32] = F64(lanes[m % 32] + F64(v[m]))
-    idx = np.arange(32)
-    for o in (16, 8, 4, 2, 1):
-        lanes = (lanes + lanes[idx ^ o]).astype(F64)
-    return F64(lanes[0])
+def exact_sum(values) -> Fraction:
+    """The exact sum of finite floating-point values, as a rational number."""
+    return sum((Fraction(float(v)) for v in values), Fraction(0))
+
+
+def nearest_f32(x: Fraction) -> np.float32:
+    """The FP32 value nearest to the rational ``x``; of two equally near ones
+    the one with an even significand (IEEE 754 round to nearest, ties to even).
+    Beyond the largest finite value by half an ulp or more: infinity."""
+    big = Fraction(float(np.finfo(F32).max)) + Fraction(2) ** (127 - 24)
+    if abs(x) >= big:
+        return F32(np.inf) if x > 0 else F32(-np.inf)
+    with np.errstate(over="ignore"):
+        guess = F32(float(x))               # within one ulp of the answer
+    if not np.isfinite(guess):
+        guess = np.finfo(F32).max
+    cands = [guess, np.nextafter(guess, F32(-np.inf)), np.nextafter(guess, F32(np.inf))]
+    cands = [c for c in cands if np.isfinite(c)]
+    best = min(abs(Fraction(float(c)) - x) for c in cands)
+    near = [c for c in cands if abs(Fraction(float(c)) - x) == best]
+    near.sort(key=lambda c: int(np.asarray(c, dtype=F32).view(np.uint32)) & 1)
+    return F32(near[0])
+
+
+def exact_sum_f32(values) -> np.float32:
+    """The exact sum of finite FP32 values rounded once to FP32 (order-free)."""
+    return nearest_f32(exact_sum(values))
 
 
 # ----------------------------------------------------------- DC (Section 2.1)

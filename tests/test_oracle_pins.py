@@ -112,6 +112,27 @@ def test_fp32_rules_within_rounding_bound(small_a):
         assert np.all(np.abs(T32 - T64) <= (I.dsub + 3) * u * s_abs * 1.01)
 
 
+@pytest.mark.parametrize("key,M", [("A", 16), ("B", 32), ("C", 48)])
+def test_fp32_lut_per_element_tolerance(key, M):
+    """Each entry of the FP32 table (the decomposed rule) is within
+    1e-5 (T64 + mean T64) of the FP64 definition, T64 the unshifted entry
+    ||r_m - y||^2 and mean T64 the pair table's mean entry: relative 1e-5 with
+    an absolute floor of 1e-5 of the table's scale, per element, on data
+    shaped like the Gaussian-mixture, SIFT-shaped (integer, uncentred) and
+    Deep-shaped (normalised) workloads."""
+    from workloads import make_dataset, train_ivfpq
+    d = make_dataset(key, n=6000, nq=3, ncomp=32)
+    I = _index(train_ivfpq(d["base"], 12, M, seed=1, device="cpu"))
+    worst = 0.0
+    for q in d["queries"]:
+        for l in range(I.nlist):
+            T32 = ivfpq.lut_fp32(q, I.centroids[l], I.books).astype(np.float64)
+            Ts = ivfpq.lut_shift_fp64(q, I.centroids[l], I.books)
+            T64 = ivfpq.lut_fp64(q, I.centroids[l], I.books)
+            worst = max(worst, float((np.abs(T32 - Ts) / (T64 + T64.mean())).max()))
+    assert worst <= 1e-5
+
+
 # ------------------------------------------------------------ P3: integer exactness
 
 def test_quantiser_hand_worked():
@@ -129,17 +150,49 @@ def test_quantiser_hand_worked():
     assert ivfpq.dequant32(S, qz["delta32"], qz["B32"])[0] == np.float32(9.0)
 
 
-def test_tree_sum_is_a_sum():
-    """The fixed-order FP64 tree sum equals the exact sum when every partial
-    sum is exact (small integers), and stays within the FP64 rounding bound of
-    math.fsum otherwise."""
-    import math
+def test_nearest_f32_is_ieee_rounding():
+    """nearest_f32 of a value that FP64 holds exactly equals numpy's IEEE
+    FP64 -> FP32 conversion (one round-to-nearest-even), over random values of
+    every magnitude, halfway cases and the overflow threshold."""
+    from fractions import Fraction
     r = np.random.Generator(np.random.PCG64(12))
-    ints = r.integers(-1000, 1000, size=120).astype(np.float32)
-    assert ivfpq.tree_sum64(ints) == float(ints.astype(np.int64).sum())
-    x = (r.standard_normal(97) * 10.0 ** r.integers(-6, 6, size=97)).astype(np.float32)
-    exact = math.fsum(float(v) for v in x)
-    assert abs(ivfpq.tree_sum64(x) - exact) <= 10 * 2.0 ** -53 * np.abs(x.astype(np.float64)).sum()
+    x = r.standard_normal(3000) * 2.0 ** r.integers(-140, 120, size=3000)
+    for v in x:
+        assert ivfpq.nearest_f32(Fraction(float(v))).tobytes() == np.float32(v).tobytes()
+    one = Fraction(1)
+    assert ivfpq.nearest_f32(one + Fraction(1, 2 ** 24)) == np.float32(1.0)           # tie -> even
+    assert ivfpq.nearest_f32(one + Fraction(3, 2 ** 24)) == np.float32(1 + 2.0 ** -22)  # tie -> even
+    fmax = Fraction(float(np.finfo(np.float32).max))
+    assert ivfpq.nearest_f32(fmax + Fraction(2) ** 103 - 1) == np.finfo(np.float32).max
+    assert ivfpq.nearest_f32(fmax + Fraction(2) ** 103) == np.float32(np.inf)
+
+
+def test_offset_is_the_exact_sum_rounded_once():
+    """The offset is the exact sum of the coarse distance and the biases,
+    rounded once to FP32 (ties to even), whatever the order of the terms:
+    1 + 2^-24 is a tie (-> 1); adding 2^-60 puts it above the tie (-> 1 + 2^-23),
+    which a sum first rounded to FP64 would miss (double rounding);
+    1e30 + 1 - 1e30 = 1, which any running FP32 or FP64 sum gets wrong;
+    two smallest subnormals sum to the next one."""
+    import math
+    f = np.float32
+    assert ivfpq.exact_sum_f32([f(1), f(2.0 ** -24)]) == f(1)
+    assert ivfpq.exact_sum_f32([f(1), f(2.0 ** -24), f(2.0 ** -60)]) == f(1 + 2.0 ** -23)
+    assert f(math.fsum([1.0, 2.0 ** -24, 2.0 ** -60])) == f(1)     # the double-rounding trap
+    assert ivfpq.exact_sum_f32([f(1e30), f(1), f(-1e30)]) == f(1)
+    assert ivfpq.exact_sum_f32([f(2.0 ** -149), f(2.0 ** -149)]) == f(2.0 ** -148)
+    assert ivfpq.exact_sum_f32([f(-3), f(3)]) == 0
+    r = np.random.Generator(np.random.PCG64(14))
+    for _ in range(20):
+        v = (r.standard_normal(129) * 10.0 ** r.integers(-30, 30, size=129)).astype(np.float32)
+        want = ivfpq.exact_sum_f32(v)
+        assert ivfpq.exact_sum_f32(v[r.permutation(len(v))]).tobytes() == want.tobytes()
+        # dyadic values of 2^-20 resolution below 2^30: math.fsum is exact in
+        # FP64, so one conversion to FP32 is the single rounding
+        w = (r.integers(-2 ** 30, 2 ** 30, size=129) * 2.0 ** -20).astype(np.float32)
+        assert ivfpq.exact_sum_f32(w) == np.float32(math.fsum(float(x) for x in w))
+    qz = ivfpq.quantize_lut(np.array([[1, 2], [2.0 ** -24, 3]], dtype=np.float32), 8, d2=0.0)
+    assert qz["B32"] == f(1) and qz["B_exact"] == 1 + __import__("fractions").Fraction(1, 2 ** 24)
 
 
 def test_single_rounding_of_fp32_scale():
