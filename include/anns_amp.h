@@ -170,17 +170,31 @@ int anns_debug_tap(anns_index* index, int32_t what, void* out, size_t bytes);
  * and the per-pair precision), with the same device code the search uses.
  * The FP32 LUT is the one the search evaluates: T'[m][c] = ||r_m - y_mc||^2
  * - ||r_m||^2 (the ADC distance is the coarse distance D2 plus sum_m T'),
- * formed as fl32(P_l - 2 Q_q) from a per-list and a per-query table; the
- * offset B of a quantised pair includes D2.
+ * formed as fl32(P_l - 2 Q_q) from a per-list and a per-query table (the
+ * IVFADC look-up-table decomposition for residual PQ); the offset B of a
+ * quantised pair is the exact sum of D2 and the M row minima, rounded once
+ * to FP32.
  *  queries  device float32 [nq * dim]; pair_q, pair_l device int32 [npairs];
  *  pair_bits device uint8 [npairs] (0 = FP32 only).
  *  T_out     device float32 [npairs * M * 256] FP32 LUT, or NULL.
  *  t_out     device uint16  [npairs * M * 256] quantised levels, or NULL.
- *  scale_out device float64 [npairs * 4]: (Delta, B, range, s), or NULL. */
+ *  scale_out device float64 [npairs * 4]: (Delta in FP64, B32, range, s), or
+ *            NULL. */
 int anns_compute_luts(anns_index* index, const float* queries, int64_t nq,
                       const int32_t* pair_q, const int32_t* pair_l, const uint8_t* pair_bits,
                       int64_t npairs, float* T_out, uint16_t* t_out, double* scale_out,
                       void* cuda_stream);
+
+/* The quantiser's offset rule on arbitrary values (a test tap for the rule
+ * that forms each quantised pair's offset B from D2 and the row minima; the
+ * quantiser itself is a reading, the paper states none, Section 3.3): for
+ * each of `nsets` sets of `n` FP32 values, the exact sum rounded once to the
+ * nearest FP32 value (ties to even), independent of summation order.
+ *  vals device float32 [nsets * n], set-major; 0 <= n < 1024, nsets <= 2^30.
+ *  out  device float32 [nsets].
+ * Asynchronous on `cuda_stream`. Errors: INVALID_ARG (null pointer with
+ * nsets > 0, n out of range), CUDA. */
+int anns_debug_exact_sum(const float* vals, int64_t nsets, int32_t n, float* out, void* cuda_stream);
 
 /* ADC scan of whole lists for explicit pairs (DC of Section 2.1): for pair p,
  * the n_l distances of list pair_l[p] in list order are written at

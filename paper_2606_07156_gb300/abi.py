@@ -32,7 +32,7 @@ SYMBOLS = (
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
     "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
-    "anns_kernel_launches", "anns_svr_fit", "anns_last_error",
+    "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_last_error",
 )
 
 
@@ -96,6 +96,7 @@ def _load():
         "anns_scan_pairs": ([vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp], i32),
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "anns_kernel_launches": ([], i64),
+        "anns_debug_exact_sum": ([vp, i64, i32, vp, vp], i32),
         "anns_svr_fit": ([vp, vp, i64, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64,
                           vp, ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
@@ -179,6 +180,11 @@ def anns_scan_pairs(index, queries, nq, pair_q, pair_l, pair_bits, npairs, out_o
                     stream=None) -> None:
     _check(_lib.anns_scan_pairs(index, queries, nq, pair_q, pair_l, pair_bits, npairs,
                                 out_off, dist_out, S_out, stream))
+
+
+def anns_debug_exact_sum(vals, nsets, n, out, stream=None) -> None:
+    """Per set of n device FP32 values, the exact sum rounded once to FP32 (the offset rule)."""
+    _check(_lib.anns_debug_exact_sum(vals, nsets, n, out, stream))
 
 
 PROFILE_STAGES = 6  # CL distances, CL selection, precision + query tables, search up to the

@@ -449,6 +449,32 @@ extern "C" int anns_compute_luts(anns_index* ix, const float* Q, int64_t nq, con
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "LUT kernel");
 }
 
+namespace anns {
+// One warp per set: the exact sum of the set's values rounded once (common.cuh).
+__global__ void debug_exact_sum_kernel(const float* __restrict__ vals, int64_t nsets, int n, float* __restrict__ out) {
+  const int64_t set = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (set >= nsets) return;
+  ExactSum acc;
+  xsum_init(acc);
+  for (int i = lane; i < n; i += 32) xsum_add(acc, vals[set * n + i]);
+  xsum_warp(acc);
+  const float r = xsum_round(acc);
+  if (lane == 0) out[set] = r;
+}
+}  // namespace anns
+
+extern "C" int anns_debug_exact_sum(const float* vals, int64_t nsets, int32_t n, float* out, void* stream) {
+  if (nsets < 0 || nsets > (int64_t(1) << 30) || n < 0 || n >= 1024)
+    return fail(ANNS_ERR_INVALID_ARG, "0 <= nsets <= 2^30 and 0 <= n < 1024 required");
+  if (nsets == 0) return ANNS_OK;
+  if (!out || (!vals && n > 0)) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
+  debug_exact_sum_kernel<<<(unsigned)((nsets + 7) / 8), 256, 0, (cudaStream_t)stream>>>(vals, nsets, n, out);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "exact sum kernel");
+}
+
 extern "C" int anns_scan_pairs(anns_index* ix, const float* Q, int64_t nq, const int32_t* pq,
                                const int32_t* pl, const uint8_t* pb, int64_t npairs,
                                const int64_t* off, float* dist_out, int32_t* S_out, void* stream) {

@@ -94,6 +94,127 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
 
+// ---- exact sum of FP32 values, rounded once --------------------------------
+// Every finite FP32 value is an integer multiple of 2^-149 of magnitude below
+// 2^277 * 2^-149, so a sum of fewer than 2^10 of them is N * 2^-149 with an
+// integer |N| < 2^287. N is held as nine base-2^32 digits, each in a 64-bit
+// accumulator whose carries are propagated only once, at the end (a digit
+// receives at most two 32-bit pieces per value). Integer addition is
+// associative, so lanes may add their values in any order and combine by any
+// reduction tree: the rounded result is the exact sum's nearest FP32 value
+// (ties to even), whatever the order. Non-finite values are summed apart in
+// FP32 and, if any occurs, are the result (IEEE inf/NaN propagation).
+struct ExactSum {
+  long long d[9];
+  float nonfinite;
+  bool any_nonfinite;
+};
+
+__device__ __forceinline__ void xsum_init(ExactSum& a) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a.d[k] = 0;
+  a.nonfinite = 0.f;
+  a.any_nonfinite = false;
+}
+
+__device__ __forceinline__ void xsum_add(ExactSum& a, float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0xffu) {
+    a.nonfinite = __fadd_rn(a.nonfinite, v);
+    a.any_nonfinite = true;
+    return;
+  }
+  // v = sig * 2^(p - 149): sig carries the hidden bit of a normal value, and a
+  // subnormal (e = 0) has the position of e = 1 without it
+  const uint32_t sig = e ? ((u & 0x7fffffu) | 0x800000u) : (u & 0x7fffffu);
+  const int p = e ? (int)e - 1 : 0;
+  const unsigned long long w = (unsigned long long)sig << (p & 31);
+  const long long lo = (long long)(w & 0xffffffffull), hi = (long long)(w >> 32);
+  const int i = p >> 5;  // 0..7: the low piece goes to digit i, the high one to i + 1
+  const bool neg = (u >> 31) != 0u;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const long long c = (k == i ? lo : 0ll) + (k == i + 1 ? hi : 0ll);
+    a.d[k] += neg ? -c : c;
+  }
+}
+
+// Sum over the warp's lanes (butterfly; every lane ends with the total).
+__device__ __forceinline__ void xsum_warp(ExactSum& a) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.d[k] += __shfl_xor_sync(0xffffffffu, a.d[k], o);
+    a.nonfinite = __fadd_rn(a.nonfinite, __shfl_xor_sync(0xffffffffu, a.nonfinite, o));
+    a.any_nonfinite = __any_sync(0xffffffffu, a.any_nonfinite);
+  }
+}
+
+// The accumulated exact sum rounded to the nearest FP32 value, ties to even.
+__device__ __forceinline__ float xsum_round(const ExactSum& a) {
+  if (a.any_nonfinite) return a.nonfinite;
+  // carry propagation: N = c * 2^288 + sum_k g[k] 2^(32k), c in {0, -1}
+  uint32_t g[9];
+  long long c = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const long long t = a.d[k] + c;
+    g[k] = (uint32_t)(t & 0xffffffffll);
+    c = t >> 32;  // arithmetic shift: the floor of t / 2^32
+  }
+  const bool neg = c < 0;
+  if (neg) {  // |N| = two's complement of the 288-bit pattern
+    unsigned long long carry = 1;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const unsigned long long t = (unsigned long long)(~g[k]) + carry;
+      g[k] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+  int h = -1;  // the highest non-zero digit
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    if (g[k] != 0u) h = k;
+  if (h < 0) return 0.f;
+  uint32_t t0 = 0u, t1 = 0u, t2 = 0u;
+  bool sticky = false;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    if (k == h) t0 = g[k];
+    if (k == h - 1) t1 = g[k];
+    if (k == h - 2) t2 = g[k];
+    if (k < h - 2 && g[k] != 0u) sticky = true;
+  }
+  const int lz = __clz(t0);
+  const int top = 32 * h + 31 - lz;  // bit index of the leading one of |N|
+  uint32_t bits;
+  if (top < 24) {
+    // |N| < 2^24: exact in FP32, and N * 2^-149 has the bit pattern N (a
+    // subnormal below 2^23; exponent field 1 from 2^23 on)
+    bits = t0;
+  } else {
+    unsigned long long W = ((unsigned long long)t0 << 32) | t1;  // digits h, h-1
+    uint32_t rest = t2;
+    if (lz) {
+      W = (W << lz) | (t2 >> (32 - lz));
+      rest = t2 << lz;
+    }
+    // W holds bits top .. top-63 of |N|, leading one at bit 63
+    uint32_t mant = (uint32_t)(W >> 40);
+    const bool half = ((W >> 39) & 1ull) != 0ull;
+    sticky = sticky || rest != 0u || (W & ((1ull << 39) - 1ull)) != 0ull;
+    int E = top - 22;  // mant * 2^(top - 23 - 149) = 1.f * 2^(E - 127)
+    if (half && (sticky || (mant & 1u))) {
+      ++mant;
+      if (mant == (1u << 24)) { mant >>= 1; ++E; }
+    }
+    bits = E >= 255 ? 0x7f800000u : (((uint32_t)E << 23) | (mant & 0x7fffffu));
+  }
+  return __uint_as_float(bits | (neg ? 0x80000000u : 0u));
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));

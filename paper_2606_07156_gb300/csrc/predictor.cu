@@ -88,21 +88,23 @@ __global__ void __launch_bounds__(256) label_kernel(const LabelArgs a) {
     }
     __syncthreads();
     if (warp == 0) {
-      double B = 0.0;
+      ExactSum B;
+      xsum_init(B);
       float range = 0.f;
       for (int m = lane; m < a.M; m += 32) {
-        B = __dadd_rn(B, (double)bias[m]);
+        xsum_add(B, bias[m]);
         range = fmaxf(range, rowmax[m]);
       }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+      if (lane == 0) xsum_add(B, d2);
+      xsum_warp(B);
+      const float B32 = xsum_round(B);
       range = warp_max(range);
       if (lane < kBitsN) {
         const int L = (1 << kBitsTab[lane]) - 1;
         scal[lane] = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
         scal[kBitsN + lane] = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
       }
-      if (lane == 0) scal[2 * kBitsN] = __double2float_rn(__dadd_rn((double)d2, B));
+      if (lane == 0) scal[2 * kBitsN] = B32;
     }
     __syncthreads();
     double err[kBitsN] = {0, 0, 0, 0, 0};

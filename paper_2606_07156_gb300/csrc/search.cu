@@ -6,7 +6,8 @@
 //      from the list's table P_l and the query's table 2 Q_q (LC),
 //   2. if the pair's precision is b bits, quantises T' with one shared step
 //      Delta = range/(2^b-1) and per-sub-table biases into a uint8 (b <= 8) or
-//      uint16 table in shared memory, the offset B = D2 + sum of biases in FP64,
+//      uint16 table in shared memory, the offset B32 = the exact sum of D2 and
+//      the biases rounded once to FP32,
 //   3. scans the list's packed codes tile by tile, one vector per lane,
 //      summing LUT entries in ascending m — FP32 sums for the plain LUT
 //      (distance fl32(D2 + sum)), exact int32 sums S for quantised LUTs
@@ -26,7 +27,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
 struct PairScal {
-  double delta64, B64;
+  double delta64;
   float s32, delta32, B32, range;
   int L;
 };
@@ -79,8 +80,8 @@ struct Smem {
 __device__ __forceinline__ uint32_t rint_bits(float y) { return __float_as_uint(add_rn(y, 12582912.0f)); }
 
 // Per-pair step Delta and offset B from the row statistics `bias`, `rowmax`
-// (every warp derives the shared step; warp 0 also the offset B in FP64, row
-// minima summed in the fixed 32-lane tree order, plus D2, and writes *out).
+// (every warp derives the shared step; warp 0 also the offset B32, the exact
+// sum of D2 and the row minima rounded once, and writes *out).
 // The FP64 step delta64 (an FP64 division) is only computed for the taps.
 // Returns s32.
 template <bool WITH_D64>
@@ -94,17 +95,18 @@ __device__ __forceinline__ float pair_scale(int M, int b, float d2, const float*
   // fl32 of the FP64 quotient equals the correctly rounded FP32 quotient
   const float s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
   if (warp == 0) {
-    double B = 0.0;
-    for (int m = lane; m < M; m += 32) B = __dadd_rn(B, (double)bias[m]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+    ExactSum B;
+    xsum_init(B);
+    for (int m = lane; m < M; m += 32) xsum_add(B, bias[m]);
+    if (lane == 0) xsum_add(B, d2);
+    xsum_warp(B);
+    const float B32 = xsum_round(B);
     if (lane == 0) {
       PairScal sc;
       sc.delta64 = WITH_D64 && range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
       sc.s32 = s32;
       sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
-      sc.B64 = __dadd_rn((double)d2, B);
-      sc.B32 = __double2float_rn(sc.B64);
+      sc.B32 = B32;
       sc.range = range;
       sc.L = L;
       *out = sc;
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) luts_kernel(const SearchArgs a, cons
     }
     if (scale_out && threadIdx.x == 0) {
       scale_out[p * 4 + 0] = b ? s.sc->delta64 : 0.0;
-      scale_out[p * 4 + 1] = b ? s.sc->B64 : (double)d2;
+      scale_out[p * 4 + 1] = b ? (double)s.sc->B32 : (double)d2;
       scale_out[p * 4 + 2] = b ? (double)s.sc->range : 0.0;
       scale_out[p * 4 + 3] = b ? (double)s.sc->s32 : 0.0;
     }

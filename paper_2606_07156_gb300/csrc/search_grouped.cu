@@ -22,8 +22,8 @@
 // the next group's item while the block scans the current one):
 //   1. row statistics: for each (slot, row) the warps form T' = P_l - 2 Q_q
 //      and its row minimum and range;
-//   2. per slot: the shared step, its reciprocal scale and the FP64 offset
-//      (lane l adding rows l, l+32, ... then the butterfly, as elsewhere);
+//   2. per slot: the shared step, its reciprocal scale and the offset (the
+//      exact sum of D2 and the row minima, rounded once, as elsewhere);
 //   3. levels: each warp recomputes T' for its rows of all four slots,
 //      quantises and interleaves the four levels of each entry;
 //   4. scan: warps take code tiles; per vector the four sums and one
@@ -260,22 +260,23 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
     if (warp < kSlots) {
       const int s = warp;
       float range = 0.f;
-      double B = 0.0;
       const int p = G.pid[s], bs = G.bits[s];
+      const float d2 = G.d2[s];
+      ExactSum B;
+      xsum_init(B);
       if (s < ns) {
         for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
         range = warp_max(range);
-        for (int m = lane; m < a.M; m += 32) B = __dadd_rn(B, (double)bias[s * Mp + m]);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
+        for (int m = lane; m < a.M; m += 32) xsum_add(B, bias[s * Mp + m]);
       }
-      const float d2 = G.d2[s];
+      if (lane == 0) xsum_add(B, d2);
+      xsum_warp(B);
       // every lane forms the same values (range and B are warp-uniform)
       const int Lv = (1 << bs) - 1;
       SlotScal sc;
       sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
       sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
-      sc.B32 = __double2float_rn(__dadd_rn((double)d2, B));
+      sc.B32 = xsum_round(B);
       sc.kq = s < ns ? G.kq[s] : 0;
       sc.bound = sc.kq > 0 ? G.bound[s] : INFINITY;
       sc.pid = p;

@@ -9,8 +9,8 @@
 //      owning entries c = 8i..8i+7 of every row: T' = fl32(P_l - 2 Q_q)
 //      (FP32 rule of search.cu); for b-bit pairs a first pass finds the row
 //      minima and the range (warp shuffles, no block barrier), a second pass
-//      writes the levels, and the offset is B = D2 + sum of row minima (FP64,
-//      lane l holding rows l, l+32, ... — the fixed tree order);
+//      writes the levels, and the offset B32 is the exact sum of D2 and the
+//      row minima rounded once to FP32;
 //   2. scans every code tile of the list (the block's warps read the same
 //      tiles, so all but the first read hit L1), offering distances to its
 //      sorted top-k list;
@@ -99,13 +99,14 @@ struct PairTable {
     const int L = (1 << b) - 1;
     const float s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
     delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
-    double B = 0.0;
+    ExactSum B;
+    xsum_init(B);
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s)
-      if (s * 32 + lane < M) B = __dadd_rn(B, (double)rm[s]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) B = __dadd_rn(B, __shfl_xor_sync(kFull, B, o));
-    B32 = __double2float_rn(__dadd_rn((double)d2, B));
+      if (s * 32 + lane < M) xsum_add(B, rm[s]);
+    if (lane == 0) xsum_add(B, d2);
+    xsum_warp(B);
+    B32 = xsum_round(B);
     // pass 2: levels
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {

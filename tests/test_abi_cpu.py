@@ -64,3 +64,22 @@ def test_argument_errors_without_gpu(abi):
         abi.anns_search(None, None, 1, 1, None, 1, None, None, None, None)
     assert "null index" in abi.anns_last_error()
     abi.anns_free(None)
+
+
+def test_binding_constants_match_the_header(abi):
+    """The binding's copies of the header's limits are the header's values."""
+    text = open(HEADER).read()
+
+    def define(name):
+        m = re.search(rf"#define {name} (\S+(?: \S+)*?)\s*(?:/\*|$)", text, flags=re.M)
+        return eval(m.group(1), {})
+
+    assert abi.STATIC_SCRATCH_FLOATS == define("ANNS_STATIC_SCRATCH_FLOATS")
+    assert (abi.MAX_M, abi.MAX_NPROBE, abi.MAX_K) == (define("ANNS_MAX_M"), define("ANNS_MAX_NPROBE"),
+                                                      define("ANNS_MAX_K"))
+
+
+def test_exact_sum_tap_rejects_bad_sizes(abi):
+    with pytest.raises(abi.AnnsError, match="n < 1024"):
+        abi.anns_debug_exact_sum(None, 1, 1024, None)
+    abi.anns_debug_exact_sum(None, 0, 5, None)   # nothing to do: no launch
