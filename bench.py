@@ -1,10 +1,12 @@
 """Benchmark: QPS of adaptive-precision vs plain-FP32 IVF-PQ search on one GB300.
 
 A step is one batched search (CL -> precision choice -> RC + LC + quantise +
-DC + TS) of the whole query batch of the SIFT-shaped workload (N = 1M,
-D = 128, nlist = 1024, M = 32, 10k queries, k = 10), queries resident in HBM.
-The index's codes (32 MB) fit in L2, so L2 is flushed (a 512 MB write)
-between timed steps.
+DC + TS) of the whole query batch, queries resident in HBM. The default
+workload is the Deep-shaped one (N = 10M, D = 96, nlist = 4096, M = 48, 10k
+queries, nprobe 32, k = 10): its codes (480 MB) exceed the 129 MB L2, and L2
+is flushed (a 512 MB write) between timed steps as well. ``--config B`` runs
+the SIFT-shaped workload (1M, D = 128, nlist = 1024, M = 32, nprobe 64),
+whose codes fit in L2.
 
 The headline policy is the learned predictor: trained on the GPU (labels,
 features, MLP training) from separate training queries, its round-up margin
@@ -13,6 +15,17 @@ most aggressive margin whose recall@10 stays within half the 1-point loss
 budget of plain FP32's. Plain FP32, uniform widths and the Eq. 2 heuristic
 (calibrated the same way) are timed beside it; the evaluation queries are
 used for neither training nor calibration.
+
+Recall. recall@10 is read as 10-recall@10 (|top-10 found ∩ exact top-10| /
+10). On these workloads IVF-PQ's codes bound it below 0.9 at every nprobe of
+the sweep, which the line states (``recall_condition``); it also reports a
+second operating point at the smallest nprobe whose plain 1-recall@10 (the
+exact nearest neighbour among the 10 returned) reaches 0.9.
+
+The CPU oracle leg (rank 0, one GPU) times the oracle single-threaded and on
+every host core, compares its sampled results with the GPU's bit for bit
+(fixed 8 bits, and the learned policy with the oracle's own inference), and
+states the measured error of every float output against FP64.
 
 Default: python bench.py [--gpus 1 --steps K --warmup W]
 Reference arm: python bench.py --impl reference (the CPU oracle, a bounded sample).
@@ -31,7 +44,8 @@ import tempfile
 import threading
 import time
 
-# the CPU oracle baseline is reported as single-threaded: keep BLAS on one thread
+# the CPU oracle runs one BLAS thread per process (single-threaded leg; the
+# all-core leg runs one process per core)
 for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -191,18 +205,6 @@ def pair_bytes(index, probes: np.ndarray, M: int) -> np.ndarray:
     return np.where(probes >= 0, sizes[np.maximum(probes, 0)], 0) * M
 
 
-def traffic_from_profile(kernel_src: str, workload_name: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    rec = json.load(open(path))
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != sha or rec.get("workload") != workload_name:
-        return None
-    return rec.get("dram_bytes_per_launch")
-
-
 def overlap(a: np.ndarray, b: np.ndarray, k: int) -> float:
     """Mean fraction of the first k ids of b also found in the first k of a."""
     return float(np.mean([len(np.intersect1d(x[:k], y[:k])) / k for x, y in zip(a, b)]))
@@ -284,6 +286,33 @@ def cl_tensor_bench(amp, dev, steps: int, warmup: int, flush) -> dict:
             "gemm_flop": flops, "bf16_effective_tflops": round(flops / (out["bf16"] / 1e3) / 1e12, 1)}
 
 
+def calibrate_margin_nn(amp, Qc, gt_c, nprobe: int, run, budget: float = LOSS_BUDGET):
+    """calibrate_margin with 1-recall@10 (exact nearest neighbour among the 10
+    returned) as the judged recall: the reading of the second operating point."""
+    base = 100.0 * nn_in_top(run(Qc, nprobe, amp.policy("plain")), gt_c, 10)
+    tried = {}
+    for m in (-8.0, -6.0, -4.0, -3.0, -2.0, -1.5, -1.0, -0.5, 0.0, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0):
+        loss = base - 100.0 * nn_in_top(run(Qc, nprobe, amp.policy("mlp", margin=m, width_map=True)), gt_c, 10)
+        tried[m] = round(loss, 3)
+        if loss <= budget:
+            return m, tried
+    return float("inf"), tried
+
+
+def roofline_profile(kernel_src: str, workload_name: str):
+    """The committed ncu record (profiles/traffic.json) for this kernel source
+    and workload: DRAM bytes per launch and the binding unit, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    recs = json.load(open(path))
+    for rec in recs if isinstance(recs, list) else [recs]:
+        if rec.get("source_sha") == sha and rec.get("workload") == workload_name:
+            return rec
+    return None
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     import __graft_entry__
@@ -311,40 +340,62 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     def run(nprobe, pol):
         return run_q(Q, nprobe, pol)
 
-    # plain FP32 recall sweep; nprobe = smallest reaching recall@10 >= 0.9, else the largest
-    sweep = cfg.get("nprobe_sweep", (cfg["nprobe"],)) if args.nprobe is None else (args.nprobe,)
+    def run_full(nprobe, pol):
+        ids, dists = index.search(Q, nprobe, k, pol, stream=stream)
+        torch.cuda.synchronize()
+        return ids.cpu().numpy(), dists.cpu().numpy()
+
+    # the workload's nprobe (SIFT-shaped: the smallest of its sweep reaching
+    # recall@10 >= 0.9, else the largest); plain FP32 recall over a sweep
     plain = amp.policy("plain")
-    rec_plain = {npb: recall(run(npb, plain), W["gt"], 10) for npb in sweep}
-    ok = [npb for npb in sweep if rec_plain[npb] >= 0.9]
-    nprobe = ok[0] if ok else max(sweep)
+    if args.nprobe is not None:
+        nprobe, sweep = args.nprobe, (args.nprobe,)
+    elif "nprobe_sweep" in cfg:
+        sweep = cfg["nprobe_sweep"]
+        nprobe = None
+    else:
+        nprobe = cfg["nprobe"]
+        sweep = tuple(sorted({max(1, nprobe // 2), nprobe, min(cfg["nlist"], 2 * nprobe, 128)}))
+    rec_plain, nn_plain = {}, {}
+    for npb in sweep:
+        ids = run(npb, plain)
+        rec_plain[npb], nn_plain[npb] = recall(ids, W["gt"], 10), nn_in_top(ids, W["gt"], 10)
+    if nprobe is None:
+        ok = [npb for npb in sweep if rec_plain[npb] >= 0.9]
+        nprobe = ok[0] if ok else max(sweep)
     ref_ids = run(nprobe, plain)
 
     # learned predictor: labels, features and training on the GPU from training queries
     ntrain = cfg.get("ntrain", args.ntrain)
     Qt = torch.from_numpy(make_queries(args.config, ntrain, stream=200)).to(dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    # trained on the two tables of the GB300 width map, wide pairs weighted up
-    # (a wide pair put on a narrow table costs recall, the reverse only speed)
-    index.train_predictor(Qt, nprobe, k, amp.train_cfg(epochs=args.epochs, batch=1024, lr=3e-3, seed=1,
-                                                       gpu_classes=True, high_weight=args.high_weight))
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    del Qt
+
+    def train(npb):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        # trained on the two tables of the GB300 width map, wide pairs weighted up
+        # (a wide pair put on a narrow table costs recall, the reverse only speed)
+        index.train_predictor(Qt, npb, k, amp.train_cfg(epochs=args.epochs, batch=1024, lr=3e-3, seed=1,
+                                                        gpu_classes=True, high_weight=args.high_weight))
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    train_s = train(nprobe)
     Qc = torch.from_numpy(W["cal_queries"]).to(dev)
     margin, tried = calibrate_margin(amp, Qc, W["cal_gt"], nprobe, k, run_q)
     eq2_th, eq2_tried = calibrate_eq2(amp, Qc, W["cal_gt"], nprobe, k, run_q)
-    del Qc
     adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True)
+    predictor_w = index.get_predictor()
     policies = {"mlp": adaptive, "plain": plain}
     if eq2_th is not None:
         policies["eq2"] = amp.policy("eq2", thresholds=eq2_th, width_map=True)
     for b in (4, 6, 8, 12, 16):
         policies[f"fixed{b}"] = amp.policy("fixed", bits=b)
-    recs, mixes = {}, {}
+    recs, mixes, full = {}, {}, {}
     for name, pol in policies.items():
-        ids = run(nprobe, pol)
-        recs[name] = (recall(ids, W["gt"], 10), overlap(ids, ref_ids, k))
+        ids, dists = run_full(nprobe, pol)
+        if name in ("mlp", "fixed8", "plain"):
+            full[name] = (ids, dists)
+        recs[name] = (recall(ids, W["gt"], 10), overlap(ids, ref_ids, k), nn_in_top(ids, W["gt"], 10))
         mixes[name] = bits_mix(index, abi, nq, nprobe)
     log(f"nprobe {nprobe}; margin {margin} {tried}; eq2 {eq2_th} {eq2_tried}; recalls {recs}")
 
@@ -365,6 +416,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         wall = time.perf_counter() - t0
     stage_ms, cnt = abi.anns_profile(index.handle, 0)
     launches_per_step = (abi.anns_kernel_launches() - launches0) / max(cnt, 1)
+    # stage view of the adaptive step (the last search before the taps below)
+    probes_ad = index.tap(abi.TAP_PROBES, (nq, nprobe), np.int32)
+    bits_ad = index.tap(abi.TAP_BITS, (nq, nprobe), np.uint8)
     ms_pol = {"mlp": ms_ad}
     for name, pol in policies.items():
         if name != "mlp":
@@ -384,7 +438,43 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         index.search_host(Qh, nprobe, k, adaptive, stream=stream, out=(ih, dh))
         e2e_t.append(time.perf_counter() - t)
     rec_e2e = recall(ih.numpy(), W["gt"], 10)
-    nn10 = nn_in_top(ih.numpy(), W["gt"], 10)
+
+    # second operating point: the smallest nprobe whose plain 1-recall@10
+    # reaches 0.9 (the predictor retrained and its margin recalibrated there,
+    # on the 1-recall@10 reading)
+    op2 = None
+    if not args.no_second_point:
+        cands = [p for p in (1, 2, 4, 8, 16, 32, 64) if p <= min(cfg["nlist"], 128)]
+        nn_sweep, np2 = {}, None
+        for npb in cands:
+            nn_sweep[npb] = nn_in_top(run(npb, plain), W["gt"], 10)
+            if nn_sweep[npb] >= 0.9:
+                np2 = npb
+                break
+        if np2 is not None:
+            train(np2)
+            m2, tried2 = calibrate_margin_nn(amp, Qc, W["cal_gt"], np2, run_q)
+            pols2 = {"plain": plain, "mlp": amp.policy("mlp", margin=m2 if np.isfinite(m2) else 3.0e38,
+                                                       width_map=True),
+                     "fixed8": amp.policy("fixed", bits=8)}
+            blk = {}
+            for name, pol in pols2.items():
+                ids = run(np2, pol)
+                ms = time_steps(lambda: index.search(Q, np2, k, pol, stream=stream, out=out), args.steps,
+                                args.warmup, stream, flush)
+                blk[name] = {"ms_per_step": round(float(np.mean(ms)), 4), "qps_per_gpu": round(nq / (np.mean(ms) / 1e3), 1),
+                             "nn_in_top10": round(nn_in_top(ids, W["gt"], 10), 4),
+                             "recall_at_10": round(recall(ids, W["gt"], 10), 4)}
+            op2 = {"reading": "1-recall@10: the exact nearest neighbour among the 10 returned", "nprobe": np2,
+                   "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_sweep.items()},
+                   "mlp_margin": m2, "margin_calibration_loss_pts": {str(a): b for a, b in tried2.items()},
+                   "policies": blk,
+                   "speedup_mlp_vs_plain": round(blk["plain"]["ms_per_step"] / blk["mlp"]["ms_per_step"], 3)}
+        else:
+            op2 = {"reading": "1-recall@10", "reached": False,
+                   "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_sweep.items()}}
+        index.set_predictor(predictor_w)  # the headline predictor back
+    del Qc, Qt
 
     totals = {name: sum(v) / 1e3 for name, v in ms_pol.items()}
     totals["_e2e"] = sum(e2e_t)
@@ -395,13 +485,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         return None
     qps = weak_scaling_qps(totals, world, nq, args.steps)
     qps_e2e = world * nq * args.steps / total_e2e
-    # roofline of the dominant kernel of the adaptive step (the last search run
-    # was the adaptive one): the grouped kernel (stage 4) over the narrow pairs
-    # of probe rank >= 1, or the query-major kernel (stage 3) over the rest
-    probes = index.tap(abi.TAP_PROBES, (nq, nprobe), np.int32)
-    bits = index.tap(abi.TAP_BITS, (nq, nprobe), np.uint8)
-    pb = pair_bytes(index, probes, cfg["M"])
-    narrow = (bits >= 1) & (bits <= 8)
+    # roofline of the dominant kernel of the adaptive step: the grouped kernel
+    # (stage 4) over the narrow pairs of probe rank >= 1, or the query-major
+    # kernel (stage 3) over the rest
+    pb = pair_bytes(index, probes_ad, cfg["M"])
+    narrow = (bits_ad >= 1) & (bits_ad <= 8)
     narrow[:, 0] = False
     st_ms = [v / max(cnt, 1) for v in stage_ms]
     if st_ms[4] > 0.0 and st_ms[4] >= st_ms[3]:
@@ -419,6 +507,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     achieved = nbytes / (kms / 1e3) / 1e9
     src = os.path.join(ROOT, "paper_2606_07156_gb300", "csrc", kfile)
     wl = f"{cfg['name']} nq={nq} nprobe={nprobe} k={k}"
+    prof = roofline_profile(src, wl)
+    roof = {"bound": prof["bound"] if prof else "hbm", "kernel": kname,
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
+            "traffic": prof["dram_bytes_per_launch"] if prof else None,
+            "algorithmic_bytes_per_launch": nbytes, "kernel_ms": round(kms, 4),
+            "lookups_per_s": round(nbytes / (kms / 1e3), 1),
+            "achieved_is": "algorithmic bytes (one code byte per LUT lookup, query-major) / kernel time"}
+    if prof:
+        dram_gbs = prof["dram_bytes_per_launch"] / (kms / 1e3) / 1e9
+        roof.update({"dram_gbs": round(dram_gbs, 1), "dram_frac": round(dram_gbs / peak, 4),
+                     "profile": prof.get("summary"), "binding_unit_pct": prof.get("binding_unit_pct")})
+    nn_best = max(rec_plain, key=lambda a: rec_plain[a])
     line = {
         "metric": METRIC, "value": round(qps["mlp"], 1), "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(totals["mlp"] * 1e3 / args.steps, 4),
@@ -432,31 +533,35 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "recall_at_10": round(recs["mlp"][0], 4),
         "top10_kept_vs_plain": round(recs["mlp"][1], 4),
-        "nn_in_top10": round(nn10, 4),
+        "nn_in_top10": round(recs["mlp"][2], 4),
+        "recall_condition": {
+            "reading": "10-recall@10 = |top-10 found ∩ exact top-10| / 10", "threshold": 0.9,
+            "reached": bool(rec_plain[nn_best] >= 0.9), "plain_recall_sweep": {str(a): round(b, 4) for a, b in
+                                                                                 rec_plain.items()},
+            "note": "not reachable on this workload by IVF-PQ with these codes at any nprobe of the sweep (the PQ "
+                    "reconstruction error bounds it); the headline compares the policies at equal nprobe, loss "
+                    "<= 1 point" if rec_plain[nn_best] < 0.9 else "reached"},
+        "second_operating_point": op2,
         "bits_mix": mixes["mlp"],
         "plain_fp32": {"qps": round(qps["plain"], 1), "recall_at_10": round(recs["plain"][0], 4),
                        "ms_per_step": round(totals["plain"] * 1e3 / args.steps, 4)},
         "speedup_vs_plain_fp32": round(qps["mlp"] / qps["plain"], 3),
+        "recall_loss_vs_plain_pts": round(100.0 * (recs["plain"][0] - recs["mlp"][0]), 3),
         "policies": {name: {"qps": round(qps[name], 1), "recall_at_10": round(recs[name][0], 4),
                             "top10_kept_vs_plain": round(recs[name][1], 4),
+                            "nn_in_top10": round(recs[name][2], 4),
                             "ms_per_step": round(totals[name] * 1e3 / args.steps, 4)} for name in qps},
         "eq2_thresholds": list(eq2_th) if eq2_th is not None else None,
         "predictor": {"train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
                       "classes": "GB300 tables (8-bit / wide)", "high_weight": args.high_weight,
                       "margin_calibration_recall_loss_pts": {str(a): b for a, b in tried.items()},
                       "recall_loss_budget_pts": LOSS_BUDGET},
-        "recall_sweep_plain": {str(a): round(b, 4) for a, b in rec_plain.items()},
+        "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_plain.items()},
         "stage_ms_per_step": {n: round(v, 4) for n, v in
                               zip(("cl_distances", "cl_select", "precision_choice+query_tables",
                                    "search_before_grouped (invert + query-major)", "grouped_kernel",
                                    "grouped_merge"), st_ms)},
-        "roofline": {"bound": "hbm", "kernel": kname,
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
-                     "traffic": traffic_from_profile(src, wl), "algorithmic_bytes_per_launch": nbytes,
-                     "kernel_ms": round(kms, 4), "lookups_per_s": round(nbytes / (kms / 1e3), 1),
-                     "note": "codes of this workload (32 MB) stay in L2: an as-if-HBM figure; the binding "
-                             "resource is the L1 / shared-memory data pipe"},
+        "roofline": roof,
         "e2e": {"value": round(qps_e2e, 1), "unit": "queries/s", "h2d_bytes_per_step": int(Qh.numel() * 4),
                 "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4), "recall_at_10": round(rec_e2e, 4)},
         "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -471,43 +576,231 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if not args.no_cl_bench:
         line["cl_fastpath"] = cl_tensor_bench(amp, dev, max(3, args.steps // 4), args.warmup, flush)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(W, cfg, nprobe, 8, args.cpu_seconds)
+        ctx = dict(amp=amp, abi=abi, index=index, Q=Q, stream=stream, margin=margin, predictor=predictor_w)
+        line.update(oracle_leg(W, cfg, nprobe, args.cpu_seconds, full, ctx))
     index.close()
     return line
 
 
-# ------------------------------------------------------------------ CPU oracle
+# ------------------------------------------------------------------ CPU oracle leg
 
-def cpu_baseline(W, cfg, nprobe: int, bits: int, seconds: float) -> dict:
-    """The oracle as it stands, on a bounded sample of the same queries."""
+_REF = None
+
+
+def _oracle_init(paths: dict, ready):
+    """Worker set-up: the oracle's index over the memory-mapped arrays; counts
+    itself in `ready` when done."""
+    global _REF
     from oracle import ivfpq
-    ref = ivfpq.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"])
+    a = {k: np.load(p, mmap_mode="r") for k, p in paths.items()}
+    _REF = ivfpq.Index(a["centroids"], a["codebooks"], a["codes"], a["list_of"])
+    with ready.get_lock():
+        ready.value += 1
+
+
+def oracle_mlp_bits(ref, Qs: np.ndarray, nprobe: int, pred: dict, margin: float) -> np.ndarray:
+    """The oracle's own widths for the learned policy: features, FP16-operand
+    MLP inference, the round-up rule and the GB300 width map."""
+    from oracle import ivfpq, predictor
+    D2 = ivfpq.coarse_d2_fp32(Qs, ref.centroids)
+    probes, pd = ivfpq.locate(D2, nprobe)
+    F = predictor.features(pd, probes, ref.radius, ref.sizes)
+    Xn = predictor.normalise(F.reshape(-1, 5), pred["mean"], pred["inv_std"])
+    z = predictor.mlp_logits16(predictor.to_fp16({k: pred[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}), Xn)
+    return predictor.gpu_width(predictor.decide_bits(z, np.float32(margin)).reshape(len(Qs), nprobe))
+
+
+def _oracle_job(job):
+    """One chunk of the oracle's search in a worker: (first row, ids, dists)."""
+    from oracle import ivfpq
+    row0, Qs, nprobe, k, mode, pred, margin = job
+    bits = oracle_mlp_bits(_REF, Qs, nprobe, pred, margin) if mode == "mlp" else 8
+    ids, dists = ivfpq.search(_REF, Qs, nprobe, k, bits=bits)
+    return row0, ids, dists
+
+
+def _margin32(margin: float) -> float:
+    return float(np.float32(margin if np.isfinite(margin) else 3.0e38))
+
+
+def oracle_all_cores(W, cfg, nprobe: int, row0: int, nrows: int, pred: dict, margin: float, cores: int):
+    """The oracle's search of queries row0 .. row0 + nrows - 1 under the learned
+    policy (widths from the oracle's own inference), one spawned process per
+    core over memory-mapped index arrays. Returns (ids, dists, seconds), the
+    seconds counted from the moment every worker has built its index."""
+    import multiprocessing as mp
+    k = cfg["k"]
     Qs = W["queries"]
-    done, t0, chunk = 0, time.perf_counter(), 8
+    paths = {}
+    os.makedirs(CACHE, exist_ok=True)
+    for key in ("centroids", "codebooks", "codes", "list_of"):
+        a = np.ascontiguousarray(W[key])
+        p = os.path.join(CACHE, f"oracle_{cfg['name']}_{a.shape[0]}_{key}.npy")
+        if not os.path.exists(p):
+            np.save(p, a)
+        paths[key] = p
+    margin = _margin32(margin)
+    jobs = [(row0 + s, Qs[row0 + s:row0 + min(s + 2, nrows)], nprobe, k, "mlp", pred, margin)
+            for s in range(0, nrows, 2)]
+    sp = mp.get_context("spawn")
+    ready = sp.Value("i", 0)
+    with sp.Pool(cores, initializer=_oracle_init, initargs=(paths, ready)) as pool:
+        t_set = time.perf_counter()
+        while ready.value < cores and time.perf_counter() - t_set < 600:
+            time.sleep(0.05)  # every worker's index is built before the clock starts
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_job, jobs, chunksize=1)
+        elc = time.perf_counter() - t0
+    res.sort(key=lambda r: r[0])
+    mi = np.concatenate([r[1] for r in res]) if res else np.zeros((0, k), np.int64)
+    md = np.concatenate([r[2] for r in res]) if res else np.zeros((0, k), np.float32)
+    return mi, md, elc
+
+
+def oracle_leg(W, cfg, nprobe: int, seconds: float, gpu_full: dict, ctx: dict) -> dict:
+    """The oracle as it stands on a bounded sample of the same queries:
+    single-threaded (fixed 8 bits) and one process per host core (the learned
+    policy, widths from the oracle's own inference), each compared with the
+    GPU's results bit for bit; then the error of every float output of the
+    GPU path against FP64 on a few queries."""
+    from oracle import ivfpq
+    k = cfg["k"]
+    Qs = W["queries"]
+    ref = ivfpq.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"])
+    # single thread, fixed 8 bits
+    done, t0, chunk = 0, time.perf_counter(), 4
+    o_ids, o_d = [], []
     while time.perf_counter() - t0 < seconds and done < len(Qs):
-        ivfpq.search(ref, Qs[done:done + chunk], nprobe, cfg["k"], bits=bits)
-        done += chunk
-    el = time.perf_counter() - t0
-    return {"value": round(done / el, 2), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of {len(Qs)} queries, nprobe={nprobe}, {bits}-bit LUTs for every pair "
-                      "(the oracle's cost per pair is the same for every width), numpy single thread",
-            "seconds": round(el, 2)}
+        i, d = ivfpq.search(ref, Qs[done:done + chunk], nprobe, k, bits=8)
+        o_ids.append(i)
+        o_d.append(d)
+        done += len(i)
+    el1 = time.perf_counter() - t0
+    n1 = done
+    oi, od = np.concatenate(o_ids), np.concatenate(o_d)
+    par8 = {"queries": n1, "ids_equal": bool(np.array_equal(oi, gpu_full["fixed8"][0][:n1])),
+            "dists_equal": bool(np.array_equal(od, gpu_full["fixed8"][1][:n1]))}
+    # every core, the learned policy (rows after the single-threaded sample)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    rate1 = n1 / el1
+    n_all = int(min(len(Qs) - n1, max(cores * 2, rate1 * cores * seconds * 0.8)))
+    mi, md, elc = oracle_all_cores(W, cfg, nprobe, n1, n_all, ctx["predictor"], ctx["margin"], cores)
+    g_i, g_d = gpu_full["mlp"]
+    parm = {"queries": len(mi), "ids_equal": bool(np.array_equal(mi, g_i[n1:n1 + len(mi)])),
+            "dists_equal": bool(np.array_equal(md, g_d[n1:n1 + len(md)])),
+            "widths": "the oracle's own features, FP16-operand MLP inference, round-up rule and width map"}
+    out = {
+        "cpu_baseline": {"value": round(len(mi) / elc, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"queries {n1}..{n1 + len(mi) - 1} of {len(Qs)}, nprobe={nprobe}, learned "
+                                   f"policy (the oracle's own inference), one numpy process per core",
+                         "seconds": round(elc, 2),
+                         "single_thread": {"value": round(n1 / el1, 2), "unit": "queries/s", "cores": 1,
+                                           "sample": f"first {n1} queries, fixed 8-bit tables",
+                                           "seconds": round(el1, 2)}},
+        "parity_at_bench_size": {"fixed8": par8, "mlp": parm,
+                                 "all_equal": bool(par8["ids_equal"] and par8["dists_equal"] and parm["ids_equal"]
+                                                   and parm["dists_equal"])},
+    }
+    out["fp64_error"] = fp64_errors(ref, W, cfg, nprobe, ctx)
+    return out
+
+
+def fp64_errors(ref, W, cfg, nprobe: int, ctx: dict, nq_s: int = 16) -> dict:
+    """Measured error against FP64 of every float output of the GPU path, on
+    the first nq_s queries: the FP32 coarse distances, the BF16 tensor-core
+    coarse distances D~, the FP32 table entries, the plain FP32 ADC distances
+    and the quantised (8-bit) distances against their M Delta / 2 bound."""
+    import torch
+
+    from oracle import ivfpq
+    amp, abi, index, stream = ctx["amp"], ctx["abi"], ctx["index"], ctx["stream"]
+    k, M = cfg["k"], cfg["M"]
+    Qs = W["queries"][:nq_s]
+    Qd = ctx["Q"][:nq_s].contiguous()
+    D64 = ivfpq.coarse_d2_fp64(Qs, ref.centroids)
+    out = {"queries": nq_s}
+    # FP32 coarse distances of the probed lists
+    ids_p, d_p = index.search(Qd, nprobe, k, amp.policy("plain"), stream=stream)
+    torch.cuda.synchronize()
+    probes = index.tap(abi.TAP_PROBES, (nq_s, nprobe), np.int32)
+    pd = index.tap(abi.TAP_PROBE_D2, (nq_s, nprobe), np.float32).astype(np.float64)
+    want = np.take_along_axis(D64, probes.astype(np.int64), axis=1)
+    out["cl_d2_fp32_max_rel"] = float((np.abs(pd - want) / want).max())
+    # plain FP32 ADC distances of the returned vectors vs FP64 ||q - x_hat||^2
+    ids_p, d_p = ids_p.cpu().numpy(), d_p.cpu().numpy().astype(np.float64)
+
+    def d64_of(ids):
+        o = np.zeros(ids.shape)
+        for i in range(ids.shape[0]):
+            v = ids[i] >= 0
+            xh = ref.reconstruct(ids[i][v])
+            o[i][v] = ((xh - Qs[i].astype(np.float64)) ** 2).sum(1)
+        return o
+
+    w = d64_of(ids_p)
+    v = ids_p >= 0
+    out["adc_fp32_max_rel"] = float((np.abs(d_p - w)[v] / w[v]).max())
+    # quantised 8-bit distances vs FP64, relative to the pair's M Delta / 2 bound
+    ids8, d8 = index.search(Qd, nprobe, k, amp.policy("fixed", bits=8), stream=stream)
+    torch.cuda.synchronize()
+    ids8, d8 = ids8.cpu().numpy(), d8.cpu().numpy().astype(np.float64)
+    w8 = d64_of(ids8)
+    D32 = ivfpq.coarse_d2_fp32(Qs, ref.centroids)
+    worst_rel, worst_ratio = 0.0, 0.0
+    for i in range(nq_s):
+        for j in range(k):
+            if ids8[i, j] < 0:
+                continue
+            l = int(W["list_of"][ids8[i, j]])
+            T32 = ivfpq.lut_fp32(Qs[i], ref.centroids[l], ref.books)
+            qz = ivfpq.quantize_lut(T32, 8, D32[i, l])
+            err = abs(d8[i, j] - w8[i, j])
+            worst_rel = max(worst_rel, err / w8[i, j])
+            # M Delta / 2 plus the FP32 table's own error (the FP32 rule's distance vs FP64)
+            t64 = ivfpq.lut_fp64(Qs[i], ref.centroids[l], ref.books)
+            bound = M * qz["delta64"] / 2 + 1e-5 * (t64.sum() / 256 + w8[i, j])
+            worst_ratio = max(worst_ratio, err / bound)
+    out["adc_q8_max_rel"] = worst_rel
+    out["adc_q8_err_over_bound_max"] = worst_ratio
+    # FP32 table entries (pairs: each sample query with its first, middle and last probe)
+    pq = np.repeat(np.arange(nq_s, dtype=np.int32), 3)
+    pl = probes[:, [0, nprobe // 2, nprobe - 1]].reshape(-1).astype(np.int32)
+    T, _, _ = index.compute_luts(Qd, torch.from_numpy(pq).to(Qd.device), torch.from_numpy(pl).to(Qd.device),
+                                 torch.zeros(len(pq), dtype=torch.uint8, device=Qd.device))
+    T = T.cpu().numpy().astype(np.float64)
+    rel, mixed = 0.0, 0.0
+    for p in range(len(pq)):
+        Ts = ivfpq.lut_shift_fp64(Qs[pq[p]], ref.centroids[pl[p]], ref.books)
+        T64 = ivfpq.lut_fp64(Qs[pq[p]], ref.centroids[pl[p]], ref.books)
+        e = np.abs(T[p] - Ts)
+        big = T64 > 1e-3 * T64.mean()
+        rel = max(rel, float((e[big] / T64[big]).max()))
+        mixed = max(mixed, float((e / (T64 + T64.mean())).max()))
+    out["lut_fp32_max_rel"] = rel
+    out["lut_fp32_max_err_over_T64_plus_mean"] = mixed
+    # BF16 tensor-core coarse distances D~ (normwise per query row)
+    index.locate(Qd, nprobe, cl="bf16", stream=stream)
+    torch.cuda.synchronize()
+    Dt = index.tap(abi.TAP_COARSE_APPROX, (nq_s, ref.nlist), np.float32).astype(np.float64)
+    out["cl_bf16_normwise_rel_max"] = float((np.linalg.norm(Dt - D64, axis=1) / np.linalg.norm(D64, axis=1)).max())
+    out["tolerances"] = {"fp32_lut": "per element <= 1e-5 (T64 + mean T64)", "fp32_distances": "rel <= 1e-5",
+                         "bf16": "normwise rel <= 2e-2", "quantised": "<= M Delta / 2 (+ FP32 rounding)"}
+    return {k2: (round(v2, 9) if isinstance(v2, float) else v2) for k2, v2 in out.items()}
 
 
 def run_reference(args, rank: int):
     if rank != 0:
         return None
     cfg, W = workload(args.config)
-    # the GPU arm's nprobe: the smallest of the sweep whose plain recall@10
-    # reaches 0.9, else the largest; on these workloads no nprobe of the sweep
-    # reaches 0.9 (IVF-PQ recall is bounded by the codes), so the largest
-    nprobe = args.nprobe or max(cfg.get("nprobe_sweep", (cfg["nprobe"],)))
+    # the GPU arm's nprobe: the workload's own (SIFT-shaped: the largest of the
+    # sweep; no nprobe of the sweep reaches recall@10 0.9 with these codes)
+    nprobe = args.nprobe or (max(cfg["nprobe_sweep"]) if "nprobe_sweep" in cfg else cfg["nprobe"])
     from oracle import ivfpq
     ref = ivfpq.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"])
     Qs = W["queries"]
-    per_step = max(8, args.ref_queries)
+    per_step = max(4, args.ref_queries)
     for i in range(args.warmup):
-        ivfpq.search(ref, Qs[:8], nprobe, cfg["k"], bits=8)
+        ivfpq.search(ref, Qs[:2], nprobe, cfg["k"], bits=8)
     ts, done = [], 0
     for i in range(args.steps):
         q = Qs[(i * per_step) % len(Qs):][:per_step]
@@ -531,15 +824,16 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
-    ap.add_argument("--config", default="B")
+    ap.add_argument("--config", default="C")
     ap.add_argument("--nprobe", type=int, default=None)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-queries", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-queries", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cl-bench", action="store_true", help="skip the coarse-stage comparison")
+    ap.add_argument("--no-second-point", action="store_true", help="skip the 1-recall@10 operating point")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

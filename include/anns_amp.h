@@ -363,9 +363,10 @@ int anns_locate(anns_index* index, const float* queries, int64_t nq, int32_t npr
                 void* cuda_stream);
 
 /* The coarse stage (cluster locating) without any allocation, for callers
- * that cannot allocate device memory: code running inside a CUDA graph
- * capture, hosts that forbid allocation after start-up, plugins whose host
- * application owns all memory pools. There is no counterpart in the paper;
+ * that cannot allocate device memory: real-time or embedded hosts that forbid
+ * allocation after start-up (cudaMalloc and cudaFree take unbounded time and
+ * may synchronise the device), and plugins whose host application owns every
+ * memory pool. There is no counterpart in the paper;
  * it is the probe selection of anns_search (same kernels, same results as
  * the PROBES / PROBE_D2 taps) with its scratch — the nq * nlist coarse
  * distance matrix — in a fixed array of ANNS_STATIC_SCRATCH_FLOATS floats

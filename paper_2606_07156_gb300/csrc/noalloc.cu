@@ -1,9 +1,9 @@
 // Cluster locating (the coarse stage) without any allocation.
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA
-// graph is being captured around it, real-time or embedded hosts that
-// forbid allocation after start-up, and plugins living inside a host
-// application that owns its memory pools. For them, anns_locate_static
+// Some callers cannot allocate device memory: real-time or embedded hosts
+// that forbid allocation after start-up (cudaMalloc and cudaFree take
+// unbounded time and may synchronise the device), and plugins living inside
+// a host application that owns every memory pool. For them, anns_locate_static
 // runs the coarse-distance and top-nprobe kernels with their scratch (the
 // nq x nlist distance matrix) in a fixed array compiled into this library,
 // instead of the index workspace that anns_search grows with cudaMalloc.
@@ -57,14 +57,18 @@ extern "C" int anns_locate_static(anns_index* ix, const float* queries, int64_t 
   if (nprobe < 1 || nprobe > ix->nlist || nprobe > ANNS_MAX_NPROBE)
     return fail(ANNS_ERR_INVALID_ARG, "nprobe must be in [1, min(nlist, 128)]");
   if (nq > 0 && (!queries || !probes_out || !probe_d2_out)) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
-  if (nq * ix->nlist > (int64_t)ANNS_STATIC_SCRATCH_FLOATS)
+  // nq <= scratch / nlist: the product nq * nlist is never formed, so no
+  // overflow can let a huge nq through
+  if (nq > (int64_t)ANNS_STATIC_SCRATCH_FLOATS / ix->nlist)
     return fail(ANNS_ERR_INVALID_ARG,
                 "nq * nlist exceeds the static scratch (ANNS_STATIC_SCRATCH_FLOATS); use anns_search "
                 "or smaller batches");
   if (nq == 0) return ANNS_OK;
   int prev = 0;
-  cudaGetDevice(&prev);
-  cudaSetDevice(ix->device);
+  cudaError_t se = cudaGetDevice(&prev);
+  if (se != cudaSuccess) return cuda_fail(se, "cudaGetDevice");
+  se = cudaSetDevice(ix->device);
+  if (se != cudaSuccess) return cuda_fail(se, "cudaSetDevice(index device)");
   float* d2 = nullptr;
   int rc = static_scratch(ix->device, &d2);
   if (rc == ANNS_OK) {

@@ -94,3 +94,29 @@ def test_pair_bytes_counts_list_sizes_of_probed_pairs():
     probes = np.array([[0, 2, -1], [3, 3, 1]], dtype=np.int32)
     pb = bench.pair_bytes(FakeIndex, probes, 32)
     np.testing.assert_array_equal(pb, [[320, 224, 0], [96, 96, 0]])
+
+
+def test_oracle_all_cores_equals_in_process_oracle(small_a, tmp_path, monkeypatch):
+    """The all-core oracle leg (spawned workers over memory-mapped arrays,
+    widths from the oracle's own MLP inference) returns exactly what the
+    oracle returns in this process, rows in order."""
+    from oracle import ivfpq, predictor
+    monkeypatch.setattr(bench, "CACHE", str(tmp_path))
+    d, ix = small_a
+    W = dict(ix, queries=d["queries"])
+    cfg = {"k": 10, "name": "tiny"}
+    o = ivfpq.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"])
+    D2 = ivfpq.coarse_d2_fp32(d["queries"], o.centroids)
+    pr, pd = ivfpq.locate(D2, 6)
+    F = predictor.features(pd, pr, o.radius, o.sizes).reshape(-1, 5)
+    pred = predictor.init_mlp(4)
+    pred["mean"] = F.mean(0).astype(np.float32)
+    pred["inv_std"] = (1.0 / (F.std(0) + 1e-3)).astype(np.float32)
+    pred["W3"] = (pred["W3"] * 4).astype(np.float32)
+    ids, dists, secs = bench.oracle_all_cores(W, cfg, 6, 3, 9, pred, 0.25, 2)
+    bits = bench.oracle_mlp_bits(o, d["queries"][3:12], 6, pred, 0.25)
+    assert len(np.unique(bits)) >= 2
+    ri, rd = ivfpq.search(o, d["queries"][3:12], 6, 10, bits=bits)
+    np.testing.assert_array_equal(ids, ri)
+    np.testing.assert_array_equal(dists, rd)
+    assert secs > 0
