@@ -226,6 +226,14 @@ int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* cou
  * captured counts once, graph replays do not count). */
 int64_t anns_kernel_launches(void);
 
+/* Failure detection (no counterpart in the paper, whose accelerator has no
+ * waits that can fail): waits for `cuda_stream` (NULL = the legacy default
+ * stream), then reads and clears the index's device status word.
+ * Returns ANNS_OK, or ANNS_ERR_TIMEOUT when a bounded wait inside a kernel of
+ * this index ran out since the last read (that call's output is invalid; the
+ * index and the context stay usable). Errors: INVALID_ARG, CUDA, TIMEOUT. */
+int anns_sync_status(anns_index* index, void* cuda_stream);
+
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
  *    ANNS_KERNEL_AUTO (default): grouped when the policy can choose tables of
@@ -252,9 +260,17 @@ int64_t anns_kernel_launches(void);
  *    chunks whose query tables take half of L2 (at least 256 queries) when
  *    the list tables and codes fit in the other half, else one chunk.
  *    Values >= 1 fix the chunk.
+ *  ANNS_OPT_WAIT_CYCLES: the limit, in SM clock cycles, of each wait inside
+ *    the tensor-core CL kernel's main loop (its mbarrier waits on TMA copies,
+ *    stage releases and the accumulator). 0 (default) = 2e9 cycles (about
+ *    one second). A wait that runs out makes the kernel record a timeout in
+ *    the index's status word (anns_sync_status), wait with the long limit for
+ *    the copies and MMAs it has issued, free its tensor memory and return;
+ *    the coarse stage's output is then invalid. Small values serve tests of
+ *    this failure path.
  * Every kernel, schedule and chunk size returns identical results.
  * Errors: INVALID_ARG. */
-enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1, ANNS_OPT_QCHUNK = 2 };
+enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1, ANNS_OPT_QCHUNK = 2, ANNS_OPT_WAIT_CYCLES = 3 };
 enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2, ANNS_KERNEL_GROUPED = 3 };
 enum { ANNS_SCHED_AUTO = 0, ANNS_SCHED_NATURAL = 1, ANNS_SCHED_LPT = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);

@@ -22,7 +22,7 @@ PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_COARSE_APPROX, TAP_COARSE_CANDIDATES = 4, 5
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS, TAP_STATUS = 10, 11, 12, 13
-OPT_KERNEL, OPT_SCHEDULE, OPT_QCHUNK = 0, 1, 2
+OPT_KERNEL, OPT_SCHEDULE, OPT_QCHUNK, OPT_WAIT_CYCLES = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR, KERNEL_GROUPED = 0, 1, 2, 3
 SCHED_AUTO, SCHED_NATURAL, SCHED_LPT = 0, 1, 2
 
@@ -32,7 +32,7 @@ SYMBOLS = (
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
     "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
-    "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_last_error",
+    "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_sync_status", "anns_last_error",
 )
 
 
@@ -97,6 +97,7 @@ def _load():
         "anns_profile": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "anns_kernel_launches": ([], i64),
         "anns_debug_exact_sum": ([vp, i64, i32, vp, vp], i32),
+        "anns_sync_status": ([vp, vp], i32),
         "anns_svr_fit": ([vp, vp, i64, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64,
                           vp, ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
@@ -218,6 +219,11 @@ def anns_svr_fit(X, y, C: float, gamma: float, eps: float, tol: float = 1e-10, m
 def anns_kernel_launches() -> int:
     """Kernels the library has enqueued since it was loaded (host-side count)."""
     return int(_lib.anns_kernel_launches())
+
+
+def anns_sync_status(index, stream=None) -> None:
+    """Waits for the stream; raises AnnsError(TIMEOUT) if a bounded wait in a kernel ran out."""
+    _check(_lib.anns_sync_status(index, stream))
 
 
 def anns_set_option(index, option: int, value: int) -> None:

@@ -525,6 +525,10 @@ extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
       if (value < 0) return fail(ANNS_ERR_INVALID_ARG, "query chunk must be >= 0");
       ix->opt_qchunk = value;
       return ANNS_OK;
+    case ANNS_OPT_WAIT_CYCLES:
+      if (value < 0) return fail(ANNS_ERR_INVALID_ARG, "wait limit must be >= 0");
+      ix->opt_wait_cycles = value;
+      return ANNS_OK;
     default: return fail(ANNS_ERR_INVALID_ARG, "unknown option");
   }
 }

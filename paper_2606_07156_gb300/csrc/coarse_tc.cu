@@ -22,9 +22,11 @@
 //    as coarse.cu) and the nprobe smallest (D2, l) kept: identical output to
 //    the plain path.
 //
-// Every mbarrier wait is bounded (about a second); on a timeout the kernel
-// records ANNS_DEV_TIMEOUT in the index's device status word, waits once
-// more (bounded) for its MMAs, frees its TMEM and returns.
+// Every mbarrier wait is bounded (by default about a second; the index option
+// ANNS_OPT_WAIT_CYCLES sets the main loop's limit); on a timeout the kernel
+// records ANNS_DEV_TIMEOUT in the index's device status word, waits (with the
+// long limit) for the copies and MMAs it has issued, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -49,7 +51,7 @@ constexpr uint32_t kBBytes = kTN * kKC * 2;   // 32 KB
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 // ring + barriers + 1 KB alignment slack; one CTA per SM (256 of 512 TMEM columns)
 constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + 1024 + 256;
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz: the default limit and the drain's
 
 // Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits 7-9 =
 // 1), B BF16 (bits 10-12 = 1), A and B K-major (bits 15, 16 = 0), N >> 3 at
@@ -87,8 +89,9 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Bounded wait on phase `parity` of the mbarrier; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait, for at most `limit` clock cycles, for the phase of parity `parity` of
+// the mbarrier to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -99,7 +102,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -173,7 +176,7 @@ __global__ void center_bf16_kernel(const float* __restrict__ X, int64_t n, int d
 __global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
     const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmC, const float* __restrict__ qn,
     const float* __restrict__ cn, int64_t nq, int64_t nlist, int Dp, float* __restrict__ dt,
-    int* __restrict__ status) {
+    int* __restrict__ status, long long wait_limit) {
   unsigned char* base = anns_dyn_smem + ((1024u - (smem_addr(anns_dyn_smem) & 1023u)) & 1023u);
   uint64_t* bars = (uint64_t*)(base + kStages * kStageBytes);  // full[S] | empty[S] | done
   uint32_t* slot = (uint32_t*)(bars + 2 * kStages + 1);
@@ -202,22 +205,24 @@ __global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
   const uint32_t tmem = *slot;
 
   bool ok = true;
+  int issued = 0;  // K chunks whose copies the producer has issued
   if (tid == 0) {
     // TMA producer
     for (int i = 0; i < nK && ok; ++i) {
       const int st = i % kStages;
-      if (i >= kStages) ok = mbar_wait(empty0 + 8 * st, (uint32_t)((i / kStages - 1) & 1));
+      if (i >= kStages) ok = mbar_wait(empty0 + 8 * st, (uint32_t)((i / kStages - 1) & 1), wait_limit);
       if (!ok) break;
       const uint32_t a_dst = ring + st * kStageBytes, b_dst = a_dst + kABytes;
       mbar_expect_tx(full0 + 8 * st, kStageBytes);
       tma_load_2d(a_dst, &tmQ, i * kKC, q0, full0 + 8 * st);
       tma_load_2d(b_dst, &tmC, i * kKC, l0, full0 + 8 * st);
+      issued = i + 1;
     }
   } else if (tid == 32) {
     // MMA issuer
     for (int i = 0; i < nK && ok; ++i) {
       const int st = i % kStages;
-      ok = mbar_wait(full0 + 8 * st, (uint32_t)((i / kStages) & 1));
+      ok = mbar_wait(full0 + 8 * st, (uint32_t)((i / kStages) & 1), wait_limit);
       if (!ok) break;
       tc_fence_after();
       const uint32_t a_addr = ring + st * kStageBytes, b_addr = a_addr + kABytes;
@@ -230,7 +235,7 @@ __global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
     tc_commit(done);  // arrives when every MMA issued above has completed
   }
   // everyone: the accumulator is complete once `done` fires
-  const bool done_ok = mbar_wait(done, 0);
+  const bool done_ok = mbar_wait(done, 0, wait_limit);
   ok = __syncthreads_and(ok && done_ok);
   tc_fence_after();
   if (ok) {
@@ -257,8 +262,14 @@ __global__ void __launch_bounds__(kGemmThreads) coarse_tc_kernel(
     atomicExch(status, ANNS_DEV_TIMEOUT);
   }
   if (!ok) {
-    // bounded: let in-flight TMA copies and MMAs finish before the CTA exits
-    for (int i = 0; i < kStages && tid == 0; ++i) mbar_wait(full0 + 8 * i, 0);
+    // let the copies and MMAs already issued finish before the CTA exits (long
+    // limit): stage st received ceil((issued - st) / kStages) copies, the last
+    // completing the phase of parity (count - 1) & 1, and no copy follows it
+    if (tid == 0)
+      for (int st = 0; st < kStages; ++st) {
+        const int count = issued > st ? (issued - st + kStages - 1) / kStages : 0;
+        if (count > 0) mbar_wait(full0 + 8 * st, (uint32_t)((count - 1) & 1));
+      }
     if (tid == 32) mbar_wait(done, 0);
   }
   tc_fence_before();
@@ -534,7 +545,9 @@ cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int np
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((ix.nlist + kTN - 1) / kTN), (unsigned)((nq + kTM - 1) / kTM));
   coarse_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(tmQ, tmC, qrows, ix.tc_cn, nq, ix.nlist, Dp, dt,
-                                                         ix.dev_status); note_launch();
+                                                         ix.dev_status,
+                                                         ix.opt_wait_cycles > 0 ? ix.opt_wait_cycles : kWaitCycles);
+  note_launch();
   const int R = (nprobe + 31) / 32;
   const unsigned g = (unsigned)nq;
   const size_t qsm = (size_t)ix.dim * sizeof(float);

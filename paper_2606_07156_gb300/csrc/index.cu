@@ -314,6 +314,25 @@ extern "C" int anns_debug_tap(anns_index* ix, int32_t what, void* out, size_t by
   return ANNS_OK;
 }
 
+extern "C" int anns_sync_status(anns_index* ix, void* stream) {
+  if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
+  int prev = 0;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  e = cudaSetDevice(ix->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice(index device)");
+  int v = 0;
+  e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess && ix->dev_status) {
+    e = cudaMemcpy(&v, ix->dev_status, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v != 0) e = cudaMemset(ix->dev_status, 0, 4);
+  }
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (v == ANNS_DEV_TIMEOUT) return fail(ANNS_ERR_TIMEOUT, "a bounded wait in a kernel of this index ran out; its output is invalid");
+  return ANNS_OK;
+}
+
 extern "C" const char* anns_last_error(void) { return anns::g_err.c_str(); }
 
 namespace anns {

@@ -78,6 +78,7 @@ struct Index {
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   int opt_schedule = 0;          // ANNS_SCHED_*
   int64_t opt_qchunk = 0;        // grouped kernel: queries per chunk (0 = automatic)
+  long long opt_wait_cycles = 0; // limit of the CL GEMM's main-loop waits in clock cycles (0 = about 1 s)
   // staging for anns_search_host
   void* st_q = nullptr; size_t st_q_cap = 0;
   void* st_out = nullptr; size_t st_out_cap = 0;
