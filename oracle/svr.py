@@ -32,6 +32,12 @@ idea; it fixes neither the solver nor the bias nor the table):
   exp(-t_k) at t_k = k * step, k = 0..n-1, linearly interpolated; 0 past the
   table. Its error is bounded by step^2 / 8 (the second derivative of exp(-t)
   is at most 1 on t >= 0) plus the tail exp(-t_max) past the table.
+* inference on the GPU (``predict32``): the same model as a fixed sequence of
+  FP32 operations, one rounding each, so that the width it decides is exact.
+  The table is the geometric sequence of a ratio rho = exp(-step) chosen as
+  a dyadic number: e_0 = 1, e_k = fl64(e_{k-1} * rho), each entry rounded
+  once to FP32 (no exponential function is evaluated, so no library's exp
+  enters the table); 1/step is a model parameter.
 """
 from __future__ import annotations
 
@@ -147,3 +153,65 @@ def exp_lut(t: np.ndarray, table: np.ndarray, step: float) -> np.ndarray:
 def exp_lut_bound(step: float, t_max: float) -> float:
     """Bound on |exp_lut(t) - exp(-t)| for t >= 0."""
     return step * step / 8.0 + float(np.exp(-t_max))
+
+
+# ------------------------------------------------- FP32 inference rule (GPU)
+
+F32 = np.float32
+
+
+def exp_table_geometric(n: int, rho: float) -> np.ndarray:
+    """FP32 table of exp(-k step), step = -ln(rho): e_0 = 1, e_k = fl64(e_{k-1} rho)
+    for k ascending, each entry rounded once to FP32."""
+    out = np.empty(n, dtype=F32)
+    e = F64(1.0)
+    for k in range(n):
+        out[k] = F32(e)
+        e = F64(e * F64(rho))
+    return out
+
+
+def normalise32(f: np.ndarray, mean, inv_std) -> np.ndarray:
+    """x = fl32(fl32(f - mean) * inv_std) per feature."""
+    return ((np.asarray(f, F32) - np.asarray(mean, F32)).astype(F32) * np.asarray(inv_std, F32)).astype(F32)
+
+
+def predict32(sv: np.ndarray, beta: np.ndarray, gamma: float, inv_step: float, table: np.ndarray,
+              X: np.ndarray) -> np.ndarray:
+    """FP32 rule of f(x) = sum_i beta_i (exp(-gamma |x - sv_i|^2) + 1) with the
+    table exponential, for normalised FP32 rows X. Per row: f = 0; for i
+    ascending: d2 = 0; for c ascending: e = fl32(x_c - sv_ic),
+    d2 = fl32(d2 + fl32(e e)); t = fl32(gamma d2); u = fl32(t * inv_step);
+    if u >= n - 1 the exponential is 0, else k = floor(u), w = fl32(u - k),
+    ex = fl32(fl32(table_k fl32(1 - w)) + fl32(table_{k+1} w));
+    f = fl32(f + fl32(beta_i fl32(ex + 1)))."""
+    sv = np.asarray(sv, F32)
+    beta = np.asarray(beta, F32)
+    X = np.asarray(X, F32)
+    table = np.asarray(table, F32)
+    n = len(table)
+    g, inv = F32(gamma), F32(inv_step)
+    f = np.zeros(len(X), dtype=F32)
+    for i in range(len(beta)):
+        d2 = np.zeros(len(X), dtype=F32)
+        for c in range(X.shape[1]):
+            e = (X[:, c] - sv[i, c]).astype(F32)
+            d2 = (d2 + (e * e).astype(F32)).astype(F32)
+        t = (g * d2).astype(F32)
+        u = (t * inv).astype(F32)
+        inside = u < F32(n - 1)
+        k = np.where(inside, np.floor(np.where(inside, u, F32(0))), 0).astype(np.int64)
+        w = (u - k.astype(F32)).astype(F32)
+        a = (table[k] * (F32(1) - w).astype(F32)).astype(F32)
+        b = (table[np.minimum(k + 1, n - 1)] * w).astype(F32)
+        ex = np.where(inside, (a + b).astype(F32), F32(0))
+        term = (beta[i] * (ex + F32(1)).astype(F32)).astype(F32)
+        f = (f + term).astype(F32)
+    return f
+
+
+def widths32(f: np.ndarray, margin: float) -> np.ndarray:
+    """Widths from FP32 regression values: index clip(ceil(fl32(f - margin)), 0, 5)."""
+    v = (np.asarray(f, F32) - F32(margin)).astype(F32)
+    idx = np.clip(np.ceil(v), 0, len(WIDTHS) - 1).astype(np.int64)
+    return np.asarray(WIDTHS, np.uint8)[idx]

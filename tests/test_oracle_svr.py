@@ -91,3 +91,61 @@ def test_rbf_kernel_values():
     np.testing.assert_allclose(K, [[1.0, np.exp(-2.5)], [np.exp(-2.5), 1.0]], rtol=0, atol=1e-15)
     y = np.array([[0.0, 0.0, 3.0, 0.0, 4.0]])
     np.testing.assert_allclose(svr.rbf(x[:1], y, 0.1), [[np.exp(-2.5)]], rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------- the FP32 inference rule
+
+RHO = 1.0 - 2.0 ** -5          # dyadic ratio of the geometric table
+
+
+def test_geometric_table_is_the_exponential():
+    """e_k = rho^k formed by FP64 products equals exp(-k step), step = -ln rho,
+    within FP32 rounding plus the products' relative error."""
+    tab = svr.exp_table_geometric(1024, RHO)
+    step = -np.log(RHO)
+    want = np.exp(-np.arange(1024) * step)
+    assert np.all(np.abs(tab.astype(np.float64) - want) <= want * (2.0 ** -24 + 1024 * 2.0 ** -52) + 1e-300)
+    assert tab[0] == 1.0 and np.all(np.diff(tab) <= 0)
+
+
+def test_predict32_within_its_error_bound_of_fp64():
+    """The FP32 rule with the table exponential stays within the table's
+    interpolation bound (step^2/8 + tail) per kernel term, summed over the
+    support vectors with their |beta|, plus FP32 rounding of the sum, of the
+    FP64 model with the exact exponential."""
+    X, y = _problem(120, 5)
+    Xn = X.astype(np.float32)
+    m = svr.fit(Xn.astype(np.float64), y, 1.0, 1.0, 0.1, max_sweeps=50)
+    n, step = 1024, -np.log(RHO)
+    tab = svr.exp_table_geometric(n, RHO)
+    inv_step = np.float32(1.0 / step)
+    beta32 = m["beta"].astype(np.float32)
+    r = np.random.Generator(np.random.PCG64(9))
+    Xq = r.standard_normal((200, 5)).astype(np.float32)
+    f32 = svr.predict32(Xn, beta32, 1.0, inv_step, tab, Xq).astype(np.float64)
+    f64 = svr.predict({"X": Xn.astype(np.float64), "beta": beta32.astype(np.float64), "gamma": 1.0}, Xq)
+    ab = np.abs(beta32.astype(np.float64)).sum()
+    # interpolation + tail + the argument's FP32 roundings (relative 4u of t,
+    # so exp changes by at most 4u t e^-t <= 4u/e) + the table's rounding
+    per_term = step * step / 8 + np.exp(-(n - 1) * step) + 4 * 2.0 ** -24 + 2 * 2.0 ** -24
+    bound = ab * per_term + len(beta32) * 2.0 ** -24 * (ab * 2 + np.abs(f64).max()) * 1.01
+    assert np.all(np.abs(f32 - f64) <= bound)
+    assert np.abs(f32 - f64).max() > 0          # the rule is not the FP64 model itself
+
+
+def test_predict32_far_from_every_support_vector_is_the_bias_sum():
+    """Past the table every kernel term is exactly 0, so f = fl32 sum of beta_i."""
+    sv = np.zeros((3, 5), np.float32)
+    beta = np.array([0.5, -0.25, 2.0], np.float32)
+    tab = svr.exp_table_geometric(64, RHO)
+    f = svr.predict32(sv, beta, 1.0, 1.0 / -np.log(RHO), tab, np.full((1, 5), 100.0, np.float32))
+    assert f[0] == np.float32(2.25)
+    # at a support vector itself (t = 0) the term is exactly 2 beta
+    f0 = svr.predict32(sv[:1], beta[:1], 1.0, 1.0 / -np.log(RHO), tab, sv[:1])
+    assert f0[0] == np.float32(1.0)
+
+
+def test_widths32_round_up_rule():
+    f = np.array([-0.5, 0.0, 0.2, 1.0, 2.4, 4.01, 9.0], np.float32)
+    np.testing.assert_array_equal(svr.widths32(f, 0.0), [4, 4, 6, 6, 12, 0, 0])
+    np.testing.assert_array_equal(svr.widths32(f, 0.5), [4, 4, 4, 6, 8, 16, 0])
