@@ -213,6 +213,51 @@ def overlap(a: np.ndarray, b: np.ndarray, k: int) -> float:
 LOSS_BUDGET = 0.5  # recall@10 points allowed on the calibration queries (half the 1-point target)
 
 
+SVR_RATIO = 1.0 - 2.0 ** -5   # ratio of the SVR's geometric exponential table (a dyadic number)
+SVR_TABLE = 1024              # entries: exp(-t) tabulated up to t = 32.5
+WIDTH_INDEX = {4: 0, 6: 1, 8: 2, 12: 3, 16: 4, 0: 5}  # regression target of a label width (0 = FP32)
+
+
+def fit_svr(amp, abi, index, Qt, nprobe: int, k: int, nsamp: int = 1280, seed: int = 3) -> dict:
+    """The SVR-RBF comparator of Section 3.4, fitted as the paper does: at most
+    1280 (feature, label) samples drawn from the GPU's training labels, gamma
+    = C = 1 (its LC setting), at most 50 sweeps of the library's solver;
+    targets = the label width's index in (4, 6, 8, 12, 16, FP32)."""
+    import torch
+    feat, lab = index.make_training_set(Qt, nprobe, k)
+    torch.cuda.synchronize()
+    F = feat.reshape(-1, 5).cpu().numpy().astype(np.float32)
+    L = lab.reshape(-1).cpu().numpy()
+    mean = F.mean(0).astype(np.float32)
+    inv_std = (1.0 / np.maximum(F.std(0), 1e-6)).astype(np.float32)
+    Xn = ((F - mean).astype(np.float32) * inv_std).astype(np.float32)
+    take = np.random.Generator(np.random.PCG64(seed)).permutation(len(L))[:nsamp]
+    y = np.array([WIDTH_INDEX[int(b)] for b in L[take]], dtype=np.float64)
+    t0 = time.perf_counter()
+    beta, sweeps = abi.anns_svr_fit(Xn[take].astype(np.float64), y, 1.0, 1.0, 0.1, 1e-10, 50)
+    fit_s = time.perf_counter() - t0
+    inv_step = np.float32(1.0 / -np.log(SVR_RATIO))
+    # only the support vectors (beta != 0) enter the model: a zero term adds exactly 0
+    sv = beta != 0.0
+    index.set_svr(Xn[take][sv], beta[sv].astype(np.float32), 1.0, mean, inv_std, SVR_TABLE, SVR_RATIO, inv_step)
+    return {"samples": int(len(take)), "gamma": 1.0, "C": 1.0, "eps": 0.1, "sweeps": int(sweeps),
+            "fit_s": round(fit_s, 3), "support_vectors": int(np.count_nonzero(beta)),
+            "table": f"{SVR_TABLE} entries, ratio 1 - 2^-5"}
+
+
+def calibrate_svr(amp, Qc, gt_c, nprobe: int, run, budget: float = LOSS_BUDGET):
+    """Most aggressive SVR width margin (widths mapped to this GPU's tables)
+    within the recall budget on the calibration queries."""
+    base = 100.0 * recall(run(Qc, nprobe, amp.policy("plain")), gt_c, 10)
+    tried = {}
+    for m in (3.0, 2.0, 1.5, 1.0, 0.75, 0.5, 0.25, 0.0, -0.25, -0.5, -1.0, -2.0):
+        loss = base - 100.0 * recall(run(Qc, nprobe, amp.policy("svr", margin=m, width_map=True)), gt_c, 10)
+        tried[m] = round(loss, 3)
+        if loss <= budget:
+            return m, tried
+    return -8.0, tried
+
+
 def calibrate_margin(amp, Qc, gt_c, nprobe: int, k: int, run, budget: float = LOSS_BUDGET):
     """Most aggressive MLP round-up margin (widths mapped to this GPU's
     tables) whose recall@10 on the calibration queries is at most `budget`
@@ -386,6 +431,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True)
     predictor_w = index.get_predictor()
     policies = {"mlp": adaptive, "plain": plain}
+    svr_info = None
+    if not args.no_svr:
+        svr_info = fit_svr(amp, abi, index, Qt, nprobe, k)
+        svr_margin, svr_tried = calibrate_svr(amp, Qc, W["cal_gt"], nprobe, run_q)
+        svr_info.update({"margin": svr_margin, "margin_calibration_recall_loss_pts": {str(a): b for a, b in
+                                                                                     svr_tried.items()}})
+        policies["svr"] = amp.policy("svr", margin=svr_margin, width_map=True)
     if eq2_th is not None:
         policies["eq2"] = amp.policy("eq2", thresholds=eq2_th, width_map=True)
     for b in (4, 6, 8, 12, 16):
@@ -552,6 +604,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                             "nn_in_top10": round(recs[name][2], 4),
                             "ms_per_step": round(totals[name] * 1e3 / args.steps, 4)} for name in qps},
         "eq2_thresholds": list(eq2_th) if eq2_th is not None else None,
+        "svr_comparator": None if svr_info is None else dict(
+            svr_info, bits_mix=mixes["svr"], speedup_vs_plain=round(qps["svr"] / qps["plain"], 3),
+            recall_at_10=round(recs["svr"][0], 4), mlp_speedup_vs_plain=round(qps["mlp"] / qps["plain"], 3),
+            mlp_recall_at_10=round(recs["mlp"][0], 4)),
         "predictor": {"train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
                       "classes": "GB300 tables (8-bit / wide)", "high_weight": args.high_weight,
                       "margin_calibration_recall_loss_pts": {str(a): b for a, b in tried.items()},
@@ -834,6 +890,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cl-bench", action="store_true", help="skip the coarse-stage comparison")
     ap.add_argument("--no-second-point", action="store_true", help="skip the 1-recall@10 operating point")
+    ap.add_argument("--no-svr", action="store_true", help="skip the SVR-RBF comparator")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

@@ -83,7 +83,8 @@ enum {
   ANNS_LUT_FIXED_BITS = 1,    /* every pair at fixed_bits */
   ANNS_LUT_HEURISTIC_EQ2 = 2, /* Eq. 2 feature f = d' - 3 r1 - r2 against thresholds */
   ANNS_LUT_MLP = 3,           /* learned predictor with full-precision fallback */
-  ANNS_LUT_EXPLICIT = 4       /* caller-provided bits per (query, probe rank) */
+  ANNS_LUT_EXPLICIT = 4,      /* caller-provided bits per (query, probe rank) */
+  ANNS_LUT_SVR = 5            /* the SVR-RBF regressor of Section 3.4 (anns_set_svr) */
 };
 enum { ANNS_PREC_FP32 = 0, ANNS_PREC_BF16 = 1, ANNS_PREC_FP8E4M3 = 2 };
 
@@ -401,6 +402,39 @@ int anns_locate(anns_index* index, const float* queries, int64_t nq, int32_t npr
 #define ANNS_STATIC_SCRATCH_FLOATS (1 << 21)
 int anns_locate_static(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
                        int32_t* probes_out, float* probe_d2_out, void* cuda_stream);
+
+/* SVR-RBF precision model for inference on the GPU (policy ANNS_LUT_SVR; the
+ * regressor of Section 3.4 with its exponential evaluated through a lookup
+ * table). Per probed pair, with the same five features as the MLP policy:
+ *   x = fl32(fl32(f - mean) * inv_std);  f = 0;  for i ascending:
+ *     d2 = FP32 sum over the 5 features, ascending, of fl32(e * e),
+ *          e = fl32(x_c - sv_ic);
+ *     u = fl32(fl32(gamma * d2) * inv_step);
+ *     ex = 0 if u >= table_n - 1, else with k = floor(u), w = fl32(u - k):
+ *          fl32(fl32(tab_k * fl32(1 - w)) + fl32(tab_{k+1} * w));
+ *     f = fl32(f + fl32(beta_i * fl32(ex + 1)));
+ *   width index = clip(ceil(fl32(f - margin)), 0, 5) into (4, 6, 8, 12, 16,
+ *   FP32), margin = the policy's fallback_margin; width_map applies after.
+ * The table is built here from table_ratio rho: e_0 = 1, e_k = fl64(e_{k-1} *
+ * rho) for k ascending, each rounded once to FP32, i.e. exp(-k step) with
+ * step = -ln(rho) and no exponential function evaluated; inv_step = 1 / step
+ * is given by the caller.
+ *  sv    host float [nsv * 5]: the support vectors (normalised features)
+ *  beta  host float [nsv]: their coefficients (anns_svr_fit's beta)
+ * Copied to the device (synchronous). Errors: INVALID_ARG (nsv out of
+ * [1, ANNS_SVR_MAX_SAMPLES], table_n out of [2, 4096], rho out of (0, 1),
+ * non-finite parameter, null pointer), OOM, CUDA. */
+typedef struct {
+  int32_t nsv;
+  const float* sv;
+  const float* beta;
+  float gamma;
+  float mean[5], inv_std[5];
+  int32_t table_n;
+  double table_ratio;
+  float inv_step;
+} anns_svr_model;
+int anns_set_svr(anns_index* index, const anns_svr_model* model);
 
 /* SVR-RBF precision model (Section 3.4), training on the host (the paper's
  * predictor, a comparator to the MLP; at most ANNS_SVR_MAX_SAMPLES samples).

@@ -27,7 +27,8 @@ idea; it fixes neither the solver nor the bias nor the table):
   -C < beta_i < 0 -> g_i = eps;  beta_i = C -> g_i <= -eps;  beta_i = -C -> g_i >= eps.
 * targets and widths: the label's index in (4, 6, 8, 12, 16, FP32) = 0..5;
   the predicted width is the one at index clip(ceil(f(x) - margin), 0, 5)
-  (margin > 0 rounds down less often: towards higher precision).
+  (margin > 0 moves pairs towards narrower widths, margin < 0 towards wider
+  ones).
 * exponential by lookup table: exp(-t) for t >= 0 from a table of
   exp(-t_k) at t_k = k * step, k = 0..n-1, linearly interpolated; 0 past the
   table. Its error is bounded by step^2 / 8 (the second derivative of exp(-t)

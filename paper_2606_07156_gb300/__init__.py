@@ -15,7 +15,7 @@ from . import abi
 from .abi import AnnsError  # noqa: F401
 
 _MODES = {"plain": abi.LUT_PLAIN_FP32, "fixed": abi.LUT_FIXED_BITS, "eq2": abi.LUT_HEURISTIC_EQ2,
-          "mlp": abi.LUT_MLP, "explicit": abi.LUT_EXPLICIT}
+          "mlp": abi.LUT_MLP, "explicit": abi.LUT_EXPLICIT, "svr": abi.LUT_SVR}
 
 
 def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), margin: float = 0.0,
@@ -197,6 +197,19 @@ class Index:
 
     def get_predictor(self) -> dict:
         return predictor_to_dict(abi.anns_get_predictor(self.handle))
+
+    def set_svr(self, sv, beta, gamma: float, mean, inv_std, table_n: int, table_ratio: float, inv_step: float):
+        """Installs an SVR-RBF model for the 'svr' policy (host arrays: sv [nsv, 5], beta [nsv])."""
+        sv = np.ascontiguousarray(sv, dtype=np.float32)
+        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        m = abi.anns_svr_model()
+        m.nsv, m.sv, m.beta = len(beta), sv.ctypes.data, beta.ctypes.data
+        m.gamma = float(gamma)
+        for i in range(5):
+            m.mean[i] = float(mean[i])
+            m.inv_std[i] = float(inv_std[i])
+        m.table_n, m.table_ratio, m.inv_step = int(table_n), float(table_ratio), float(inv_step)
+        abi.anns_set_svr(self.handle, m)
 
     def make_training_set(self, train_q, nprobe: int, k: int, stream=None):
         """Raw features [nq, nprobe, 5] and label bits [nq, nprobe] (CUDA tensors)."""

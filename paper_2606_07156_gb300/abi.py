@@ -17,7 +17,7 @@ ANNS_OK = 0
 STATIC_SCRATCH_FLOATS = 1 << 21
 MAX_M, MAX_NPROBE, MAX_K = 128, 128, 128
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSUPPORTED"}
-LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT = 0, 1, 2, 3, 4
+LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT, LUT_SVR = 0, 1, 2, 3, 4, 5
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_COARSE_APPROX, TAP_COARSE_CANDIDATES = 4, 5
@@ -32,7 +32,7 @@ SYMBOLS = (
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
     "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
-    "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_sync_status", "anns_last_error",
+    "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_sync_status", "anns_set_svr", "anns_last_error",
 )
 
 
@@ -70,6 +70,12 @@ class anns_predictor(ctypes.Structure):
                 ("mean", ctypes.c_float * 5), ("inv_std", ctypes.c_float * 5)]
 
 
+class anns_svr_model(ctypes.Structure):
+    _fields_ = [("nsv", ctypes.c_int32), ("sv", ctypes.c_void_p), ("beta", ctypes.c_void_p),
+                ("gamma", ctypes.c_float), ("mean", ctypes.c_float * 5), ("inv_std", ctypes.c_float * 5),
+                ("table_n", ctypes.c_int32), ("table_ratio", ctypes.c_double), ("inv_step", ctypes.c_float)]
+
+
 class anns_tune_result(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32), ("ms", ctypes.c_float)]
 
@@ -98,6 +104,7 @@ def _load():
         "anns_kernel_launches": ([], i64),
         "anns_debug_exact_sum": ([vp, i64, i32, vp, vp], i32),
         "anns_sync_status": ([vp, vp], i32),
+        "anns_set_svr": ([vp, ctypes.POINTER(anns_svr_model)], i32),
         "anns_svr_fit": ([vp, vp, i64, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64,
                           vp, ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
@@ -219,6 +226,10 @@ def anns_svr_fit(X, y, C: float, gamma: float, eps: float, tol: float = 1e-10, m
 def anns_kernel_launches() -> int:
     """Kernels the library has enqueued since it was loaded (host-side count)."""
     return int(_lib.anns_kernel_launches())
+
+
+def anns_set_svr(index, model: "anns_svr_model") -> None:
+    _check(_lib.anns_set_svr(index, ctypes.byref(model)))
 
 
 def anns_sync_status(index, stream=None) -> None:

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -77,6 +78,66 @@ __global__ void policy_kernel(const PolicyArgs p) {
         if (p.width_map) b = gpu_width(b);
         break;
     }
+  }
+  p.bits[idx] = b;
+  if (p.feat) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) p.feat[idx * 5 + i] = f[i];
+  }
+}
+
+// SVR-RBF policy (Section 3.4): one thread per pair, the support vectors,
+// coefficients and exponential table staged in shared memory; the FP32 rule
+// of anns_set_svr in anns_amp.h.
+struct SvrArgs {
+  const float* dev;  // [sv nsv*5 | beta nsv | table tn]
+  int nsv, tn;
+  float gamma, inv_step, mean[5], inv_std[5];
+};
+
+__global__ void __launch_bounds__(256) svr_policy_kernel(const PolicyArgs p, const SvrArgs m) {
+  float* s_sv = (float*)anns_dyn_smem;
+  float* s_beta = s_sv + m.nsv * 5;
+  float* s_tab = s_beta + m.nsv;
+  const int total = m.nsv * 6 + m.tn;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) s_sv[i] = m.dev[i];
+  __syncthreads();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p.nq * p.nprobe) return;
+  const int64_t q = idx / p.nprobe;
+  const int j = (int)(idx % p.nprobe);
+  const int np = p.npq ? min(max(p.npq[q], 0), p.nprobe) : p.nprobe;
+  const int l = p.probes[idx];
+  float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  uint8_t b = 0;
+  if (j < np && l >= 0) {
+    features_of(p, q, j, np, f);
+    float x[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) x[c] = mul_rn(sub_rn(f[c], m.mean[c]), m.inv_std[c]);
+    const float ulim = (float)(m.tn - 1);
+    float acc = 0.f;
+    for (int i = 0; i < m.nsv; ++i) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const float e = sub_rn(x[c], s_sv[i * 5 + c]);
+        d2 = add_rn(d2, mul_rn(e, e));
+      }
+      const float u = mul_rn(mul_rn(m.gamma, d2), m.inv_step);
+      float ex = 0.f;
+      if (u < ulim) {
+        const int k = (int)floorf(u);
+        const float w = sub_rn(u, (float)k);
+        ex = add_rn(mul_rn(s_tab[k], sub_rn(1.f, w)), mul_rn(s_tab[k + 1], w));
+      }
+      acc = add_rn(acc, mul_rn(s_beta[i], add_rn(ex, 1.f)));
+    }
+    const float c = ceilf(sub_rn(acc, p.margin));
+    const int wi = c >= 5.f ? 5 : (c > 0.f ? (int)c : 0);
+    constexpr uint8_t kW[6] = {4, 6, 8, 12, 16, 0};
+    b = kW[wi];
+    if (p.width_map) b = gpu_width(b);
   }
   p.bits[idx] = b;
   if (p.feat) {
@@ -194,7 +255,17 @@ int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq,
   p.width_map = pol.width_map;
   p.bits = bits; p.feat = feat;
   const int64_t n = nq * nprobe;
-  policy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p); note_launch();
+  if (pol.lut_mode == ANNS_LUT_SVR) {
+    SvrArgs m{};
+    m.dev = ix.svr_dev; m.nsv = ix.svr_nsv; m.tn = ix.svr_tn; m.gamma = ix.svr_gamma; m.inv_step = ix.svr_inv_step;
+    for (int i = 0; i < 5; ++i) { m.mean[i] = ix.svr_mean[i]; m.inv_std[i] = ix.svr_inv_std[i]; }
+    const size_t smem = (size_t)(m.nsv * 6 + m.tn) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(svr_policy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "svr policy kernel attribute");
+    svr_policy_kernel<<<(unsigned)((n + 255) / 256), 256, smem, s>>>(p, m); note_launch();
+  } else {
+    policy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p); note_launch();
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "policy kernel");
 }
@@ -226,6 +297,10 @@ int anns::check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t 
         if (!ix->has_mlp) return fail(ANNS_ERR_INVALID_ARG, "MLP policy needs a trained or loaded predictor");
         if (std::isnan(pol->fallback_margin)) return fail(ANNS_ERR_INVALID_ARG, "MLP round-up margin is NaN");
         break;
+      case ANNS_LUT_SVR:
+        if (!ix->has_svr) return fail(ANNS_ERR_INVALID_ARG, "SVR policy needs a model (anns_set_svr)");
+        if (std::isnan(pol->fallback_margin)) return fail(ANNS_ERR_INVALID_ARG, "SVR margin is NaN");
+        break;
       default: return fail(ANNS_ERR_INVALID_ARG, "unknown lut_mode");
     }
     if (pol->cl_prec != ANNS_PREC_FP32 && pol->cl_prec != ANNS_PREC_BF16)
@@ -243,7 +318,7 @@ static bool use_grouped(const Index& ix, const anns_precision_policy& P, int k) 
   if (ix.opt_kernel == ANNS_KERNEL_GROUPED) return grouped_supported(ix, k);
   if (ix.opt_kernel != ANNS_KERNEL_AUTO) return false;
   const bool narrow_possible = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2 ||
-                               P.lut_mode == ANNS_LUT_EXPLICIT ||
+                               P.lut_mode == ANNS_LUT_EXPLICIT || P.lut_mode == ANNS_LUT_SVR ||
                                (P.lut_mode == ANNS_LUT_FIXED_BITS && P.fixed_bits <= 8);
   return narrow_possible && grouped_supported(ix, k);
 }
@@ -292,7 +367,8 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
   }
   if (e != cudaSuccess) return cuda_fail(e, "coarse kernels");
   if (ev) cudaEventRecord(ev[2], s);
-  const bool want_feat = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2;
+  const bool want_feat = P.lut_mode == ANNS_LUT_MLP || P.lut_mode == ANNS_LUT_HEURISTIC_EQ2 ||
+                         P.lut_mode == ANNS_LUT_SVR;
   if ((rc = launch_policy(ix, P, nq, nprobe, nprobe_per_q, ix.ws_probes, ix.ws_probe_d2, ix.ws_bits,
                           want_feat ? ix.ws_feat : nullptr, s)))
     return rc;
@@ -506,6 +582,37 @@ extern "C" int anns_profile(anns_index* ix, int32_t enable, double* out_ms, int6
   if (out_ms)
     for (int st = 0; st < Index::kStages; ++st) out_ms[st] = ix->prof_ms[st];
   if (count) *count = ix->prof_count;
+  return ANNS_OK;
+}
+
+extern "C" int anns_set_svr(anns_index* ix, const anns_svr_model* m) {
+  if (!ix || !m) return fail(ANNS_ERR_INVALID_ARG, "null index or model");
+  if (m->nsv < 1 || m->nsv > ANNS_SVR_MAX_SAMPLES) return fail(ANNS_ERR_INVALID_ARG, "nsv out of range");
+  if (m->table_n < 2 || m->table_n > 4096) return fail(ANNS_ERR_INVALID_ARG, "table_n must be in [2, 4096]");
+  if (!(m->table_ratio > 0.0 && m->table_ratio < 1.0)) return fail(ANNS_ERR_INVALID_ARG, "table_ratio must be in (0, 1)");
+  if (!m->sv || !m->beta) return fail(ANNS_ERR_INVALID_ARG, "null support vectors or coefficients");
+  bool finite = std::isfinite(m->gamma) && std::isfinite(m->inv_step);
+  for (int i = 0; i < 5; ++i) finite = finite && std::isfinite(m->mean[i]) && std::isfinite(m->inv_std[i]);
+  for (int64_t i = 0; i < (int64_t)m->nsv * 5 && finite; ++i) finite = std::isfinite(m->sv[i]);
+  for (int i = 0; i < m->nsv && finite; ++i) finite = std::isfinite(m->beta[i]);
+  if (!finite) return fail(ANNS_ERR_INVALID_ARG, "non-finite model parameter");
+  std::vector<float> h((size_t)m->nsv * 6 + m->table_n);
+  std::memcpy(h.data(), m->sv, (size_t)m->nsv * 5 * sizeof(float));
+  std::memcpy(h.data() + (size_t)m->nsv * 5, m->beta, (size_t)m->nsv * sizeof(float));
+  double e = 1.0;  // geometric table: e_k = fl64(e_{k-1} * rho), rounded once to FP32
+  for (int k = 0; k < m->table_n; ++k) {
+    h[(size_t)m->nsv * 6 + k] = (float)e;
+    e = e * m->table_ratio;
+  }
+  DeviceGuard g(ix->device);
+  if (ix->svr_dev) { cudaFree(ix->svr_dev); ix->svr_dev = nullptr; ix->has_svr = false; }
+  cudaError_t ce = cudaMalloc((void**)&ix->svr_dev, h.size() * sizeof(float));
+  if (ce != cudaSuccess) { ix->svr_dev = nullptr; return cuda_fail(ce, "cudaMalloc(svr model)"); }
+  ce = cudaMemcpy(ix->svr_dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) return cuda_fail(ce, "svr model copy");
+  ix->svr_nsv = m->nsv; ix->svr_tn = m->table_n; ix->svr_gamma = m->gamma; ix->svr_inv_step = m->inv_step;
+  for (int i = 0; i < 5; ++i) { ix->svr_mean[i] = m->mean[i]; ix->svr_inv_std[i] = m->inv_std[i]; }
+  ix->has_svr = true;
   return ANNS_OK;
 }
 

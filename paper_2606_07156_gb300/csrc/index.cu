@@ -46,7 +46,7 @@ static void free_index(anns_index* ix) {
   cudaSetDevice(ix->device);
   void* ptrs[] = {ix->centroids, ix->codebooks, ix->codes, ix->ids, ix->list_len,
                   ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->order, ix->mlp_dev,
-                  ix->tc_mu, ix->tc_cb, ix->tc_cn, ix->dev_status};
+                  ix->tc_mu, ix->tc_cb, ix->tc_cn, ix->dev_status, ix->svr_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_workspace(*ix);

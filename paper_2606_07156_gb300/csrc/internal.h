@@ -94,6 +94,11 @@ struct Index {
   bool has_mlp = false;
   void* mlp_dev = nullptr;       // device MlpParams16
   anns_predictor mlp_host{};     // FP32 master copy of the installed predictor
+  // SVR-RBF model (policy ANNS_LUT_SVR): device [sv nsv*5 | beta nsv | table tn] floats
+  bool has_svr = false;
+  float* svr_dev = nullptr;
+  int svr_nsv = 0, svr_tn = 0;
+  float svr_gamma = 0.f, svr_inv_step = 0.f, svr_mean[5] = {}, svr_inv_std[5] = {};
 };
 
 void set_error(const std::string& msg);
