@@ -358,6 +358,40 @@ def roofline_profile(kernel_src: str, workload_name: str):
     return None
 
 
+def index_build_bench(amp, dev, key: str, n: int = 1_000_000, nlist: int = 1024) -> dict:
+    """Index training on the GPU (anns_train_index: k-means, PQ codebooks,
+    encoding, packing) against the PyTorch trainer that builds the
+    benchmark's workloads, on n vectors of the workload's distribution; both
+    indexes are judged by the recall@10 of a plain search (nprobe 16, 1000
+    queries) against exact ground truth."""
+    import torch
+    from workloads import CONFIGS, exact_knn, make_dataset, train_ivfpq
+    cfg = CONFIGS[key]
+    d = make_dataset(key, n=n, nq=1000)
+    gt, _ = exact_knn(d["base"], d["queries"], 10, device=dev)
+    Xd = torch.from_numpy(d["base"]).to(dev)
+    Q = torch.from_numpy(d["queries"]).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = amp.Index.train(Xd, nlist, cfg["M"], iters=10, pq_iters=10, seed=1, per_centroid=256, pq_sample=65536,
+                        device=dev.index)
+    torch.cuda.synchronize()
+    t_gpu = time.perf_counter() - t0
+    ids, _ = g.search(Q, 16, 10, amp.policy("plain"))
+    rec_gpu = recall(ids.cpu().numpy(), gt, 10)
+    g.close()
+    t0 = time.perf_counter()
+    ix = train_ivfpq(d["base"], nlist, cfg["M"], seed=1, device=dev)
+    t_ref = time.perf_counter() - t0
+    h = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=dev.index)
+    ids, _ = h.search(Q, 16, 10, amp.policy("plain"))
+    rec_ref = recall(ids.cpu().numpy(), gt, 10)
+    h.close()
+    return {"workload": f"{cfg['name']} distribution, n={n}, nlist={nlist}, M={cfg['M']}, 10 + 10 iterations",
+            "anns_train_index_s": round(t_gpu, 3), "recall_at_10_nprobe16": round(rec_gpu, 4),
+            "torch_trainer_s": round(t_ref, 3), "torch_trainer_recall_at_10_nprobe16": round(rec_ref, 4)}
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     import __graft_entry__
@@ -631,6 +665,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     line["graph_ms_per_step"] = round(float(np.mean(ms_graph)), 4)
     if not args.no_cl_bench:
         line["cl_fastpath"] = cl_tensor_bench(amp, dev, max(3, args.steps // 4), args.warmup, flush)
+    if not args.no_build_bench and world == 1:
+        line["index_build"] = index_build_bench(amp, dev, args.config)
     if not args.no_cpu_baseline and world == 1:
         ctx = dict(amp=amp, abi=abi, index=index, Q=Q, stream=stream, margin=margin, predictor=predictor_w)
         line.update(oracle_leg(W, cfg, nprobe, args.cpu_seconds, full, ctx))
@@ -891,6 +927,7 @@ def main():
     ap.add_argument("--no-cl-bench", action="store_true", help="skip the coarse-stage comparison")
     ap.add_argument("--no-second-point", action="store_true", help="skip the 1-recall@10 operating point")
     ap.add_argument("--no-svr", action="store_true", help="skip the SVR-RBF comparator")
+    ap.add_argument("--no-build-bench", action="store_true", help="skip the index-training comparison")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

@@ -73,6 +73,63 @@ typedef struct {
  * outside [0, nlist)), OOM, CUDA. *out is set only on success. */
 int anns_build_index_from_arrays(const anns_build_desc* desc, anns_index** out);
 
+/* Index training on the GPU (the offline IVF-PQ index of Section 2.1: Lloyd
+ * k-means for the nlist centroids, k-means of 256 entries per sub-space on
+ * the residuals for the PQ codebooks, then every vector's list and codes).
+ * The paper fixes none of the following; they make training a deterministic
+ * function of (base, desc), identical however the GPU schedules its threads:
+ *   sample: row i is drawn when the SplitMix64 output of the state
+ *     seed + (i + 1) * 0x9E3779B97F4A7C15 (mod 2^64) is below
+ *     floor(target * 2^64 / n), target = nlist * per_centroid (every row
+ *     when target >= n); drawn rows keep their order;
+ *   k-means over S rows and k clusters: initial centroid j = sample row
+ *     floor(j * S / k); each of `iters` iterations assigns every row to its
+ *     nearest centroid by the FP32 distance rule of CL (ties to the lower
+ *     index), sets each coordinate of a centroid with members to the exact
+ *     sum of the members' FP32 values rounded once to FP32, divided (one IEEE
+ *     FP32 division) by the member count, and gives the e-th empty centroid
+ *     (ascending) the e-th farthest row from its centroid (ties to the lower
+ *     row);
+ *   PQ: a second sample of pq_sample rows (seed + 1), the residuals
+ *     fl32(x - c) to their nearest centroid, one k-means of 256 clusters and
+ *     pq_iters iterations per sub-space on that sub-space's coordinates;
+ *   encoding: each row's nearest centroid, then per sub-space the nearest
+ *     entry to the residual's sub-vector (FP32 rule, ties to the lower entry).
+ * The index is then built as by anns_build_index_from_arrays (ids = row
+ * index).
+ *  base  float32 [n * dim], host (on_device = 0) or device memory.
+ * Synchronous. Errors: INVALID_ARG (dim % M != 0, M > 128, dim / M > 16,
+ * nlist > n, n >= 2^31, nlist > 2^20, iters < 0, per_centroid < 1,
+ * pq_sample < 256, a sample smaller than its cluster count), OOM, CUDA. */
+typedef struct {
+  int64_t nlist, M;
+  int32_t iters, pq_iters;
+  uint64_t seed;
+  int64_t per_centroid;   /* coarse sample = nlist * per_centroid rows */
+  int64_t pq_sample;      /* rows whose residuals train the codebooks */
+} anns_train_desc;
+int anns_train_index(const float* base, int64_t n, int64_t dim, const anns_train_desc* desc,
+                     int32_t on_device, int32_t device, anns_index** out);
+
+/* The index's arrays, in list order, into host buffers (each may be NULL):
+ *  centroids float [nlist * dim], codebooks float [M * 256 * dsub],
+ *  codes uint8 [n * M] (row-major per vector), ids int64 [n] (the ids the
+ *  search returns), list_len int64 [nlist] (vectors per list; list l's
+ *  vectors follow list l-1's). Synchronous. Errors: INVALID_ARG, CUDA. */
+int anns_export_index(anns_index* index, float* centroids, float* codebooks, uint8_t* codes, int64_t* ids,
+                      int64_t* list_len);
+
+/* Saves the index to a file and loads it back (no counterpart in the paper).
+ * The file holds the shapes, the arrays of anns_export_index, the installed
+ * MLP predictor and SVR model if any, and a 64-bit FNV-1a checksum of all
+ * preceding bytes; it is little-endian. anns_load builds the index on
+ * `device` as anns_build_index_from_arrays would from those arrays, then
+ * installs the predictor and the SVR model: every search returns what the
+ * saved index returned. Errors: INVALID_ARG (null argument, unreadable or
+ * corrupt file: bad magic, version, shape or checksum), OOM, CUDA. */
+int anns_save(anns_index* index, const char* path);
+int anns_load(const char* path, int32_t device, anns_index** out);
+
 /* Frees the index and all device memory it owns. NULL is a no-op. */
 void anns_free(anns_index* index);
 

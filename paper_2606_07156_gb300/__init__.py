@@ -112,6 +112,47 @@ class Index:
         self.info = abi.anns_get_info(self.handle)
         self.dim, self.nlist, self.M = self.info.dim, self.info.nlist, self.info.M
 
+    @classmethod
+    def _wrap(cls, handle: int, device: int) -> "Index":
+        self = cls.__new__(cls)
+        self.device = device
+        self.handle = handle
+        self.info = abi.anns_get_info(self.handle)
+        self.dim, self.nlist, self.M = self.info.dim, self.info.nlist, self.info.M
+        return self
+
+    @classmethod
+    def train(cls, base, nlist: int, M: int, iters: int = 10, pq_iters: int = 10, seed: int = 0,
+              per_centroid: int = 256, pq_sample: int = 65536, device: int = 0) -> "Index":
+        """Trains and builds an index on the GPU (anns_train_index). ``base`` is a
+        float32 numpy array or CUDA tensor [n, dim]."""
+        d = abi.anns_train_desc()
+        d.nlist, d.M, d.iters, d.pq_iters, d.seed = nlist, M, iters, pq_iters, seed
+        d.per_centroid, d.pq_sample = per_centroid, pq_sample
+        if isinstance(base, np.ndarray):
+            base = np.ascontiguousarray(base, dtype=np.float32)
+            h = abi.anns_train_index(base.ctypes.data, base.shape[0], base.shape[1], d, 0, device)
+        else:
+            h = abi.anns_train_index(base.data_ptr(), base.shape[0], base.shape[1], d, 1, device)
+        return cls._wrap(h, device)
+
+    @classmethod
+    def load(cls, path: str, device: int = 0) -> "Index":
+        return cls._wrap(abi.anns_load(path, device), device)
+
+    def save(self, path: str) -> None:
+        abi.anns_save(self.handle, path)
+
+    def export(self) -> dict:
+        """The index's arrays in list order (anns_export_index)."""
+        n, dim, nlist, M = self.info.n, self.dim, self.nlist, self.M
+        out = dict(centroids=np.empty((nlist, dim), np.float32),
+                   codebooks=np.empty((M, 256, dim // M), np.float32),
+                   codes=np.empty((n, M), np.uint8), ids=np.empty(n, np.int64), list_len=np.empty(nlist, np.int64))
+        abi.anns_export_index(self.handle, *(out[k].ctypes.data for k in
+                                             ("centroids", "codebooks", "codes", "ids", "list_len")))
+        return out
+
     def close(self):
         if getattr(self, "handle", None):
             abi.anns_free(self.handle)

@@ -32,7 +32,8 @@ SYMBOLS = (
     "anns_set_option", "anns_locate_static", "anns_set_predictor", "anns_get_predictor",
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
     "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
-    "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_sync_status", "anns_set_svr", "anns_last_error",
+    "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_sync_status", "anns_set_svr", "anns_train_index", "anns_export_index", "anns_save",
+    "anns_load", "anns_last_error",
 )
 
 
@@ -76,6 +77,12 @@ class anns_svr_model(ctypes.Structure):
                 ("table_n", ctypes.c_int32), ("table_ratio", ctypes.c_double), ("inv_step", ctypes.c_float)]
 
 
+class anns_train_desc(ctypes.Structure):
+    _fields_ = [("nlist", ctypes.c_int64), ("M", ctypes.c_int64), ("iters", ctypes.c_int32),
+                ("pq_iters", ctypes.c_int32), ("seed", ctypes.c_uint64), ("per_centroid", ctypes.c_int64),
+                ("pq_sample", ctypes.c_int64)]
+
+
 class anns_tune_result(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32), ("ms", ctypes.c_float)]
 
@@ -105,6 +112,10 @@ def _load():
         "anns_debug_exact_sum": ([vp, i64, i32, vp, vp], i32),
         "anns_sync_status": ([vp, vp], i32),
         "anns_set_svr": ([vp, ctypes.POINTER(anns_svr_model)], i32),
+        "anns_train_index": ([vp, i64, i64, ctypes.POINTER(anns_train_desc), i32, i32, ctypes.POINTER(vp)], i32),
+        "anns_export_index": ([vp, vp, vp, vp, vp, vp], i32),
+        "anns_save": ([vp, ctypes.c_char_p], i32),
+        "anns_load": ([ctypes.c_char_p, i32, ctypes.POINTER(vp)], i32),
         "anns_svr_fit": ([vp, vp, i64, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64,
                           vp, ctypes.POINTER(i64)], i32),
         "anns_set_option": ([vp, i32, i64], i32),
@@ -226,6 +237,26 @@ def anns_svr_fit(X, y, C: float, gamma: float, eps: float, tol: float = 1e-10, m
 def anns_kernel_launches() -> int:
     """Kernels the library has enqueued since it was loaded (host-side count)."""
     return int(_lib.anns_kernel_launches())
+
+
+def anns_train_index(base_ptr, n, dim, desc: "anns_train_desc", on_device: int, device: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.anns_train_index(base_ptr, n, dim, ctypes.byref(desc), on_device, device, ctypes.byref(h)))
+    return h.value
+
+
+def anns_export_index(index, centroids, codebooks, codes, ids, list_len) -> None:
+    _check(_lib.anns_export_index(index, centroids, codebooks, codes, ids, list_len))
+
+
+def anns_save(index, path: str) -> None:
+    _check(_lib.anns_save(index, path.encode()))
+
+
+def anns_load(path: str, device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.anns_load(path.encode(), device, ctypes.byref(h)))
+    return h.value
 
 
 def anns_set_svr(index, model: "anns_svr_model") -> None:

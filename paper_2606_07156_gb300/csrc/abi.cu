@@ -611,6 +611,8 @@ extern "C" int anns_set_svr(anns_index* ix, const anns_svr_model* m) {
   ce = cudaMemcpy(ix->svr_dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) return cuda_fail(ce, "svr model copy");
   ix->svr_nsv = m->nsv; ix->svr_tn = m->table_n; ix->svr_gamma = m->gamma; ix->svr_inv_step = m->inv_step;
+  ix->svr_ratio = m->table_ratio;
+  ix->svr_host.assign(h.begin(), h.begin() + (size_t)m->nsv * 6);
   for (int i = 0; i < 5; ++i) { ix->svr_mean[i] = m->mean[i]; ix->svr_inv_std[i] = m->inv_std[i]; }
   ix->has_svr = true;
   return ANNS_OK;

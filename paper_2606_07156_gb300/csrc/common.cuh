@@ -96,10 +96,11 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 
 // ---- exact sum of FP32 values, rounded once --------------------------------
 // Every finite FP32 value is an integer multiple of 2^-149 of magnitude below
-// 2^277 * 2^-149, so a sum of fewer than 2^10 of them is N * 2^-149 with an
-// integer |N| < 2^287. N is held as nine base-2^32 digits, each in a 64-bit
-// accumulator whose carries are propagated only once, at the end (a digit
-// receives at most two 32-bit pieces per value). Integer addition is
+// 2^277 * 2^-149, so a sum of them is N * 2^-149 with an integer N. N is held
+// as nine base-2^32 digits, each in a 64-bit accumulator whose carries are
+// propagated only once, at the end (a digit receives at most two 32-bit
+// pieces per value, so fewer than 2^31 values fit). A sum with |N| >= 2^287
+// is beyond the FP32 range and rounds to infinity. Integer addition is
 // associative, so lanes may add their values in any order and combine by any
 // reduction tree: the rounded result is the exact sum's nearest FP32 value
 // (ties to even), whatever the order. Non-finite values are summed apart in
@@ -163,6 +164,10 @@ __device__ __forceinline__ float xsum_round(const ExactSum& a) {
     g[k] = (uint32_t)(t & 0xffffffffll);
     c = t >> 32;  // arithmetic shift: the floor of t / 2^32
   }
+  // |N| >= 2^288 (a carry beyond the top digit): the value exceeds 2^139, far
+  // past the largest FP32 value, so it rounds to infinity of its sign
+  if (c > 0) return INFINITY;
+  if (c < -1) return -INFINITY;
   const bool neg = c < 0;
   if (neg) {  // |N| = two's complement of the 288-bit pattern
     unsigned long long carry = 1;

@@ -99,6 +99,8 @@ struct Index {
   float* svr_dev = nullptr;
   int svr_nsv = 0, svr_tn = 0;
   float svr_gamma = 0.f, svr_inv_step = 0.f, svr_mean[5] = {}, svr_inv_std[5] = {};
+  double svr_ratio = 0.0;
+  std::vector<float> svr_host;   // [sv nsv*5 | beta nsv]: the installed model, for anns_save
 };
 
 void set_error(const std::string& msg);

@@ -83,3 +83,32 @@ def test_exact_sum_tap_rejects_bad_sizes(abi):
     with pytest.raises(abi.AnnsError, match="n < 1024"):
         abi.anns_debug_exact_sum(None, 1, 1024, None)
     abi.anns_debug_exact_sum(None, 0, 5, None)   # nothing to do: no launch
+
+
+def test_load_rejects_bad_files_without_a_gpu(abi, tmp_path):
+    """anns_load checks the checksum, magic and shapes before any device call."""
+    p = tmp_path / "bad.anns"
+    with pytest.raises(abi.AnnsError, match="cannot open"):
+        abi.anns_load(str(tmp_path / "missing.anns"))
+    p.write_bytes(b"short")
+    with pytest.raises(abi.AnnsError, match="too short"):
+        abi.anns_load(str(p))
+    import struct
+    body = b"ANNSAMP1" + struct.pack("<II", 1, 0) + struct.pack("<qqqq", 10, 8, 2, 4) + b"\0" * 64
+
+    def fnv(b):
+        h = 0xcbf29ce484222325
+        for x in b:
+            h = ((h ^ x) * 0x100000001b3) & ((1 << 64) - 1)
+        return h
+
+    p.write_bytes(body + struct.pack("<Q", fnv(body) ^ 1))
+    with pytest.raises(abi.AnnsError, match="checksum"):
+        abi.anns_load(str(p))
+    bad = b"NOTANNS!" + body[8:]
+    p.write_bytes(bad + struct.pack("<Q", fnv(bad)))
+    with pytest.raises(abi.AnnsError, match="magic"):
+        abi.anns_load(str(p))
+    p.write_bytes(body + struct.pack("<Q", fnv(body)))
+    with pytest.raises(abi.AnnsError, match="shorter than its shapes"):
+        abi.anns_load(str(p))
