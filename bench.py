@@ -392,6 +392,60 @@ def index_build_bench(amp, dev, key: str, n: int = 1_000_000, nlist: int = 1024)
             "torch_trainer_s": round(t_ref, 3), "torch_trainer_recall_at_10_nprobe16": round(rec_ref, 4)}
 
 
+SUBSPACE_TH = (4.0, 2.0, 1.0)   # Eq. 2 thresholds of g for 2, 4 and 6 bits at the sub-space level
+
+
+def subspace_sweep(amp, index, W, cfg, nprobe: int, k: int, dev, nq: int = 2000) -> dict:
+    """The paper's sub-space granularity (Section 5.3, Fig. 13): for a sweep
+    of dimension slices S and sub-spaces per slice K, the share of CL partial
+    distances computed below 8 bits and the recall@10 of the search whose CL
+    runs at sub-space precision (FP32 LUT after it); then LC at sub-space
+    precision (codebook-entry groups, integer tables) on the FP32 probes.
+    Judged against plain FP32 on the same queries."""
+    import torch
+    Q = torch.from_numpy(W["queries"][:nq]).to(dev)
+    gt = W["gt"][:nq]
+    dim, nlist = cfg["dim"], cfg["nlist"]
+    ids, _ = index.search(Q, nprobe, k, amp.policy("plain"))
+    base = recall(ids.cpu().numpy(), gt, 10)
+    slices = [s for s in (1, 2, 4, 8, 16, 32) if dim % s == 0]
+    Ks = [kk for kk in (64, 128, 256, 512) if kk <= nlist]
+    rows = []
+
+    def one(S, K):
+        index.build_subspaces(S, K, 16, iters=10)
+        torch.cuda.synchronize()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        ids, _, low = index.search_subspace(Q, nprobe, k, SUBSPACE_TH, SUBSPACE_TH, cl=True, lc=False)
+        ev[1].record()
+        torch.cuda.synchronize()
+        low = low.cpu().numpy()
+        return {"slices": S, "K": K, "cl_low_share": round(float(low[0]) / (nq * nlist * S), 4),
+                "recall_at_10": round(recall(ids.cpu().numpy(), gt, 10), 4),
+                "recall_loss_pts": round(100.0 * (base - recall(ids.cpu().numpy(), gt, 10)), 3),
+                "ms": round(ev[0].elapsed_time(ev[1]), 3)}
+
+    for S in slices:
+        rows.append(one(S, 256 if 256 <= nlist else Ks[-1]))
+    S16 = 16 if dim % 16 == 0 else slices[-1]
+    for K in Ks:
+        if K != 256:
+            rows.append(one(S16, K))
+    index.build_subspaces(S16, 256 if 256 <= nlist else Ks[-1], 16, iters=10)
+    ids, _, low = index.search_subspace(Q, nprobe, k, SUBSPACE_TH, SUBSPACE_TH, cl=False, lc=True)
+    torch.cuda.synchronize()
+    low = low.cpu().numpy()
+    lc_rec = recall(ids.cpu().numpy(), gt, 10)
+    ids, _, _ = index.search_subspace(Q, nprobe, k, (np.inf,) * 3, (np.inf,) * 3, cl=False, lc=True)
+    lc8_rec = recall(ids.cpu().numpy(), gt, 10)
+    return {"queries": nq, "nprobe": nprobe, "thresholds_2_4_6_bits": list(SUBSPACE_TH),
+            "plain_fp32_recall_at_10": round(base, 4), "cl": rows,
+            "lc": {"K_lc": 16, "low_share": round(float(low[1]) / (nq * nprobe * cfg["M"] * 256), 4),
+                   "recall_at_10": round(lc_rec, 4), "recall_at_10_all_8bit": round(lc8_rec, 4),
+                   "note": "integer tables of uint8 operands (the codebook's map); all-8-bit is the map's own loss"}}
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     import __graft_entry__
@@ -665,6 +719,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     line["graph_ms_per_step"] = round(float(np.mean(ms_graph)), 4)
     if not args.no_cl_bench:
         line["cl_fastpath"] = cl_tensor_bench(amp, dev, max(3, args.steps // 4), args.warmup, flush)
+    if not args.no_subspace and world == 1:
+        line["subspace_granularity"] = subspace_sweep(amp, index, W, cfg, nprobe, k, dev)
     if not args.no_build_bench and world == 1:
         line["index_build"] = index_build_bench(amp, dev, args.config)
     if not args.no_cpu_baseline and world == 1:
@@ -928,6 +984,7 @@ def main():
     ap.add_argument("--no-second-point", action="store_true", help="skip the 1-recall@10 operating point")
     ap.add_argument("--no-svr", action="store_true", help="skip the SVR-RBF comparator")
     ap.add_argument("--no-build-bench", action="store_true", help="skip the index-training comparison")
+    ap.add_argument("--no-subspace", action="store_true", help="skip the sub-space granularity sweep")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

@@ -130,6 +130,65 @@ int anns_export_index(anns_index* index, float* centroids, float* codebooks, uin
 int anns_save(anns_index* index, const char* path);
 int anns_load(const char* path, int32_t device, anns_index** out);
 
+/* The paper's sub-space precision granularity (Section 3.2: the dimensions
+ * cut into slices and, inside each slice, the vectors clustered into
+ * sub-spaces; Section 3.3: features per sub-space; Section 4.2: precision as
+ * the operands' most significant bits; Section 5.3, Fig. 13: slices x
+ * sub-spaces per slice in CL, and LC alike). anns_build_subspaces partitions
+ * the index's centroids and codebooks:
+ *   CL: slice s (`slices` slices of dim / slices consecutive dimensions) of
+ *     the nlist centroids into K sub-spaces; LC: the 256 entries of each
+ *     codebook m into K_lc groups; both by the k-means rules of
+ *     anns_train_index (`iters` iterations) on the GPU. Per sub-space: its
+ *     centre, size, and covering radius (FP64, squares summed over dimensions
+ *     in ascending order, square root, rounded to FP32).
+ *   uint8 maps: x8 = clamp(rint(fl32(fl32(x - lo) * inv)), 0, 255) (half to
+ *     even), inv = fl32(255 / fl32(hi - lo)); CL: lo / hi = the smallest /
+ *     largest centroid coordinate (queries use the same map); LC: the
+ *     codebook's, applied to residuals fl32(q - c).
+ * Errors: INVALID_ARG (slices not dividing dim, dim > 4096, K outside
+ * [1, min(nlist, 1024)], slices * K > 16384, K_lc outside [1, 256]), OOM,
+ * CUDA. Synchronous; replaces earlier partitions. */
+typedef struct {
+  int32_t slices, K, K_lc, iters;
+} anns_subspace_desc;
+int anns_build_subspaces(anns_index* index, const anns_subspace_desc* desc);
+
+/* Sizes of the sub-spaces (host int64 [slices * K] and [M * K_lc], either NULL). */
+int anns_subspace_sizes(anns_index* index, int64_t* cl_size, int64_t* lc_size);
+
+/* A search whose CL and/or LC + DC run at sub-space precision.
+ * Bits per (query, slice, sub-space) (CL; in LC per (pair, codebook m,
+ * group)): with D_k the FP32-rule squared distance from the query's slice
+ * (the pair's residual sub-vector) to centre k, d_k = fl32(sqrt(D_k)), k1 the
+ * nearest centre (ties to the lower index), g = fl32(fl32(fl32(fl32(d_k -
+ * d_k1) - fl32(3 r_k1)) - r_k) / r_k) (Eq. 2 with the distance measured
+ * beyond the nearest sub-space; -inf when r_k = 0): 2 bits if g >= th[0],
+ * else 4 if g >= th[1], else 6 if g >= th[2], else 8. Keeping b bits:
+ * x_b = (x8 >> (8 - b)) << (8 - b).
+ *  cl != 0: D2_int[l] = sum over slices and their dimensions of
+ *    (q_b - c_b)^2, b the bits of (query, slice, sub-space of c_l's slice);
+ *    the nprobe smallest (D2_int, l) are probed, ordered by their FP32-rule
+ *    coarse distance. cl == 0: the FP32 CL of anns_search.
+ *  lc != 0: T_int[m][c] = sum over the sub-vector's dimensions of
+ *    (r_b - y_b)^2, b the bits of (pair, m, group of entry c); a vector's
+ *    distance is S = sum_m T_int[m][code_m] (exact), the top-k by (S, id),
+ *    reported as fl32(fl32(S) * fl32(1 / inv^2)). lc == 0: the plain FP32
+ *    LUT of anns_search on the probed lists.
+ *  low_counts: device uint64 [2] or NULL; atomically increased by the number
+ *    of (query, list, slice) partial distances (CL) and of table entries
+ *    (LC) computed below 8 bits.
+ * Queries, ids_out and dists_out as for anns_search (device). Asynchronous
+ * on cuda_stream. Errors: INVALID_ARG (no partitions, NaN threshold, as
+ * anns_search), CUDA. */
+typedef struct {
+  float th_cl[3], th_lc[3];
+  int32_t cl, lc;
+} anns_subspace_policy;
+int anns_search_subspace(anns_index* index, const float* queries, int64_t nq, int32_t nprobe, int32_t k,
+                         const anns_subspace_policy* policy, int64_t* ids_out, float* dists_out,
+                         unsigned long long* low_counts, void* cuda_stream);
+
 /* Frees the index and all device memory it owns. NULL is a no-op. */
 void anns_free(anns_index* index);
 

@@ -21,7 +21,8 @@ Readings (the paper states none of these):
   of codebook m are clustered into K_lc groups the same way.
 * Statistics per sub-space: its centre (the k-means centroid), its size n
   (members) and its covering radius r = max over members of the distance to
-  the centre (FP64, rounded to FP32).
+  the centre (FP64: squares summed over dimensions in ascending order, IEEE
+  square root, rounded to FP32).
 * Operands in uint8 fixed point: x8 = clamp(rint(fl32(fl32(x - lo) * inv)),
   0, 255) (round half to even) with inv = fl32(255 / fl32(hi - lo)); in CL,
   lo / hi are the smallest / largest centroid coordinate, and queries use the
@@ -83,7 +84,11 @@ def partition(X: np.ndarray, K: int, iters: int) -> dict:
     for k in range(K):
         mem = X[a == k].astype(F64)
         if len(mem):
-            rad[k] = np.sqrt(((mem - C[k].astype(F64)) ** 2).sum(1)).max()
+            acc = np.zeros(len(mem), F64)          # FP64 sum over dimensions, ascending
+            for j in range(X.shape[1]):
+                e = mem[:, j] - F64(C[k, j])
+                acc = acc + e * e
+            rad[k] = np.sqrt(acc).max()
     return dict(centres=C, assign=a, size=size, radius=rad.astype(F32))
 
 

@@ -140,6 +140,28 @@ class Index:
     def load(cls, path: str, device: int = 0) -> "Index":
         return cls._wrap(abi.anns_load(path, device), device)
 
+    def build_subspaces(self, slices: int, K: int, K_lc: int, iters: int = 10) -> None:
+        """The paper's sub-space partitions of the centroids and codebooks (anns_build_subspaces)."""
+        d = abi.anns_subspace_desc()
+        d.slices, d.K, d.K_lc, d.iters = slices, K, K_lc, iters
+        abi.anns_build_subspaces(self.handle, d)
+
+    def search_subspace(self, queries, nprobe: int, k: int, th_cl=(np.inf,) * 3, th_lc=(np.inf,) * 3,
+                        cl: bool = True, lc: bool = True, stream=None):
+        """Search at sub-space precision; returns (ids, dists, low-precision counts [CL, LC])."""
+        import torch
+        nq = queries.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+        low = torch.zeros(2, dtype=torch.int64, device=queries.device)
+        p = abi.anns_subspace_policy()
+        for i in range(3):
+            p.th_cl[i], p.th_lc[i] = float(th_cl[i]), float(th_lc[i])
+        p.cl, p.lc = int(cl), int(lc)
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        abi.anns_search_subspace(self.handle, _ptr(queries), nq, nprobe, k, p, _ptr(ids), _ptr(dists), _ptr(low), s)
+        return ids, dists, low
+
     def save(self, path: str) -> None:
         abi.anns_save(self.handle, path)
 

@@ -33,7 +33,7 @@ SYMBOLS = (
     "anns_make_training_set", "anns_mlp_grad", "anns_mlp_train", "anns_train_predictor",
     "anns_graph_capture", "anns_graph_launch", "anns_graph_free", "anns_autotune", "anns_locate",
     "anns_kernel_launches", "anns_svr_fit", "anns_debug_exact_sum", "anns_sync_status", "anns_set_svr", "anns_train_index", "anns_export_index", "anns_save",
-    "anns_load", "anns_last_error",
+    "anns_load", "anns_build_subspaces", "anns_subspace_sizes", "anns_search_subspace", "anns_last_error",
 )
 
 
@@ -83,6 +83,15 @@ class anns_train_desc(ctypes.Structure):
                 ("pq_sample", ctypes.c_int64)]
 
 
+class anns_subspace_desc(ctypes.Structure):
+    _fields_ = [("slices", ctypes.c_int32), ("K", ctypes.c_int32), ("K_lc", ctypes.c_int32), ("iters", ctypes.c_int32)]
+
+
+class anns_subspace_policy(ctypes.Structure):
+    _fields_ = [("th_cl", ctypes.c_float * 3), ("th_lc", ctypes.c_float * 3), ("cl", ctypes.c_int32),
+                ("lc", ctypes.c_int32)]
+
+
 class anns_tune_result(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32), ("ms", ctypes.c_float)]
 
@@ -115,6 +124,9 @@ def _load():
         "anns_train_index": ([vp, i64, i64, ctypes.POINTER(anns_train_desc), i32, i32, ctypes.POINTER(vp)], i32),
         "anns_export_index": ([vp, vp, vp, vp, vp, vp], i32),
         "anns_save": ([vp, ctypes.c_char_p], i32),
+        "anns_build_subspaces": ([vp, ctypes.POINTER(anns_subspace_desc)], i32),
+        "anns_subspace_sizes": ([vp, vp, vp], i32),
+        "anns_search_subspace": ([vp, vp, i64, i32, i32, ctypes.POINTER(anns_subspace_policy), vp, vp, vp, vp], i32),
         "anns_load": ([ctypes.c_char_p, i32, ctypes.POINTER(vp)], i32),
         "anns_svr_fit": ([vp, vp, i64, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i64,
                           vp, ctypes.POINTER(i64)], i32),
@@ -247,6 +259,20 @@ def anns_train_index(base_ptr, n, dim, desc: "anns_train_desc", on_device: int, 
 
 def anns_export_index(index, centroids, codebooks, codes, ids, list_len) -> None:
     _check(_lib.anns_export_index(index, centroids, codebooks, codes, ids, list_len))
+
+
+def anns_build_subspaces(index, desc: "anns_subspace_desc") -> None:
+    _check(_lib.anns_build_subspaces(index, ctypes.byref(desc)))
+
+
+def anns_subspace_sizes(index, cl_size, lc_size) -> None:
+    _check(_lib.anns_subspace_sizes(index, cl_size, lc_size))
+
+
+def anns_search_subspace(index, queries, nq, nprobe, k, policy: "anns_subspace_policy", ids_out, dists_out,
+                         low_counts=None, stream=None) -> None:
+    _check(_lib.anns_search_subspace(index, queries, nq, nprobe, k, ctypes.byref(policy), ids_out, dists_out,
+                                     low_counts, stream))
 
 
 def anns_save(index, path: str) -> None:

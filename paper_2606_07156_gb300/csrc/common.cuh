@@ -19,29 +19,35 @@ template <> struct IdMax<int32_t> { static __device__ __forceinline__ int32_t v(
 template <> struct IdMax<int64_t> { static __device__ __forceinline__ int64_t v() { return INT64_MAX; } };
 
 // Strict order on (distance, id): the tie rule of the top-k selection.
-template <typename IdT>
-__device__ __forceinline__ bool key_less(float d1, IdT i1, float d2, IdT i2) {
+template <typename DT, typename IdT>
+__device__ __forceinline__ bool key_less(DT d1, IdT i1, DT d2, IdT i2) {
   return d1 < d2 || (d1 == d2 && i1 < i2);
 }
+
+// Largest value of a distance type: the empty entry of a top-k list.
+template <typename DT> struct DMax;
+template <> struct DMax<float> { static __device__ __forceinline__ float v() { return INFINITY; } };
+template <> struct DMax<uint32_t> { static __device__ __forceinline__ uint32_t v() { return 0xFFFFFFFFu; } };
 
 // A warp-wide sorted list of the R*32 smallest (distance, id) keys seen so far
 // (the priority queue of the TSM, Section 4.1, initialised to the maximum).
 // Entry e = r*32 + lane lives in register slot r of lane `lane`; entries are
 // ascending in e. All methods must be called by the whole warp with
-// warp-uniform arguments.
-template <int R, typename IdT>
+// warp-uniform arguments. DT is the distance type (FP32, or exact integer
+// distances).
+template <int R, typename IdT, typename DT = float>
 struct WarpTopK {
-  float d[R];
+  DT d[R];
   IdT id[R];
 
   __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int r = 0; r < R; ++r) { d[r] = INFINITY; id[r] = IdMax<IdT>::v(); }
+    for (int r = 0; r < R; ++r) { d[r] = DMax<DT>::v(); id[r] = IdMax<IdT>::v(); }
   }
 
   // Entry e (warp-uniform e < R*32), broadcast to all lanes.
-  __device__ __forceinline__ void get(int e, float& od, IdT& oid) const {
-    float vd = d[0];
+  __device__ __forceinline__ void get(int e, DT& od, IdT& oid) const {
+    DT vd = d[0];
     IdT vi = id[0];
 #pragma unroll
     for (int r = 1; r < R; ++r) if ((e >> 5) == r) { vd = d[r]; vi = id[r]; }
@@ -50,17 +56,17 @@ struct WarpTopK {
   }
 
   // Inserts (cd, cid) in order; the last entry falls off.
-  __device__ __forceinline__ void insert(float cd, IdT cid) {
+  __device__ __forceinline__ void insert(DT cd, IdT cid) {
     const int lane = threadIdx.x & 31;
     int pos = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) pos += __popc(__ballot_sync(kFull, key_less(d[r], id[r], cd, cid)));
 #pragma unroll
     for (int r = R - 1; r >= 0; --r) {
-      float ud = __shfl_up_sync(kFull, d[r], 1);
+      DT ud = __shfl_up_sync(kFull, d[r], 1);
       IdT ui = __shfl_up_sync(kFull, id[r], 1);
       if (r > 0) {
-        float cdd = __shfl_sync(kFull, d[r - 1], 31);
+        DT cdd = __shfl_sync(kFull, d[r - 1], 31);
         IdT cii = __shfl_sync(kFull, id[r - 1], 31);
         if (lane == 0) { ud = cdd; ui = cii; }
       }
@@ -72,12 +78,12 @@ struct WarpTopK {
 
   // Offers one candidate per lane (valid lanes only); keeps the k smallest.
   // thd/thi hold entry k-1 on entry and are updated.
-  __device__ __forceinline__ void offer(bool valid, float cd, IdT cid, int k, float& thd, IdT& thi) {
+  __device__ __forceinline__ void offer(bool valid, DT cd, IdT cid, int k, DT& thd, IdT& thi) {
     unsigned mask = __ballot_sync(kFull, valid && key_less(cd, cid, thd, thi));
     while (mask) {
       const int src = __ffs(mask) - 1;
       mask &= mask - 1;
-      const float bd = __shfl_sync(kFull, cd, src);
+      const DT bd = __shfl_sync(kFull, cd, src);
       const IdT bi = __shfl_sync(kFull, cid, src);
       if (key_less(bd, bi, thd, thi)) {
         insert(bd, bi);

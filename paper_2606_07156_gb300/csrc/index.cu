@@ -50,6 +50,7 @@ static void free_index(anns_index* ix) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_workspace(*ix);
+  free_subspaces(*ix);
   for (auto& set : ix->prof_ev)
     for (cudaEvent_t e : set)
       if (e) cudaEventDestroy(e);

@@ -11,6 +11,8 @@
 
 namespace anns {
 
+struct Subspaces;  // sub-space partitions (subspace.cu)
+
 constexpr int kKsub = 256;
 constexpr int kTileVecs = 32;         // vectors per code tile (one per lane)
 constexpr int kChunkBytes = 16;       // code bytes a lane loads at once
@@ -101,7 +103,10 @@ struct Index {
   float svr_gamma = 0.f, svr_inv_step = 0.f, svr_mean[5] = {}, svr_inv_std[5] = {};
   double svr_ratio = 0.0;
   std::vector<float> svr_host;   // [sv nsv*5 | beta nsv]: the installed model, for anns_save
+  Subspaces* ss = nullptr;       // the paper's sub-space partitions (anns_build_subspaces)
 };
+
+void free_subspaces(Index& ix);
 
 void set_error(const std::string& msg);
 // Counts one kernel launch enqueued by the library (host side; a launch into a
@@ -202,6 +207,13 @@ cudaError_t launch_scan_pairs(const Index& ix, const float* Q, const float* qt, 
                               const int32_t* pq, const int32_t* pl, const uint8_t* pb,
                               int64_t npairs, const int64_t* off, float* dist_out, int32_t* S_out,
                               cudaStream_t s);
+
+// Index training (train.cu): Lloyd k-means of the S rows of X [S x dim]
+// (device) into C [k x dim] (device), and the nearest centroid of each row
+// (FP32 rule, ties to the lower index) with its distance.
+int kmeans(const float* X, int64_t S, int64_t dim, int64_t k, int iters, float* C, cudaStream_t s);
+int nearest(const float* X, int64_t nrows, int64_t dim, const float* C, int64_t k, int32_t* a, float* dist,
+            cudaStream_t s);
 
 }  // namespace anns
 

@@ -203,6 +203,8 @@ struct DevBuf {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+}  // namespace
+
 // Nearest centroid of rows X[0..nrows) (FP32 rule, ties to the lower index),
 // chunked so that the distance matrix stays under about 1 GB.
 int nearest(const float* X, int64_t nrows, int64_t dim, const float* C, int64_t k, int32_t* a, float* dist,
@@ -220,6 +222,8 @@ int nearest(const float* X, int64_t nrows, int64_t dim, const float* C, int64_t 
   }
   return ANNS_OK;
 }
+
+namespace {
 
 // Rows of an n-row matrix drawn for a sample of `target` (ascending); *S is
 // the count. rows must hold n entries.
@@ -245,6 +249,8 @@ int sample(int64_t n, int64_t target, uint64_t seed, int64_t* rows, int64_t* S, 
   *S = tot;
   return ANNS_OK;
 }
+
+}  // namespace
 
 // Lloyd k-means of the S rows of X (device, [S x dim]) into C [k x dim].
 int kmeans(const float* X, int64_t S, int64_t dim, int64_t k, int iters, float* C, cudaStream_t s) {
@@ -301,7 +307,6 @@ int kmeans(const float* X, int64_t S, int64_t dim, int64_t k, int iters, float* 
   return ANNS_OK;
 }
 
-}  // namespace
 }  // namespace anns
 
 using namespace anns;
