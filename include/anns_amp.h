@@ -354,12 +354,12 @@ int anns_sync_status(anns_index* index, void* cuda_stream);
 /* Index options.
  *  ANNS_OPT_KERNEL: which search kernel anns_search launches.
  *    ANNS_KERNEL_AUTO (default): grouped when the policy can choose tables of
- *      at most 8 bits and k <= 32, else query-major.
+ *      at most 8 bits (k <= 128), else query-major.
  *    ANNS_KERNEL_BASIC: query-major, one block per query walking its probes.
  *    ANNS_KERNEL_GROUPED: the pairs on 1..8-bit tables taken four per list,
  *      their byte tables interleaved so that one shared-memory gather serves
  *      four queries; the other pairs query-major; then a per-query merge
- *      (k <= 32, else query-major).
+ *      (k <= 128).
  *    ANNS_KERNEL_LIST_MAJOR: the probed pairs regrouped by list; one warp per
  *      (query, list) pair, blocks of pairs sharing a list, work items taken
  *      largest list first; then a per-query merge of the pairs' top-k.

@@ -313,7 +313,7 @@ int anns::check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t 
 namespace anns {
 
 // The grouped kernel (narrow pairs packed four to a word): on request, or by
-// default for a policy that can choose 1..8-bit tables, when k <= 32.
+// default for a policy that can choose 1..8-bit tables, when k <= 128.
 static bool use_grouped(const Index& ix, const anns_precision_policy& P, int k) {
   if (ix.opt_kernel == ANNS_KERNEL_GROUPED) return grouped_supported(ix, k);
   if (ix.opt_kernel != ANNS_KERNEL_AUTO) return false;

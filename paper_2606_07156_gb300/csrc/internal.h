@@ -186,7 +186,7 @@ cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, in
                                 float* dists_out, cudaStream_t s);
 // Grouped search (search_grouped.cu): the pairs on 1..8-bit tables packed four
 // queries to a shared-memory word per list, the wide pairs query-major, then a
-// per-query merge. k <= 32.
+// per-query merge. k <= 128.
 bool grouped_supported(const Index& ix, int k);
 // Queries per chunk of the grouped kernel's work order: chunks whose query
 // tables fit in L2 beside the list tables and codes, when those fit; else nq.

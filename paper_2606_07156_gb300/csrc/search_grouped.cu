@@ -74,7 +74,7 @@ struct GItem {
 // Bytes of the block's shared memory (256-aligned offsets).
 struct GLayout {
   size_t tab, bias, rowmax, scal, item, lim, md, mi, total;
-  __host__ __device__ GLayout(int Mp) {
+  __host__ __device__ GLayout(int Mp, int R) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t o = 0;
     tab = o; o += al((size_t)Mp * kKsub * 4);
@@ -83,8 +83,8 @@ struct GLayout {
     scal = o; o += al(sizeof(SlotScal) * kSlots);
     item = o; o += al(2 * sizeof(GItem));  // double buffer
     lim = o; o += al(2 * 4);
-    md = o; o += al((size_t)kSlots * kGWarps * 32 * 4);
-    mi = o; o += al((size_t)kSlots * kGWarps * 32 * 8);
+    md = o; o += al((size_t)kSlots * kGWarps * R * 32 * 4);
+    mi = o; o += al((size_t)kSlots * kGWarps * R * 32 * 8);
     total = o + 256;
   }
 };
@@ -183,11 +183,12 @@ __device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItem* 
   }
 }
 
-template <int NCHUNK>
+// R: the warps' top-k lists hold R * 32 entries (k <= 32 R).
+template <int NCHUNK, int R>
 __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 : (NCHUNK <= 6 ? 2 : 1)))
     packed_kernel(const GArgs a) {
   constexpr int Mp = NCHUNK * 16;
-  const GLayout L(Mp);
+  const GLayout L(Mp, R);
   const uint32_t raw = smem_addr(anns_dyn_smem);
   const uint32_t pad = (256u - (raw & 255u)) & 255u;
   unsigned char* base = anns_dyn_smem + pad;
@@ -289,10 +290,12 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
     }
     // the warps' top-k lists start empty
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-      md[(s * kGWarps + warp) * 32 + lane] = INFINITY;
-      mi[(s * kGWarps + warp) * 32 + lane] = INT64_MAX;
-    }
+    for (int s = 0; s < kSlots; ++s)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        md[(s * kGWarps + warp) * R * 32 + r * 32 + lane] = INFINITY;
+        mi[(s * kGWarps + warp) * R * 32 + r * 32 + lane] = INT64_MAX;
+      }
     __syncthreads();
     // 3. interleaved levels, row by row
     float s32[kSlots];
@@ -361,11 +364,11 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
           const bool ok = any && ((pm >> ((s >> 1) * 16 + 15)) & 1u);
           if (__any_sync(kFull, ok)) {
             const SlotScal sc = scal[s];
-            float* ld = md + (s * kGWarps + warp) * 32;
-            int64_t* li = mi + (s * kGWarps + warp) * 32;
-            WarpTopK<1, int64_t> top;
-            top.d[0] = ld[lane];
-            top.id[0] = li[lane];
+            float* ld = md + (s * kGWarps + warp) * R * 32;
+            int64_t* li = mi + (s * kGWarps + warp) * R * 32;
+            WarpTopK<R, int64_t> top;
+#pragma unroll
+            for (int r = 0; r < R; ++r) { top.d[r] = ld[r * 32 + lane]; top.id[r] = li[r * 32 + lane]; }
             // the warp's k-th entry, at most the bound (ties kept: the id decides)
             float thd = ld[sc.kq - 1];
             int64_t thi = li[sc.kq - 1];
@@ -374,8 +377,8 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
                                    sc.B32);
             top.offer(ok, d, id, sc.kq, thd, thi);
             if (sc.bound < thd) thd = sc.bound;
-            ld[lane] = top.d[0];
-            li[lane] = top.id[0];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { ld[r * 32 + lane] = top.d[r]; li[r * 32 + lane] = top.id[r]; }
             if (thd != INFINITY) {
               const int sm = smax_warp(thd, sc.delta32, sc.B32);
               if (lane == 0) lim_min(lim, s, (uint32_t)(0x8000 + sm));
@@ -395,19 +398,25 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
     if (warp < ns) {
       const int s = warp;
       const SlotScal sc = scal[s];
-      WarpTopK<1, int64_t> m;
+      WarpTopK<R, int64_t> m;
       m.init();
       float th = INFINITY;
       int64_t ti = INT64_MAX;
-      for (int w2 = 0; w2 < kGWarps && sc.kq > 0; ++w2) {
-        const float cd = md[(s * kGWarps + w2) * 32 + lane];
-        const int64_t ci = mi[(s * kGWarps + w2) * 32 + lane];
-        m.offer(cd != INFINITY, cd, ci, sc.kq, th, ti);
-      }
-      if (lane < a.k) {
-        const bool ok = lane < sc.kq && m.d[0] != INFINITY;
-        a.part_d[(size_t)sc.pid * a.k + lane] = ok ? m.d[0] : INFINITY;
-        a.part_i[(size_t)sc.pid * a.k + lane] = ok ? m.id[0] : -1;
+      for (int w2 = 0; w2 < kGWarps && sc.kq > 0; ++w2)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float cd = md[(s * kGWarps + w2) * R * 32 + r * 32 + lane];
+          const int64_t ci = mi[(s * kGWarps + w2) * R * 32 + r * 32 + lane];
+          m.offer(cd != INFINITY, cd, ci, sc.kq, th, ti);
+        }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        if (e < a.k) {
+          const bool ok = e < sc.kq && m.d[r] != INFINITY;
+          a.part_d[(size_t)sc.pid * a.k + e] = ok ? m.d[r] : INFINITY;
+          a.part_i[(size_t)sc.pid * a.k + e] = ok ? m.id[r] : -1;
+        }
       }
     }
     cur ^= 1;
@@ -416,6 +425,7 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
 
 // One warp per query: the k smallest (d, id) over the query-major partial
 // top-k (wide pairs) and the partial top-k of the query's narrow pairs.
+template <int R>
 __global__ void __launch_bounds__(256) merge_grouped_kernel(
     const float* __restrict__ qm_d, const int64_t* __restrict__ qm_i, const float* __restrict__ part_d,
     const int64_t* __restrict__ part_i, const int32_t* __restrict__ probes, const uint8_t* __restrict__ bits,
@@ -426,36 +436,49 @@ __global__ void __launch_bounds__(256) merge_grouped_kernel(
   if (q >= nq) return;
   const int np = npq ? min(max(npq[q], 0), nprobe) : nprobe;
   const int kq = kpq ? min(max(kpq[q], 0), k) : k;
-  WarpTopK<1, int64_t> top;
+  WarpTopK<R, int64_t> top;
   top.init();
   float thd = INFINITY;
   int64_t thi = INT64_MAX;
-  if (kq > 0) {
-    const bool in = lane < kq;
-    const float d = in ? qm_d[q * k + lane] : INFINITY;
-    const int64_t id = in ? qm_i[q * k + lane] : -1;
-    top.offer(in && id >= 0, d, id, kq, thd, thi);
-  }
+  if (kq > 0)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = r * 32 + lane;
+      const bool in = e < kq;
+      const float d = in ? qm_d[q * k + e] : INFINITY;
+      const int64_t id = in ? qm_i[q * k + e] : -1;
+      top.offer(in && id >= 0, d, id, kq, thd, thi);
+    }
   for (int j = 0; kq > 0 && j < np; ++j) {
     const int64_t pid = q * nprobe + j;
     const int b = bits[pid];
     if (j == 0 || probes[pid] < 0 || b < 1 || b > 8) continue;
-    const bool in = lane < kq;
-    const float d = in ? part_d[pid * k + lane] : INFINITY;
-    const int64_t id = in ? part_i[pid * k + lane] : -1;
-    top.offer(in && id >= 0, d, id, kq, thd, thi);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = r * 32 + lane;
+      const bool in = e < kq;
+      const float d = in ? part_d[pid * k + e] : INFINITY;
+      const int64_t id = in ? part_i[pid * k + e] : -1;
+      top.offer(in && id >= 0, d, id, kq, thd, thi);
+    }
   }
-  if (lane < k) {
-    const bool ok = lane < kq && top.d[0] != INFINITY;
-    ids_out[q * k + lane] = ok ? top.id[0] : -1;
-    dists_out[q * k + lane] = ok ? top.d[0] : INFINITY;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = r * 32 + lane;
+    if (e < k) {
+      const bool ok = e < kq && top.d[r] != INFINITY;
+      ids_out[q * k + e] = ok ? top.id[r] : -1;
+      dists_out[q * k + e] = ok ? top.d[r] : INFINITY;
+    }
   }
 }
 
-template <int NCHUNK>
-cudaError_t run_packed(const GArgs& a, cudaStream_t s) {
-  auto kern = packed_kernel<NCHUNK>;
-  const GLayout L(NCHUNK * 16);
+inline int grouped_R(int k) { return k <= 32 ? 1 : 4; }
+
+template <int NCHUNK, int R>
+cudaError_t run_packed_r(const GArgs& a, cudaStream_t s) {
+  auto kern = packed_kernel<NCHUNK, R>;
+  const GLayout L(NCHUNK * 16, R);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -468,14 +491,19 @@ cudaError_t run_packed(const GArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int NCHUNK>
+cudaError_t run_packed(const GArgs& a, cudaStream_t s) {
+  return grouped_R(a.k) == 1 ? run_packed_r<NCHUNK, 1>(a, s) : run_packed_r<NCHUNK, 4>(a, s);
+}
+
 }  // namespace
 
 bool grouped_supported(const Index& ix, int k) {
-  if (k > 32) return false;
+  if (k > 128) return false;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return GLayout((int)ix.Mp).total <= (size_t)optin;
+  return GLayout((int)ix.Mp, grouped_R(k)).total <= (size_t)optin;
 }
 
 size_t grouped_workspace_bytes(int64_t nq, int k) { return (size_t)nq * k * 12 + 256; }
@@ -529,9 +557,15 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
   }
   if (e != cudaSuccess) return e;
   if (after_packed) cudaEventRecord(after_packed, s);
-  merge_grouped_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(qm_d, qm_i, w.part_d, w.part_i, probes, bits,
-                                                                nprobe_per_q, k_per_q, nq, nprobe, k, ids_out,
-                                                                dists_out); note_launch();
+  if (grouped_R(k) == 1)
+    merge_grouped_kernel<1><<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(qm_d, qm_i, w.part_d, w.part_i, probes, bits,
+                                                                   nprobe_per_q, k_per_q, nq, nprobe, k, ids_out,
+                                                                   dists_out);
+  else
+    merge_grouped_kernel<4><<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(qm_d, qm_i, w.part_d, w.part_i, probes, bits,
+                                                                   nprobe_per_q, k_per_q, nq, nprobe, k, ids_out,
+                                                                   dists_out);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -41,11 +41,11 @@ def sift_case(amp):
     g.close()
 
 
-@pytest.mark.parametrize("mode", ["fixed8", "plain", "mixed", "fixed8_qchunk37"])
+@pytest.mark.parametrize("mode", ["fixed8", "plain", "mixed", "fixed8_qchunk37", "fixed8_k100"])
 def test_bench_size_search_bit_exact(amp, sift_case, mode):
     d, ix, g, o = sift_case
     Q = d["queries"]
-    nq, nprobe, k = len(Q), 64, 10
+    nq, nprobe, k = len(Q), 64, (100 if mode.endswith("k100") else 10)
     assert 700 <= np.median(o.sizes) <= 1300
     bits = 8 if mode.startswith("fixed8") else 0
     pol = amp.policy("fixed", bits=8) if bits else amp.policy("plain")
