@@ -409,8 +409,11 @@ int anns_graph_capture(anns_index* index, const float* queries, int64_t nq, int3
 int anns_graph_launch(anns_graph* graph, void* cuda_stream);
 void anns_graph_free(anns_graph* graph);
 
-/* Autotuner: times every available (kernel, schedule) configuration on the
- * given batch (reps timed searches each, after one untimed), installs the
+/* Autotuner: times every available configuration on the given batch (reps
+ * timed searches each, after one untimed): the query-major kernel in query
+ * order and longest first, the list-major kernel, and the grouped kernel in
+ * both query orders with its automatic work order and with query chunks of
+ * a half and a quarter of the batch (when >= 256 queries). Installs the
  * fastest as the index's options and reports all of them (at most cap, in
  * trial order) with their mean milliseconds. Uses temporary output buffers;
  * synchronous. Errors as anns_search, plus INVALID_ARG for reps outside
@@ -418,6 +421,7 @@ void anns_graph_free(anns_graph* graph);
 typedef struct {
   int32_t kernel, schedule; /* ANNS_KERNEL_*, ANNS_SCHED_* */
   float ms;                 /* mean time of one search */
+  int64_t qchunk;           /* ANNS_OPT_QCHUNK of the trial (0 = automatic) */
 } anns_tune_result;
 int anns_autotune(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,
                   const int32_t* nprobe_per_q, int32_t k, const int32_t* k_per_q,

@@ -93,7 +93,8 @@ class anns_subspace_policy(ctypes.Structure):
 
 
 class anns_tune_result(ctypes.Structure):
-    _fields_ = [("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32), ("ms", ctypes.c_float)]
+    _fields_ = [("kernel", ctypes.c_int32), ("schedule", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("qchunk", ctypes.c_int64)]
 
 
 class anns_train_cfg(ctypes.Structure):
@@ -351,10 +352,10 @@ def anns_graph_free(graph) -> None:
 
 
 def anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, policy, reps, stream=None):
-    res = (anns_tune_result * 8)()
+    res = (anns_tune_result * 16)()
     n = ctypes.c_int32()
     pol = ctypes.byref(policy) if policy is not None else None
-    _check(_lib.anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, pol, reps, res, 8,
+    _check(_lib.anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, pol, reps, res, 16,
                               ctypes.byref(n), stream))
     return [(res[i].kernel, res[i].schedule, res[i].ms) for i in range(n.value)]
 

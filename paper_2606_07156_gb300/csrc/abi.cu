@@ -389,16 +389,23 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
   } else if (use_grouped(ix, P, k)) {
     ListWork w{};
     if ((rc = list_workspace(ix, nq, nprobe, k, w, grouped_qchunk(ix, nq)))) return rc;
+    // longest-first order of the query-major pass, over the pairs it scans
+    const int32_t* order = nullptr;
+    if (use_lpt(ix, nprobe_per_q)) {
+      e = launch_lpt_order(ix, ix.ws_probes, nprobe_per_q, nq, nprobe, ix.ws_sched, s, ix.ws_bits, true);
+      if (e != cudaSuccess) return cuda_fail(e, "schedule kernels");
+      order = lpt_order_ptr(ix.ws_sched, nq);
+    }
     if (ev) cudaEventRecord(ev[3], s);
     e = launch_search_grouped(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
                               ix.ws_bits, w, ix.ws_grp, ids_out, dists_out, s, ev ? ev[4] : nullptr,
-                              ev ? ev[5] : nullptr);
+                              ev ? ev[5] : nullptr, order);
     if (e == cudaSuccess && ev) cudaEventRecord(ev[6], s);
     return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "search kernel");
   } else {
     const int32_t* order = nullptr;
     if (use_lpt(ix, nprobe_per_q)) {
-      e = launch_lpt_order(ix, ix.ws_probes, nprobe_per_q, nq, nprobe, ix.ws_sched, s);
+      e = launch_lpt_order(ix, ix.ws_probes, nprobe_per_q, nq, nprobe, ix.ws_sched, s, ix.ws_bits, false);
       if (e != cudaSuccess) return cuda_fail(e, "schedule kernels");
       order = lpt_order_ptr(ix.ws_sched, nq);
     }

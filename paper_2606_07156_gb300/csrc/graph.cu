@@ -6,6 +6,7 @@
 // and predictor, but gets its own workspace, allocated before capture, so the
 // captured kernels keep valid scratch pointers whatever else runs on the
 // index. Nothing inside the captured sequence allocates or synchronises.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -142,15 +143,23 @@ extern "C" int anns_autotune(anns_index* ix, const float* Q, int64_t nq, int32_t
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   if (e != cudaSuccess) rc = cuda_fail(e, "autotune setup");
   const int kern0 = ix->opt_kernel, sched0 = ix->opt_schedule;
-  struct Cand { int kernel, schedule; };
-  std::vector<Cand> cands = {{ANNS_KERNEL_BASIC, ANNS_SCHED_NATURAL}, {ANNS_KERNEL_BASIC, ANNS_SCHED_LPT},
-                             {ANNS_KERNEL_LIST_MAJOR, ANNS_SCHED_NATURAL}, {ANNS_KERNEL_GROUPED, ANNS_SCHED_NATURAL},
-                             {ANNS_KERNEL_GROUPED, ANNS_SCHED_LPT}};
+  const int64_t qchunk0 = ix->opt_qchunk;
+  struct Cand { int kernel, schedule; int64_t qchunk; };
+  std::vector<Cand> cands = {{ANNS_KERNEL_BASIC, ANNS_SCHED_NATURAL, 0}, {ANNS_KERNEL_BASIC, ANNS_SCHED_LPT, 0},
+                             {ANNS_KERNEL_LIST_MAJOR, ANNS_SCHED_NATURAL, 0}};
+  // the grouped kernel under both query orders, with its automatic work order
+  // and with query chunks of a half and a quarter of the batch (at least 256)
+  std::vector<int64_t> chunks = {0};
+  for (int64_t c : {nq / 2, nq / 4})
+    if (c >= 256 && std::find(chunks.begin(), chunks.end(), c) == chunks.end()) chunks.push_back(c);
+  for (int sched : {ANNS_SCHED_NATURAL, ANNS_SCHED_LPT})
+    for (int64_t c : chunks) cands.push_back({ANNS_KERNEL_GROUPED, sched, c});
   std::vector<anns_tune_result> got;
   for (const Cand& c : cands) {
     if (rc != ANNS_OK) break;
     ix->opt_kernel = c.kernel;
     ix->opt_schedule = c.schedule;
+    ix->opt_qchunk = c.qchunk;
     // one untimed run (allocations, attributes); a configuration this index
     // cannot run (a list-major table too large) is skipped
     int r = search_sequence(*ix, Q, nq, nprobe, nprobe_per_q, k, k_per_q, P, (int64_t*)ids, (float*)dists, s,
@@ -171,16 +180,19 @@ extern "C" int anns_autotune(anns_index* ix, const float* Q, int64_t nq, int32_t
     t.kernel = c.kernel;
     t.schedule = c.schedule;
     t.ms = ms / (float)reps;
+    t.qchunk = c.qchunk;
     got.push_back(t);
   }
   ix->opt_kernel = kern0;
   ix->opt_schedule = sched0;
+  ix->opt_qchunk = qchunk0;
   if (rc == ANNS_OK && !got.empty()) {
     size_t best = 0;
     for (size_t i = 1; i < got.size(); ++i)
       if (got[i].ms < got[best].ms) best = i;
     ix->opt_kernel = got[best].kernel;
     ix->opt_schedule = got[best].schedule;
+    ix->opt_qchunk = got[best].qchunk;
     for (size_t i = 0; i < got.size() && (int)i < cap; ++i) results[i] = got[i];
     if (n_results) *n_results = (int32_t)got.size();
   }

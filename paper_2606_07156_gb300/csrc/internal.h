@@ -148,8 +148,11 @@ cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int npro
 // lpt_workspace_bytes(nq); the order is at lpt_order_ptr(ws, nq).
 size_t lpt_workspace_bytes(int64_t nq);
 int32_t* lpt_order_ptr(void* ws, int64_t nq);
+// `bits` (NULL = every pair FP32) weights each pair's lookups by its table
+// width; `skip_narrow` leaves out the pairs the grouped kernel takes.
 cudaError_t launch_lpt_order(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
-                             int nprobe, void* ws, cudaStream_t s);
+                             int nprobe, void* ws, cudaStream_t s, const uint8_t* bits = nullptr,
+                             bool skip_narrow = false);
 // The whole search sequence of anns_search on stream s (abi.cu), for an index
 // whose workspace is already large enough when `no_alloc` is set.
 int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int32_t* nprobe_per_q, int k,
@@ -197,7 +200,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
                                   const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
                                   cudaStream_t s, cudaEvent_t after_qm = nullptr,
-                                  cudaEvent_t after_packed = nullptr);
+                                  cudaEvent_t after_packed = nullptr, const int32_t* qm_order = nullptr);
 // Pair-level debug paths; qt are the queries' tables from launch_query_tables.
 cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt, int64_t nq,
                                 const int32_t* pq, const int32_t* pl, const uint8_t* pb,

@@ -525,7 +525,8 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
                                   const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                                   const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
-                                  cudaStream_t s, cudaEvent_t after_qm, cudaEvent_t after_packed) {
+                                  cudaStream_t s, cudaEvent_t after_qm, cudaEvent_t after_packed,
+                                  const int32_t* qm_order) {
   // narrow pairs regrouped by list, groups of four, largest lists first
   cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kSlots, w, s, bits);
   if (e != cudaSuccess) return e;
@@ -534,7 +535,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
   // rank 0 and the wide pairs, query-major, into a partial top-k per query
   float* qm_d = (float*)qm_ws;
   int64_t* qm_i = (int64_t*)((char*)qm_ws + (((size_t)nq * k * 4 + 255) & ~size_t(255)));
-  e = launch_search(ix, qt, nq, nprobe, nprobe_per_q, k, k_per_q, probes, probe_d2, bits, nullptr, qm_i, qm_d, s,
+  e = launch_search(ix, qt, nq, nprobe, nprobe_per_q, k, k_per_q, probes, probe_d2, bits, qm_order, qm_i, qm_d, s,
                     true);
   if (e != cudaSuccess) return e;
   if (after_qm) cudaEventRecord(after_qm, s);

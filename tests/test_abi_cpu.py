@@ -45,6 +45,7 @@ def test_struct_layouts(abi):
     assert abi.anns_precision_policy.width_map.offset == 48
     assert ctypes.sizeof(abi.anns_predictor) == 4 * (160 + 32 + 1024 + 32 + 160 + 5 + 5 + 5)
     assert ctypes.sizeof(abi.anns_train_cfg) == 4 + 4 + 4 + 4 + 8 + 4 + 4
+    assert ctypes.sizeof(abi.anns_tune_result) == 24 and abi.anns_tune_result.qchunk.offset == 16
 
 
 def test_argument_errors_without_gpu(abi):
