@@ -465,6 +465,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if args.nq:
         W = dict(W, queries=W["queries"][:args.nq], gt=W["gt"][:args.nq])
     index = amp.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"], device=local_rank)
+    if args.no_nibble:
+        index.set_nibble(False)
     Q = torch.from_numpy(W["queries"]).to(dev)
     nq, k = Q.shape[0], cfg["k"]
     stream = torch.cuda.current_stream(dev)
@@ -513,7 +515,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         # trained on the two tables of the GB300 width map, wide pairs weighted up
         # (a wide pair put on a narrow table costs recall, the reverse only speed)
         index.train_predictor(Qt, npb, k, amp.train_cfg(epochs=args.epochs, batch=1024, lr=3e-3, seed=1,
-                                                        gpu_classes=True, high_weight=args.high_weight))
+                                                        gpu_classes=True, high_weight=args.high_weight,
+                                                        nibble_classes=not args.two_classes))
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
@@ -674,7 +677,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
                    "policy": f"learned MLP per (query, list) trained on GB300 table classes, round-up "
                              f"margin {margin} (recall-loss budget {LOSS_BUDGET} pt on calibration queries), widths 6->8 bits "
-                             f"and 12/16->FP32",
+                             f"and 12/16->FP32; 4-bit tables eight queries per gather",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "recall_at_10": round(recs["mlp"][0], 4),
         "top10_kept_vs_plain": round(recs["mlp"][1], 4),
@@ -702,7 +705,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             recall_at_10=round(recs["svr"][0], 4), mlp_speedup_vs_plain=round(qps["mlp"] / qps["plain"], 3),
             mlp_recall_at_10=round(recs["mlp"][0], 4)),
         "predictor": {"train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
-                      "classes": "GB300 tables (8-bit / wide)", "high_weight": args.high_weight,
+                      "classes": "GB300 tables (8-bit / wide)" if args.two_classes else "GB300 tables (4-bit / 8-bit / wide)", "high_weight": args.high_weight,
                       "margin_calibration_recall_loss_pts": {str(a): b for a, b in tried.items()},
                       "recall_loss_budget_pts": LOSS_BUDGET},
         "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_plain.items()},
@@ -779,7 +782,8 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
     Qt = torch.from_numpy(make_queries(args.config, args.ntrain, stream=200)).to(dev)
     t0 = time.perf_counter()
     index.train_predictor(Qt, 20, 10, amp.train_cfg(epochs=args.epochs, batch=1024, lr=3e-3, seed=1,
-                                                    gpu_classes=True, high_weight=args.high_weight))
+                                                    gpu_classes=True, high_weight=args.high_weight,
+                                                    nibble_classes=not args.two_classes))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del Qt
@@ -1113,6 +1117,9 @@ def main():
     ap.add_argument("--no-svr", action="store_true", help="skip the SVR-RBF comparator")
     ap.add_argument("--no-build-bench", action="store_true", help="skip the index-training comparison")
     ap.add_argument("--no-subspace", action="store_true", help="skip the sub-space granularity sweep")
+    ap.add_argument("--two-classes", action="store_true",
+                    help="train the predictor on two GB300 tables (8-bit / wide) instead of three (4 / 8 / wide)")
+    ap.add_argument("--no-nibble", action="store_true", help="4-bit pairs four per word (no nibble packing)")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

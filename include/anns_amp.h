@@ -385,9 +385,14 @@ int anns_sync_status(anns_index* index, void* cuda_stream);
  *    the copies and MMAs it has issued, free its tensor memory and return;
  *    the coarse stage's output is then invalid. Small values serve tests of
  *    this failure path.
- * Every kernel, schedule and chunk size returns identical results.
+ *  ANNS_OPT_NIBBLE: 1 (default) = in the grouped search (k <= 32), the pairs
+ *    on tables of at most 4 bits are taken eight per list, their levels
+ *    interleaved as nibbles so that one gather serves eight queries (the
+ *    5..8-bit pairs stay four per word); 0 = all 1..8-bit pairs four per word.
+ * Every kernel, schedule, chunk size and packing returns identical results.
  * Errors: INVALID_ARG. */
-enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1, ANNS_OPT_QCHUNK = 2, ANNS_OPT_WAIT_CYCLES = 3 };
+enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1, ANNS_OPT_QCHUNK = 2, ANNS_OPT_WAIT_CYCLES = 3,
+       ANNS_OPT_NIBBLE = 4 };
 enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2, ANNS_KERNEL_GROUPED = 3 };
 enum { ANNS_SCHED_AUTO = 0, ANNS_SCHED_NATURAL = 1, ANNS_SCHED_LPT = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);
@@ -446,7 +451,9 @@ typedef struct {
   int32_t label_map;     /* anns_train_predictor: 0 = classes of the label widths 4, 6, 8,
                             12, 16 ("needs FP32" trains as 16); 1 = the two tables of
                             the GB300 width map: labels 4, 6, 8 -> the 8-bit class,
-                            12, 16 and "needs FP32" -> the 16-bit class */
+                            12, 16 and "needs FP32" -> the 16-bit class; 2 = its three
+                            tables: 4 -> the 4-bit class (nibble tables), 6 and 8 ->
+                            the 8-bit class, 12, 16 and "needs FP32" -> 16 bits */
   float high_weight;     /* loss weight of samples whose class is 12 or 16 bits (a
                             missed wide pair costs recall, a missed narrow one only
                             speed); 0 is read as 1 */

@@ -305,12 +305,15 @@ def gpu_width(bits: np.ndarray) -> np.ndarray:
     return np.where(b == 6, np.uint8(8), np.where((b == 12) | (b == 16), np.uint8(0), b)).astype(np.uint8)
 
 
-def bits_to_class(bits: np.ndarray, gpu: bool = False) -> np.ndarray:
+def bits_to_class(bits: np.ndarray, gpu: bool = False, nibble: bool = False) -> np.ndarray:
     """Training target: class of the label bits; "needs FP32" trains as 16 bits.
     With `gpu`, the two tables of the GB300 width map: 4, 6, 8 -> class 2
-    (8 bits); 12, 16 and FP32 -> class 4 (16 bits)."""
+    (8 bits); 12, 16 and FP32 -> class 4 (16 bits). With `nibble`, its three
+    tables: 4 -> class 0; 6, 8 -> class 2; 12, 16 and FP32 -> class 4."""
     b = np.asarray(bits)
     lut = {4: 0, 6: 1, 8: 2, 12: 3, 16: 4, 0: 4}
     if gpu:
         lut = {4: 2, 6: 2, 8: 2, 12: 4, 16: 4, 0: 4}
+    if nibble:
+        lut = {4: 0, 6: 2, 8: 2, 12: 4, 16: 4, 0: 4}
     return np.vectorize(lambda v: lut[int(v)])(b).astype(np.int64)

@@ -57,10 +57,12 @@ def predictor_to_dict(s: abi.anns_predictor) -> dict:
 
 
 def train_cfg(epochs: int = 10, batch: int = 1024, lr: float = 3e-3, seed: int = 0, gpu_classes: bool = False,
-              high_weight: float = 1.0) -> abi.anns_train_cfg:
+              high_weight: float = 1.0, nibble_classes: bool = False) -> abi.anns_train_cfg:
+    """Training settings; ``gpu_classes`` trains on the two GB300 tables (8-bit / wide),
+    ``nibble_classes`` on its three (4-bit nibble tables / 8-bit / wide)."""
     c = abi.anns_train_cfg()
     c.epochs, c.batch, c.lr, c.seed = epochs, batch, lr, seed
-    c.label_map = 1 if gpu_classes else 0
+    c.label_map = 2 if nibble_classes else (1 if gpu_classes else 0)
     c.high_weight = high_weight
     return c
 
@@ -232,6 +234,10 @@ class Index:
     def set_qchunk(self, queries: int):
         """Queries per chunk of the grouped kernel's work order (0 = automatic)."""
         abi.anns_set_option(self.handle, abi.OPT_QCHUNK, int(queries))
+
+    def set_nibble(self, on: bool):
+        """Grouped search: pairs on <= 4-bit tables eight to a word (default on)."""
+        abi.anns_set_option(self.handle, abi.OPT_NIBBLE, 1 if on else 0)
 
     def set_schedule(self, which: str):
         """'auto', 'natural' or 'lpt' (longest query first) for the query-major kernel."""

@@ -22,7 +22,7 @@ PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_COARSE_APPROX, TAP_COARSE_CANDIDATES = 4, 5
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS, TAP_STATUS = 10, 11, 12, 13
-OPT_KERNEL, OPT_SCHEDULE, OPT_QCHUNK, OPT_WAIT_CYCLES = 0, 1, 2, 3
+OPT_KERNEL, OPT_SCHEDULE, OPT_QCHUNK, OPT_WAIT_CYCLES, OPT_NIBBLE = 0, 1, 2, 3, 4
 KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR, KERNEL_GROUPED = 0, 1, 2, 3
 SCHED_AUTO, SCHED_NATURAL, SCHED_LPT = 0, 1, 2
 

@@ -189,7 +189,7 @@ int list_workspace(Index& ix, int64_t nq, int nprobe, int k, ListWork& w, int64_
   const size_t L = (size_t)(w.nbuckets + 1) * 4, P = (size_t)nq * nprobe;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t G = (P + (size_t)w.nbuckets + 1) * 4;  // groups: at most one per pair plus one per bucket
-  const size_t bytes = 4 * al(L) + al(P * 4) + al(P * k * 4) + al(P * k * 8) + al(G);
+  const size_t bytes = 2 * (4 * al(L) + al(P * 4) + al(G)) + al(P * k * 4) + al(P * k * 8);
   int rc = grow(&ix.ws_lists, &ix.ws_lists_cap, bytes);
   if (rc) return rc;
   char* b = (char*)ix.ws_lists;
@@ -200,8 +200,15 @@ int list_workspace(Index& ix, int64_t nq, int nprobe, int k, ListWork& w, int64_
   w.pairs = (int32_t*)b; b += al(P * 4);
   w.part_d = (float*)b; b += al(P * k * 4);
   w.part_i = (int64_t*)b; b += al(P * k * 8);
-  w.gtab = (int*)b;
+  w.gtab = (int*)b; b += al(G);
   w.counter = ix.ws_counter;
+  w.cnt4 = (int*)b; b += al(L);
+  w.off4 = (int*)b; b += al(L);
+  w.ioff4 = (int*)b; b += al(L);
+  w.fill4 = (int*)b; b += al(L);
+  w.pairs4 = (int32_t*)b; b += al(P * 4);
+  w.gtab4 = (int*)b;
+  w.counter4 = ix.ws_counter + 8;
   return ANNS_OK;
 }
 
@@ -644,6 +651,10 @@ extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
     case ANNS_OPT_WAIT_CYCLES:
       if (value < 0) return fail(ANNS_ERR_INVALID_ARG, "wait limit must be >= 0");
       ix->opt_wait_cycles = value;
+      return ANNS_OK;
+    case ANNS_OPT_NIBBLE:
+      if (value != 0 && value != 1) return fail(ANNS_ERR_INVALID_ARG, "nibble option must be 0 or 1");
+      ix->opt_nibble = (int)value;
       return ANNS_OK;
     default: return fail(ANNS_ERR_INVALID_ARG, "unknown option");
   }

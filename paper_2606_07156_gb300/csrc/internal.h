@@ -80,6 +80,7 @@ struct Index {
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   int opt_schedule = 0;          // ANNS_SCHED_*
   int64_t opt_qchunk = 0;        // grouped kernel: queries per chunk (0 = automatic)
+  int opt_nibble = 1;            // grouped search: pairs on <= 4-bit tables eight to a word
   long long opt_wait_cycles = 0; // limit of the CL GEMM's main-loop waits in clock cycles (0 = about 1 s)
   // staging for anns_search_host
   void* st_q = nullptr; size_t st_q_cap = 0;
@@ -176,10 +177,15 @@ struct ListWork {
   int64_t qchunk;                           // queries per chunk
   int nbuckets;                             // chunks * nlist
   int* gtab;                                // grouped kernel: bucket of each group [<= pairs + nbuckets]
+  // a second set of buckets for the grouped search's pairs on tables of at
+  // most 4 bits (groups of eight; the sets above then hold the 5..8-bit pairs)
+  int *cnt4, *off4, *ioff4, *fill4, *gtab4, *counter4;
+  int32_t* pairs4;
 };
+// With narrow_bits, only the pairs of probe rank >= 1 on tables of blo..bhi bits.
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
                           int nprobe, int batch, const ListWork& w, cudaStream_t s,
-                          const uint8_t* narrow_bits = nullptr);
+                          const uint8_t* narrow_bits = nullptr, int blo = 1, int bhi = 8);
 // Warps per block the list-major kernel gets for tables of `table_bytes_per_entry`.
 int list_major_warps(const Index& ix, int table_bytes_per_entry);
 cudaError_t launch_search_lists(const Index& ix, const float* qt, int64_t nq, int nprobe,

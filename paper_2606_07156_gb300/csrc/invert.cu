@@ -10,7 +10,8 @@
 // chunk, so that only one chunk's query tables are in use at a time.
 //
 //   count:   cnt[key] = number of valid pairs of the bucket (with narrow_bits:
-//            only the pairs the grouped kernel packs: 1..8-bit tables, rank >= 1)
+//            only the pairs a grouped kernel packs: rank >= 1 on tables of
+//            blo..bhi bits, 1..8 or the 1..4 and 5..8 classes)
 //   offsets: off[key] = exclusive prefix of cnt over keys;
 //            ioff[c * nlist + r] = exclusive prefix of
 //                      ceil(cnt[c * nlist + order[r]] / batch) over chunks and
@@ -32,14 +33,14 @@ namespace {
 // rank >= 1 (rank 0 goes through the query-major kernel, whose result bounds
 // the query's k-th distance for the grouped pairs).
 __device__ __forceinline__ bool pair_selected(const int32_t* probes, const int32_t* npq, const uint8_t* bits,
-                                              int64_t i, int nprobe) {
+                                              int64_t i, int nprobe, int blo, int bhi) {
   const int64_t q = i / nprobe;
   const int j = (int)(i % nprobe);
   const int np = npq ? min(max(npq[q], 0), nprobe) : nprobe;
   if (j >= np || probes[i] < 0) return false;
   if (!bits) return true;
   const int b = bits[i];
-  return j >= 1 && b >= 1 && b <= 8;
+  return j >= 1 && b >= blo && b <= bhi;
 }
 
 __device__ __forceinline__ int bucket_of(const int32_t* probes, int64_t i, int nprobe, int64_t qchunk, int nlist) {
@@ -47,11 +48,12 @@ __device__ __forceinline__ int bucket_of(const int32_t* probes, int64_t i, int n
 }
 
 __global__ void count_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
-                             const uint8_t* __restrict__ bits, int64_t nq, int nprobe, int64_t qchunk, int nlist,
-                             int* __restrict__ cnt) {
+                             const uint8_t* __restrict__ bits, int blo, int bhi, int64_t nq, int nprobe,
+                             int64_t qchunk, int nlist, int* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq * nprobe) return;
-  if (pair_selected(probes, npq, bits, i, nprobe)) atomicAdd(cnt + bucket_of(probes, i, nprobe, qchunk, nlist), 1);
+  if (pair_selected(probes, npq, bits, i, nprobe, blo, bhi))
+    atomicAdd(cnt + bucket_of(probes, i, nprobe, qchunk, nlist), 1);
 }
 
 // One block: exclusive scans over bucket keys (pair offsets) and over
@@ -103,11 +105,12 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int* __restrict__ c
 }
 
 __global__ void scatter_kernel(const int32_t* __restrict__ probes, const int32_t* __restrict__ npq,
-                               const uint8_t* __restrict__ bits, int64_t nq, int nprobe, int64_t qchunk, int nlist,
-                               const int* __restrict__ off, int* __restrict__ fill, int32_t* __restrict__ pairs) {
+                               const uint8_t* __restrict__ bits, int blo, int bhi, int64_t nq, int nprobe,
+                               int64_t qchunk, int nlist, const int* __restrict__ off, int* __restrict__ fill,
+                               int32_t* __restrict__ pairs) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq * nprobe) return;
-  if (!pair_selected(probes, npq, bits, i, nprobe)) return;
+  if (!pair_selected(probes, npq, bits, i, nprobe, blo, bhi)) return;
   const int b = bucket_of(probes, i, nprobe, qchunk, nlist);
   pairs[off[b] + atomicAdd(fill + b, 1)] = (int32_t)i;
 }
@@ -122,15 +125,18 @@ __global__ void group_table_kernel(const int* __restrict__ ioff, int nb, int* __
 }  // namespace
 
 cudaError_t launch_invert(const Index& ix, const int32_t* probes, const int32_t* npq, int64_t nq,
-                          int nprobe, int batch, const ListWork& w, cudaStream_t s, const uint8_t* narrow_bits) {
+                          int nprobe, int batch, const ListWork& w, cudaStream_t s, const uint8_t* narrow_bits,
+                          int blo, int bhi) {
   const int64_t n = nq * nprobe;
   const int nlist = (int)ix.nlist;
   cudaError_t e = cudaMemsetAsync(w.cnt, 0, sizeof(int) * w.nbuckets, s);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((n + 255) / 256);
-  count_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, w.qchunk, nlist, w.cnt); note_launch();
+  count_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, blo, bhi, nq, nprobe, w.qchunk, nlist, w.cnt);
+  note_launch();
   offsets_kernel<<<1, 1024, 0, s>>>(w.cnt, ix.order, nlist, w.nbuckets, batch, w.off, w.ioff, w.fill); note_launch();
-  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, nq, nprobe, w.qchunk, nlist, w.off, w.fill, w.pairs);
+  scatter_kernel<<<g, 256, 0, s>>>(probes, npq, narrow_bits, blo, bhi, nq, nprobe, w.qchunk, nlist, w.off, w.fill,
+                                   w.pairs);
   note_launch();
   if (narrow_bits) {  // the grouped kernel looks its groups up in a table
     group_table_kernel<<<(unsigned)((w.nbuckets + 255) / 256), 256, 0, s>>>(w.ioff, w.nbuckets, w.gtab);

@@ -295,13 +295,15 @@ __global__ void adam_kernel(float* w, const float* g, float* m, float* v, float 
 }
 
 // Bits -> class (4, 6, 8, 12, 16 -> 0..4; "needs FP32" trains as 16 bits; 255 = no sample).
-// With `gpu`, the two tables of the GB300 width map: 4, 6, 8 -> 2; 12, 16, FP32 -> 4.
-__global__ void class_kernel(const uint8_t* bits, int64_t n, int gpu, uint8_t* cls) {
+// map 1, the two tables of the GB300 width map: 4, 6, 8 -> 2; 12, 16, FP32 -> 4.
+// map 2, its three tables: 4 -> 0 (nibble tables); 6, 8 -> 2; 12, 16, FP32 -> 4.
+__global__ void class_kernel(const uint8_t* bits, int64_t n, int map, uint8_t* cls) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = bits[i];
   uint8_t c = b == 4 ? 0 : b == 6 ? 1 : b == 8 ? 2 : b == 12 ? 3 : (b == 16 || b == 0) ? 4 : 255;
-  if (gpu && c < 5) c = c <= 2 ? 2 : 4;
+  if (map == 1 && c < 5) c = c <= 2 ? 2 : 4;
+  if (map == 2 && c < 5) c = c == 0 ? 0 : (c <= 2 ? 2 : 4);
   cls[i] = c;
 }
 

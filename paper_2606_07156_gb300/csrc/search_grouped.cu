@@ -64,27 +64,29 @@ struct SlotScal { float s32, delta32, B32, bound; int kq, pid, pad0, pad1; };
 // query, table width, D2, k and bound (the query's k-th distance over its
 // query-major pairs). Fetched by one warp while the block scans the previous
 // group, so that the block never waits on this chain of dependent loads.
-struct GItem {
+template <int S>
+struct GItemT {
   int it, l, ns, n_l;
-  int pid[4], q[4], bits[4], kq[4];
-  float d2[4], bound[4];
+  int pid[S], q[S], bits[S], kq[S];
+  float d2[S], bound[S];
   long long tile0, vec0;  // the list's first code tile and first id
 };
+using GItem = GItemT<4>;
 
 // Bytes of the block's shared memory (256-aligned offsets).
 struct GLayout {
   size_t tab, bias, rowmax, scal, item, lim, md, mi, total;
-  __host__ __device__ GLayout(int Mp, int R) {
+  __host__ __device__ GLayout(int Mp, int R, int S = kSlots) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t o = 0;
     tab = o; o += al((size_t)Mp * kKsub * 4);
-    bias = o; o += al((size_t)kSlots * Mp * 4);
-    rowmax = o; o += al((size_t)kSlots * Mp * 4);
-    scal = o; o += al(sizeof(SlotScal) * kSlots);
-    item = o; o += al(2 * sizeof(GItem));  // double buffer
-    lim = o; o += al(2 * 4);
-    md = o; o += al((size_t)kSlots * kGWarps * R * 32 * 4);
-    mi = o; o += al((size_t)kSlots * kGWarps * R * 32 * 8);
+    bias = o; o += al((size_t)S * Mp * 4);
+    rowmax = o; o += al((size_t)S * Mp * 4);
+    scal = o; o += al(sizeof(SlotScal) * S);
+    item = o; o += al(2 * (S == kSlots ? sizeof(GItemT<kSlots>) : sizeof(GItemT<8>)));  // double buffer
+    lim = o; o += al(4 * 4);
+    md = o; o += al((size_t)S * kGWarps * R * 32 * 4);
+    mi = o; o += al((size_t)S * kGWarps * R * 32 * 8);
     total = o + 256;
   }
 };
@@ -134,11 +136,12 @@ __device__ __forceinline__ int smax_warp(float x, float delta, float B) {
   return lo;
 }
 
-// Lowers slot s's 16-bit lane of the block's packed limits to v (if lower).
-// A retry lost to the cap leaves a larger limit, which only prunes less.
-__device__ __forceinline__ void lim_min(uint32_t* lim, int s, uint32_t v) {
-  uint32_t* w = lim + (s & 1);
-  const int sh = (s >> 1) * 16;
+// Lowers a slot's 16-bit lane (word `reg`, half `half`) of the block's packed
+// limits to v (if lower). A retry lost to the cap leaves a larger limit, which
+// only prunes less.
+__device__ __forceinline__ void lim_min_at(uint32_t* lim, int reg, int half, uint32_t v) {
+  uint32_t* w = lim + reg;
+  const int sh = half * 16;
   uint32_t old = *(volatile uint32_t*)w;
   for (int it = 0; it < 256; ++it) {
     if (((old >> sh) & 0xFFFFu) <= v) return;
@@ -148,8 +151,12 @@ __device__ __forceinline__ void lim_min(uint32_t* lim, int s, uint32_t v) {
   }
 }
 
-// The next group from the work queue (whole warp; lanes 0..3 take the slots).
-__device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItem* out, int lane) {
+// Byte tables: slots 0 and 2 share limit word 0, slots 1 and 3 word 1.
+__device__ __forceinline__ void lim_min(uint32_t* lim, int s, uint32_t v) { lim_min_at(lim, s & 1, s >> 1, v); }
+
+// The next group from the work queue (whole warp; lanes 0..S-1 take the slots).
+template <int S = kSlots>
+__device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItemT<S>* out, int lane) {
   int it = 0;
   if (lane == 0) it = atomicAdd(a.counter, 1);
   it = __shfl_sync(kFull, it, 0);
@@ -161,9 +168,9 @@ __device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItem* 
   const int l = a.order[b % a.nlist];
   const int key = (b / a.nlist) * a.nlist + l;
   const int i = it - a.ioff[b];
-  const int ns = min(kSlots, a.cnt[key] - kSlots * i);
-  if (lane < kSlots) {
-    const int p = lane < ns ? a.pairs[a.off[key] + kSlots * i + lane] : -1;
+  const int ns = min(S, a.cnt[key] - S * i);
+  if (lane < S) {
+    const int p = lane < ns ? a.pairs[a.off[key] + S * i + lane] : -1;
     int qs = 0, bs = 8, kq = 0;
     float d2 = 0.f, bound = INFINITY;
     if (p >= 0) {
@@ -423,6 +430,263 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
   }
 }
 
+// ---- 4-bit tables, eight queries per word ----------------------------------
+//
+// The pairs on tables of at most 4 bits are taken eight at a time: entry c of
+// row m holds the eight queries' levels as nibbles (slot s in bits 4s..4s+3),
+// so one shared-memory gather per (vector, sub-space) serves eight queries.
+// The nibbles add up as byte lanes for the 16 sub-spaces of a code chunk
+// (16 * 15 = 240 < 256), slots 0, 2, 4, 6 in one register and 1, 3, 5, 7 in
+// another, and then widen into 16-bit lanes of four registers: W0 = (slot 0,
+// slot 4), W1 = (2, 6), W2 = (1, 5), W3 = (3, 7); a sum of at most 128 levels
+// of 15 stays below 2^15. Everything else (build, scale, offset, limits,
+// top-k) is the 8-bit kernel's, with eight slots; the warps keep 32-entry
+// lists (k <= 32).
+constexpr int kNSlots = 8;
+using NItem = GItemT<kNSlots>;
+
+// Register and half of slot s's 16-bit sum lane (and limit lane).
+__device__ __forceinline__ int nib_reg(int s) { return 2 * (s & 1) + ((s >> 1) & 1); }
+__device__ __forceinline__ int nib_half(int s) { return s >> 2; }
+
+template <int K, int NCHUNK>
+__device__ __forceinline__ void nibble_acc(uint32_t base, const uint4 (&w)[NCHUNK], uint32_t& lo, uint32_t& hi) {
+  const uint32_t x = code_word<K & ~3, NCHUNK>(w);
+  const uint32_t code = __byte_perm(x, 0u, 0x4440u + (K & 3));
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(base + code * 4u), "n"(K * 1024));
+  lo += v & 0x0F0F0F0Fu;          // slots 0, 2, 4, 6 as byte lanes
+  hi += (v >> 4) & 0x0F0F0F0Fu;   // slots 1, 3, 5, 7
+}
+template <int NCHUNK, int C, int... J>
+__device__ __forceinline__ void nibble_chunk(uint32_t base, const uint4 (&w)[NCHUNK], uint32_t (&W)[4],
+                                             std::integer_sequence<int, J...>) {
+  uint32_t lo = 0u, hi = 0u;
+  (nibble_acc<C * 16 + J, NCHUNK>(base, w, lo, hi), ...);
+  W[0] += __byte_perm(lo, 0u, 0x4240u);
+  W[1] += __byte_perm(lo, 0u, 0x4341u);
+  W[2] += __byte_perm(hi, 0u, 0x4240u);
+  W[3] += __byte_perm(hi, 0u, 0x4341u);
+}
+template <int NCHUNK, int... C>
+__device__ __forceinline__ void adc_nibble_seq(uint32_t base, const uint4 (&w)[NCHUNK], uint32_t (&W)[4],
+                                               std::integer_sequence<int, C...>) {
+  (nibble_chunk<NCHUNK, C>(base, w, W, std::make_integer_sequence<int, 16>{}), ...);
+}
+
+template <int NCHUNK>
+__global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 3 : (NCHUNK <= 4 ? 2 : 1)) nibble_kernel(const GArgs a) {
+  constexpr int Mp = NCHUNK * 16;
+  const GLayout L(Mp, 1, kNSlots);
+  const uint32_t raw = smem_addr(anns_dyn_smem);
+  const uint32_t pad = (256u - (raw & 255u)) & 255u;
+  unsigned char* base = anns_dyn_smem + pad;
+  uint32_t* tab = (uint32_t*)(base + L.tab);
+  float* bias = (float*)(base + L.bias);
+  float* rowmax = (float*)(base + L.rowmax);
+  SlotScal* scal = (SlotScal*)(base + L.scal);
+  NItem* items = (NItem*)(base + L.item);
+  uint32_t* lim = (uint32_t*)(base + L.lim);  // 0x8000 + Smax per slot in the lanes of W0..W3
+  float* md = (float*)(base + L.md);
+  int64_t* mi = (int64_t*)(base + L.mi);
+  const uint32_t tab_addr = raw + pad + (uint32_t)L.tab;
+  const uint32_t lim_addr = raw + pad + (uint32_t)L.lim;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ngroups = a.ioff[a.nb];
+  const size_t tstride = (size_t)Mp * kKsub;
+  int cur = 0;
+  if (warp == kGWarps - 1) fetch_group<kNSlots>(a, ngroups, items, lane);
+  for (;;) {
+    __syncthreads();  // the previous group is done with the shared tables; items[cur] is complete
+    if (threadIdx.x < 4) lim[threadIdx.x] = 0xFFFFFFFFu;  // every sum passes until the seeds
+    const NItem& G = items[cur];
+    if (G.it >= ngroups) break;
+    const int l = G.l, ns = G.ns;
+    int q[kNSlots];
+#pragma unroll
+    for (int s = 0; s < kNSlots; ++s) q[s] = G.q[s];
+    const float* P = a.ltab + (size_t)l * tstride;
+    // 1. row statistics of the eight slots (the list-table row loaded once)
+    for (int m = warp; m < a.M; m += kGWarps) {
+      float p[8], lo_v[kNSlots], hi_v[kNSlots];
+      ldg_row8(P + m * kKsub, lane, p);
+#pragma unroll
+      for (int s0 = 0; s0 < kNSlots; s0 += 2) {
+        float qq[2][8];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) ldg_row8(a.qt + (size_t)q[s0 + u] * tstride + m * kKsub, lane, qq[u]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int s = s0 + u;
+          lo_v[s] = hi_v[s] = sub_rn(p[0], qq[u][0]);
+#pragma unroll
+          for (int e = 1; e < 8; ++e) {
+            const float tv = sub_rn(p[e], qq[u][e]);
+            lo_v[s] = fminf(lo_v[s], tv);
+            hi_v[s] = fmaxf(hi_v[s], tv);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1)
+#pragma unroll
+        for (int s = 0; s < kNSlots; ++s) {
+          lo_v[s] = fminf(lo_v[s], __shfl_xor_sync(kFull, lo_v[s], o));
+          hi_v[s] = fmaxf(hi_v[s], __shfl_xor_sync(kFull, hi_v[s], o));
+        }
+#pragma unroll
+      for (int s = 0; s < kNSlots; ++s)
+        if (lane == 0 && s < ns) { bias[s * Mp + m] = lo_v[s]; rowmax[s * Mp + m] = sub_rn(hi_v[s], lo_v[s]); }
+    }
+    __syncthreads();
+    // 2. per slot (warp s): step, scale, offset (exact sum), k, bound and the limit seed
+    {
+      const int s = warp;
+      float range = 0.f;
+      const int p = G.pid[s], bs = G.bits[s];
+      const float d2 = G.d2[s];
+      ExactSum B;
+      xsum_init(B);
+      if (s < ns) {
+        for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
+        range = warp_max(range);
+        for (int m = lane; m < a.M; m += 32) xsum_add(B, bias[s * Mp + m]);
+      }
+      if (lane == 0) xsum_add(B, d2);
+      xsum_warp(B);
+      const int Lv = (1 << bs) - 1;
+      SlotScal sc;
+      sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
+      sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
+      sc.B32 = xsum_round(B);
+      sc.kq = s < ns ? G.kq[s] : 0;
+      sc.bound = sc.kq > 0 ? G.bound[s] : INFINITY;
+      sc.pid = p;
+      sc.pad0 = sc.pad1 = 0;
+      const int seed = sc.kq == 0 ? -1 : (sc.bound == INFINITY ? 0x7FFF : smax_warp(sc.bound, sc.delta32, sc.B32));
+      if (lane == 0) {
+        scal[s] = sc;
+        lim_min_at(lim, nib_reg(s), nib_half(s), (uint32_t)(0x8000 + seed));
+      }
+    }
+    // the warps' top-k lists start empty
+#pragma unroll
+    for (int s = 0; s < kNSlots; ++s) {
+      md[(s * kGWarps + warp) * 32 + lane] = INFINITY;
+      mi[(s * kGWarps + warp) * 32 + lane] = INT64_MAX;
+    }
+    __syncthreads();
+    // 3. interleaved levels: nibble s of entry e's word = slot s's level (<= 15)
+    float s32[kNSlots];
+#pragma unroll
+    for (int s = 0; s < kNSlots; ++s) s32[s] = s < ns ? scal[s].s32 : 0.f;
+    for (int m = warp; m < Mp; m += kGWarps) {
+      uint32_t wv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) wv[e] = 0u;
+      if (m < a.M) {
+        float p[8];
+        ldg_row8(P + m * kKsub, lane, p);
+#pragma unroll
+        for (int s = 0; s < kNSlots; ++s) {
+          float qq[8];
+          ldg_row8(a.qt + (size_t)q[s] * tstride + m * kKsub, lane, qq);
+          if (s < ns) {
+            const float mn = bias[s * Mp + m];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              wv[e] |= (rint_bits_g(mul_rn(sub_rn(sub_rn(p[e], qq[e]), mn), s32[s])) & 0xFu) << (4 * s);
+          }
+        }
+      }
+      *(uint4*)(tab + m * kKsub + row_at(lane, 0)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      *(uint4*)(tab + m * kKsub + row_at(lane, 1)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+    __syncthreads();
+    // 4. scan: four 32-bit sum registers hold the eight slots' 16-bit lanes;
+    //    lim holds 0x8000 + Smax in the same lanes (one integer test per lane)
+    const int n_l = G.n_l;
+    const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
+    const size_t tile_bytes = (size_t)NCHUNK * kTileChunkBytes;
+    const uint8_t* tp = a.codes + (size_t)G.tile0 * tile_bytes + (size_t)warp * tile_bytes + lane * kChunkBytes;
+    const int64_t* idp = a.ids + G.vec0;
+    if (warp == kGWarps - 1) fetch_group<kNSlots>(a, ngroups, items + (cur ^ 1), lane);
+    uint4 w[NCHUNK];
+    if (warp < ntile) load_codes<NCHUNK>(tp, w);
+    for (int t = warp; t < ntile; t += kGWarps) {
+      uint4 wn[NCHUNK];
+      const bool more = t + kGWarps < ntile;
+      if (more) load_codes<NCHUNK>(tp + kGWarps * tile_bytes, wn);
+      uint32_t W[4] = {0u, 0u, 0u, 0u};
+      adc_nibble_seq<NCHUNK>(tab_addr, w, W, std::make_integer_sequence<int, NCHUNK>{});
+      uint32_t lv[4];
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(lv[0]), "=r"(lv[1]), "=r"(lv[2]), "=r"(lv[3]) : "r"(lim_addr));
+      uint32_t pass[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) pass[r] = (lv[r] - W[r]) & 0x80008000u;
+      const int v = t * kTileVecs + lane;
+      const bool any = v < n_l && (pass[0] | pass[1] | pass[2] | pass[3]) != 0u;
+      if (__any_sync(kFull, any)) {
+        const int64_t id = any ? __ldg(idp + v) : INT64_MAX;
+#pragma unroll
+        for (int s = 0; s < kNSlots; ++s) {
+          const int rg = nib_reg(s), hf = nib_half(s);
+          const bool ok = any && ((pass[rg] >> (hf * 16 + 15)) & 1u);
+          if (__any_sync(kFull, ok)) {
+            const SlotScal sc = scal[s];
+            float* ld = md + (s * kGWarps + warp) * 32;
+            int64_t* li = mi + (s * kGWarps + warp) * 32;
+            WarpTopK<1, int64_t> top;
+            top.d[0] = ld[lane];
+            top.id[0] = li[lane];
+            float thd = ld[sc.kq - 1];
+            int64_t thi = li[sc.kq - 1];
+            if (sc.bound < thd) { thd = sc.bound; thi = INT64_MAX; }
+            const float d = add_rn(mul_rn(sc.delta32, __int2float_rn((int)((W[rg] >> (hf * 16)) & 0xFFFFu))),
+                                   sc.B32);
+            top.offer(ok, d, id, sc.kq, thd, thi);
+            if (sc.bound < thd) thd = sc.bound;
+            ld[lane] = top.d[0];
+            li[lane] = top.id[0];
+            if (thd != INFINITY) {
+              const int sm = smax_warp(thd, sc.delta32, sc.B32);
+              if (lane == 0) lim_min_at(lim, rg, hf, (uint32_t)(0x8000 + sm));
+            }
+            __syncwarp();
+          }
+        }
+      }
+      if (more) {
+#pragma unroll
+        for (int c = 0; c < NCHUNK; ++c) w[c] = wn[c];
+      }
+      tp += kGWarps * tile_bytes;
+    }
+    __syncthreads();
+    // merge the warps' lists per slot; warp s writes slot s
+    if (warp < ns) {
+      const int s = warp;
+      const SlotScal sc = scal[s];
+      WarpTopK<1, int64_t> m;
+      m.init();
+      float th = INFINITY;
+      int64_t ti = INT64_MAX;
+      for (int w2 = 0; w2 < kGWarps && sc.kq > 0; ++w2) {
+        const float cd = md[(s * kGWarps + w2) * 32 + lane];
+        const int64_t ci = mi[(s * kGWarps + w2) * 32 + lane];
+        m.offer(cd != INFINITY, cd, ci, sc.kq, th, ti);
+      }
+      if (lane < a.k) {
+        const bool ok = lane < sc.kq && m.d[0] != INFINITY;
+        a.part_d[(size_t)sc.pid * a.k + lane] = ok ? m.d[0] : INFINITY;
+        a.part_i[(size_t)sc.pid * a.k + lane] = ok ? m.id[0] : -1;
+      }
+    }
+    cur ^= 1;
+  }
+}
+
 // One warp per query: the k smallest (d, id) over the query-major partial
 // top-k (wide pairs) and the partial top-k of the query's narrow pairs.
 template <int R>
@@ -496,6 +760,32 @@ cudaError_t run_packed(const GArgs& a, cudaStream_t s) {
   return grouped_R(a.k) == 1 ? run_packed_r<NCHUNK, 1>(a, s) : run_packed_r<NCHUNK, 4>(a, s);
 }
 
+template <int NCHUNK>
+cudaError_t run_nibble(const GArgs& a, cudaStream_t s) {
+  auto kern = nibble_kernel<NCHUNK>;
+  const GLayout L(NCHUNK * 16, 1, kNSlots);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGThreads, L.total);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  kern<<<sms * per_sm, kGThreads, L.total, s>>>(a); note_launch();
+  return cudaGetLastError();
+}
+
+// The 4-bit pairs take the nibble kernel when the warps' lists are 32 wide
+// (k <= 32), the option is on and its shared memory fits.
+bool nibble_used(const Index& ix, int k) {
+  if (!ix.opt_nibble || grouped_R(k) != 1) return false;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return GLayout((int)ix.Mp, 1, kNSlots).total <= (size_t)optin;
+}
+
 }  // namespace
 
 bool grouped_supported(const Index& ix, int k) {
@@ -527,10 +817,20 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
                                   cudaStream_t s, cudaEvent_t after_qm, cudaEvent_t after_packed,
                                   const int32_t* qm_order) {
-  // narrow pairs regrouped by list, groups of four, largest lists first
-  cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kSlots, w, s, bits);
+  // narrow pairs regrouped by list, largest lists first: the pairs on tables
+  // of 5..8 bits in groups of four, those of 1..4 bits in groups of eight
+  // (or all 1..8-bit pairs in groups of four without the nibble kernel)
+  const bool nib = nibble_used(ix, k);
+  ListWork w4 = w;
+  w4.cnt = w.cnt4; w4.off = w.off4; w4.ioff = w.ioff4; w4.fill = w.fill4; w4.pairs = w.pairs4;
+  w4.gtab = w.gtab4; w4.counter = w.counter4;
+  cudaError_t e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kSlots, w, s, bits, nib ? 5 : 1, 8);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(w.counter, 0, sizeof(int), s);
+  if (nib) {
+    e = launch_invert(ix, probes, nprobe_per_q, nq, nprobe, kNSlots, w4, s, bits, 1, 4);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemsetAsync(w.counter, 0, 16 * sizeof(int), s);  // both queues' counters
   if (e != cudaSuccess) return e;
   // rank 0 and the wide pairs, query-major, into a partial top-k per query
   float* qm_d = (float*)qm_ws;
@@ -557,6 +857,21 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
     default: e = run_packed<8>(a, s); break;
   }
   if (e != cudaSuccess) return e;
+  if (nib) {
+    GArgs b = a;
+    b.cnt = w4.cnt; b.off = w4.off; b.ioff = w4.ioff; b.pairs = w4.pairs; b.gtab = w4.gtab; b.counter = w4.counter;
+    switch (ix.nchunk) {
+      case 1: e = run_nibble<1>(b, s); break;
+      case 2: e = run_nibble<2>(b, s); break;
+      case 3: e = run_nibble<3>(b, s); break;
+      case 4: e = run_nibble<4>(b, s); break;
+      case 5: e = run_nibble<5>(b, s); break;
+      case 6: e = run_nibble<6>(b, s); break;
+      case 7: e = run_nibble<7>(b, s); break;
+      default: e = run_nibble<8>(b, s); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
   if (after_packed) cudaEventRecord(after_packed, s);
   if (grouped_R(k) == 1)
     merge_grouped_kernel<1><<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(qm_d, qm_i, w.part_d, w.part_i, probes, bits,

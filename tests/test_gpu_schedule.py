@@ -168,21 +168,24 @@ def test_workload_geometries_bit_exact(amp, key, M, nlist, bits_set):
 
 def test_stage_profile_and_launch_count(amp, pair_a):
     """Stage timing splits the grouped search into its query-major pass, the
-    grouped kernel and the merge; the library's launch counter sees every
+    grouped kernels and the merge; the library's launch counter sees every
     kernel of a search (5 query-major: CL distances, CL selection, precision
-    choice, query tables, search; 11 grouped: the same four, pair regrouping
-    (count, offsets, scatter, group table), query-major pass, grouped kernel,
-    merge)."""
+    choice, query tables, search; 11 grouped without nibble packing: the same
+    four, pair regrouping (count, offsets, scatter, group table), query-major
+    pass, grouped kernel, merge; 16 with it: a second regrouping for the 4-bit
+    pairs and the nibble kernel)."""
     d, g, o = pair_a
     Q = cuda(d["queries"])
     abi = amp.abi
-    cases = (("basic", "natural", amp.policy("plain"), 5, False),
-             ("grouped", "auto", amp.policy("fixed", bits=8), 11, True))
+    cases = (("basic", "natural", amp.policy("plain"), 5, False, True),
+             ("grouped", "auto", amp.policy("fixed", bits=8), 11, True, False),
+             ("grouped", "auto", amp.policy("fixed", bits=8), 16, True, True))
     idle = {}
     try:
-        for kern, sched, pol, n_launch, grouped in cases:
+        for kern, sched, pol, n_launch, grouped, nib in cases:
             g.set_kernel(kern)
             g.set_schedule(sched)
+            g.set_nibble(nib)
             g.search(Q, 8, 10, pol)
             torch.cuda.synchronize()
             abi.anns_profile(g.handle, 1)
@@ -201,6 +204,33 @@ def test_stage_profile_and_launch_count(amp, pair_a):
     finally:
         g.set_kernel("auto")
         g.set_schedule("auto")
+        g.set_nibble(True)
+
+
+@pytest.mark.parametrize("nib", [True, False])
+def test_nibble_packing_bit_exact(amp, pair_a, nib):
+    """4-bit pairs eight to a word (or four, with the option off) return the
+    oracle's results, mixed with 6-bit, 8-bit and wide pairs, uneven nprobe
+    and k, and two query chunks."""
+    d, g, o = pair_a
+    Q = d["queries"]
+    nq, nprobe = len(Q), 12
+    npq, kpq = _uneven(nq, 17, nprobe, (1, 10, 32))
+    r = np.random.Generator(np.random.PCG64(19))
+    bits = r.choice(np.array([4, 4, 4, 4, 6, 8, 0, 12], np.uint8), size=(nq, nprobe))
+    g.set_kernel("grouped")
+    g.set_nibble(nib)
+    g.set_qchunk(9)
+    try:
+        pol = amp.policy("explicit", pair_bits=cuda(bits))
+        ids, dists = g.search(cuda(Q), nprobe, 32, pol, nprobe_per_q=cuda(npq), k_per_q=cuda(kpq))
+        ri, rd = ivfpq.search(o, Q, nprobe, 32, bits=bits, nprobe_per_q=npq, k_per_q=kpq)
+        np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+        np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+    finally:
+        g.set_kernel("auto")
+        g.set_nibble(True)
+        g.set_qchunk(0)
 
 
 @pytest.mark.parametrize("qchunk", [1, 7, 64, 0])
