@@ -467,6 +467,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     index = amp.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"], device=local_rank)
     if args.no_nibble:
         index.set_nibble(False)
+    if args.qchunk:
+        index.set_qchunk(args.qchunk)
     Q = torch.from_numpy(W["queries"]).to(dev)
     nq, k = Q.shape[0], cfg["k"]
     stream = torch.cuda.current_stream(dev)
@@ -520,9 +522,34 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
-    train_s = train(nprobe)
     Qc = torch.from_numpy(W["cal_queries"]).to(dev)
-    margin, tried = calibrate_margin(amp, Qc, W["cal_gt"], nprobe, k, run_q)
+
+    def cal_ms(pol):
+        """Mean time of a search of the calibration queries (3 runs after one)."""
+        run_q(Qc, nprobe, pol)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
+        for _ in range(3):
+            index.search(Qc, nprobe, k, pol, stream=stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 3
+
+    # the predictor's classes chosen on the calibration queries: trained on
+    # the three GB300 tables (4-bit / 8-bit / wide) and on two (8-bit / wide),
+    # each calibrated on the recall budget; the faster one is kept
+    class_maps = [False] if args.two_classes else [True, False]
+    choice = {}
+    for nib in class_maps:
+        args.two_classes = not nib
+        t_s = train(nprobe)
+        m, tr = calibrate_margin(amp, Qc, W["cal_gt"], nprobe, k, run_q)
+        pol = amp.policy("mlp", margin=m if np.isfinite(m) else 3.0e38, width_map=True)
+        choice[nib] = dict(margin=m, tried=tr, train_s=t_s, cal_ms=cal_ms(pol), weights=index.get_predictor())
+    best_nib = min(choice, key=lambda c: choice[c]["cal_ms"])
+    args.two_classes = not best_nib
+    index.set_predictor(choice[best_nib]["weights"])
+    margin, tried, train_s = choice[best_nib]["margin"], choice[best_nib]["tried"], choice[best_nib]["train_s"]
     eq2_th, eq2_tried = calibrate_eq2(amp, Qc, W["cal_gt"], nprobe, k, run_q)
     adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True)
     predictor_w = index.get_predictor()
@@ -704,7 +731,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             svr_info, bits_mix=mixes["svr"], speedup_vs_plain=round(qps["svr"] / qps["plain"], 3),
             recall_at_10=round(recs["svr"][0], 4), mlp_speedup_vs_plain=round(qps["mlp"] / qps["plain"], 3),
             mlp_recall_at_10=round(recs["mlp"][0], 4)),
-        "predictor": {"train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
+        "predictor": {"class_map_choice": {("3 tables (4/8/wide)" if c else "2 tables (8/wide)"): {
+                          "margin": choice[c]["margin"], "calibration_ms": round(choice[c]["cal_ms"], 4)}
+                          for c in choice},
+                      "train_queries": ntrain, "train_s": round(train_s, 2), "epochs": args.epochs,
                       "classes": "GB300 tables (8-bit / wide)" if args.two_classes else "GB300 tables (4-bit / 8-bit / wide)", "high_weight": args.high_weight,
                       "margin_calibration_recall_loss_pts": {str(a): b for a, b in tried.items()},
                       "recall_loss_budget_pts": LOSS_BUDGET},
@@ -1120,6 +1150,7 @@ def main():
     ap.add_argument("--two-classes", action="store_true",
                     help="train the predictor on two GB300 tables (8-bit / wide) instead of three (4 / 8 / wide)")
     ap.add_argument("--no-nibble", action="store_true", help="4-bit pairs four per word (no nibble packing)")
+    ap.add_argument("--qchunk", type=int, default=0, help="queries per chunk of the grouped work order (0 = auto)")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

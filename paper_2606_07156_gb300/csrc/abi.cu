@@ -545,11 +545,7 @@ __global__ void debug_exact_sum_kernel(const float* __restrict__ vals, int64_t n
   const int64_t set = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (set >= nsets) return;
-  ExactSum acc;
-  xsum_init(acc);
-  for (int i = lane; i < n; i += 32) xsum_add(acc, vals[set * n + i]);
-  xsum_warp(acc);
-  const float r = xsum_round(acc);
+  const float r = warp_exact_sum(vals + set * n, n, 0.f, false);
   if (lane == 0) out[set] = r;
 }
 }  // namespace anns

@@ -226,6 +226,51 @@ __device__ __forceinline__ float xsum_round(const ExactSum& a) {
   return __uint_as_float(bits | (neg ? 0x80000000u : 0u));
 }
 
+// The exact sum of v[0..n) (lanes striding) and, if with_extra, `extra`
+// (added by lane 0), rounded once to FP32; every lane gets the result. Fast
+// path: when the nonzero values' lowest set-bit positions (LSB weights
+// 2^(p-149), p = max(exponent field, 1) - 1) span at most 21 positions, any
+// partial sum of up to 256 of them is a multiple of the smallest weight below
+// 2^(21 + 24 + 8) of it, so every FP64 addition is exact and one FP64 -> FP32
+// conversion is the single rounding; otherwise (or with a non-finite value)
+// the fixed-point accumulator above.
+__device__ __forceinline__ float warp_exact_sum(const float* v, int n, float extra, bool with_extra) {
+  const int lane = threadIdx.x & 31;
+  int pmin = 0x7fffffff, pmax = -1;
+  bool odd = false;
+  auto look = [&](float x) {
+    const uint32_t u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xffu);
+    if (e == 0xff) { odd = true; return; }
+    if ((u & 0x7fffffffu) == 0u) return;
+    const int p = e ? e - 1 : 0;
+    pmin = min(pmin, p);
+    pmax = max(pmax, p);
+  };
+  for (int i = lane; i < n; i += 32) look(v[i]);
+  if (with_extra && lane == 0) look(extra);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    pmin = min(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+    pmax = max(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+  }
+  odd = __any_sync(0xffffffffu, odd);
+  if (!odd && n < 256 && (pmax < 0 || pmax - pmin <= 21)) {
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) acc = __dadd_rn(acc, (double)v[i]);
+    if (with_extra && lane == 0) acc = __dadd_rn(acc, (double)extra);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    return __double2float_rn(acc);
+  }
+  ExactSum B;
+  xsum_init(B);
+  for (int i = lane; i < n; i += 32) xsum_add(B, v[i]);
+  if (with_extra && lane == 0) xsum_add(B, extra);
+  xsum_warp(B);
+  return xsum_round(B);
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));

@@ -88,16 +88,9 @@ __global__ void __launch_bounds__(256) label_kernel(const LabelArgs a) {
     }
     __syncthreads();
     if (warp == 0) {
-      ExactSum B;
-      xsum_init(B);
       float range = 0.f;
-      for (int m = lane; m < a.M; m += 32) {
-        xsum_add(B, bias[m]);
-        range = fmaxf(range, rowmax[m]);
-      }
-      if (lane == 0) xsum_add(B, d2);
-      xsum_warp(B);
-      const float B32 = xsum_round(B);
+      for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[m]);
+      const float B32 = warp_exact_sum(bias, a.M, d2, true);
       range = warp_max(range);
       if (lane < kBitsN) {
         const int L = (1 << kBitsTab[lane]) - 1;

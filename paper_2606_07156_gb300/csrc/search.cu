@@ -85,8 +85,7 @@ __device__ __forceinline__ uint32_t rint_bits(float y) { return __float_as_uint(
 // The FP64 step delta64 (an FP64 division) is only computed for the taps.
 // Returns s32.
 template <bool WITH_D64>
-__device__ __forceinline__ float pair_scale(int M, int b, float d2, const float* bias, const float* rowmax,
-                                            PairScal* out) {
+__device__ __forceinline__ float pair_scale(int M, int b, const float* rowmax, PairScal* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float range = 0.f;
   for (int m = lane; m < M; m += 32) range = fmaxf(range, rowmax[m]);
@@ -94,25 +93,25 @@ __device__ __forceinline__ float pair_scale(int M, int b, float d2, const float*
   const int L = (1 << b) - 1;
   // fl32 of the FP64 quotient equals the correctly rounded FP32 quotient
   const float s32 = range > 0.f ? __fdiv_rn((float)L, range) : 0.f;
-  if (warp == 0) {
-    ExactSum B;
-    xsum_init(B);
-    for (int m = lane; m < M; m += 32) xsum_add(B, bias[m]);
-    if (lane == 0) xsum_add(B, d2);
-    xsum_warp(B);
-    const float B32 = xsum_round(B);
-    if (lane == 0) {
-      PairScal sc;
-      sc.delta64 = WITH_D64 && range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
-      sc.s32 = s32;
-      sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
-      sc.B32 = B32;
-      sc.range = range;
-      sc.L = L;
-      *out = sc;
-    }
+  if (warp == 0 && lane == 0) {
+    PairScal sc;
+    sc.delta64 = WITH_D64 && range > 0.f ? __ddiv_rn((double)range, (double)L) : 0.0;
+    sc.s32 = s32;
+    sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)L) : 0.f;
+    sc.B32 = 0.f;  // pair_offset writes it
+    sc.range = range;
+    sc.L = L;
+    *out = sc;
   }
   return s32;
+}
+
+// The pair's offset B32 (warp 0): the exact sum of D2 and the row minima,
+// rounded once. Called once the levels are written, when the build's
+// registers are free; the caller synchronises before the scan reads it.
+__device__ __noinline__ void pair_offset(int M, float d2, const float* bias, PairScal* out) {
+  const float B32 = warp_exact_sum(bias, M, d2, true);
+  if ((threadIdx.x & 31) == 0) out->B32 = B32;
 }
 
 // Levels of 8 entries of one row: t = rint(fl32(fl32(T' - bias) * s32)).
@@ -175,7 +174,7 @@ __device__ void build_lut(const float* __restrict__ P, const float* __restrict__
   }
   __syncthreads();
   if (b == 0) return;
-  const float s32 = pair_scale<true>(M, b, d2, s.bias, s.rowmax, s.sc);
+  const float s32 = pair_scale<true>(M, b, s.rowmax, s.sc);
   const size_t esz = b <= 8 ? 1 : 2;
   for (int m = warp; m < Mp; m += nwarps) {
     float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -190,6 +189,7 @@ __device__ void build_lut(const float* __restrict__ P, const float* __restrict__
     quantise8(x, mn, s32, n);
     store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub * esz, lane);
   }
+  if (warp == 0) pair_offset(M, d2, s.bias, s.sc);
   __syncthreads();
 }
 
@@ -241,7 +241,7 @@ __device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, cons
     }
   }
   __syncthreads();
-  const float s32 = pair_scale<false>(M, b, d2, bias, rowmax, sc);
+  const float s32 = pair_scale<false>(M, b, rowmax, sc);
   const size_t esz = b <= 8 ? 1 : 2;
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
@@ -249,6 +249,7 @@ __device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, cons
     quantise8(t[r], mn[r], s32, n);
     store_levels(b, n, (uint8_t*)lv + (size_t)(warp + r * nwarps) * kKsub * esz, lane);
   }
+  if (warp == 0) pair_offset(M, d2, bias, sc);
 }
 
 template <int NCHUNK>
@@ -324,9 +325,10 @@ __device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, Wa
 
 // Query-major search: one query per block at a time. Per pair the block builds
 // the table (in registers for Mp <= 32, else staged in shared memory), then
-// every warp scans tiles of the list. Four blocks per SM for Mp <= 32.
+// every warp scans tiles of the list. Four blocks per SM for Mp <= 32 (two
+// with the 128-entry lists of k > 32).
 template <int NCHUNK, int R>
-__global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? 4 : 1) search_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? (R == 1 ? 4 : 2) : 1) search_kernel(const SearchArgs a) {
   Smem s(a.lay);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tstride = (int64_t)a.Mp * kKsub;

@@ -154,6 +154,13 @@ __device__ __forceinline__ void lim_min_at(uint32_t* lim, int reg, int half, uin
 // Byte tables: slots 0 and 2 share limit word 0, slots 1 and 3 word 1.
 __device__ __forceinline__ void lim_min(uint32_t* lim, int s, uint32_t v) { lim_min_at(lim, s & 1, s >> 1, v); }
 
+// A slot's offset (whole warp): the exact sum of D2 and the slot's row
+// minima, rounded once (kept out of line: its accumulator does not add to the
+// scan's register pressure).
+__device__ __forceinline__ float slot_offset(const float* bias_s, int M, float d2, bool present) {
+  return warp_exact_sum(bias_s, present ? M : 0, d2, true);
+}
+
 // The next group from the work queue (whole warp; lanes 0..S-1 take the slots).
 template <int S = kSlots>
 __device__ __forceinline__ void fetch_group(const GArgs& a, int ngroups, GItemT<S>* out, int lane) {
@@ -270,21 +277,17 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
       float range = 0.f;
       const int p = G.pid[s], bs = G.bits[s];
       const float d2 = G.d2[s];
-      ExactSum B;
-      xsum_init(B);
       if (s < ns) {
         for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
         range = warp_max(range);
-        for (int m = lane; m < a.M; m += 32) xsum_add(B, bias[s * Mp + m]);
       }
-      if (lane == 0) xsum_add(B, d2);
-      xsum_warp(B);
+      const float B32 = slot_offset(bias + s * Mp, a.M, d2, s < ns);
       // every lane forms the same values (range and B are warp-uniform)
       const int Lv = (1 << bs) - 1;
       SlotScal sc;
       sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
       sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
-      sc.B32 = xsum_round(B);
+      sc.B32 = B32;
       sc.kq = s < ns ? G.kq[s] : 0;
       sc.bound = sc.kq > 0 ? G.bound[s] : INFINITY;
       sc.pid = p;
@@ -545,20 +548,16 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 3 : (NCHUNK <= 4 ? 2 
       float range = 0.f;
       const int p = G.pid[s], bs = G.bits[s];
       const float d2 = G.d2[s];
-      ExactSum B;
-      xsum_init(B);
       if (s < ns) {
         for (int m = lane; m < a.M; m += 32) range = fmaxf(range, rowmax[s * Mp + m]);
         range = warp_max(range);
-        for (int m = lane; m < a.M; m += 32) xsum_add(B, bias[s * Mp + m]);
       }
-      if (lane == 0) xsum_add(B, d2);
-      xsum_warp(B);
+      const float B32 = slot_offset(bias + s * Mp, a.M, d2, s < ns);
       const int Lv = (1 << bs) - 1;
       SlotScal sc;
       sc.s32 = range > 0.f ? __fdiv_rn((float)Lv, range) : 0.f;
       sc.delta32 = range > 0.f ? __fdiv_rn(range, (float)Lv) : 0.f;
-      sc.B32 = xsum_round(B);
+      sc.B32 = B32;
       sc.kq = s < ns ? G.kq[s] : 0;
       sc.bound = sc.kq > 0 ? G.bound[s] : INFINITY;
       sc.pid = p;
