@@ -565,8 +565,34 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         policies["eq2"] = amp.policy("eq2", thresholds=eq2_th, width_map=True)
     for b in (4, 6, 8, 12, 16):
         policies[f"fixed{b}"] = amp.policy("fixed", bits=b)
+    # the adaptive policies run in the configuration the library's autotuner
+    # picks on this batch (kernel, query order, grouped work-order chunk);
+    # the others in the automatic one
+    KN = {abi.KERNEL_BASIC: "query-major", abi.KERNEL_LIST_MAJOR: "list-major", abi.KERNEL_GROUPED: "grouped"}
+    SN = {abi.SCHED_NATURAL: "natural", abi.SCHED_LPT: "longest-first"}
+    tuned = None
+    if not args.no_autotune:
+        trials = index.autotune(Q, nprobe, k, adaptive, reps=2)
+        best_t = min(trials, key=lambda r: r[2])
+        tuned = {"kernel": KN.get(best_t[0], str(best_t[0])), "schedule": SN.get(best_t[1], str(best_t[1])),
+                 "qchunk": int(best_t[3]),
+                 "trials_ms": {f"{KN.get(t[0], t[0])}/{SN.get(t[1], t[1])}/q{t[3]}": round(t[2], 3) for t in trials}}
+        cfg_tuned = (best_t[0], best_t[1], best_t[3])
+
+    def use(name):
+        """The adaptive policies in the tuned configuration, the rest automatic."""
+        if tuned is not None and name in ("mlp", "svr"):
+            abi.anns_set_option(index.handle, abi.OPT_KERNEL, cfg_tuned[0])
+            abi.anns_set_option(index.handle, abi.OPT_SCHEDULE, cfg_tuned[1])
+            abi.anns_set_option(index.handle, abi.OPT_QCHUNK, cfg_tuned[2])
+        else:
+            index.set_kernel("auto")
+            index.set_schedule("auto")
+            index.set_qchunk(args.qchunk)
+
     recs, mixes, full = {}, {}, {}
     for name, pol in policies.items():
+        use(name)
         ids, dists = run_full(nprobe, pol)
         if name in ("mlp", "fixed8", "plain"):
             full[name] = (ids, dists)
@@ -575,6 +601,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     log(f"nprobe {nprobe}; margin {margin} {tried}; eq2 {eq2_th} {eq2_tried}; recalls {recs}")
 
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    use("mlp")
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -597,8 +624,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     ms_pol = {"mlp": ms_ad}
     for name, pol in policies.items():
         if name != "mlp":
+            use(name)
             ms_pol[name] = time_steps(lambda: index.search(Q, nprobe, k, pol, stream=stream, out=out),
                                       args.steps, args.warmup, stream, flush)
+    use("mlp")
     # end to end through the host-buffer entry point (pinned in, pinned out)
     Qh = torch.from_numpy(W["queries"]).pin_memory()
     ih = torch.empty((nq, k), dtype=torch.int64).pin_memory()
@@ -618,6 +647,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     # reaches 0.9 (the predictor retrained and its margin recalibrated there,
     # on the 1-recall@10 reading)
     op2 = None
+    use("plain")
     if not args.no_second_point:
         cands = [p for p in (1, 2, 4, 8, 16, 32, 64) if p <= min(cfg["nlist"], 128)]
         nn_sweep, np2 = {}, None
@@ -726,6 +756,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                             "top10_kept_vs_plain": round(recs[name][1], 4),
                             "nn_in_top10": round(recs[name][2], 4),
                             "ms_per_step": round(totals[name] * 1e3 / args.steps, 4)} for name in qps},
+        "autotuned": tuned,
         "eq2_thresholds": list(eq2_th) if eq2_th is not None else None,
         "svr_comparator": None if svr_info is None else dict(
             svr_info, bits_mix=mixes["svr"], speedup_vs_plain=round(qps["svr"] / qps["plain"], 3),
@@ -751,6 +782,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "wall_s_timed": round(wall, 3),
     }
     # the same step replayed as one CUDA graph
+    use("mlp")
     graph, _, _ = index.capture_graph(Q, nprobe, k, adaptive, out=out)
     ms_graph = time_steps(lambda: graph.launch(stream), args.steps, args.warmup, stream, flush)
     graph.close()
@@ -1151,6 +1183,7 @@ def main():
                     help="train the predictor on two GB300 tables (8-bit / wide) instead of three (4 / 8 / wide)")
     ap.add_argument("--no-nibble", action="store_true", help="4-bit pairs four per word (no nibble packing)")
     ap.add_argument("--qchunk", type=int, default=0, help="queries per chunk of the grouped work order (0 = auto)")
+    ap.add_argument("--no-autotune", action="store_true", help="run the adaptive policies in the automatic configuration")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

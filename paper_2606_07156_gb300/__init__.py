@@ -257,7 +257,8 @@ class Index:
         return Graph(h), ids, dists
 
     def autotune(self, queries, nprobe: int, k: int, pol=None, nprobe_per_q=None, k_per_q=None, reps: int = 3):
-        """Times every (kernel, schedule) choice, installs the fastest; returns [(kernel, schedule, ms)]."""
+        """Times every (kernel, schedule, work-order chunk) choice, installs the fastest;
+        returns [(kernel, schedule, ms, qchunk)]."""
         return abi.anns_autotune(self.handle, _ptr(queries), queries.shape[0], nprobe, _ptr(nprobe_per_q), k,
                                  _ptr(k_per_q), pol, reps)
 

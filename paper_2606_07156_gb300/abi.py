@@ -357,7 +357,7 @@ def anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, policy, 
     pol = ctypes.byref(policy) if policy is not None else None
     _check(_lib.anns_autotune(index, queries, nq, nprobe, nprobe_per_q, k, k_per_q, pol, reps, res, 16,
                               ctypes.byref(n), stream))
-    return [(res[i].kernel, res[i].schedule, res[i].ms) for i in range(n.value)]
+    return [(res[i].kernel, res[i].schedule, res[i].ms, res[i].qchunk) for i in range(n.value)]
 
 
 def anns_locate(index, queries, nq, nprobe, nprobe_per_q, cl_prec, probes_out, probe_d2_out, stream=None) -> None:

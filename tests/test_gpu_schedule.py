@@ -112,10 +112,11 @@ def test_autotune_installs_a_configuration(amp, pair_a):
     d, g, o = pair_a
     Q = d["queries"]
     res = g.autotune(cuda(Q), 8, 10, amp.policy("fixed", bits=8), reps=2)
-    kinds = {(kk, s) for kk, s, _ in res}
+    kinds = {(kk, s) for kk, s, *_ in res}
     assert (amp.abi.KERNEL_BASIC, amp.abi.SCHED_NATURAL) in kinds
     assert (amp.abi.KERNEL_BASIC, amp.abi.SCHED_LPT) in kinds
-    assert all(ms > 0 for _, _, ms in res)
+    assert all(r[2] > 0 for r in res)
+    assert (amp.abi.KERNEL_GROUPED, amp.abi.SCHED_LPT) in kinds
     ids, dists = g.search(cuda(Q), 8, 10, amp.policy("fixed", bits=8))
     ri, rd = ivfpq.search(o, Q, 8, 10, bits=8)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
