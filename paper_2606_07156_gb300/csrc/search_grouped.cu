@@ -477,10 +477,33 @@ __device__ __forceinline__ void adc_nibble_seq(uint32_t base, const uint4 (&w)[N
   (nibble_chunk<NCHUNK, C>(base, w, W, std::make_integer_sequence<int, 16>{}), ...);
 }
 
+// Shared memory of the nibble kernel: the row statistics (bias, rowmax) live
+// in the space of the warps' top-k lists, which start only after the levels
+// are written (three blocks per SM at 48 sub-spaces).
+struct NLayout {
+  size_t tab, scal, item, lim, md, mi, bias, rowmax, total;
+  __host__ __device__ explicit NLayout(int Mp) {
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t o = 0;
+    tab = o; o += al((size_t)Mp * kKsub * 4);
+    scal = o; o += al(sizeof(SlotScal) * kNSlots);
+    item = o; o += al(2 * sizeof(GItemT<kNSlots>));
+    lim = o; o += al(4 * 4);
+    md = o;
+    const size_t lists = al((size_t)kNSlots * kGWarps * 32 * 4) + al((size_t)kNSlots * kGWarps * 32 * 8);
+    const size_t stats = 2 * al((size_t)kNSlots * Mp * 4);
+    mi = md + al((size_t)kNSlots * kGWarps * 32 * 4);
+    bias = md;
+    rowmax = md + al((size_t)kNSlots * Mp * 4);
+    o += lists > stats ? lists : stats;
+    total = o + 256;
+  }
+};
+
 template <int NCHUNK>
-__global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 3 : (NCHUNK <= 4 ? 2 : 1)) nibble_kernel(const GArgs a) {
+__global__ void __launch_bounds__(kGThreads, NCHUNK <= 4 ? 3 : 1) nibble_kernel(const GArgs a) {
   constexpr int Mp = NCHUNK * 16;
-  const GLayout L(Mp, 1, kNSlots);
+  const NLayout L(Mp);
   const uint32_t raw = smem_addr(anns_dyn_smem);
   const uint32_t pad = (256u - (raw & 255u)) & 255u;
   unsigned char* base = anns_dyn_smem + pad;
@@ -568,12 +591,6 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 3 : (NCHUNK <= 4 ? 2 
         lim_min_at(lim, nib_reg(s), nib_half(s), (uint32_t)(0x8000 + seed));
       }
     }
-    // the warps' top-k lists start empty
-#pragma unroll
-    for (int s = 0; s < kNSlots; ++s) {
-      md[(s * kGWarps + warp) * 32 + lane] = INFINITY;
-      mi[(s * kGWarps + warp) * 32 + lane] = INT64_MAX;
-    }
     __syncthreads();
     // 3. interleaved levels: nibble s of entry e's word = slot s's level (<= 15)
     float s32[kNSlots];
@@ -600,6 +617,13 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 3 : (NCHUNK <= 4 ? 2 
       }
       *(uint4*)(tab + m * kKsub + row_at(lane, 0)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
       *(uint4*)(tab + m * kKsub + row_at(lane, 1)) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+    __syncthreads();
+    // the warps' top-k lists start empty (over the row statistics, no longer needed)
+#pragma unroll
+    for (int s = 0; s < kNSlots; ++s) {
+      md[(s * kGWarps + warp) * 32 + lane] = INFINITY;
+      mi[(s * kGWarps + warp) * 32 + lane] = INT64_MAX;
     }
     __syncthreads();
     // 4. scan: four 32-bit sum registers hold the eight slots' 16-bit lanes;
@@ -762,7 +786,7 @@ cudaError_t run_packed(const GArgs& a, cudaStream_t s) {
 template <int NCHUNK>
 cudaError_t run_nibble(const GArgs& a, cudaStream_t s) {
   auto kern = nibble_kernel<NCHUNK>;
-  const GLayout L(NCHUNK * 16, 1, kNSlots);
+  const NLayout L(NCHUNK * 16);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -782,7 +806,7 @@ bool nibble_used(const Index& ix, int k) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return GLayout((int)ix.Mp, 1, kNSlots).total <= (size_t)optin;
+  return NLayout((int)ix.Mp).total <= (size_t)optin;
 }
 
 }  // namespace
