@@ -462,6 +462,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     cfg, W = workload(args.config, device=dev)
+    if args.cl == "auto":
+        args.cl = "bf16" if cfg["dim"] >= 256 else "fp32"
     if args.nq:
         W = dict(W, queries=W["queries"][:args.nq], gt=W["gt"][:args.nq])
     index = amp.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"], device=local_rank)
@@ -551,7 +553,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     index.set_predictor(choice[best_nib]["weights"])
     margin, tried, train_s = choice[best_nib]["margin"], choice[best_nib]["tried"], choice[best_nib]["train_s"]
     eq2_th, eq2_tried = calibrate_eq2(amp, Qc, W["cal_gt"], nprobe, k, run_q)
-    adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True)
+    # the adaptive policies run CL on the tensor cores (BF16 GEMM, exact FP32
+    # re-rank: the same probes as the FP32 CL)
+    adaptive = amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True, cl=args.cl)
     predictor_w = index.get_predictor()
     policies = {"mlp": adaptive, "plain": plain}
     svr_info = None
@@ -560,7 +564,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         svr_margin, svr_tried = calibrate_svr(amp, Qc, W["cal_gt"], nprobe, run_q)
         svr_info.update({"margin": svr_margin, "margin_calibration_recall_loss_pts": {str(a): b for a, b in
                                                                                      svr_tried.items()}})
-        policies["svr"] = amp.policy("svr", margin=svr_margin, width_map=True)
+        policies["svr"] = amp.policy("svr", margin=svr_margin, width_map=True, cl=args.cl)
     if eq2_th is not None:
         policies["eq2"] = amp.policy("eq2", thresholds=eq2_th, width_map=True)
     for b in (4, 6, 8, 12, 16):
@@ -732,6 +736,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "data": f"synthetic (seeded {cfg['name']} mixture; no public dataset)",
         "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
+                   "cl": f"{args.cl} (adaptive policies; plain FP32 uses the FP32 rule)",
                    "policy": f"learned MLP per (query, list) trained on GB300 table classes, round-up "
                              f"margin {margin} (recall-loss budget {LOSS_BUDGET} pt on calibration queries), widths 6->8 bits "
                              f"and 12/16->FP32; 4-bit tables eight queries per gather",
@@ -1184,6 +1189,9 @@ def main():
     ap.add_argument("--no-nibble", action="store_true", help="4-bit pairs four per word (no nibble packing)")
     ap.add_argument("--qchunk", type=int, default=0, help="queries per chunk of the grouped work order (0 = auto)")
     ap.add_argument("--no-autotune", action="store_true", help="run the adaptive policies in the automatic configuration")
+    ap.add_argument("--cl", default="auto", choices=("auto", "fp32", "bf16"),
+                    help="CL of the adaptive policies: FP32 rule, BF16 tensor cores + exact re-rank, or auto "
+                         "(BF16 from D = 256 on; below it the GEMM is too small to repay the re-rank)")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)
