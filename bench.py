@@ -304,10 +304,11 @@ def bits_mix(index, abi, nq: int, nprobe: int, npq=None) -> dict:
 
 def cl_tensor_bench(amp, dev, steps: int, warmup: int, flush) -> dict:
     """The coarse stage alone at the embedding-shaped CL size (20000 queries x
-    8192 centroids x D = 768, nprobe 64): FP32 CUDA-core path vs the tcgen05
-    BF16 GEMM + exact re-rank. Centroids are draws of the same mixture as the
-    queries (stand-ins for trained centroids; the stage's cost does not depend
-    on the lists' contents)."""
+    8192 centroids x D = 768, nprobe 64): the FP32 CUDA-core path vs the
+    tcgen05 GEMM with BF16, FP16 or FP8 E4M3 operands + the exact re-rank.
+    Centroids are draws of the same mixture as the queries (stand-ins for
+    trained centroids; the stage's cost does not depend on the lists'
+    contents)."""
     import torch
     from workloads import make_queries
     nq, nlist, dim, M, nprobe = 20000, 8192, 768, 96, 64
@@ -317,23 +318,25 @@ def cl_tensor_bench(amp, dev, steps: int, warmup: int, flush) -> dict:
     codes = np.zeros((nlist, M), np.uint8)
     ix = amp.Index(C, books, codes, np.arange(nlist, dtype=np.int32), device=dev.index)
     st = torch.cuda.current_stream(dev)
-    out = {}
-    res = {}
-    for cl in ("fp32", "bf16"):
-        res[cl] = ix.locate(Q, nprobe, cl=cl, stream=st)
-        ms = time_steps(lambda: ix.locate(Q, nprobe, cl=cl, stream=st), steps, warmup, st, flush)
-        out[cl] = float(np.median(ms))
-    torch.cuda.synchronize()
-    same = bool(torch.equal(res["fp32"][0], res["bf16"][0]) and torch.equal(res["fp32"][1], res["bf16"][1]))
-    ncand = ix.tap(amp.abi.TAP_COARSE_CANDIDATES, (nq,), np.int32)
+    out = {"workload": f"embedding-shaped CL: {nq} queries x {nlist} centroids x D={dim}, nprobe={nprobe}"}
+    ref = None
+    for cl in ("fp32", "bf16", "fp16", "fp8"):
+        res = ix.locate(Q, nprobe, cl=cl, stream=st)
+        ms = float(np.median(time_steps(lambda: ix.locate(Q, nprobe, cl=cl, stream=st), steps, warmup, st, flush)))
+        torch.cuda.synchronize()
+        rec = {"ms": round(ms, 4)}
+        if cl == "fp32":
+            ref = res
+        else:
+            rec["identical_probes"] = bool(torch.equal(ref[0], res[0]) and torch.equal(ref[1], res[1]))
+            rec["rerank_candidates_mean"] = round(float(ix.tap(amp.abi.TAP_COARSE_CANDIDATES, (nq,),
+                                                               np.int32).mean()), 1)
+            rec["speedup_vs_fp32"] = round(out["fp32"]["ms"] / ms, 2)
+            per = 128 if cl == "fp8" else 64
+            rec["gemm_flop"] = 2.0 * nq * nlist * ((dim + per - 1) // per * per)
+        out[cl] = rec
     ix.close()
-    Dp = (dim + 63) // 64 * 64
-    flops = 2.0 * nq * nlist * Dp
-    return {"workload": f"embedding-shaped CL: {nq} queries x {nlist} centroids x D={dim}, nprobe={nprobe}",
-            "fp32_ms": round(out["fp32"], 4), "bf16_tc_ms": round(out["bf16"], 4),
-            "speedup": round(out["fp32"] / out["bf16"], 2), "identical_probes": same,
-            "rerank_candidates_mean": round(float(ncand.mean()), 1),
-            "gemm_flop": flops, "bf16_effective_tflops": round(flops / (out["bf16"] / 1e3) / 1e12, 1)}
+    return out
 
 
 def calibrate_margin_nn(amp, Qc, gt_c, nprobe: int, run, budget: float = LOSS_BUDGET):
@@ -1189,9 +1192,10 @@ def main():
     ap.add_argument("--no-nibble", action="store_true", help="4-bit pairs four per word (no nibble packing)")
     ap.add_argument("--qchunk", type=int, default=0, help="queries per chunk of the grouped work order (0 = auto)")
     ap.add_argument("--no-autotune", action="store_true", help="run the adaptive policies in the automatic configuration")
-    ap.add_argument("--cl", default="auto", choices=("auto", "fp32", "bf16"),
-                    help="CL of the adaptive policies: FP32 rule, BF16 tensor cores + exact re-rank, or auto "
-                         "(BF16 from D = 256 on; below it the GEMM is too small to repay the re-rank)")
+    ap.add_argument("--cl", default="auto", choices=("auto", "fp32", "bf16", "fp16", "fp8"),
+                    help="CL of the adaptive policies: FP32 rule, tensor cores (BF16, FP16 or FP8 E4M3 "
+                         "operands) + exact re-rank, or auto (the tensor cores from D = 256 on; below it the "
+                         "GEMM is too small to repay the re-rank)")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

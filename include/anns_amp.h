@@ -202,15 +202,17 @@ enum {
   ANNS_LUT_EXPLICIT = 4,      /* caller-provided bits per (query, probe rank) */
   ANNS_LUT_SVR = 5            /* the SVR-RBF regressor of Section 3.4 (anns_set_svr) */
 };
-enum { ANNS_PREC_FP32 = 0, ANNS_PREC_BF16 = 1, ANNS_PREC_FP8E4M3 = 2 };
+enum { ANNS_PREC_FP32 = 0, ANNS_PREC_BF16 = 1, ANNS_PREC_FP8E4M3 = 2, ANNS_PREC_FP16 = 3 };
 
 typedef struct {
   int32_t lut_mode;        /* ANNS_LUT_* */
   int32_t fixed_bits;      /* 4, 6, 8, 12 or 16 (FIXED_BITS) */
-  int32_t cl_prec;         /* coarse distances: ANNS_PREC_FP32, or ANNS_PREC_BF16 = BF16
-                              tensor-core GEMM on centred operands, then every list
-                              within the GEMM's error bound of the nprobe-th re-ranked
-                              by the FP32 rule: same probes and distances as FP32 */
+  int32_t cl_prec;         /* coarse distances: ANNS_PREC_FP32, or a tensor-core GEMM
+                              on centred operands scaled per row by a power of two,
+                              in ANNS_PREC_BF16, ANNS_PREC_FP16 or ANNS_PREC_FP8E4M3
+                              with FP32 accumulation, then every list within the
+                              GEMM's error bound of the nprobe-th re-ranked by the
+                              FP32 rule: same probes and distances as FP32 */
   int32_t lc_prec;         /* ANNS_PREC_* for the LUT build; FP32 only */
   float eq2_thresholds[4]; /* HEURISTIC_EQ2: g thresholds for 4, 6, 8, 12 bits */
   float fallback_margin;   /* MLP round-up margin tau (not NaN): the fewest bits b such
@@ -268,8 +270,8 @@ int anns_get_info(const anns_index* index, anns_index_info* out);
  *   PROBE_D2 float [nq * nprobe]  their FP32 coarse distances
  *   BITS     uint8 [nq * nprobe]  chosen bits per pair (0 = FP32 LUT)
  *   FEATURES float [nq * nprobe * 5] predictor features (MLP / EQ2 modes)
- *   COARSE_APPROX     float [nq * nlist] BF16 tensor-core distances D~ (last
- *                     search with cl_prec = BF16)
+ *   COARSE_APPROX     float [nq * nlist] tensor-core distances D~ (last
+ *                     search with cl_prec = BF16, FP16 or FP8E4M3)
  *   COARSE_CANDIDATES int32 [nq] lists re-ranked in FP32 per query (same)
  * Index taps:
  *   LIST_SIZES int64 [nlist], LIST_RADIUS float [nlist],
@@ -498,8 +500,9 @@ int anns_train_predictor(anns_index* index, const float* train_q, int64_t nq, in
 
 /* The coarse stage (cluster locating, CL of Section 2.1) alone: the nprobe
  * nearest lists of each query by the FP32 rule, ties by list id, computed
- * with cl_prec = ANNS_PREC_FP32 (CUDA cores) or ANNS_PREC_BF16 (tensor-core
- * GEMM + exact re-rank; same output). probes_out device int32 [nq * nprobe],
+ * with cl_prec = ANNS_PREC_FP32 (CUDA cores), or ANNS_PREC_BF16 / FP16 /
+ * FP8E4M3 (tensor-core GEMM + exact re-rank; same output). probes_out device
+ * int32 [nq * nprobe],
  * probe_d2_out device float32 [nq * nprobe] (padding -1 / +inf past a query's
  * nprobe_per_q). Uses the index workspace (asynchronous on cuda_stream). */
 int anns_locate(anns_index* index, const float* queries, int64_t nq, int32_t nprobe,

@@ -16,6 +16,8 @@ from .abi import AnnsError  # noqa: F401
 
 _MODES = {"plain": abi.LUT_PLAIN_FP32, "fixed": abi.LUT_FIXED_BITS, "eq2": abi.LUT_HEURISTIC_EQ2,
           "mlp": abi.LUT_MLP, "explicit": abi.LUT_EXPLICIT, "svr": abi.LUT_SVR}
+# CL operands: FP32 on the CUDA cores, or a tensor-core GEMM (+ exact re-rank)
+CL_PREC = {"fp32": abi.PREC_FP32, "bf16": abi.PREC_BF16, "fp16": abi.PREC_FP16, "fp8": abi.PREC_FP8E4M3}
 
 
 def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), margin: float = 0.0,
@@ -27,7 +29,7 @@ def policy(mode: str = "plain", bits: int = 8, thresholds=(0.0, 0.0, 0.0, 0.0), 
     p = abi.anns_precision_policy()
     p.lut_mode = _MODES[mode]
     p.fixed_bits = int(bits)
-    p.cl_prec = {"fp32": abi.PREC_FP32, "bf16": abi.PREC_BF16}[cl]
+    p.cl_prec = CL_PREC[cl]
     p.lc_prec = abi.PREC_FP32
     for i, t in enumerate(thresholds):
         p.eq2_thresholds[i] = float(t)
@@ -228,7 +230,7 @@ class Index:
         pd = torch.empty((nq, nprobe), dtype=torch.float32, device=queries.device)
         s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         abi.anns_locate(self.handle, _ptr(queries), nq, nprobe, _ptr(nprobe_per_q),
-                        {"fp32": abi.PREC_FP32, "bf16": abi.PREC_BF16}[cl], _ptr(probes), _ptr(pd), s)
+                        CL_PREC[cl], _ptr(probes), _ptr(pd), s)
         return probes, pd
 
     def set_qchunk(self, queries: int):

@@ -18,7 +18,7 @@ STATIC_SCRATCH_FLOATS = 1 << 21
 MAX_M, MAX_NPROBE, MAX_K = 128, 128, 128
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSUPPORTED"}
 LUT_PLAIN_FP32, LUT_FIXED_BITS, LUT_HEURISTIC_EQ2, LUT_MLP, LUT_EXPLICIT, LUT_SVR = 0, 1, 2, 3, 4, 5
-PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8E4M3, PREC_FP16 = 0, 1, 2, 3
 TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_COARSE_APPROX, TAP_COARSE_CANDIDATES = 4, 5
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS, TAP_STATUS = 10, 11, 12, 13

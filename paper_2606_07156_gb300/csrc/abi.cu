@@ -310,8 +310,8 @@ int anns::check_search_args(anns_index* ix, const float* Q, int64_t nq, int32_t 
         break;
       default: return fail(ANNS_ERR_INVALID_ARG, "unknown lut_mode");
     }
-    if (pol->cl_prec != ANNS_PREC_FP32 && pol->cl_prec != ANNS_PREC_BF16)
-      return fail(ANNS_ERR_UNSUPPORTED, "CL operands: FP32 or BF16 (with exact re-rank)");
+    if (pol->cl_prec != ANNS_PREC_FP32 && !coarse_tc_format(pol->cl_prec))
+      return fail(ANNS_ERR_UNSUPPORTED, "CL operands: FP32, or BF16 / FP16 / FP8 E4M3 (with exact re-rank)");
     if (pol->lc_prec != ANNS_PREC_FP32) return fail(ANNS_ERR_UNSUPPORTED, "LC operands: FP32 only");
   }
   return ANNS_OK;
@@ -349,7 +349,7 @@ int reserve_search(Index& ix, int64_t nq, int nprobe, int k, const anns_precisio
   if (ix.opt_kernel != ANNS_KERNEL_LIST_MAJOR && use_lpt(ix, nprobe_per_q)) {
     if ((rc = grow(&ix.ws_sched, &ix.ws_sched_cap, lpt_workspace_bytes(nq)))) return rc;
   }
-  if (P.cl_prec == ANNS_PREC_BF16) {
+  if (coarse_tc_format(P.cl_prec)) {
     if ((rc = grow(&ix.ws_tc, &ix.ws_tc_cap, coarse_tc_workspace_bytes(ix, nq)))) return rc;
   }
   return ANNS_OK;
@@ -363,11 +363,13 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
   cudaEvent_t* ev = profile ? next_profile_slot(ix) : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
   cudaError_t e;
-  ix.ws_tc_valid = P.cl_prec == ANNS_PREC_BF16;
+  ix.ws_tc_valid = coarse_tc_format(P.cl_prec);
+  ix.ws_tc_prec = P.cl_prec;
   ix.ws_tc_nq = nq;
   if (ix.ws_tc_valid) {
     if (ev) cudaEventRecord(ev[1], s);
-    e = launch_coarse_tc(ix, Q, nq, nprobe, nprobe_per_q, ix.ws_tc, ix.ws_d2, ix.ws_probes, ix.ws_probe_d2, s);
+    e = launch_coarse_tc(ix, P.cl_prec, Q, nq, nprobe, nprobe_per_q, ix.ws_tc, ix.ws_d2, ix.ws_probes,
+                         ix.ws_probe_d2, s);
   } else {
     e = launch_coarse(ix, Q, nq, nprobe, nprobe_per_q, ix.ws_d2, ix.ws_probes, ix.ws_probe_d2, s,
                       ev ? ev[1] : nullptr);
@@ -466,8 +468,8 @@ extern "C" int anns_locate(anns_index* ix, const float* Q, int64_t nq, int32_t n
   if (nq < 0) return fail(ANNS_ERR_INVALID_ARG, "nq must be >= 0");
   if (nprobe < 1 || nprobe > ix->nlist || nprobe > ANNS_MAX_NPROBE)
     return fail(ANNS_ERR_INVALID_ARG, "nprobe must be in [1, min(nlist, 128)]");
-  if (cl_prec != ANNS_PREC_FP32 && cl_prec != ANNS_PREC_BF16)
-    return fail(ANNS_ERR_UNSUPPORTED, "CL operands: FP32 or BF16 (with exact re-rank)");
+  if (cl_prec != ANNS_PREC_FP32 && !coarse_tc_format(cl_prec))
+    return fail(ANNS_ERR_UNSUPPORTED, "CL operands: FP32, or BF16 / FP16 / FP8 E4M3 (with exact re-rank)");
   if (nq == 0) return ANNS_OK;
   if (!Q || !probes_out || !probe_d2_out) return fail(ANNS_ERR_INVALID_ARG, "null buffer");
   DeviceGuard g(ix->device);
@@ -475,11 +477,13 @@ extern "C" int anns_locate(anns_index* ix, const float* Q, int64_t nq, int32_t n
   int rc = grow((void**)&ix->ws_d2, &ix->ws_d2_cap, (size_t)nq * ix->nlist * 4);
   if (rc) return rc;
   cudaError_t e;
-  ix->ws_tc_valid = cl_prec == ANNS_PREC_BF16;
+  ix->ws_tc_valid = coarse_tc_format(cl_prec);
+  ix->ws_tc_prec = cl_prec;
   ix->ws_tc_nq = nq;
-  if (cl_prec == ANNS_PREC_BF16) {
+  if (ix->ws_tc_valid) {
     if ((rc = grow(&ix->ws_tc, &ix->ws_tc_cap, coarse_tc_workspace_bytes(*ix, nq)))) return rc;
-    e = launch_coarse_tc(*ix, Q, nq, nprobe, nprobe_per_q, ix->ws_tc, ix->ws_d2, probes_out, probe_d2_out, s);
+    e = launch_coarse_tc(*ix, cl_prec, Q, nq, nprobe, nprobe_per_q, ix->ws_tc, ix->ws_d2, probes_out, probe_d2_out,
+                         s);
   } else {
     e = launch_coarse(*ix, Q, nq, nprobe, nprobe_per_q, ix->ws_d2, probes_out, probe_d2_out, s);
   }

@@ -46,7 +46,8 @@ static void free_index(anns_index* ix) {
   cudaSetDevice(ix->device);
   void* ptrs[] = {ix->centroids, ix->codebooks, ix->codes, ix->ids, ix->list_len,
                   ix->vec_off, ix->tile_off, ix->radius, ix->ltab, ix->order, ix->mlp_dev,
-                  ix->tc_mu, ix->tc_cb, ix->tc_cn, ix->dev_status, ix->svr_dev};
+                  ix->tc_mu, ix->tc_c[0], ix->tc_c[1], ix->tc_c[2], ix->tc_crows[0], ix->tc_crows[1],
+                  ix->tc_crows[2], ix->dev_status, ix->svr_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_workspace(*ix);
@@ -278,12 +279,11 @@ extern "C" int anns_debug_tap(anns_index* ix, int32_t what, void* out, size_t by
     case ANNS_TAP_LIST_RADIUS: src = ix->h_radius; need = (size_t)ix->nlist * 4; host = true; break;
     case ANNS_TAP_PACKED_IDS: src = ix->ids; need = (size_t)ix->n * 8; break;
     case ANNS_TAP_COARSE_APPROX:
-      if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use BF16 CL");
+      if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use the tensor-core CL");
       src = ix->ws_d2; need = (size_t)ix->ws_tc_nq * ix->nlist * 4; break;
     case ANNS_TAP_COARSE_CANDIDATES: {
-      if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use BF16 CL");
-      const size_t qb = ((size_t)ix->ws_tc_nq * coarse_tc_dp(*ix) * 2 + 255) & ~size_t(255);
-      src = (const char*)ix->ws_tc + qb + (size_t)ix->ws_tc_nq * 12;
+      if (!ix->ws_tc_valid) return fail(ANNS_ERR_INVALID_ARG, "last search did not use the tensor-core CL");
+      src = coarse_tc_candidates(*ix, ix->ws_tc, ix->ws_tc_nq);
       need = (size_t)ix->ws_tc_nq * 4;
       break;
     }

@@ -45,11 +45,12 @@ struct Index {
   // pair's LUT T' = P_l - 2 Q_q (the LUT shifted by ||r_m||^2, Section 2.1).
   float* ltab = nullptr;
   int32_t* order = nullptr;     // [nlist] list ids by size, largest first (ties by id)
-  // CL fast path (coarse_tc.cu): centroid mean, BF16 centred centroids
-  // [nlist * Dp], per-row norms (cn, ch, ce: [3 * nlist]); device status word
+  // CL fast path (coarse_tc.cu): centroid mean; per operand format (BF16,
+  // FP16, FP8 E4M3) the centred, scaled, rounded centroids [nlist * Dp] and
+  // their rows (cn, cd, cs: [3 * nlist]); device status word
   float* tc_mu = nullptr;
-  void* tc_cb = nullptr;
-  float* tc_cn = nullptr;
+  void* tc_c[3] = {};
+  float* tc_crows[3] = {};
   int* dev_status = nullptr;
   // host copies of the small per-list tables
   std::string err;
@@ -76,6 +77,7 @@ struct Index {
   void* ws_tc = nullptr;         // BF16 centred queries, norms, candidate counts (coarse_tc.cu)
   size_t ws_tc_cap = 0;
   bool ws_tc_valid = false;      // the last search (or anns_locate) used the CL fast path
+  int ws_tc_prec = 0;            // ... with this operand format
   int64_t ws_tc_nq = 0;          // ... for this many queries
   int opt_kernel = 0;            // ANNS_KERNEL_* (anns_set_option)
   int opt_schedule = 0;          // ANNS_SCHED_*
@@ -125,11 +127,14 @@ int grow(void** p, size_t* cap, size_t bytes);
 cudaError_t launch_coarse(const Index& ix, const float* Q, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, float* d2, int32_t* probes,
                           float* probe_d2, cudaStream_t s, cudaEvent_t between = nullptr);
-// CL fast path: BF16 tensor-core distances, then the exact re-rank (coarse_tc.cu).
-int coarse_tc_dp(const Index& ix);
+// CL fast path: tensor-core distances with BF16, FP16 or FP8 E4M3 operands
+// (ANNS_PREC_*), then the exact re-rank (coarse_tc.cu).
+bool coarse_tc_format(int prec);
+int coarse_tc_dp(const Index& ix, int prec);
 int prepare_coarse_tc(Index& ix, const std::vector<float>& cent);
 size_t coarse_tc_workspace_bytes(const Index& ix, int64_t nq);
-cudaError_t launch_coarse_tc(const Index& ix, const float* Q, int64_t nq, int nprobe,
+const int* coarse_tc_candidates(const Index& ix, const void* ws, int64_t nq);
+cudaError_t launch_coarse_tc(const Index& ix, int prec, const float* Q, int64_t nq, int nprobe,
                              const int32_t* nprobe_per_q, void* ws, float* dt, int32_t* probes,
                              float* probe_d2, cudaStream_t s);
 // Per-query tables 2*Q_q[m][c] = 2 <q_m, y_mc> (FP32 dot rule), rows M..Mp-1 zero.

@@ -1,8 +1,9 @@
-"""CL on the tensor cores (tcgen05 BF16 GEMM + exact re-rank) vs the oracle.
+"""CL on the tensor cores (tcgen05 GEMM with BF16, FP16 or FP8 E4M3 operands,
+FP32 accumulation, + exact re-rank) vs the oracle.
 
 The probed lists and their coarse distances must be identical to the FP32
-rule (the re-rank makes the fast path exact); the BF16 distances themselves
-must lie within the error bound the re-rank relies on.
+rule (the re-rank makes the fast path exact); the tensor-core distances
+themselves must lie within the error bound the re-rank relies on.
 """
 import numpy as np
 import pytest
@@ -11,6 +12,11 @@ from oracle import ivfpq
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+FORMATS = ("bf16", "fp16", "fp8")
+# (torch dtype, top exponent of the per-row scale, K elements per 128-byte chunk, unit roundoff)
+FMT = {"bf16": (torch.bfloat16, 14, 64, 2.0 ** -8), "fp16": (torch.float16, 14, 64, 2.0 ** -11),
+       "fp8": (torch.float8_e4m3fn, 8, 128, 2.0 ** -4)}
 
 
 @pytest.fixture(scope="module")
@@ -43,20 +49,33 @@ def geo(amp, request):
     g.close()
 
 
-def _bound(Q, C, dt):
+def _operand(X, mu, cl):
+    """Rows centred, scaled by 2^e (largest magnitude in [2^(top-1), 2^top)),
+    rounded to the format by torch and scaled back (FP64), with the centred
+    FP32 rows."""
+    dtype, top, _, _ = FMT[cl]
+    v = (X - mu).astype(np.float32)
+    amax = np.abs(v).max(axis=1)
+    _, ex = np.frexp(amax)                       # amax = m 2^ex, m in [0.5, 1)
+    e = np.where(amax > 0, np.clip(top - ex, -126, 126), 0)
+    w = (v * np.exp2(e)[:, None].astype(np.float32)).astype(np.float32)
+    r = torch.from_numpy(w).to(dtype).float().numpy().astype(np.float64)
+    return r * np.exp2(-e)[:, None], v
+
+
+def _bound(Q, C, dt, cl):
     """The kernel's per-pair bound, evaluated in FP64 from the same inputs."""
     mu = C.astype(np.float64).mean(axis=0).astype(np.float32)
-    qh_ = (Q - mu).astype(np.float32)
-    ch_ = (C - mu).astype(np.float32)
-    qb = torch.from_numpy(qh_).to(torch.bfloat16).float().numpy().astype(np.float64)
-    cb = torch.from_numpy(ch_).to(torch.bfloat16).float().numpy().astype(np.float64)
+    qb, qh_ = _operand(Q, mu, cl)
+    cb, ch_ = _operand(C, mu, cl)
     qn, cn = (qb ** 2).sum(1), (cb ** 2).sum(1)
     qh = np.linalg.norm(qh_.astype(np.float64), axis=1)
     ch = np.linalg.norm(ch_.astype(np.float64), axis=1)
     qe = np.linalg.norm(qb - qh_, axis=1)
     ce = np.linalg.norm(cb - ch_, axis=1)
     dim = Q.shape[1]
-    Dp = (dim + 63) // 64 * 64
+    per = FMT[cl][2]
+    Dp = (dim + per - 1) // per * per
     ef = (2 * Dp + 8) * 2.0 ** -24 * (qn[:, None] + cn[None, :])
     dn = qe[:, None] + ce[None, :] + 2.0 ** -23 * (qh[:, None] + ch[None, :])
     sup = np.maximum(dt, 0) + ef
@@ -64,11 +83,12 @@ def _bound(Q, C, dt):
     return ef + E + (dim + 2) * 2.0 ** -24 * (sup + E)
 
 
+@pytest.mark.parametrize("cl", FORMATS)
 @pytest.mark.parametrize("nprobe", [1, 7, 40])
-def test_bf16_probes_identical_to_fp32_rule(amp, geo, nprobe):
+def test_tc_probes_identical_to_fp32_rule(amp, geo, nprobe, cl):
     key, d, ix, g, o = geo
     Q = d["queries"]
-    pol = amp.policy("fixed", bits=8, cl="bf16")
+    pol = amp.policy("fixed", bits=8, cl=cl)
     ids, dists = g.search(cuda(Q), nprobe, 10, pol)
     torch.cuda.synchronize()
     probes = g.tap(amp.abi.TAP_PROBES, (len(Q), nprobe), np.int32)
@@ -79,15 +99,15 @@ def test_bf16_probes_identical_to_fp32_rule(amp, geo, nprobe):
     np.testing.assert_array_equal(pd, rd)
     ncand = g.tap(amp.abi.TAP_COARSE_CANDIDATES, (len(Q),), np.int32)
     assert np.all(ncand >= nprobe) and np.all(ncand <= o.nlist)
-    # the BF16 tensor-core distances lie within the bound the re-rank uses
+    # the tensor-core distances lie within the bound the re-rank uses
     dt = g.tap(amp.abi.TAP_COARSE_APPROX, (len(Q), o.nlist), np.float32).astype(np.float64)
     err = np.abs(dt - D2.astype(np.float64))
-    bound = _bound(Q, o.centroids, dt)
+    bound = _bound(Q, o.centroids, dt, cl)
     assert np.all(err <= bound), float(np.max(err / bound))
-    # and they are BF16-accurate, not merely bounded: relative to the norms
+    # and they are as accurate as the format, not merely bounded: relative to the norms
     scale = (np.linalg.norm(Q - o.centroids.mean(0), axis=1)[:, None] +
              np.linalg.norm(o.centroids - o.centroids.mean(0), axis=1)[None, :]) ** 2
-    assert np.median(err / scale) < 2.0 ** -8
+    assert np.median(err / scale) < FMT[cl][3]
     ri, rd = ivfpq.search(o, Q, nprobe, 10, bits=8)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
     np.testing.assert_array_equal(dists.cpu().numpy(), rd)
@@ -96,13 +116,14 @@ def test_bf16_probes_identical_to_fp32_rule(amp, geo, nprobe):
     assert st[0] == 0
 
 
-def test_bf16_uneven_batch_and_graph(amp, geo):
+@pytest.mark.parametrize("cl", FORMATS)
+def test_tc_uneven_batch_and_graph(amp, geo, cl):
     key, d, ix, g, o = geo
     from workloads import zipf_nprobe
     Q = d["queries"]
     npq = zipf_nprobe(len(Q), 2, lo=1, hi=30)
     npq[::7] = 0
-    pol = amp.policy("plain", cl="bf16")
+    pol = amp.policy("plain", cl=cl)
     ids, dists = g.search(cuda(Q), 30, 5, pol, nprobe_per_q=cuda(npq))
     ri, rd = ivfpq.search(o, Q, 30, 5, bits=0, nprobe_per_q=npq)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
@@ -129,7 +150,54 @@ def test_locate_entry_point(amp, geo):
     key, d, ix, g, o = geo
     Q = d["queries"]
     rp, rd = ivfpq.locate(ivfpq.coarse_d2_fp32(Q, o.centroids), 9)
-    for cl in ("fp32", "bf16"):
+    for cl in ("fp32",) + FORMATS:
         p, pd = g.locate(cuda(Q), 9, cl=cl)
         np.testing.assert_array_equal(p.cpu().numpy(), rp)
         np.testing.assert_array_equal(pd.cpu().numpy(), rd)
+
+
+def _random_index(amp, nlist, dim, seed):
+    """An index whose centroids are clustered random draws (the coarse stage
+    reads only the centroids): lists of one vector each."""
+    rng = np.random.default_rng(seed)
+    centres = rng.normal(size=(max(nlist // 40, 1), dim)).astype(np.float32) * 3
+    C = (centres[rng.integers(0, len(centres), nlist)] + rng.normal(size=(nlist, dim))).astype(np.float32)
+    M = 2 if dim % 2 == 0 else 1
+    books = rng.normal(size=(M, 256, dim // M)).astype(np.float32)
+    codes = rng.integers(0, 256, size=(nlist, M)).astype(np.uint8)
+    Q = (centres[rng.integers(0, len(centres), 300)] + rng.normal(size=(300, dim))).astype(np.float32)
+    g = amp.Index(C, books, codes, np.arange(nlist, dtype=np.int32), device=0)
+    return g, C, Q
+
+
+@pytest.mark.parametrize("nlist,dim", [(12000, 24), (700, 18), (900, 37)])
+def test_tc_streaming_and_unaligned_rerank(amp, nlist, dim):
+    """nlist 12000 leaves the re-rank's keys out of shared memory (the
+    streaming re-rank); dims 18 and 37 are not multiples of 4 (element-wise
+    row staging). Probes and distances must still be the FP32 rule's."""
+    g, C, Q = _random_index(amp, nlist, dim, nlist + dim)
+    try:
+        for nprobe in (1, 33, 100):
+            rp, rd = ivfpq.locate(ivfpq.coarse_d2_fp32(Q, C), nprobe)
+            for cl in FORMATS:
+                p, pd = g.locate(cuda(Q), nprobe, cl=cl)
+                np.testing.assert_array_equal(p.cpu().numpy(), rp)
+                np.testing.assert_array_equal(pd.cpu().numpy(), rd)
+                ncand = g.tap(amp.abi.TAP_COARSE_CANDIDATES, (len(Q),), np.int32)
+                assert np.all(ncand >= nprobe) and np.all(ncand <= nlist)
+    finally:
+        g.close()
+
+
+def test_tc_candidates_shrink_with_the_format(amp):
+    """A finer operand format gives a tighter bound, hence fewer lists to
+    re-rank: FP16 (11 significant bits) <= BF16 (8) <= FP8 E4M3 (4)."""
+    g, C, Q = _random_index(amp, 4096, 64, 7)
+    try:
+        mean = {}
+        for cl in FORMATS:
+            g.locate(cuda(Q), 16, cl=cl)
+            mean[cl] = float(g.tap(amp.abi.TAP_COARSE_CANDIDATES, (len(Q),), np.int32).mean())
+        assert mean["fp16"] <= mean["bf16"] <= mean["fp8"], mean
+    finally:
+        g.close()
