@@ -574,106 +574,150 @@ __device__ uint32_t block_select(const uint32_t* keys, int64_t n, int np, uint32
   return kmin + lo;
 }
 
+// Candidate lists of the split re-rank: up to kCap candidates per query in
+// the workspace, their distances computed by rerank_dist_kernel (one warp per
+// 32 candidates, over all queries at once) and merged by rerank_merge_kernel.
+constexpr int kCap = 512;
+
+struct RerankSplit {
+  int32_t* cbuf;   // [nq][kCap] candidate lists
+  float* cdist;    // [nq][kCap] their FP32-rule distances
+  int2* items;     // [nq * kCap / 32] work items (query, batch)
+  int* nitems;     // item count (zeroed before the select kernel)
+};
+
+// Writes the np <= 128 entries of a warp's list (padding -1 / +inf) as the
+// query's probes.
+template <int R>
+__device__ __forceinline__ void write_probes(const RerankArgs& a, int64_t q, int np, const WarpTopK<R, int32_t>& top) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = r * 32 + lane;
+    if (e < a.nprobe) {
+      const bool ok = e < np && top.d[r] != INFINITY;
+      a.probes[q * a.nprobe + e] = ok ? top.id[r] : -1;
+      a.probe_d2[q * a.nprobe + e] = ok ? top.d[r] : INFINITY;
+    }
+  }
+}
+
 // One block per query, every list's upper key and lower bound held in shared
 // memory.
 // A: eps, the key of D~ + eps and the lower bound D~ - eps of every list, and
 //    the keys' range.
 // B: T = the np-th smallest key, exactly (block_select).
 // C: the candidates, D~ - eps <= T, appended to a block-wide list.
-// D: their FP32-rule distances, 32 per warp batch (batches dealt round-robin
-//    to the warps), each warp keeping its top-np by (D2, l); the warps' lists
-//    are merged at the end. Writes nprobe entries (padding -1 / +inf) and the
-//    number of candidates.
-// Dynamic shared memory: tiles [8][1056] | qs [dim rounded up to 4] | keys
-// [nlist] (then the candidate list) | lower [nlist].
+// Then, with at most kCap candidates, the list goes to the workspace with one
+// work item per 32 candidates; otherwise the block computes their FP32-rule
+// distances itself, 32 per warp batch (batches dealt round-robin to the
+// warps), each warp keeping its top-np by (D2, l), the warps' lists merged at
+// the end. Queries with np = 0 get their padding here.
+// Dynamic shared memory: qs [dim rounded up to 4] | keys [nlist rounded up to
+// 4] (then the candidate list) | lower [nlist], whose space then holds the
+// warps' staging tiles [8][1056].
 template <int R, bool V4>
-__global__ void __launch_bounds__(kRThreads, 2) rerank_kernel(RerankArgs a) {
+__global__ void __launch_bounds__(kRThreads, 3) rerank_select_kernel(RerankArgs a, RerankSplit sp) {
   __shared__ int hist[256];
   __shared__ uint32_t sh[2];
   __shared__ int total;
   __shared__ uint32_t kr[2][kRWarps];
-  float* tiles = (float*)anns_dyn_smem;
-  float* qs = tiles + kRWarps * kRTile;
   const int dq = (a.dim + 3) & ~3;
+  const int64_t nl4 = (a.nlist + 3) & ~3;
+  float* qs = (float*)anns_dyn_smem;
   uint32_t* keys = (uint32_t*)(qs + dq);
-  float* lower = (float*)(keys + a.nlist);
+  float* lower = (float*)(keys + nl4);
+  float* tiles = lower;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q = blockIdx.x, nlist = a.nlist;
   const int np = a.npq ? min(max(a.npq[q], 0), a.nprobe) : a.nprobe;
-  const float* row = a.dt + q * nlist;
-  const float qn = a.qrows[q], qd = a.qrows[a.nq + q];
-  for (int d = threadIdx.x; d < dq; d += kRThreads) qs[d] = d < a.dim ? a.Q[q * a.dim + d] : 0.f;
-  if (threadIdx.x == 0) total = 0;
   WarpTopK<R, int32_t> top;
   top.init();
+  if (np == 0) {
+    if (warp == 0) write_probes<R>(a, q, 0, top);
+    if (threadIdx.x == 0 && a.ncand) a.ncand[q] = 0;
+    return;
+  }
+  const float* row = a.dt + q * nlist;
+  const float qn = a.qrows[q], qd = a.qrows[a.nq + q];
+  if (threadIdx.x == 0) total = 0;
+  // A: eight lists per thread per round, all their loads issued before any
+  // use (D~ streams from HBM once)
+  uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+  for (int64_t b0 = threadIdx.x; b0 < nlist; b0 += 8 * kRThreads) {
+    float d[8], cn[8], cd[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t l = b0 + j * kRThreads;
+      const bool in = l < nlist;
+      d[j] = in ? row[l] : 0.f;
+      cn[j] = in ? a.crows[l] : 0.f;
+      cd[j] = in ? a.crows[nlist + l] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t l = b0 + j * kRThreads;
+      if (l < nlist) {
+        const float b = rerank_bound(d[j], qn, qd, cn[j], cd[j], a.kef, a.kfp);
+        const uint32_t k = upper_key(d[j] + b);
+        keys[l] = k;
+        lower[l] = d[j] - b;
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(kFull, kmin, o));
+    kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+  }
+  if (lane == 0) { kr[0][warp] = kmin; kr[1][warp] = kmax; }
+  __syncthreads();
+  kmin = 0xFFFFFFFFu;
+  kmax = 0;
+  for (int w = 0; w < kRWarps; ++w) {
+    kmin = min(kmin, kr[0][w]);
+    kmax = max(kmax, kr[1][w]);
+  }
+  // B
+  const float T = __uint_as_float(block_select(keys, nlist, np, kmin, kmax, hist, sh));
+  __syncthreads();  // keys are free: they become the candidate list
+  // C
+  int32_t* cand = (int32_t*)keys;
+  for (int64_t b0 = (int64_t)warp * 32; b0 < nlist; b0 += kRThreads) {
+    const int64_t l = b0 + lane;
+    const bool c = l < nlist && !(lower[l] > T);
+    const unsigned m = __ballot_sync(kFull, c);
+    if (m) {
+      int at = 0;
+      if (lane == 0) at = atomicAdd(&total, __popc(m));
+      at = __shfl_sync(kFull, at, 0);
+      if (c) cand[at + __popc(m & ((1u << lane) - 1u))] = (int32_t)l;
+    }
+  }
+  __syncthreads();
+  const int nc_all = total;
+  if (threadIdx.x == 0 && a.ncand) a.ncand[q] = nc_all;
+  if (nc_all <= kCap) {
+    for (int i = threadIdx.x; i < nc_all; i += kRThreads) sp.cbuf[q * kCap + i] = cand[i];
+    const int nb = (nc_all + 31) >> 5;
+    if (threadIdx.x == 0) sh[0] = (uint32_t)atomicAdd(sp.nitems, nb);
+    __syncthreads();
+    if (threadIdx.x < nb) sp.items[sh[0] + threadIdx.x] = make_int2((int)q, threadIdx.x);
+    return;
+  }
+  // D, in the block: the query itself and the staging tiles (over `lower`)
+  for (int d = threadIdx.x; d < dq; d += kRThreads) qs[d] = d < a.dim ? a.Q[q * a.dim + d] : 0.f;
+  __syncthreads();
   float thd = INFINITY;
   int32_t thi = INT32_MAX;
-  if (np > 0) {
-    // A: eight lists per thread per round, all their loads issued before
-    // any use (D~ streams from HBM once)
-    uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
-    for (int64_t b0 = threadIdx.x; b0 < nlist; b0 += 8 * kRThreads) {
-      float d[8], cn[8], cd[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t l = b0 + j * kRThreads;
-        const bool in = l < nlist;
-        d[j] = in ? row[l] : 0.f;
-        cn[j] = in ? a.crows[l] : 0.f;
-        cd[j] = in ? a.crows[nlist + l] : 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t l = b0 + j * kRThreads;
-        if (l < nlist) {
-          const float b = rerank_bound(d[j], qn, qd, cn[j], cd[j], a.kef, a.kfp);
-          const uint32_t k = upper_key(d[j] + b);
-          keys[l] = k;
-          lower[l] = d[j] - b;
-          kmin = min(kmin, k);
-          kmax = max(kmax, k);
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      kmin = min(kmin, __shfl_xor_sync(kFull, kmin, o));
-      kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
-    }
-    if (lane == 0) { kr[0][warp] = kmin; kr[1][warp] = kmax; }
-    __syncthreads();
-    kmin = 0xFFFFFFFFu;
-    kmax = 0;
-    for (int w = 0; w < kRWarps; ++w) {
-      kmin = min(kmin, kr[0][w]);
-      kmax = max(kmax, kr[1][w]);
-    }
-    // B
-    const float T = __uint_as_float(block_select(keys, nlist, np, kmin, kmax, hist, sh));
-    __syncthreads();  // keys are free: they become the candidate list
-    // C
-    int32_t* cand = (int32_t*)keys;
-    for (int64_t b0 = (int64_t)warp * 32; b0 < nlist; b0 += kRThreads) {
-      const int64_t l = b0 + lane;
-      const bool c = l < nlist && !(lower[l] > T);
-      const unsigned m = __ballot_sync(kFull, c);
-      if (m) {
-        int at = 0;
-        if (lane == 0) at = atomicAdd(&total, __popc(m));
-        at = __shfl_sync(kFull, at, 0);
-        if (c) cand[at + __popc(m & ((1u << lane) - 1u))] = (int32_t)l;
-      }
-    }
-    __syncthreads();
-    // D
-    const int nc_all = total;
-    float* tile = tiles + warp * kRTile;
-    for (int b0 = warp * 32; b0 < nc_all; b0 += kRWarps * 32) {
-      const int nc = min(32, nc_all - b0);
-      const float d = V4 ? batch_d2_v4(a.C, qs, a.dim, cand + b0, nc, tile)
-                         : batch_d2_any(a.C, qs, a.dim, cand + b0, nc, tile);
-      top.offer(lane < nc, d, lane < nc ? cand[b0 + lane] : 0, np, thd, thi);
-    }
+  float* tile = tiles + warp * kRTile;
+  for (int b0 = warp * 32; b0 < nc_all; b0 += kRWarps * 32) {
+    const int nc = min(32, nc_all - b0);
+    const float d = V4 ? batch_d2_v4(a.C, qs, a.dim, cand + b0, nc, tile)
+                       : batch_d2_any(a.C, qs, a.dim, cand + b0, nc, tile);
+    top.offer(lane < nc, d, lane < nc ? cand[b0 + lane] : 0, np, thd, thi);
   }
   __syncthreads();  // tiles are free: they hold the warps' lists
   float* md = tiles;
@@ -682,23 +726,59 @@ __global__ void __launch_bounds__(kRThreads, 2) rerank_kernel(RerankArgs a) {
   for (int r = 0; r < R; ++r) { md[(warp * R + r) * 32 + lane] = top.d[r]; mi[(warp * R + r) * 32 + lane] = top.id[r]; }
   __syncthreads();
   if (warp == 0) {
-    for (int w = 1; w < kRWarps && np > 0; ++w)
+    for (int w = 1; w < kRWarps; ++w)
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const float v = md[(w * R + r) * 32 + lane];
         top.offer(v != INFINITY, v, mi[(w * R + r) * 32 + lane], np, thd, thi);
       }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int e = r * 32 + lane;
-      if (e < a.nprobe) {
-        const bool ok = e < np && top.d[r] != INFINITY;
-        a.probes[q * a.nprobe + e] = ok ? top.id[r] : -1;
-        a.probe_d2[q * a.nprobe + e] = ok ? top.d[r] : INFINITY;
-      }
-    }
-    if (lane == 0 && a.ncand) a.ncand[q] = total;
+    write_probes<R>(a, q, np, top);
   }
+}
+
+constexpr int kDWarps = 4;  // warps per block of the distance kernel
+
+// FP32-rule distances of the work items' candidates, one warp per item (a
+// query and 32 of its candidates), the warps walking the item list; the query
+// is read from global memory (a broadcast load per 16 bytes).
+template <bool V4>
+__global__ void __launch_bounds__(kDWarps * 32) rerank_dist_kernel(RerankArgs a, RerankSplit sp) {
+  __shared__ __align__(16) float tiles[kDWarps][kRTile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = *sp.nitems;
+  for (int it = blockIdx.x * kDWarps + warp; it < n; it += gridDim.x * kDWarps) {
+    const int2 w = sp.items[it];
+    const int64_t q = w.x;
+    const int b0 = w.y * 32;
+    const int nc = min(32, a.ncand[q] - b0);
+    const int32_t* cand = sp.cbuf + q * kCap + b0;
+    const float* qrow = a.Q + q * a.dim;
+    const float d = V4 ? batch_d2_v4(a.C, qrow, a.dim, cand, nc, tiles[warp])
+                       : batch_d2_any(a.C, qrow, a.dim, cand, nc, tiles[warp]);
+    if (lane < nc) sp.cdist[q * kCap + b0 + lane] = d;
+  }
+}
+
+// The top-np of each query's candidates by (D2, l), one warp per query
+// (queries with np = 0 or more than kCap candidates were finished by the
+// select kernel).
+template <int R>
+__global__ void __launch_bounds__(256) rerank_merge_kernel(RerankArgs a, RerankSplit sp) {
+  const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= a.nq) return;
+  const int np = a.npq ? min(max(a.npq[q], 0), a.nprobe) : a.nprobe;
+  const int nc = a.ncand[q];
+  if (np == 0 || nc > kCap) return;
+  WarpTopK<R, int32_t> top;
+  top.init();
+  float thd = INFINITY;
+  int32_t thi = INT32_MAX;
+  for (int b0 = 0; b0 < nc; b0 += 32) {
+    const bool v = b0 + lane < nc;
+    top.offer(v, v ? sp.cdist[q * kCap + b0 + lane] : 0.f, v ? sp.cbuf[q * kCap + b0 + lane] : 0, np, thd, thi);
+  }
+  write_probes<R>(a, q, np, top);
 }
 
 // The re-rank for index sizes whose keys do not fit in shared memory: the
@@ -834,11 +914,13 @@ constexpr int kFmts[3] = {ANNS_PREC_BF16, ANNS_PREC_FP16, ANNS_PREC_FP8E4M3};
 int fmt_slot(int prec) { return prec == ANNS_PREC_BF16 ? 0 : prec == ANNS_PREC_FP16 ? 1 : 2; }
 int fmt_elem(int prec) { return prec == ANNS_PREC_FP8E4M3 ? 1 : 2; }
 
-// Dynamic shared memory of the cached re-rank for this index.
+// Dynamic shared memory of the select kernel for this index: qs | keys |
+// lower (or the tiles).
 size_t rerank_smem(const Index& ix) {
-  return (size_t)kRWarps * kRTile * 4 + (size_t)((ix.dim + 3) & ~3) * 4 + (size_t)ix.nlist * 8;
+  const size_t nl4 = (size_t)((ix.nlist + 3) & ~3);
+  return (size_t)((ix.dim + 3) & ~3) * 4 + nl4 * 4 + std::max(nl4 * 4, (size_t)kRWarps * kRTile * 4);
 }
-constexpr size_t kRerankSmemMax = 110 * 1024;  // two blocks per SM
+constexpr size_t kRerankSmemMax = 200 * 1024;  // beyond it: the streaming re-rank
 
 template <int F>
 cudaError_t launch_center(const float* X, int64_t n, int dim, int Dp, const float* mu, void* Xf, float* rows,
@@ -918,15 +1000,18 @@ static cudaError_t make_tmap(CUtensorMap* map, CUtensorMapDataType type, int ele
 }
 
 // Workspace: the queries' operand [nq x Dp] (any format) | rows [3][nq] |
-// candidate counts [nq].
+// candidate counts [nq] | item count | candidate lists [nq][kCap] | their
+// distances [nq][kCap] | work items [nq * kCap / 32].
 static size_t tc_operand_bytes(const Index& ix, int64_t nq) {
   size_t b = 0;
   for (int prec : kFmts) b = std::max(b, (size_t)nq * coarse_tc_dp(ix, prec) * fmt_elem(prec));
   return (b + 255) & ~size_t(255);
 }
 
+static size_t tc_small_bytes(int64_t nq) { return ((size_t)nq * 16 + 16 + 255) & ~size_t(255); }
+
 size_t coarse_tc_workspace_bytes(const Index& ix, int64_t nq) {
-  return tc_operand_bytes(ix, nq) + (size_t)nq * 4 * 4 + 256;
+  return tc_operand_bytes(ix, nq) + tc_small_bytes(nq) + (size_t)nq * kCap * 8 + (size_t)nq * (kCap / 32) * 8;
 }
 
 const int* coarse_tc_candidates(const Index& ix, const void* ws, int64_t nq) {
@@ -960,7 +1045,7 @@ cudaError_t launch_coarse_tc(const Index& ix, int prec, const float* Q, int64_t 
   const int f = fmt_slot(prec), Dp = coarse_tc_dp(ix, prec);
   void* Qf = ws;
   float* qrows = (float*)((char*)ws + tc_operand_bytes(ix, nq));  // qn | qd | qs
-  int* ncand = (int*)(qrows + 3 * nq);
+  int* ncand = (int*)(qrows + 3 * nq);                               // then the item count
   cudaError_t e = center_any(prec, Q, nq, (int)ix.dim, Dp, ix.tc_mu, Qf, qrows, s);
   if (e != cudaSuccess) return e;
   switch (prec) {
@@ -972,22 +1057,41 @@ cudaError_t launch_coarse_tc(const Index& ix, int prec, const float* Q, int64_t 
   RerankArgs a{Q, ix.centroids, dt, qrows, ix.tc_crows[f], nq, ix.nlist, (int)ix.dim,
                (float)((2.0 * Dp + 8.0) * 5.9604644775390625e-8 * 1.01), (float)((ix.dim + 2) * 5.9604644775390625e-8),
                nprobe, nprobe_per_q, probes, probe_d2, ncand};
+  char* after = (char*)ws + tc_operand_bytes(ix, nq) + tc_small_bytes(nq);
+  RerankSplit sp{(int32_t*)after, (float*)(after + (size_t)nq * kCap * 4), (int2*)(after + (size_t)nq * kCap * 8),
+                 (int*)(ncand + nq)};
   const int R = (nprobe + 31) / 32;
   const unsigned g = (unsigned)nq;
   const size_t smem = rerank_smem(ix);
-  const bool cached = smem <= kRerankSmemMax;
-  const bool v4 = ix.dim % 4 == 0;
-  auto run = [&](auto kern, size_t sm) {
+  const bool v4 = ix.dim % 4 == 0, q16 = ((uintptr_t)Q & 15u) == 0;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
+  if (e != cudaSuccess) return e;
+  auto run = [&](auto kern, unsigned grid, unsigned threads, size_t sm, auto... args) {
     cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e2 != cudaSuccess) return e2;
-    kern<<<g, kRThreads, sm, s>>>(a);
+    kern<<<grid, threads, sm, s>>>(args...);
     note_launch();
     return cudaGetLastError();
   };
   auto run_r = [&](auto r_tag) {
     constexpr int RR = decltype(r_tag)::value;
-    if (!cached) return run(rerank_stream_kernel<RR>, (size_t)ix.dim * sizeof(float));
-    return v4 ? run(rerank_kernel<RR, true>, smem) : run(rerank_kernel<RR, false>, smem);
+    if (smem > kRerankSmemMax) return run(rerank_stream_kernel<RR>, g, kRThreads, (size_t)ix.dim * 4, a);
+    cudaError_t e2 = cudaMemsetAsync(sp.nitems, 0, sizeof(int), s);
+    if (e2 == cudaSuccess)
+      e2 = v4 ? run(rerank_select_kernel<RR, true>, g, kRThreads, smem, a, sp)
+              : run(rerank_select_kernel<RR, false>, g, kRThreads, smem, a, sp);
+    // the distance kernel's grid: every block resident at once (the warps
+    // stride over the item list)
+    auto dist = [&](auto kern) {
+      int per_sm = 0;
+      cudaError_t e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDWarps * 32, 0);
+      if (e3 != cudaSuccess) return e3;
+      return run(kern, (unsigned)(sms * std::max(per_sm, 1)), kDWarps * 32, 0, a, sp);
+    };
+    if (e2 == cudaSuccess) e2 = v4 && q16 ? dist(rerank_dist_kernel<true>) : dist(rerank_dist_kernel<false>);
+    if (e2 == cudaSuccess) e2 = run(rerank_merge_kernel<RR>, (unsigned)((nq + 7) / 8), 256, 0, a, sp);
+    return e2;
   };
   switch (R) {
     case 1: e = run_r(std::integral_constant<int, 1>{}); break;
