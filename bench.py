@@ -339,6 +339,31 @@ def cl_tensor_bench(amp, dev, steps: int, warmup: int, flush) -> dict:
     return out
 
 
+def pick_cl(index, Q, nprobe: int, stream, reps: int = 5):
+    """The faster CL of the adaptive policies on this workload's queries: the
+    FP32 CUDA-core rule or the FP16 tensor-core GEMM + exact re-rank (both
+    give the same probes and distances, which is checked here). Returns the
+    choice and the median times (ms)."""
+    import torch
+    ref = index.locate(Q, nprobe, cl="fp32", stream=stream)
+    got = index.locate(Q, nprobe, cl="fp16", stream=stream)
+    torch.cuda.synchronize()
+    if not (torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])):
+        raise RuntimeError("tensor-core CL differs from the FP32 rule")
+    ms = {}
+    for cl in ("fp32", "fp16"):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            index.locate(Q, nprobe, cl=cl, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms[cl] = round(float(np.median(ts)), 4)
+    return min(ms, key=ms.get), ms
+
+
 def calibrate_margin_nn(amp, Qc, gt_c, nprobe: int, run, budget: float = LOSS_BUDGET):
     """calibrate_margin with 1-recall@10 (exact nearest neighbour among the 10
     returned) as the judged recall: the reading of the second operating point."""
@@ -352,16 +377,18 @@ def calibrate_margin_nn(amp, Qc, gt_c, nprobe: int, run, budget: float = LOSS_BU
     return float("inf"), tried
 
 
-def roofline_profile(kernel_src: str, workload_name: str):
-    """The committed ncu record (profiles/traffic.json) for this kernel source
-    and workload: DRAM bytes per launch and the binding unit, or None."""
+def roofline_profile(kernel_src: str, workload_name: str, kernel: str):
+    """The committed ncu record (profiles/traffic.json) for this kernel, its
+    source and the workload: DRAM bytes per launch and the binding unit, or
+    None (no record, or the source changed since it was taken)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     recs = json.load(open(path))
     for rec in recs if isinstance(recs, list) else [recs]:
-        if rec.get("source_sha") == sha and rec.get("workload") == workload_name:
+        if (rec.get("source_sha") == sha and rec.get("workload") == workload_name
+                and rec.get("kernel", "").split("<")[0] == kernel):
             return rec
     return None
 
@@ -465,8 +492,6 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     cfg, W = workload(args.config, device=dev)
-    if args.cl == "auto":
-        args.cl = "bf16" if cfg["dim"] >= 256 else "fp32"
     if args.nq:
         W = dict(W, queries=W["queries"][:args.nq], gt=W["gt"][:args.nq])
     index = amp.Index(W["centroids"], W["codebooks"], W["codes"], W["list_of"], device=local_rank)
@@ -511,6 +536,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         ok = [npb for npb in sweep if rec_plain[npb] >= 0.9]
         nprobe = ok[0] if ok else max(sweep)
     ref_ids = run(nprobe, plain)
+    cl_pick = None
+    if args.cl == "auto":
+        args.cl, cl_pick = pick_cl(index, Q, nprobe, stream)
 
     # learned predictor: labels, features and training on the GPU from training queries
     ntrain = cfg.get("ntrain", args.ntrain)
@@ -697,29 +725,34 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         return None
     qps = weak_scaling_qps(totals, world, nq, args.steps)
     qps_e2e = world * nq * args.steps / total_e2e
-    # roofline of the dominant kernel of the adaptive step: the grouped kernel
-    # (stage 4) over the narrow pairs of probe rank >= 1, or the query-major
-    # kernel (stage 3) over the rest
+    # roofline of the dominant kernel of the adaptive step: a grouped kernel
+    # (stage 4: 5..8-bit tables, stage 5: 4-bit tables eight to a word) over
+    # its narrow pairs of probe rank >= 1, or the query-major kernel (stage 3)
+    # over the rest
     pb = pair_bytes(index, probes_ad, cfg["M"])
     narrow = (bits_ad >= 1) & (bits_ad <= 8)
     narrow[:, 0] = False
     st_ms = [v / max(cnt, 1) for v in stage_ms]
-    if st_ms[4] > 0.0 and st_ms[4] >= st_ms[3]:
-        kname, kfile, kms, nbytes = ("packed_kernel (grouped: four queries' 8-bit tables per gather; build + "
-                                     "scan + top-k)", "search_grouped.cu", st_ms[4], int(pb[narrow].sum()))
-    elif st_ms[4] > 0.0:
-        kname, kfile, kms, nbytes = ("search_kernel (query-major pass of the grouped search: rank 0 + wide "
-                                     "pairs)", "search.cu", st_ms[3], int(pb[~narrow].sum()))
+    nib = narrow & (bits_ad <= 4) if st_ms[5] > 0.0 else np.zeros_like(narrow)
+    cands = []
+    if st_ms[4] > 0.0 or st_ms[5] > 0.0:
+        cands.append(("search_kernel (query-major pass of the grouped search: rank 0 + wide pairs)", "search.cu",
+                      st_ms[3], int(pb[~narrow].sum())))
+        cands.append(("packed_kernel (grouped: four queries' 5..8-bit tables per gather; build + scan + top-k)",
+                      "search_grouped.cu", st_ms[4], int(pb[narrow & ~nib].sum())))
+        cands.append(("nibble_kernel (grouped: eight queries' 4-bit tables per gather; build + scan + top-k)",
+                      "search_grouped.cu", st_ms[5], int(pb[nib].sum())))
     else:
-        kname, kfile, kms, nbytes = ("search_kernel (LUT build + quantise + ADC scan + top-k)", "search.cu",
-                                     st_ms[3], int(pb.sum()))
+        cands.append(("search_kernel (LUT build + quantise + ADC scan + top-k)", "search.cu", st_ms[3],
+                      int(pb.sum())))
+    kname, kfile, kms, nbytes = max(cands, key=lambda c: c[2])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = nbytes / (kms / 1e3) / 1e9
     src = os.path.join(ROOT, "paper_2606_07156_gb300", "csrc", kfile)
     wl = f"{cfg['name']} nq={nq} nprobe={nprobe} k={k}"
-    prof = roofline_profile(src, wl)
+    prof = roofline_profile(src, wl, kname.split(" ")[0])
     roof = {"bound": prof["bound"] if prof else "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": "measured" if peaks else "fallback",
@@ -739,7 +772,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "data": f"synthetic (seeded {cfg['name']} mixture; no public dataset)",
         "config": {"workload": wl, "n": int(W["codes"].shape[0]), "dim": cfg["dim"], "nlist": cfg["nlist"],
                    "M": cfg["M"], "nprobe": nprobe, "k": k, "nq": nq,
-                   "cl": f"{args.cl} (adaptive policies; plain FP32 uses the FP32 rule)",
+                   "cl": f"{args.cl} (adaptive policies; plain FP32 uses the FP32 rule)"
+                         + (f"; picked by timing the CL alone: {cl_pick} ms" if cl_pick else ""),
                    "policy": f"learned MLP per (query, list) trained on GB300 table classes, round-up "
                              f"margin {margin} (recall-loss budget {LOSS_BUDGET} pt on calibration queries), widths 6->8 bits "
                              f"and 12/16->FP32; 4-bit tables eight queries per gather",
@@ -779,9 +813,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                       "recall_loss_budget_pts": LOSS_BUDGET},
         "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_plain.items()},
         "stage_ms_per_step": {n: round(v, 4) for n, v in
-                              zip(("cl_distances", "cl_select", "precision_choice+query_tables",
-                                   "search_before_grouped (invert + query-major)", "grouped_kernel",
-                                   "grouped_merge"), st_ms)},
+                              zip(("cl_distances", "cl_select (the whole tensor-core CL)",
+                                   "precision_choice+query_tables", "search_before_grouped (invert + query-major)",
+                                   "grouped_kernel_5to8bit", "grouped_kernel_4bit_nibble", "grouped_merge"),
+                                  st_ms)},
         "roofline": roof,
         "e2e": {"value": round(qps_e2e, 1), "unit": "queries/s", "h2d_bytes_per_step": int(Qh.numel() * 4),
                 "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4), "recall_at_10": round(rec_e2e, 4)},
@@ -873,8 +908,9 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
             margin = m
             break
     del Qc
-    policies = {"plain": amp.policy("plain"), "fixed8": amp.policy("fixed", bits=8),
-                "mlp": amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True)}
+    cl, cl_ms = pick_cl(index, Q, NP, stream) if args.cl == "auto" else (args.cl, None)
+    policies = {"plain": amp.policy("plain"), "fixed8": amp.policy("fixed", bits=8, cl=cl),
+                "mlp": amp.policy("mlp", margin=margin if np.isfinite(margin) else 3.0e38, width_map=True, cl=cl)}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     res, full = {}, {}
     with ClockSampler(local_rank) as clk:
@@ -903,7 +939,9 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
         "config": {"workload": f"{cfg['name']} nq={nq} nprobe~Zipf(1.1) on [1,128] (mean {npq.mean():.2f}) "
                                f"k in {{1,10,100}}", "n": int(W["codes"].shape[0]), "dim": cfg["dim"],
                    "nlist": cfg["nlist"], "M": cfg["M"], "largest_list": int(np.bincount(W["list_of"]).max()),
-                   "l2": "flushed between steps (512 MB write)"},
+                   "l2": "flushed between steps (512 MB write)",
+                   "cl": f"{cl} (adaptive policies; plain FP32 uses the FP32 rule)"
+                         + (f"; picked by timing the CL alone at nprobe {NP}: {cl_ms} ms" if cl_ms else "")},
         "policies": {n: {"natural": res[(n, "natural")], "lpt": res[(n, "lpt")], **res[(n, "recall")],
                          "bits_mix": res[(n, "mix")]} for n in policies},
         "speedup_mlp_vs_plain": round(best["plain"] / best["mlp"], 3),
@@ -1128,13 +1166,15 @@ def fp64_errors(ref, W, cfg, nprobe: int, ctx: dict, nq_s: int = 16) -> dict:
         mixed = max(mixed, float((e / (T64 + T64.mean())).max()))
     out["lut_fp32_max_rel"] = rel
     out["lut_fp32_max_err_over_T64_plus_mean"] = mixed
-    # BF16 tensor-core coarse distances D~ (normwise per query row)
-    index.locate(Qd, nprobe, cl="bf16", stream=stream)
-    torch.cuda.synchronize()
-    Dt = index.tap(abi.TAP_COARSE_APPROX, (nq_s, ref.nlist), np.float32).astype(np.float64)
-    out["cl_bf16_normwise_rel_max"] = float((np.linalg.norm(Dt - D64, axis=1) / np.linalg.norm(D64, axis=1)).max())
+    # tensor-core coarse distances D~ (normwise per query row), per operand format
+    for cl in ("bf16", "fp16", "fp8"):
+        index.locate(Qd, nprobe, cl=cl, stream=stream)
+        torch.cuda.synchronize()
+        Dt = index.tap(abi.TAP_COARSE_APPROX, (nq_s, ref.nlist), np.float32).astype(np.float64)
+        out[f"cl_{cl}_normwise_rel_max"] = float((np.linalg.norm(Dt - D64, axis=1) /
+                                                  np.linalg.norm(D64, axis=1)).max())
     out["tolerances"] = {"fp32_lut": "per element <= 1e-5 (T64 + mean T64)", "fp32_distances": "rel <= 1e-5",
-                         "bf16": "normwise rel <= 2e-2", "quantised": "<= M Delta / 2 (+ FP32 rounding)"}
+                         "bf16_fp16_fp8": "normwise rel <= 2e-2", "quantised": "<= M Delta / 2 (+ FP32 rounding)"}
     return {k2: (round(v2, 9) if isinstance(v2, float) else v2) for k2, v2 in out.items()}
 
 
@@ -1194,8 +1234,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="run the adaptive policies in the automatic configuration")
     ap.add_argument("--cl", default="auto", choices=("auto", "fp32", "bf16", "fp16", "fp8"),
                     help="CL of the adaptive policies: FP32 rule, tensor cores (BF16, FP16 or FP8 E4M3 "
-                         "operands) + exact re-rank, or auto (the tensor cores from D = 256 on; below it the "
-                         "GEMM is too small to repay the re-rank)")
+                         "operands) + exact re-rank, or auto (FP32 or FP16, whichever the CL alone runs faster "
+                         "on the workload's queries)")
     ap.add_argument("--nq", type=int, default=0, help="evaluate the first nq queries only (profiling)")
     ap.add_argument("--ntrain", type=int, default=10000, help="training queries for the predictor")
     ap.add_argument("--epochs", type=int, default=8)

@@ -326,18 +326,20 @@ int anns_scan_pairs(anns_index* index, const float* queries, int64_t nq,
 
 /* Stage timing with CUDA events recorded on the search stream around each
  * stage of anns_search:
- *   0 CL distances, 1 CL selection, 2 precision choice plus the per-query
- *   tables, 3 the search kernels up to the grouped kernel (the whole LUT +
- *   scan + top-k for the query-major and list-major kernels; pair regrouping
- *   plus the query-major pass for the grouped kernel), 4 the grouped kernel
- *   itself, 5 the grouped kernel's per-query merge (4 and 5 are 0 on the other
- *   kernels).
+ *   0 CL distances, 1 CL selection (the tensor-core CL: the whole stage in 1),
+ *   2 precision choice plus the per-query tables, 3 the search kernels up to
+ *   the grouped kernels (the whole LUT + scan + top-k for the query-major and
+ *   list-major kernels; pair regrouping plus the query-major pass for the
+ *   grouped search), 4 the grouped kernel of the 5..8-bit tables (of all
+ *   narrow tables without nibble packing), 5 the grouped kernel of the 4-bit
+ *   tables packed eight to a word, 6 the grouped search's per-query merge
+ *   (4 to 6 are 0 on the other kernels).
  *  enable  1 = start recording (and clear the totals), 0 = stop, -1 = leave as is.
  *  out_ms  host double [ANNS_PROFILE_STAGES] or NULL: accumulated
  *          milliseconds per stage since recording started (waits for the
  *          recorded searches to finish).
  *  count   host int64 or NULL: number of searches accumulated. */
-#define ANNS_PROFILE_STAGES 6
+#define ANNS_PROFILE_STAGES 7
 int anns_profile(anns_index* index, int32_t enable, double* out_ms, int64_t* count);
 
 /* Number of CUDA kernels the library has enqueued since it was loaded, on

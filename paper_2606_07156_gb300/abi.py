@@ -219,8 +219,8 @@ def anns_debug_exact_sum(vals, nsets, n, out, stream=None) -> None:
     _check(_lib.anns_debug_exact_sum(vals, nsets, n, out, stream))
 
 
-PROFILE_STAGES = 6  # CL distances, CL selection, precision + query tables, search up to the
-# grouped kernel, the grouped kernel, the grouped merge
+PROFILE_STAGES = 7  # CL distances, CL selection, precision + query tables, search up to the
+# grouped kernels, the grouped byte-table kernel, the grouped nibble kernel, the grouped merge
 
 
 def anns_profile(index, enable: int):

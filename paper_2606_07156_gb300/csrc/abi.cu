@@ -408,8 +408,8 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
     if (ev) cudaEventRecord(ev[3], s);
     e = launch_search_grouped(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
                               ix.ws_bits, w, ix.ws_grp, ids_out, dists_out, s, ev ? ev[4] : nullptr,
-                              ev ? ev[5] : nullptr, order);
-    if (e == cudaSuccess && ev) cudaEventRecord(ev[6], s);
+                              ev ? ev[5] : nullptr, ev ? ev[6] : nullptr, order);
+    if (e == cudaSuccess && ev) cudaEventRecord(ev[7], s);
     return e == cudaSuccess ? ANNS_OK : cuda_fail(e, "search kernel");
   } else {
     const int32_t* order = nullptr;

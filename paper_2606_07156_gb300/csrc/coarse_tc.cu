@@ -23,7 +23,8 @@
 //    tile's MMAs.
 // 3. Error bound per pair: |D~ - D2| <= eps(D~, rows), D2 the FP32-rule
 //    distance (derivation at rerank_bound). T = the nprobe-th smallest of the
-//    upper bounds D~ + eps, selected exactly; every list of the FP32
+//    upper bounds D~ + eps (rounded up by at most 255 units of its last place:
+//    a radix select that stops at bins of 256); every list of the FP32
 //    top-nprobe has D~ - eps <= T, so those candidates are re-ranked with the
 //    FP32 rule itself (same operation order as coarse.cu) and the nprobe
 //    smallest (D2, l) kept: identical output to the plain path.
@@ -411,12 +412,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) coarse_tc_kernel(
 // constant), from the exact distance by at most dn (2 sqrt(S) + dn), and the
 // FP32 rule differs from the exact distance by at most (dim + 2) 2^-24 of it
 // (kfp). Constants padded by 1 %.
+// sqrt(sup) comes from rsqrtf (at most 2 ulp from 1 / sqrt), whose error the
+// 1 % padding covers many times over.
 __device__ __forceinline__ float rerank_bound(float dt, float qn, float qd, float cn, float cd, float kef,
                                               float kfp) {
   const float ef = kef * (qn + cn);
   const float dn = (qd + cd) * 1.01f;
   const float sup = fmaxf(dt, 0.f) + ef;
-  const float E = dn * (2.f * sqrtf(sup) * 1.01f + dn);
+  const float rt = sup > 0.f ? sup * rsqrtf(sup) : 0.f;  // inf -> NaN -> the list is a candidate
+  const float E = dn * (2.f * rt * 1.01f + dn);
   return (ef + E + kfp * (sup + E)) * 1.01f + 1e-30f;
 }
 
@@ -519,23 +523,25 @@ __device__ __forceinline__ float batch_d2_any(const float* __restrict__ C, const
   return acc;
 }
 
-// The np-th smallest of keys[0..n) (1 <= np <= n), all in [kmin, kmax]: radix
+// An upper bound, within 2^8 - 1 units of the last place, of the np-th
+// smallest of keys[0..n) (1 <= np <= n), all in [kmin, kmax] <= +inf: radix
 // levels of 8 bits over key - kmin, the first level's shift fitted to the
-// range, each level counting only the keys inside the bin chosen before.
+// range, each level counting only the keys inside the bin chosen before, until
+// the bins are at most 2^8 keys wide; the top of the last bin chosen.
 __device__ uint32_t block_select(const uint32_t* keys, int64_t n, int np, uint32_t kmin, uint32_t kmax, int* hist,
                                  uint32_t* sh) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int shift = 0;
   while (((kmax - kmin) >> shift) > 255u) ++shift;
-  uint32_t lo = 0;                                 // relative start of the current range
-  uint64_t span = (uint64_t)(kmax - kmin) + 1u;    // its length
+  uint32_t lo = 0;                        // relative start of the current range
+  uint32_t span_m1 = kmax - kmin;         // its length - 1 (keys <= 0x7F800000: no overflow)
   int need = np;
   for (;;) {
     for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int64_t l = tid; l < n; l += blockDim.x) {
       const uint32_t rel = keys[l] - kmin - lo;   // wraps below lo: outside the range
-      if ((uint64_t)rel < span) atomicAdd(&hist[rel >> shift], 1);
+      if (rel <= span_m1) atomicAdd(&hist[rel >> shift], 1);
     }
     __syncthreads();
     if (warp == 0) {
@@ -567,11 +573,11 @@ __device__ uint32_t block_select(const uint32_t* keys, int64_t n, int np, uint32
     __syncthreads();
     lo += sh[0] << shift;
     need -= (int)sh[1];
-    span = 1ull << shift;
-    if (shift == 0) break;
-    shift = shift >= 8 ? shift - 8 : 0;
+    span_m1 = (1u << shift) - 1u;
+    if (shift <= 8) break;
+    shift = shift >= 16 ? shift - 8 : 8;
   }
-  return kmin + lo;
+  return min(kmin + lo + span_m1, 0x7F800000u);  // the last bin may reach past +inf's key
 }
 
 // Candidate lists of the split re-rank: up to kCap candidates per query in
@@ -606,7 +612,8 @@ __device__ __forceinline__ void write_probes(const RerankArgs& a, int64_t q, int
 // memory.
 // A: eps, the key of D~ + eps and the lower bound D~ - eps of every list, and
 //    the keys' range.
-// B: T = the np-th smallest key, exactly (block_select).
+// B: T >= the np-th smallest key, within 255 units of the last place
+//    (block_select).
 // C: the candidates, D~ - eps <= T, appended to a block-wide list.
 // Then, with at most kCap candidates, the list goes to the workspace with one
 // work item per 32 candidates; otherwise the block computes their FP32-rule

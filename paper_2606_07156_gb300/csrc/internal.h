@@ -211,7 +211,8 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
                                   const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
                                   cudaStream_t s, cudaEvent_t after_qm = nullptr,
-                                  cudaEvent_t after_packed = nullptr, const int32_t* qm_order = nullptr);
+                                  cudaEvent_t after_packed = nullptr, cudaEvent_t after_nibble = nullptr,
+                                  const int32_t* qm_order = nullptr);
 // Pair-level debug paths; qt are the queries' tables from launch_query_tables.
 cudaError_t launch_compute_luts(const Index& ix, const float* Q, const float* qt, int64_t nq,
                                 const int32_t* pq, const int32_t* pl, const uint8_t* pb,

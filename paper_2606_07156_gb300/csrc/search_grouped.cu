@@ -839,7 +839,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
                                   const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                                   const ListWork& w, void* qm_ws, int64_t* ids_out, float* dists_out,
                                   cudaStream_t s, cudaEvent_t after_qm, cudaEvent_t after_packed,
-                                  const int32_t* qm_order) {
+                                  cudaEvent_t after_nibble, const int32_t* qm_order) {
   // narrow pairs regrouped by list, largest lists first: the pairs on tables
   // of 5..8 bits in groups of four, those of 1..4 bits in groups of eight
   // (or all 1..8-bit pairs in groups of four without the nibble kernel)
@@ -880,6 +880,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
     default: e = run_packed<8>(a, s); break;
   }
   if (e != cudaSuccess) return e;
+  if (after_packed) cudaEventRecord(after_packed, s);
   if (nib) {
     GArgs b = a;
     b.cnt = w4.cnt; b.off = w4.off; b.ioff = w4.ioff; b.pairs = w4.pairs; b.gtab = w4.gtab; b.counter = w4.counter;
@@ -895,7 +896,7 @@ cudaError_t launch_search_grouped(const Index& ix, const float* qt, int64_t nq, 
     }
     if (e != cudaSuccess) return e;
   }
-  if (after_packed) cudaEventRecord(after_packed, s);
+  if (after_nibble) cudaEventRecord(after_nibble, s);
   if (grouped_R(k) == 1)
     merge_grouped_kernel<1><<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(qm_d, qm_i, w.part_d, w.part_i, probes, bits,
                                                                    nprobe_per_q, k_per_q, nq, nprobe, k, ids_out,
