@@ -144,7 +144,7 @@ def _geometry_case(key, n, nlist, M, ncomp, nq):
 
 
 @pytest.mark.parametrize("key,M,nlist,bits_set", [
-    ("C", 48, 24, (0, 8, 12)),       # Deep-shaped: D = 96, dsub = 2, Mp = 48
+    ("C", 48, 24, (0, 4, 8, 12)),    # Deep-shaped: D = 96, dsub = 2 (query tables formed in place), Mp = 48
     ("D", 120, 16, (0, 4, 16)),      # GIST-shaped: D = 960, dsub = 8, Mp = 128
     ("E", 96, 16, (0, 6, 8)),        # embedding-shaped: D = 768, dsub = 8, Mp = 96
 ])
