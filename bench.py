@@ -603,7 +603,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     # the adaptive policies run in the configuration the library's autotuner
     # picks on this batch (kernel, query order, grouped work-order chunk);
     # the others in the automatic one
-    KN = {abi.KERNEL_BASIC: "query-major", abi.KERNEL_LIST_MAJOR: "list-major", abi.KERNEL_GROUPED: "grouped"}
+    KN = {abi.KERNEL_BASIC: "query-major", abi.KERNEL_LIST_MAJOR: "list-major", abi.KERNEL_GROUPED: "grouped",
+          abi.KERNEL_SPLIT: "split"}
     SN = {abi.SCHED_NATURAL: "natural", abi.SCHED_LPT: "longest-first"}
     tuned = None
     if not args.no_autotune:

@@ -330,8 +330,9 @@ int anns_scan_pairs(anns_index* index, const float* queries, int64_t nq,
  *   2 precision choice plus the per-query tables, 3 the search kernels up to
  *   the grouped kernels (the whole LUT + scan + top-k for the query-major and
  *   list-major kernels; pair regrouping plus the query-major pass for the
- *   grouped search), 4 the grouped kernel of the 5..8-bit tables (of all
- *   narrow tables without nibble packing), 5 the grouped kernel of the 4-bit
+ *   grouped search; the wide pass of the split search), 4 the grouped kernel
+ *   of the 5..8-bit tables (of all narrow tables without nibble packing; the
+ *   narrow pass of the split search), 5 the grouped kernel of the 4-bit
  *   tables packed eight to a word, 6 the grouped search's per-query merge
  *   (4 to 6 are 0 on the other kernels).
  *  enable  1 = start recording (and clear the totals), 0 = stop, -1 = leave as is.
@@ -368,6 +369,10 @@ int anns_sync_status(anns_index* index, void* cuda_stream);
  *      (query, list) pair, blocks of pairs sharing a list, work items taken
  *      largest list first; then a per-query merge of the pairs' top-k.
  *      UNSUPPORTED at search time if one table does not fit.
+ *    ANNS_KERNEL_SPLIT: query-major in two passes split by table width: the
+ *      FP32 and 12/16-bit pairs into a per-query partial top-k, then the
+ *      1..8-bit pairs with byte tables only (no FP32 table in shared memory,
+ *      so more blocks per SM), bounded by and merged with the partial.
  *  ANNS_OPT_SCHEDULE: the order in which the query-major kernel takes queries
  *    (the greedy load scheduling of Section 4.3, applied to queries).
  *    ANNS_SCHED_AUTO (default): longest first when nprobe_per_q is given (an
@@ -397,7 +402,8 @@ int anns_sync_status(anns_index* index, void* cuda_stream);
  * Errors: INVALID_ARG. */
 enum { ANNS_OPT_KERNEL = 0, ANNS_OPT_SCHEDULE = 1, ANNS_OPT_QCHUNK = 2, ANNS_OPT_WAIT_CYCLES = 3,
        ANNS_OPT_NIBBLE = 4 };
-enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2, ANNS_KERNEL_GROUPED = 3 };
+enum { ANNS_KERNEL_AUTO = 0, ANNS_KERNEL_BASIC = 1, ANNS_KERNEL_LIST_MAJOR = 2, ANNS_KERNEL_GROUPED = 3,
+       ANNS_KERNEL_SPLIT = 4 };
 enum { ANNS_SCHED_AUTO = 0, ANNS_SCHED_NATURAL = 1, ANNS_SCHED_LPT = 2 };
 int anns_set_option(anns_index* index, int32_t option, int64_t value);
 

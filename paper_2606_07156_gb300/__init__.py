@@ -216,10 +216,11 @@ class Index:
         return ids, dists
 
     def set_kernel(self, which: str):
-        """'auto', 'basic' (query-major), 'lists' (list-major, one warp per pair) or
-        'grouped' (narrow pairs packed four queries to a gather)."""
+        """'auto', 'basic' (query-major), 'lists' (list-major, one warp per pair),
+        'grouped' (narrow pairs packed four or eight queries to a gather) or 'split'
+        (query-major in two passes: wide pairs, then 1..8-bit pairs on byte tables only)."""
         v = {"auto": abi.KERNEL_AUTO, "basic": abi.KERNEL_BASIC, "lists": abi.KERNEL_LIST_MAJOR,
-             "grouped": abi.KERNEL_GROUPED}[which]
+             "grouped": abi.KERNEL_GROUPED, "split": abi.KERNEL_SPLIT}[which]
         abi.anns_set_option(self.handle, abi.OPT_KERNEL, v)
 
     def locate(self, queries, nprobe: int, cl: str = "fp32", nprobe_per_q=None, stream=None):

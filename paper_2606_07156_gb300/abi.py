@@ -23,7 +23,7 @@ TAP_PROBES, TAP_PROBE_D2, TAP_BITS, TAP_FEATURES = 0, 1, 2, 3
 TAP_COARSE_APPROX, TAP_COARSE_CANDIDATES = 4, 5
 TAP_LIST_SIZES, TAP_LIST_RADIUS, TAP_PACKED_IDS, TAP_STATUS = 10, 11, 12, 13
 OPT_KERNEL, OPT_SCHEDULE, OPT_QCHUNK, OPT_WAIT_CYCLES, OPT_NIBBLE = 0, 1, 2, 3, 4
-KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR, KERNEL_GROUPED = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_BASIC, KERNEL_LIST_MAJOR, KERNEL_GROUPED, KERNEL_SPLIT = 0, 1, 2, 3, 4
 SCHED_AUTO, SCHED_NATURAL, SCHED_LPT = 0, 1, 2
 
 SYMBOLS = (

@@ -330,6 +330,20 @@ static bool use_grouped(const Index& ix, const anns_precision_policy& P, int k) 
   return narrow_possible && grouped_supported(ix, k);
 }
 
+// Whether every pair the policy can put outside 1..8 bits is an FP32 pair
+// (no 12- or 16-bit tables): the split search's wide pass then needs no
+// level table.
+static bool wide_tables_fp32(const anns_precision_policy& P) {
+  switch (P.lut_mode) {
+    case ANNS_LUT_PLAIN_FP32: return true;
+    case ANNS_LUT_FIXED_BITS: return P.fixed_bits <= 8;
+    case ANNS_LUT_HEURISTIC_EQ2:
+    case ANNS_LUT_MLP:
+    case ANNS_LUT_SVR: return P.width_map != 0;
+    default: return false;
+  }
+}
+
 static bool use_lpt(const Index& ix, const int32_t* nprobe_per_q) {
   return ix.opt_schedule == ANNS_SCHED_LPT || (ix.opt_schedule == ANNS_SCHED_AUTO && nprobe_per_q);
 }
@@ -343,7 +357,7 @@ int reserve_search(Index& ix, int64_t nq, int nprobe, int k, const anns_precisio
     const int64_t qchunk = ix.opt_kernel == ANNS_KERNEL_LIST_MAJOR ? nq : grouped_qchunk(ix, nq);
     if ((rc = list_workspace(ix, nq, nprobe, k, w, qchunk))) return rc;
   }
-  if (use_grouped(ix, P, k)) {
+  if (use_grouped(ix, P, k) || ix.opt_kernel == ANNS_KERNEL_SPLIT) {
     if ((rc = grow(&ix.ws_grp, &ix.ws_grp_cap, grouped_workspace_bytes(nq, k)))) return rc;
   }
   if (ix.opt_kernel != ANNS_KERNEL_LIST_MAJOR && use_lpt(ix, nprobe_per_q)) {
@@ -419,8 +433,28 @@ int search_sequence(Index& ix, const float* Q, int64_t nq, int nprobe, const int
       order = lpt_order_ptr(ix.ws_sched, nq);
     }
     if (ev) cudaEventRecord(ev[3], s);
+    if (ix.opt_kernel == ANNS_KERNEL_SPLIT) {
+      // wide pairs (FP32, 12/16 bits) into a partial top-k per query, then
+      // the 1..8-bit pairs with byte tables only, merged with it
+      float* part_d = (float*)ix.ws_grp;
+      int64_t* part_i = (int64_t*)((char*)ix.ws_grp + (((size_t)nq * k * 4 + 255) & ~size_t(255)));
+      e = launch_search(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
+                        ix.ws_bits, order, part_i, part_d, s, 2, wide_tables_fp32(P) ? QM_TABLES_FP32 : QM_TABLES_ALL);
+      if (e == cudaSuccess && ev) cudaEventRecord(ev[4], s);
+      if (e == cudaSuccess)
+        e = launch_search(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
+                          ix.ws_bits, order, ids_out, dists_out, s, 0, QM_TABLES_NARROW, part_d, part_i);
+      if (e != cudaSuccess) return cuda_fail(e, "search kernel");
+      if (ev)
+        for (int st = 5; st <= Index::kStages; ++st) cudaEventRecord(ev[st], s);
+      return ANNS_OK;
+    }
+    // a plain-FP32 policy needs no level table, a fixed <= 8-bit one no FP32 table
+    const int tables = P.lut_mode == ANNS_LUT_PLAIN_FP32 ? QM_TABLES_FP32
+                       : P.lut_mode == ANNS_LUT_FIXED_BITS && P.fixed_bits <= 8 ? QM_TABLES_NARROW
+                                                                                 : QM_TABLES_ALL;
     e = launch_search(ix, ix.ws_qt, nq, nprobe, nprobe_per_q, k, k_per_q, ix.ws_probes, ix.ws_probe_d2,
-                      ix.ws_bits, order, ids_out, dists_out, s);
+                      ix.ws_bits, order, ids_out, dists_out, s, 0, tables);
   }
   if (e != cudaSuccess) return cuda_fail(e, "search kernel");
   if (ev)
@@ -636,7 +670,7 @@ extern "C" int anns_set_option(anns_index* ix, int32_t option, int64_t value) {
   if (!ix) return fail(ANNS_ERR_INVALID_ARG, "null index");
   switch (option) {
     case ANNS_OPT_KERNEL:
-      if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_GROUPED)
+      if (value < ANNS_KERNEL_AUTO || value > ANNS_KERNEL_SPLIT)
         return fail(ANNS_ERR_INVALID_ARG, "unknown kernel choice");
       ix->opt_kernel = (int)value;
       return ANNS_OK;

@@ -146,6 +146,7 @@ extern "C" int anns_autotune(anns_index* ix, const float* Q, int64_t nq, int32_t
   const int64_t qchunk0 = ix->opt_qchunk;
   struct Cand { int kernel, schedule; int64_t qchunk; };
   std::vector<Cand> cands = {{ANNS_KERNEL_BASIC, ANNS_SCHED_NATURAL, 0}, {ANNS_KERNEL_BASIC, ANNS_SCHED_LPT, 0},
+                             {ANNS_KERNEL_SPLIT, ANNS_SCHED_NATURAL, 0}, {ANNS_KERNEL_SPLIT, ANNS_SCHED_LPT, 0},
                              {ANNS_KERNEL_LIST_MAJOR, ANNS_SCHED_NATURAL, 0}};
   // the grouped kernel under both query orders, with its automatic work order
   // and with query chunks of a half and a quarter of the batch (at least 256)

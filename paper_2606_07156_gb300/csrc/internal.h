@@ -143,13 +143,22 @@ cudaError_t launch_query_tables(const Index& ix, const float* Q, int64_t nq, flo
 int launch_policy(const Index& ix, const anns_precision_policy& pol, int64_t nq, int nprobe,
                   const int32_t* nprobe_per_q, const int32_t* probes, const float* probe_d2,
                   uint8_t* bits, float* feat, cudaStream_t s);
+// Table widths a query-major launch serves: all (an FP32 table and a level
+// table of up to 16 bits), FP32 pairs only, or 1..8-bit pairs only (no FP32
+// table: fewer bytes of shared memory per block, more blocks per SM).
+enum { QM_TABLES_ALL = 0, QM_TABLES_FP32 = 1, QM_TABLES_NARROW = 2 };
 // RC + LC + quantise + DC + TS for every query; `order` (NULL = 0..nq-1) is
-// the order in which blocks take the queries.
+// the order in which blocks take the queries. skip_narrow 1 leaves out the
+// 1..8-bit pairs of probe rank >= 1, 2 those of every rank. With
+// QM_TABLES_NARROW only the 1..8-bit pairs are scanned, and part_d / part_i
+// (or NULL), the query's top-k over its other pairs ([nq * k]), bound the
+// scan and join the final merge.
 cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int nprobe,
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                           const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s,
-                          bool skip_narrow = false);
+                          int skip_narrow = 0, int tables = QM_TABLES_ALL, const float* part_d = nullptr,
+                          const int64_t* part_i = nullptr);
 // Longest-first query order (schedule.cu) into a workspace of
 // lpt_workspace_bytes(nq); the order is at lpt_order_ptr(ws, nq).
 size_t lpt_workspace_bytes(int64_t nq);

@@ -32,17 +32,24 @@ struct PairScal {
   int L;
 };
 
+// Table widths a query-major launch serves: every width (the FP32 table T'
+// and a level table of up to 2 bytes an entry), FP32 pairs only (no level
+// table), or 1..8-bit pairs only (a 1-byte level table and no FP32 table:
+// the levels are built in two passes from global memory).
+enum : int { kModeFull = 0, kModeFp32 = 1, kModeNarrow = 2 };
+
 // Offsets from a 256-byte aligned base inside the block's dynamic shared
 // memory (256 bytes of slack are allocated for the alignment): the FP32 table
 // T, the level table q (1 or 2 bytes an entry), row statistics and scales.
+// A table the mode does not use takes no space.
 struct SmemLayout {
   size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, d2 = 0, plist = 0, md = 0, mi = 0, total = 0;
   static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   SmemLayout() = default;
-  SmemLayout(int64_t Mp, int R) {
+  SmemLayout(int64_t Mp, int R, int mode = kModeFull) {
     size_t o = 0;   // the tables first, at multiples of 256 bytes
-    T = o; o += al(Mp * kKsub * 4);
-    q = o; o += al(Mp * kKsub * 2);
+    T = o; o += mode == kModeNarrow ? 0 : al(Mp * kKsub * 4);
+    q = o; o += mode == kModeFp32 ? 0 : al(Mp * kKsub * (mode == kModeNarrow ? 1 : 2));
     bias = o; o += al(Mp * 4);
     rowmax = o; o += al(Mp * 4);
     scal = o; o += al(sizeof(PairScal));
@@ -252,6 +259,49 @@ __device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, cons
   if (warp == 0) pair_offset(M, d2, bias, sc);
 }
 
+// Steps 1-2 for a 1..8-bit pair without an FP32 table (kModeNarrow): the row
+// statistics from T' formed in registers, then the levels from T' formed
+// again (the same operations, so the same values as build_lut), written as
+// bytes. Two block barriers; the caller synchronises before the scan.
+__device__ void build_lut_2pass(const float* __restrict__ P, const float* __restrict__ qt2, int M, int Mp, int b,
+                                float d2, Smem& s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int m = warp; m < M; m += nwarps) {
+    float p[8], q[8];
+    ldg_row8(P + m * kKsub, lane, p);
+    ldg_row8(qt2 + m * kKsub, lane, q);
+    float lo = sub_rn(p[0], q[0]), hi = lo;
+#pragma unroll
+    for (int e = 1; e < 8; ++e) {
+      const float t = sub_rn(p[e], q[e]);
+      lo = fminf(lo, t);
+      hi = fmaxf(hi, t);
+    }
+    const float mn = warp_min(lo);
+    // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
+    const float mx = sub_rn(warp_max(hi), mn);
+    if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
+  }
+  __syncthreads();
+  const float s32 = pair_scale<false>(M, b, s.rowmax, s.sc);
+  for (int m = warp; m < Mp; m += nwarps) {
+    float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float mn = 0.f;
+    if (m < M) {
+      float p[8], q[8];
+      ldg_row8(P + m * kKsub, lane, p);
+      ldg_row8(qt2 + m * kKsub, lane, q);
+      mn = s.bias[m];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) x[e] = sub_rn(p[e], q[e]);
+    }
+    uint32_t n[8];
+    quantise8(x, mn, s32, n);
+    store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub, lane);
+  }
+  if (warp == 0) pair_offset(M, d2, s.bias, s.sc);
+}
+
 template <int NCHUNK>
 __device__ __forceinline__ void load_tile(const uint8_t* __restrict__ tile, int lane, uint4 (&w)[NCHUNK]) {
 #pragma unroll
@@ -285,8 +335,13 @@ struct SearchArgs {
   const int32_t* npq; const int32_t* kpq;
   const int32_t* probes; const float* probe_d2; const uint8_t* bits;
   const int32_t* order;
-  int skip_narrow;   // leave out the pairs on 1..8-bit tables of rank >= 1 (the grouped kernel takes them)
+  // 1: leave out the pairs on 1..8-bit tables of rank >= 1 (the grouped
+  // kernels take them); 2: of every rank (the narrow pass takes them)
+  int skip_narrow;
   int64_t* ids_out; float* dists_out;
+  // kModeNarrow: the query's top-k over its other pairs ([nq * k], padding
+  // +inf), which bounds the scan and joins the final merge; or null
+  const float* part_d; const int64_t* part_i;
   SmemLayout lay;
 };
 
@@ -296,6 +351,16 @@ template <int R>
 __device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, WarpTopK<R, int64_t>& top,
                                                 int64_t q, int kq, float& thd, int64_t& thi) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (a.part_d && kq > 0) {
+    // the top-k of the query's other pairs joins warp 0's list
+    if (warp == 0)
+      for (int e0 = 0; e0 < kq; e0 += 32) {
+        const int e = e0 + lane;
+        const float cd = e < kq ? a.part_d[q * a.k + e] : INFINITY;
+        const int64_t ci = e < kq ? a.part_i[q * a.k + e] : INT64_MAX;
+        top.offer(cd != INFINITY, cd, ci, kq, thd, thi);
+      }
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     s.md[(warp * R + r) * 32 + lane] = top.d[r];
@@ -324,11 +389,20 @@ __device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, Wa
 }
 
 // Query-major search: one query per block at a time. Per pair the block builds
-// the table (in registers for Mp <= 32, else staged in shared memory), then
-// every warp scans tiles of the list. Four blocks per SM for Mp <= 32 (two
-// with the 128-entry lists of k > 32).
-template <int NCHUNK, int R>
-__global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? (R == 1 ? 4 : 2) : 1) search_kernel(const SearchArgs a) {
+// the table (in registers for Mp <= 32, else staged in shared memory; in two
+// passes from global memory for kModeNarrow), then every warp scans tiles of
+// the list. Four blocks per SM for Mp <= 32 (two with the 128-entry lists of
+// k > 32); without the FP32 table (kModeNarrow) three (two with the 128-entry
+// lists, whose inserts need the registers); without the level table
+// (kModeFp32) two for larger Mp, where shared memory allows.
+template <int MODE, int NCHUNK, int R>
+constexpr int qm_blocks() {
+  return MODE == kModeNarrow ? (R == 1 ? (NCHUNK <= 2 ? 4 : 3) : 2)
+                             : (NCHUNK <= 2 ? (R == 1 ? 4 : 2) : (MODE == kModeFp32 ? 2 : 1));
+}
+
+template <int NCHUNK, int R, int MODE>
+__global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search_kernel(const SearchArgs a) {
   Smem s(a.lay);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tstride = (int64_t)a.Mp * kKsub;
@@ -357,7 +431,10 @@ __global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? (R == 1 ? 4 : 2) : 1) 
           d2 = a.probe_d2[i];
           if (l >= 0) n_l = a.list_len[l];
         }
-        const bool use = l >= 0 && n_l > 0 && !(a.skip_narrow && j >= 1 && b >= 1 && b <= 8);
+        const bool narrow = b >= 1 && b <= 8;
+        const bool use = l >= 0 && n_l > 0 &&
+                         (MODE == kModeNarrow ? narrow
+                                              : !(narrow && (a.skip_narrow == 2 || (a.skip_narrow == 1 && j >= 1))));
         const unsigned m = __ballot_sync(kFull, use);
         if (use) s.plist[base + __popc(m & ((1u << lane) - 1u))] = make_int4(l, n_l, b, __float_as_int(d2));
         base += __popc(m);
@@ -366,12 +443,18 @@ __global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? (R == 1 ? 4 : 2) : 1) 
     }
     __syncthreads();
     const int npairs = *s.npairs;
+    // kModeNarrow: no vector beyond the k-th distance of the query's other
+    // pairs can enter the final top-k (equal distances are kept: the id decides)
+    const float bnd = MODE == kModeNarrow && a.part_d && kq > 0 ? a.part_d[q * a.k + kq - 1] : INFINITY;
     for (int e = 0; e < npairs; ++e) {
       const int4 pe = s.plist[e];
       const int l = pe.x, n_l = pe.y, b = pe.z;
       const float d2 = __int_as_float(pe.w);
       const int64_t tile0 = a.tile_off[l], vec0 = a.vec_off[l];  // requested before the table build
-      if constexpr (NCHUNK <= 2) {
+      if constexpr (MODE == kModeNarrow) {
+        build_lut_2pass(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
+        __syncthreads();
+      } else if constexpr (NCHUNK <= 2) {
         build_lut_regs<NCHUNK * 16 / kWarps>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, b, d2,
                                              s.T, s.q, s.bias, s.rowmax, s.sc);
         __syncthreads();
@@ -388,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, NCHUNK <= 2 ? (R == 1 ? 4 : 2) : 1) 
         load_tile<NCHUNK>(tp, lane, w);
         const float d = pair_distance<NCHUNK>(b, d2, s.T_addr, s.q_addr, sc, w);
         const int v = t * kTileVecs + lane;
-        const bool pre = v < n_l && d <= thd;
+        const bool pre = v < n_l && d <= thd && d <= bnd;
         if (__any_sync(kFull, pre)) {
           const int64_t id = pre ? __ldg(idp + v) : INT64_MAX;
           top.offer(pre, d, id, kq, thd, thi);
@@ -477,13 +560,13 @@ __global__ void __launch_bounds__(kThreads) scan_pairs_kernel(const SearchArgs a
   }
 }
 
-SearchArgs make_args(const Index& ix, const float* Q, const float* qt, int R) {
+SearchArgs make_args(const Index& ix, const float* Q, const float* qt, int R, int mode = kModeFull) {
   SearchArgs a{};
   a.Q = Q; a.qt = qt; a.dim = ix.dim; a.nlist = ix.nlist;
   a.centroids = ix.centroids; a.ltab = ix.ltab; a.codes = ix.codes; a.ids = ix.ids;
   a.list_len = ix.list_len; a.vec_off = ix.vec_off; a.tile_off = ix.tile_off;
   a.M = (int)ix.M; a.Mp = (int)ix.Mp;
-  a.lay = SmemLayout(ix.Mp, R);
+  a.lay = SmemLayout(ix.Mp, R, mode);
   return a;
 }
 
@@ -506,13 +589,17 @@ cudaError_t launch_query_major(K kern, const SearchArgs& a, cudaStream_t s) {
 }
 
 template <int NCHUNK, int R>
-cudaError_t run_search(const SearchArgs& a, cudaStream_t s) {
-  return launch_query_major(search_kernel<NCHUNK, R>, a, s);
+cudaError_t run_search(const SearchArgs& a, int mode, cudaStream_t s) {
+  switch (mode) {
+    case kModeFp32: return launch_query_major(search_kernel<NCHUNK, R, kModeFp32>, a, s);
+    case kModeNarrow: return launch_query_major(search_kernel<NCHUNK, R, kModeNarrow>, a, s);
+    default: return launch_query_major(search_kernel<NCHUNK, R, kModeFull>, a, s);
+  }
 }
 
 template <int NCHUNK>
-cudaError_t run_search_r(const SearchArgs& a, int R, cudaStream_t s) {
-  return R == 1 ? run_search<NCHUNK, 1>(a, s) : run_search<NCHUNK, 4>(a, s);
+cudaError_t run_search_r(const SearchArgs& a, int R, int mode, cudaStream_t s) {
+  return R == 1 ? run_search<NCHUNK, 1>(a, mode, s) : run_search<NCHUNK, 4>(a, mode, s);
 }
 
 template <int NCHUNK>
@@ -533,21 +620,24 @@ cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int npro
                           const int32_t* nprobe_per_q, int k, const int32_t* k_per_q,
                           const int32_t* probes, const float* probe_d2, const uint8_t* bits,
                           const int32_t* order, int64_t* ids_out, float* dists_out, cudaStream_t s,
-                          bool skip_narrow) {
+                          int skip_narrow, int tables, const float* part_d, const int64_t* part_i) {
   const int R = k <= 32 ? 1 : 4;
-  SearchArgs a = make_args(ix, nullptr, qt, R);
+  const int mode = tables == QM_TABLES_FP32 ? kModeFp32 : tables == QM_TABLES_NARROW ? kModeNarrow : kModeFull;
+  SearchArgs a = make_args(ix, nullptr, qt, R, mode);
   a.nq = nq; a.nprobe = nprobe; a.k = k; a.npq = nprobe_per_q; a.kpq = k_per_q;
-  a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.order = order; a.skip_narrow = skip_narrow ? 1 : 0;
+  a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.order = order; a.skip_narrow = skip_narrow;
   a.ids_out = ids_out; a.dists_out = dists_out;
+  a.part_d = mode == kModeNarrow ? part_d : nullptr;
+  a.part_i = mode == kModeNarrow ? part_i : nullptr;
   switch (ix.nchunk) {
-    case 1: return run_search_r<1>(a, R, s);
-    case 2: return run_search_r<2>(a, R, s);
-    case 3: return run_search_r<3>(a, R, s);
-    case 4: return run_search_r<4>(a, R, s);
-    case 5: return run_search_r<5>(a, R, s);
-    case 6: return run_search_r<6>(a, R, s);
-    case 7: return run_search_r<7>(a, R, s);
-    default: return run_search_r<8>(a, R, s);
+    case 1: return run_search_r<1>(a, R, mode, s);
+    case 2: return run_search_r<2>(a, R, mode, s);
+    case 3: return run_search_r<3>(a, R, mode, s);
+    case 4: return run_search_r<4>(a, R, mode, s);
+    case 5: return run_search_r<5>(a, R, mode, s);
+    case 6: return run_search_r<6>(a, R, mode, s);
+    case 7: return run_search_r<7>(a, R, mode, s);
+    default: return run_search_r<8>(a, R, mode, s);
   }
 }
 

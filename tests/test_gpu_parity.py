@@ -29,7 +29,7 @@ def _pair(amp, ix, ids=None):
     return g, o
 
 
-@pytest.fixture(scope="module", params=["basic", "lists", "grouped"])
+@pytest.fixture(scope="module", params=["basic", "lists", "grouped", "split"])
 def case_a(amp, small_a, request):
     """Config A shape, searched by each of the three search kernels."""
     d, ix = small_a

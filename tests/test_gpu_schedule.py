@@ -117,6 +117,7 @@ def test_autotune_installs_a_configuration(amp, pair_a):
     assert (amp.abi.KERNEL_BASIC, amp.abi.SCHED_LPT) in kinds
     assert all(r[2] > 0 for r in res)
     assert (amp.abi.KERNEL_GROUPED, amp.abi.SCHED_LPT) in kinds
+    assert (amp.abi.KERNEL_SPLIT, amp.abi.SCHED_NATURAL) in kinds
     ids, dists = g.search(cuda(Q), 8, 10, amp.policy("fixed", bits=8))
     ri, rd = ivfpq.search(o, Q, 8, 10, bits=8)
     np.testing.assert_array_equal(ids.cpu().numpy(), ri)
@@ -157,7 +158,7 @@ def test_workload_geometries_bit_exact(amp, key, M, nlist, bits_set):
     try:
         for bits in bits_set:
             pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
-            for kern in ("auto", "lists", "grouped", "basic"):
+            for kern in ("auto", "lists", "grouped", "basic", "split"):
                 g.set_kernel(kern)
                 ids, dists = g.search(cuda(Q), 8, 100, pol, nprobe_per_q=cuda(npq), k_per_q=cuda(kpq))
                 ri, rd = ivfpq.search(o, Q, 8, 100, bits=bits, nprobe_per_q=npq, k_per_q=kpq)
