@@ -394,11 +394,13 @@ __device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, Wa
 // the list. Four blocks per SM for Mp <= 32 (two with the 128-entry lists of
 // k > 32); without the FP32 table (kModeNarrow) three (two with the 128-entry
 // lists, whose inserts need the registers); without the level table
-// (kModeFp32) two for larger Mp, where shared memory allows.
+// (kModeFp32) two up to Mp = 96, where two FP32 tables fit in shared memory
+// (beyond it a second block cannot be resident, and the register cap would
+// only cost spills).
 template <int MODE, int NCHUNK, int R>
 constexpr int qm_blocks() {
   return MODE == kModeNarrow ? (R == 1 ? (NCHUNK <= 2 ? 4 : 3) : 2)
-                             : (NCHUNK <= 2 ? (R == 1 ? 4 : 2) : (MODE == kModeFp32 ? 2 : 1));
+                             : (NCHUNK <= 2 ? (R == 1 ? 4 : 2) : (MODE == kModeFp32 && NCHUNK <= 6 ? 2 : 1));
 }
 
 template <int NCHUNK, int R, int MODE>
