@@ -42,8 +42,12 @@ enum : int { kModeFull = 0, kModeFp32 = 1, kModeNarrow = 2 };
 // memory (256 bytes of slack are allocated for the alignment): the FP32 table
 // T, the level table q (1 or 2 bytes an entry), row statistics and scales.
 // A table the mode does not use takes no space.
+// Rows of P_l and 2 Q_q a warp of a kModeNarrow block keeps in flight while
+// it builds a table (cp.async ring in shared memory).
+__host__ __device__ constexpr int ring_rows(int R) { return R == 1 ? 2 : 4; }
+
 struct SmemLayout {
-  size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, d2 = 0, plist = 0, md = 0, mi = 0, total = 0;
+  size_t T = 0, q = 0, bias = 0, rowmax = 0, scal = 0, d2 = 0, plist = 0, md = 0, mi = 0, ring = 0, total = 0;
   static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   SmemLayout() = default;
   SmemLayout(int64_t Mp, int R, int mode = kModeFull) {
@@ -57,6 +61,7 @@ struct SmemLayout {
     plist = o; o += al((size_t)ANNS_MAX_NPROBE * 16 + 16);  // + the count
     md = o; o += al((size_t)kWarps * R * 32 * 4);
     mi = o; o += al((size_t)kWarps * R * 32 * 8);
+    ring = o; o += mode == kModeNarrow ? al((size_t)kWarps * ring_rows(R) * 2 * kKsub * 4) : 0;
     total = o + 256;
   }
 };
@@ -68,6 +73,7 @@ __device__ __forceinline__ unsigned char* aligned_smem() {
 
 struct Smem {
   float* T; void* q; float* bias; float* rowmax; PairScal* sc; float* d2; float* md; int64_t* mi;
+  float* ring;  // kModeNarrow: per warp, ring_rows(R) slots of [P row | 2 Q row]
   int4* plist; int* npairs;  // query-major kernel: the block's pairs (list, n_l, bits, D2 bits) and their count
   uint32_t T_addr, q_addr;  // shared-memory byte addresses of the two tables
   __device__ explicit Smem(const SmemLayout& L) {
@@ -75,6 +81,7 @@ struct Smem {
     T = (float*)(b + L.T); q = b + L.q; bias = (float*)(b + L.bias); rowmax = (float*)(b + L.rowmax);
     sc = (PairScal*)(b + L.scal); d2 = (float*)(b + L.d2); md = (float*)(b + L.md); mi = (int64_t*)(b + L.mi);
     plist = (int4*)(b + L.plist); npairs = (int*)(b + L.plist + (size_t)ANNS_MAX_NPROBE * 16);
+    ring = (float*)(b + L.ring);
     T_addr = smem_addr(T);
     q_addr = smem_addr(q);
   }
@@ -259,45 +266,88 @@ __device__ __forceinline__ void build_lut_regs(const float* __restrict__ P, cons
   if (warp == 0) pair_offset(M, d2, bias, sc);
 }
 
+// 16-byte asynchronous copy global -> shared (no register staging), and the
+// group bookkeeping: wait_group N returns once at most N of this thread's most
+// recent groups are still in flight.
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Steps 1-2 for a 1..8-bit pair without an FP32 table (kModeNarrow): the row
-// statistics from T' formed in registers, then the levels from T' formed
+// statistics from T' formed from the rows, then the levels from T' formed
 // again (the same operations, so the same values as build_lut), written as
-// bytes. Two block barriers; the caller synchronises before the scan.
+// bytes. Each warp streams its rows of P_l and 2 Q_q through a ring of RS
+// slots in shared memory, RS rows in flight (a lane copies, and later reads,
+// exactly the 16-byte pieces at row_at(lane, 0) and row_at(lane, 1)). Two
+// block barriers; the caller synchronises before the scan.
+template <int RS>
 __device__ void build_lut_2pass(const float* __restrict__ P, const float* __restrict__ qt2, int M, int Mp, int b,
                                 float d2, Smem& s) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int m = warp; m < M; m += nwarps) {
+  float* slots = s.ring + (size_t)warp * RS * 2 * kKsub;
+  const int nr = warp < M ? (M - warp + nwarps - 1) / nwarps : 0;  // rows m = warp + nwarps i < M
+  auto issue = [&](int i) {
+    if (i < nr) {
+      const int m = warp + nwarps * i;
+      float* d = slots + (i % RS) * 2 * kKsub;
+      cp_async16(d + row_at(lane, 0), P + m * kKsub + row_at(lane, 0));
+      cp_async16(d + row_at(lane, 1), P + m * kKsub + row_at(lane, 1));
+      cp_async16(d + kKsub + row_at(lane, 0), qt2 + m * kKsub + row_at(lane, 0));
+      cp_async16(d + kKsub + row_at(lane, 1), qt2 + m * kKsub + row_at(lane, 1));
+    }
+    cp_async_commit();  // every lane commits one group per row index (possibly empty)
+  };
+  auto row = [&](int i, float (&t)[8]) {
+    const float* d = slots + (i % RS) * 2 * kKsub;
     float p[8], q[8];
-    ldg_row8(P + m * kKsub, lane, p);
-    ldg_row8(qt2 + m * kKsub, lane, q);
-    float lo = sub_rn(p[0], q[0]), hi = lo;
+    const float4 p0 = *(const float4*)(d + row_at(lane, 0)), p1 = *(const float4*)(d + row_at(lane, 1));
+    const float4 q0 = *(const float4*)(d + kKsub + row_at(lane, 0)), q1 = *(const float4*)(d + kKsub + row_at(lane, 1));
+    p[0] = p0.x; p[1] = p0.y; p[2] = p0.z; p[3] = p0.w; p[4] = p1.x; p[5] = p1.y; p[6] = p1.z; p[7] = p1.w;
+    q[0] = q0.x; q[1] = q0.y; q[2] = q0.z; q[3] = q0.w; q[4] = q1.x; q[5] = q1.y; q[6] = q1.z; q[7] = q1.w;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) t[e] = sub_rn(p[e], q[e]);
+  };
+  // pass 1: row statistics
+  for (int i = 0; i < RS; ++i) issue(i);
+  for (int i = 0; i < nr; ++i) {
+    cp_async_wait<RS - 1>();  // row i's group has landed
+    float t[8];
+    row(i, t);
+    float lo = t[0], hi = t[0];
 #pragma unroll
     for (int e = 1; e < 8; ++e) {
-      const float t = sub_rn(p[e], q[e]);
-      lo = fminf(lo, t);
-      hi = fmaxf(hi, t);
+      lo = fminf(lo, t[e]);
+      hi = fmaxf(hi, t[e]);
     }
+    const int m = warp + nwarps * i;
     const float mn = warp_min(lo);
     // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
     const float mx = sub_rn(warp_max(hi), mn);
     if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
+    issue(i + RS);  // into the slot just read (this lane's own pieces)
   }
+  cp_async_wait<0>();
   __syncthreads();
   const float s32 = pair_scale<false>(M, b, s.rowmax, s.sc);
-  for (int m = warp; m < Mp; m += nwarps) {
-    float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float mn = 0.f;
-    if (m < M) {
-      float p[8], q[8];
-      ldg_row8(P + m * kKsub, lane, p);
-      ldg_row8(qt2 + m * kKsub, lane, q);
-      mn = s.bias[m];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) x[e] = sub_rn(p[e], q[e]);
-    }
+  // pass 2: levels
+  for (int i = 0; i < RS; ++i) issue(i);
+  for (int i = 0; i < nr; ++i) {
+    cp_async_wait<RS - 1>();
+    float t[8];
+    row(i, t);
+    const int m = warp + nwarps * i;
     uint32_t n[8];
-    quantise8(x, mn, s32, n);
+    quantise8(t, s.bias[m], s32, n);
     store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub, lane);
+    issue(i + RS);
+  }
+  cp_async_wait<0>();
+  for (int m = M + ((warp - M % nwarps + nwarps) % nwarps); m < Mp; m += nwarps) {  // padding rows: level 0
+    const uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    store_levels(b, z, (uint8_t*)s.q + (size_t)m * kKsub, lane);
   }
   if (warp == 0) pair_offset(M, d2, s.bias, s.sc);
 }
@@ -416,6 +466,11 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
     top.init();
     float thd = INFINITY;
     int64_t thi = INT64_MAX;
+    // 128-entry lists (k > 32): the block shares the smallest k-th distance
+    // any warp holds (at least k vectors lie at or below it, so no farther
+    // vector can enter the final top-k; equal distances are kept)
+    float* blim = s.d2 + 1;
+    if (R > 1 && threadIdx.x == 0) *blim = INFINITY;
     // the probe ranks this block scans, found by warp 0 in one parallel pass
     // (lane i reads rank 32 r + i) and kept in shared memory: the pairs'
     // metadata costs one round of loads per query instead of a dependent chain
@@ -454,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
       const float d2 = __int_as_float(pe.w);
       const int64_t tile0 = a.tile_off[l], vec0 = a.vec_off[l];  // requested before the table build
       if constexpr (MODE == kModeNarrow) {
-        build_lut_2pass(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
+        build_lut_2pass<ring_rows(R)>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
         __syncthreads();
       } else if constexpr (NCHUNK <= 2) {
         build_lut_regs<NCHUNK * 16 / kWarps>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, b, d2,
@@ -473,10 +528,22 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
         load_tile<NCHUNK>(tp, lane, w);
         const float d = pair_distance<NCHUNK>(b, d2, s.T_addr, s.q_addr, sc, w);
         const int v = t * kTileVecs + lane;
-        const bool pre = v < n_l && d <= thd && d <= bnd;
+        const float lim = R > 1 ? *(volatile float*)blim : INFINITY;
+        const bool pre = v < n_l && d <= thd && d <= bnd && d <= lim;
         if (__any_sync(kFull, pre)) {
           const int64_t id = pre ? __ldg(idp + v) : INT64_MAX;
+          const float before = thd;
           top.offer(pre, d, id, kq, thd, thi);
+          if (R > 1 && lane == 0 && thd < before && thd < lim) {
+            // lower the shared limit (a retry lost to the cap only prunes less)
+            int* w = (int*)blim;
+            int old = *(volatile int*)w;
+            for (int it = 0; it < 64 && thd < __int_as_float(old); ++it) {
+              const int seen = atomicCAS(w, old, __float_as_int(thd));
+              if (seen == old) break;
+              old = seen;
+            }
+          }
         }
       }
       __syncthreads();  // the next pair overwrites the LUT
