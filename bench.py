@@ -1213,7 +1213,11 @@ def fp64_errors(ref, W, cfg, nprobe: int, ctx: dict, nq_s: int = 16) -> dict:
 def run_reference(args, rank: int):
     if rank != 0:
         return None
-    cfg, W = workload(args.config)
+    # the workload (index training, ground truth) is built on the GPU when
+    # there is one, as for the GPU arm; only the oracle's search is timed,
+    # on the host
+    import torch
+    cfg, W = workload(args.config, device=torch.device("cuda", 0) if torch.cuda.is_available() else None)
     # the GPU arm's nprobe: the workload's own (SIFT-shaped: the largest of the
     # sweep; no nprobe of the sweep reaches recall@10 0.9 with these codes)
     nprobe = args.nprobe or (max(cfg["nprobe_sweep"]) if "nprobe_sweep" in cfg else cfg["nprobe"])

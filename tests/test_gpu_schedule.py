@@ -88,6 +88,39 @@ def test_graph_replays_with_new_queries(amp, pair_a):
         graph.close()
 
 
+def test_graph_of_the_split_search(amp, pair_a):
+    """The split query-major search (wide pairs into a partial top-k, then the
+    1..8-bit pairs on byte tables only) captured as one CUDA graph, with mixed
+    widths per pair (the explicit policy) and new queries and widths between
+    replays: every replay equals the oracle."""
+    d, g, o = pair_a
+    Q = d["queries"]
+    nq = len(Q)
+    r = np.random.Generator(np.random.PCG64(21))
+    widths = np.array([0, 4, 6, 8, 12, 16], np.uint8)
+    qbuf = cuda(Q)
+    bbuf = cuda(widths[r.integers(0, len(widths), nq * 9)])
+    g.set_kernel("split")
+    try:
+        graph, ids, dists = g.capture_graph(qbuf, 9, 40, amp.policy("explicit", pair_bits=bbuf))
+    finally:
+        g.set_kernel("auto")
+    try:
+        for rep in range(3):
+            Q2 = (Q[r.permutation(nq)] + r.normal(0, 0.01, Q.shape)).astype(np.float32)
+            b2 = widths[r.integers(0, len(widths), nq * 9)]
+            qbuf.copy_(cuda(Q2))
+            bbuf.copy_(cuda(b2))
+            ids.fill_(-7)
+            graph.launch()
+            torch.cuda.synchronize()
+            ri, rd = ivfpq.search(o, Q2, 9, 40, bits=b2.reshape(nq, 9))
+            np.testing.assert_array_equal(ids.cpu().numpy(), ri)
+            np.testing.assert_array_equal(dists.cpu().numpy(), rd)
+    finally:
+        graph.close()
+
+
 def test_graph_on_stream_and_list_major(amp, pair_a):
     d, g, o = pair_a
     Q = d["queries"]
