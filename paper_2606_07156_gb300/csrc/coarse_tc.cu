@@ -27,7 +27,12 @@
 //    a radix select that stops at bins of 256); every list of the FP32
 //    top-nprobe has D~ - eps <= T, so those candidates are re-ranked with the
 //    FP32 rule itself (same operation order as coarse.cu) and the nprobe
-//    smallest (D2, l) kept: identical output to the plain path.
+//    smallest (D2, l) kept: identical output to the plain path. The re-rank
+//    runs in three kernels: a select kernel per query (bounds, T, the
+//    candidate list, up to kCap of them to the workspace as work items of 32),
+//    a distance kernel whose warps walk every query's items, and a merge
+//    kernel (one warp per query); indexes whose keys do not fit in shared
+//    memory take a streaming kernel instead.
 //
 // Every mbarrier wait is bounded (by default about a second; the index option
 // ANNS_OPT_WAIT_CYCLES sets the main loop's limit); on a timeout the kernel

@@ -201,3 +201,21 @@ def test_tc_candidates_shrink_with_the_format(amp):
         assert mean["fp16"] <= mean["bf16"] <= mean["fp8"], mean
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("nlist,dim,nq", [(333, 4, 1), (257, 8, 129), (1000, 12, 7)])
+def test_tc_edge_geometries(amp, nlist, dim, nq):
+    """One query, nq not a multiple of the 128-row tile, nlist odd and below one
+    256-column tile, dims far below one K chunk (mostly zero padding), nprobe
+    from 1 to 128: every format still gives the FP32 rule's probes."""
+    g, C, Q = _random_index(amp, nlist, dim, 3 * nlist + dim)
+    Q = Q[:nq] if nq <= len(Q) else np.concatenate([Q] * (nq // len(Q) + 1))[:nq]
+    try:
+        for nprobe in (1, min(nlist, 128)):
+            rp, rd = ivfpq.locate(ivfpq.coarse_d2_fp32(Q, C), nprobe)
+            for cl in FORMATS:
+                p, pd = g.locate(cuda(Q), nprobe, cl=cl)
+                np.testing.assert_array_equal(p.cpu().numpy(), rp, err_msg=f"{cl} {nprobe}")
+                np.testing.assert_array_equal(pd.cpu().numpy(), rd, err_msg=f"{cl} {nprobe}")
+    finally:
+        g.close()
