@@ -696,10 +696,22 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             train(np2)
             m2, tried2 = calibrate_margin_nn(amp, Qc, W["cal_gt"], np2, run_q)
             pols2 = {"plain": plain, "mlp": amp.policy("mlp", margin=m2 if np.isfinite(m2) else 3.0e38,
-                                                       width_map=True),
+                                                       width_map=True, cl=args.cl),
                      "fixed8": amp.policy("fixed", bits=8)}
+            # the learned policy in the configuration the autotuner picks at
+            # this nprobe (one probe per query leaves nothing to group)
+            tuned2 = None
+            if not args.no_autotune:
+                t2 = min(index.autotune(Q, np2, k, pols2["mlp"], reps=2), key=lambda r: r[2])
+                tuned2 = (t2[0], t2[1], t2[3])
             blk = {}
             for name, pol in pols2.items():
+                if name == "mlp" and tuned2 is not None:
+                    abi.anns_set_option(index.handle, abi.OPT_KERNEL, tuned2[0])
+                    abi.anns_set_option(index.handle, abi.OPT_SCHEDULE, tuned2[1])
+                    abi.anns_set_option(index.handle, abi.OPT_QCHUNK, tuned2[2])
+                else:
+                    use("plain")
                 ids = run(np2, pol)
                 ms = time_steps(lambda: index.search(Q, np2, k, pol, stream=stream, out=out), args.steps,
                                 args.warmup, stream, flush)
@@ -709,8 +721,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             op2 = {"reading": "1-recall@10: the exact nearest neighbour among the 10 returned", "nprobe": np2,
                    "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_sweep.items()},
                    "mlp_margin": m2, "margin_calibration_loss_pts": {str(a): b for a, b in tried2.items()},
-                   "policies": blk,
+                   "policies": blk, "mlp_config": None if tuned2 is None else
+                   f"{KN.get(tuned2[0], tuned2[0])}/{SN.get(tuned2[1], tuned2[1])}/q{tuned2[2]}",
                    "speedup_mlp_vs_plain": round(blk["plain"]["ms_per_step"] / blk["mlp"]["ms_per_step"], 3)}
+            use("plain")
         else:
             op2 = {"reading": "1-recall@10", "reached": False,
                    "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_sweep.items()}}
