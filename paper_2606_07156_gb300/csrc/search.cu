@@ -14,6 +14,14 @@
 //      (distance fl32(fl32(Delta32 * S) + B32)) (DC),
 //   4. offers each distance to a per-warp sorted top-k list (TS).
 // The LUT never leaves shared memory. At the end the warps' lists are merged.
+//
+// A launch keeps only the tables its pairs need: every width (the FP32 T',
+// staged, and a level table of up to 16 bits), FP32 pairs only (no level
+// table), or 1..8-bit pairs only (no FP32 table: the levels are built in two
+// passes from rows streamed through a cp.async ring). Fewer bytes of shared
+// memory per block leave room for more blocks per SM; the split search runs
+// its wide pairs in one launch and its 1..8-bit pairs in a second, which
+// merges the first one's per-query top-k.
 #include <algorithm>
 
 #include "common.cuh"
