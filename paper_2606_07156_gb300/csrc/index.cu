@@ -220,6 +220,8 @@ extern "C" int anns_build_index_from_arrays(const anns_build_desc* d, anns_index
   ix->device = d->device;
   ix->n = n; ix->dim = dim; ix->nlist = nlist; ix->M = M; ix->dsub = dsub; ix->Mp = Mp;
   ix->nchunk = nchunk; ix->ntiles = ntiles; ix->max_list = max_list;
+  ix->ids32 = std::all_of(pids.begin(), pids.end(),
+                          [](int64_t v) { return v >= (int64_t)INT32_MIN && v < (int64_t)INT32_MAX; });
   ix->h_list_len64 = new int64_t[nlist];
   ix->h_radius = new float[nlist];
   std::vector<int32_t> len32(nlist);

@@ -32,6 +32,7 @@ struct Index {
   int device = 0;
   int64_t n = 0, dim = 0, nlist = 0, M = 0, dsub = 0, Mp = 0, nchunk = 0;
   int64_t ntiles = 0, max_list = 0;
+  bool ids32 = false;           // every id in [INT32_MIN, INT32_MAX): 32-bit ids in the 128-entry top-k lists
   float* centroids = nullptr;   // [nlist*dim]
   float* codebooks = nullptr;   // [M*256*dsub]
   uint8_t* codes = nullptr;     // [ntiles*nchunk*512]

@@ -396,6 +396,7 @@ struct SearchArgs {
   // 1: leave out the pairs on 1..8-bit tables of rank >= 1 (the grouped
   // kernels take them); 2: of every rank (the narrow pass takes them)
   int skip_narrow;
+  int ids32;  // every id fits in int32 (the 128-entry lists then hold 32-bit ids)
   int64_t* ids_out; float* dists_out;
   // kModeNarrow: the query's top-k over its other pairs ([nq * k], padding
   // +inf), which bounds the scan and joins the final merge; or null
@@ -405,9 +406,9 @@ struct SearchArgs {
 
 // End of a query: the warps' lists are merged into warp 0, which writes the
 // query's k results (padding id -1, distance +inf). Ends with a barrier.
-template <int R>
-__device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, WarpTopK<R, int64_t>& top,
-                                                int64_t q, int kq, float& thd, int64_t& thi) {
+template <int R, typename IdT>
+__device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, WarpTopK<R, IdT>& top,
+                                                int64_t q, int kq, float& thd, IdT& thi) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (a.part_d && kq > 0) {
     // the top-k of the query's other pairs joins warp 0's list
@@ -415,14 +416,14 @@ __device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, Wa
       for (int e0 = 0; e0 < kq; e0 += 32) {
         const int e = e0 + lane;
         const float cd = e < kq ? a.part_d[q * a.k + e] : INFINITY;
-        const int64_t ci = e < kq ? a.part_i[q * a.k + e] : INT64_MAX;
+        const IdT ci = e < kq ? (IdT)a.part_i[q * a.k + e] : IdMax<IdT>::v();
         top.offer(cd != INFINITY, cd, ci, kq, thd, thi);
       }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     s.md[(warp * R + r) * 32 + lane] = top.d[r];
-    s.mi[(warp * R + r) * 32 + lane] = top.id[r];
+    s.mi[(warp * R + r) * 32 + lane] = (int64_t)top.id[r];
   }
   __syncthreads();
   if (warp == 0) {
@@ -430,7 +431,7 @@ __device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, Wa
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const float cd = s.md[(w2 * R + r) * 32 + lane];
-        const int64_t ci = s.mi[(w2 * R + r) * 32 + lane];
+        const IdT ci = (IdT)s.mi[(w2 * R + r) * 32 + lane];
         top.offer(cd != INFINITY, cd, ci, kq, thd, thi);
       }
 #pragma unroll
@@ -438,7 +439,7 @@ __device__ __forceinline__ void merge_and_write(const SearchArgs& a, Smem& s, Wa
       const int e = r * 32 + lane;
       if (e < a.k) {
         const bool ok = e < kq && top.d[r] != INFINITY;
-        a.ids_out[q * a.k + e] = ok ? top.id[r] : -1;
+        a.ids_out[q * a.k + e] = ok ? (int64_t)top.id[r] : -1;
         a.dists_out[q * a.k + e] = ok ? top.d[r] : INFINITY;
       }
     }
@@ -461,7 +462,9 @@ constexpr int qm_blocks() {
                              : (NCHUNK <= 2 ? (R == 1 ? 4 : 2) : (MODE == kModeFp32 && NCHUNK <= 6 ? 2 : 1));
 }
 
-template <int NCHUNK, int R, int MODE>
+// IdT: the id type of the warps' lists (int32_t when every id of the index
+// fits, for the 128-entry lists: fewer registers and shuffles per insert).
+template <int NCHUNK, int R, int MODE, typename IdT = int64_t>
 __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search_kernel(const SearchArgs a) {
   Smem s(a.lay);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -470,10 +473,10 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
     const int64_t q = a.order ? (int64_t)a.order[qi] : qi;
     const int np = a.npq ? min(max(a.npq[q], 0), a.nprobe) : a.nprobe;
     const int kq = a.kpq ? min(max(a.kpq[q], 0), a.k) : a.k;
-    WarpTopK<R, int64_t> top;
+    WarpTopK<R, IdT> top;
     top.init();
     float thd = INFINITY;
-    int64_t thi = INT64_MAX;
+    IdT thi = IdMax<IdT>::v();
     // 128-entry lists (k > 32): the block shares the smallest k-th distance
     // any warp holds (at least k vectors lie at or below it, so no farther
     // vector can enter the final top-k; equal distances are kept)
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
         const float lim = R > 1 ? *(volatile float*)blim : INFINITY;
         const bool pre = v < n_l && d <= thd && d <= bnd && d <= lim;
         if (__any_sync(kFull, pre)) {
-          const int64_t id = pre ? __ldg(idp + v) : INT64_MAX;
+          const IdT id = pre ? (IdT)__ldg(idp + v) : IdMax<IdT>::v();
           const float before = thd;
           top.offer(pre, d, id, kq, thd, thi);
           if (R > 1 && lane == 0 && thd < before && thd < lim) {
@@ -556,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
       }
       __syncthreads();  // the next pair overwrites the LUT
     }
-    merge_and_write<R>(a, s, top, q, kq, thd, thi);
+    merge_and_write<R, IdT>(a, s, top, q, kq, thd, thi);
   }
 }
 
@@ -665,13 +668,21 @@ cudaError_t launch_query_major(K kern, const SearchArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int NCHUNK, int R, typename IdT>
+cudaError_t run_search_id(const SearchArgs& a, int mode, cudaStream_t s) {
+  switch (mode) {
+    case kModeFp32: return launch_query_major(search_kernel<NCHUNK, R, kModeFp32, IdT>, a, s);
+    case kModeNarrow: return launch_query_major(search_kernel<NCHUNK, R, kModeNarrow, IdT>, a, s);
+    default: return launch_query_major(search_kernel<NCHUNK, R, kModeFull, IdT>, a, s);
+  }
+}
+
 template <int NCHUNK, int R>
 cudaError_t run_search(const SearchArgs& a, int mode, cudaStream_t s) {
-  switch (mode) {
-    case kModeFp32: return launch_query_major(search_kernel<NCHUNK, R, kModeFp32>, a, s);
-    case kModeNarrow: return launch_query_major(search_kernel<NCHUNK, R, kModeNarrow>, a, s);
-    default: return launch_query_major(search_kernel<NCHUNK, R, kModeFull>, a, s);
+  if constexpr (R > 1) {
+    if (a.ids32) return run_search_id<NCHUNK, R, int32_t>(a, mode, s);
   }
+  return run_search_id<NCHUNK, R, int64_t>(a, mode, s);
 }
 
 template <int NCHUNK>
@@ -703,6 +714,7 @@ cudaError_t launch_search(const Index& ix, const float* qt, int64_t nq, int npro
   SearchArgs a = make_args(ix, nullptr, qt, R, mode);
   a.nq = nq; a.nprobe = nprobe; a.k = k; a.npq = nprobe_per_q; a.kpq = k_per_q;
   a.probes = probes; a.probe_d2 = probe_d2; a.bits = bits; a.order = order; a.skip_narrow = skip_narrow;
+  a.ids32 = ix.ids32 ? 1 : 0;
   a.ids_out = ids_out; a.dists_out = dists_out;
   a.part_d = mode == kModeNarrow ? part_d : nullptr;
   a.part_i = mode == kModeNarrow ? part_i : nullptr;
