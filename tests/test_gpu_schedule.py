@@ -305,3 +305,28 @@ def test_qchunk_option_errors(amp, pair_a):
     d, g, o = pair_a
     with pytest.raises(amp.abi.AnnsError):
         amp.abi.anns_set_option(g.handle, amp.abi.OPT_QCHUNK, -1)
+
+
+def test_wide_ids_with_128_entry_lists(amp, small_a):
+    """Ids beyond 32 bits (not ascending in row order) keep the 128-entry
+    lists (k > 32) on 64-bit ids; every search kernel still gives the
+    oracle's ids and distances, ties broken by the 64-bit id."""
+    d, ix = small_a
+    n = len(ix["list_of"])
+    r = np.random.Generator(np.random.PCG64(5))
+    ids = (np.int64(1) << 40) + r.permutation(n).astype(np.int64) * 3
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], ids=ids, device=0)
+    o = ivfpq.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], ids=ids)
+    Q = d["queries"]
+    try:
+        for bits in (0, 4, 8):
+            pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
+            ri, rd = ivfpq.search(o, Q, 6, 40, bits=bits)
+            for kern in ("basic", "grouped", "split"):
+                g.set_kernel(kern)
+                gi, gd = g.search(cuda(Q), 6, 40, pol)
+                np.testing.assert_array_equal(gi.cpu().numpy(), ri, err_msg=f"{bits} {kern}")
+                np.testing.assert_array_equal(gd.cpu().numpy(), rd, err_msg=f"{bits} {kern}")
+    finally:
+        g.set_kernel("auto")
+        g.close()
