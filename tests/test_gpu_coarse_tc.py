@@ -170,11 +170,12 @@ def _random_index(amp, nlist, dim, seed):
     return g, C, Q
 
 
-@pytest.mark.parametrize("nlist,dim", [(12000, 24), (700, 18), (900, 37)])
+@pytest.mark.parametrize("nlist,dim", [(30000, 24), (12000, 24), (700, 18), (900, 37)])
 def test_tc_streaming_and_unaligned_rerank(amp, nlist, dim):
-    """nlist 12000 leaves the re-rank's keys out of shared memory (the
-    streaming re-rank); dims 18 and 37 are not multiples of 4 (element-wise
-    row staging). Probes and distances must still be the FP32 rule's."""
+    """nlist 30000 leaves the re-rank's keys out of shared memory (the
+    streaming re-rank); 12000 keeps them (the select kernel at one block per
+    SM); dims 18 and 37 are not multiples of 4 (element-wise row staging).
+    Probes and distances must still be the FP32 rule's."""
     g, C, Q = _random_index(amp, nlist, dim, nlist + dim)
     try:
         for nprobe in (1, 33, 100):
