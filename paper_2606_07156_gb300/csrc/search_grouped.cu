@@ -233,13 +233,17 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
     const float* P = a.ltab + (size_t)l * tstride;
     // 1. row statistics: warp w takes rows m = w, w + 8, ...; the list-table
     //    row is loaded once for the group's slots, the query-table rows two
-    //    slots at a time, and the eight reductions run side by side (an
-    //    absent slot reads its query 0 row and stores nothing)
+    //    slots at a time (an absent pair of slots reads nothing), and the
+    //    reductions run side by side
     for (int m = warp; m < a.M; m += kGWarps) {
       float p[8], lo_v[kSlots], hi_v[kSlots];
       ldg_row8(P + m * kKsub, lane, p);
 #pragma unroll
       for (int s0 = 0; s0 < kSlots; s0 += 2) {
+        if (s0 >= ns) {  // absent slots (the group's uniform count): nothing to read
+          lo_v[s0] = hi_v[s0] = lo_v[s0 + 1] = hi_v[s0 + 1] = 0.f;
+          continue;
+        }
         float qq[2][8];
 #pragma unroll
         for (int u = 0; u < 2; ++u) ldg_row8(a.qt + (size_t)q[s0 + u] * tstride + m * kKsub, lane, qq[u]);
@@ -322,9 +326,9 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 2 ? 4 : (NCHUNK <= 4 ? 3 
         ldg_row8(P + m * kKsub, lane, p);
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) {
-          float qq[8];
-          ldg_row8(a.qt + (size_t)q[s] * tstride + m * kKsub, lane, qq);
           if (s < ns) {
+            float qq[8];
+            ldg_row8(a.qt + (size_t)q[s] * tstride + m * kKsub, lane, qq);
             const float mn = bias[s * Mp + m];
             // levels t = rint(fl32(fl32(T' - bias) * s32)) <= L, in the low byte
 #pragma unroll
@@ -538,6 +542,10 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 4 ? 3 : 1) nibble_kernel(
       ldg_row8(P + m * kKsub, lane, p);
 #pragma unroll
       for (int s0 = 0; s0 < kNSlots; s0 += 2) {
+        if (s0 >= ns) {  // absent slots (the group's uniform count): nothing to read
+          lo_v[s0] = hi_v[s0] = lo_v[s0 + 1] = hi_v[s0 + 1] = 0.f;
+          continue;
+        }
         float qq[2][8];
 #pragma unroll
         for (int u = 0; u < 2; ++u) ldg_row8(a.qt + (size_t)q[s0 + u] * tstride + m * kKsub, lane, qq[u]);
@@ -605,9 +613,9 @@ __global__ void __launch_bounds__(kGThreads, NCHUNK <= 4 ? 3 : 1) nibble_kernel(
         ldg_row8(P + m * kKsub, lane, p);
 #pragma unroll
         for (int s = 0; s < kNSlots; ++s) {
-          float qq[8];
-          ldg_row8(a.qt + (size_t)q[s] * tstride + m * kKsub, lane, qq);
           if (s < ns) {
+            float qq[8];
+            ldg_row8(a.qt + (size_t)q[s] * tstride + m * kKsub, lane, qq);
             const float mn = bias[s * Mp + m];
 #pragma unroll
             for (int e = 0; e < 8; ++e)
