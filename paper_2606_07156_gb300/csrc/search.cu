@@ -284,81 +284,100 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Steps 1-2 for a 1..8-bit pair without an FP32 table (kModeNarrow): the row
-// statistics from T' formed from the rows, then the levels from T' formed
-// again (the same operations, so the same values as build_lut), written as
-// bytes. Each warp streams its rows of P_l and 2 Q_q through a ring of RS
-// slots in shared memory, RS rows in flight (a lane copies, and later reads,
-// exactly the 16-byte pieces at row_at(lane, 0) and row_at(lane, 1)). Two
-// block barriers; the caller synchronises before the scan.
+// Steps 1-2 for a 1..8-bit pair without an FP32 table (kModeNarrow), in two
+// passes over the pair's rows of P_l and 2 Q_q: the row statistics from T'
+// formed from the rows, then the levels from T' formed again (the same
+// operations, so the same values as build_lut), written as bytes. Each warp
+// streams its rows m = warp + nwarps i through a ring of RS slots in shared
+// memory, RS rows in flight; a lane copies, and later reads, exactly the
+// 16-byte pieces at row_at(lane, 0) and row_at(lane, 1), so the slots need no
+// warp barrier. A pass starts with the rows 0..RS-1 requested (prime()) and
+// ends with no copy in flight, which lets the search kernel request a pass's
+// first rows before the work that precedes it, and run the statistics pass
+// of the next pair right after each warp's share of the scan.
 template <int RS>
-__device__ void build_lut_2pass(const float* __restrict__ P, const float* __restrict__ qt2, int M, int Mp, int b,
-                                float d2, Smem& s) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  float* slots = s.ring + (size_t)warp * RS * 2 * kKsub;
-  const int nr = warp < M ? (M - warp + nwarps - 1) / nwarps : 0;  // rows m = warp + nwarps i < M
-  auto issue = [&](int i) {
+struct NarrowBuild {
+  const float* P;
+  const float* qt2;
+  float* slots;
+  int nr, warp, lane;
+  static constexpr int kWarpsPerBlock = kWarps;
+  __device__ NarrowBuild(const float* __restrict__ P_, const float* __restrict__ qt2_, int M, const Smem& s)
+      : P(P_), qt2(qt2_) {
+    warp = threadIdx.x >> 5;
+    lane = threadIdx.x & 31;
+    slots = s.ring + (size_t)warp * RS * 2 * kKsub;
+    nr = warp < M ? (M - warp + kWarpsPerBlock - 1) / kWarpsPerBlock : 0;  // rows m = warp + nwarps i < M
+  }
+  // Requests row index i into slot i % RS and commits one group per call
+  // (empty beyond the warp's rows), so wait_group counts rows.
+  __device__ __forceinline__ void issue(int i) const {
     if (i < nr) {
-      const int m = warp + nwarps * i;
+      const int m = warp + kWarpsPerBlock * i;
       float* d = slots + (i % RS) * 2 * kKsub;
       cp_async16(d + row_at(lane, 0), P + m * kKsub + row_at(lane, 0));
       cp_async16(d + row_at(lane, 1), P + m * kKsub + row_at(lane, 1));
       cp_async16(d + kKsub + row_at(lane, 0), qt2 + m * kKsub + row_at(lane, 0));
       cp_async16(d + kKsub + row_at(lane, 1), qt2 + m * kKsub + row_at(lane, 1));
     }
-    cp_async_commit();  // every lane commits one group per row index (possibly empty)
-  };
-  auto row = [&](int i, float (&t)[8]) {
+    cp_async_commit();
+  }
+  __device__ __forceinline__ void prime() const {
+#pragma unroll
+    for (int i = 0; i < RS; ++i) issue(i);
+  }
+  // T' of this lane's 8 entries of row index i (landed in its slot)
+  __device__ __forceinline__ void row(int i, float (&t)[8]) const {
     const float* d = slots + (i % RS) * 2 * kKsub;
-    float p[8], q[8];
     const float4 p0 = *(const float4*)(d + row_at(lane, 0)), p1 = *(const float4*)(d + row_at(lane, 1));
     const float4 q0 = *(const float4*)(d + kKsub + row_at(lane, 0)), q1 = *(const float4*)(d + kKsub + row_at(lane, 1));
-    p[0] = p0.x; p[1] = p0.y; p[2] = p0.z; p[3] = p0.w; p[4] = p1.x; p[5] = p1.y; p[6] = p1.z; p[7] = p1.w;
-    q[0] = q0.x; q[1] = q0.y; q[2] = q0.z; q[3] = q0.w; q[4] = q1.x; q[5] = q1.y; q[6] = q1.z; q[7] = q1.w;
+    t[0] = sub_rn(p0.x, q0.x); t[1] = sub_rn(p0.y, q0.y); t[2] = sub_rn(p0.z, q0.z); t[3] = sub_rn(p0.w, q0.w);
+    t[4] = sub_rn(p1.x, q1.x); t[5] = sub_rn(p1.y, q1.y); t[6] = sub_rn(p1.z, q1.z); t[7] = sub_rn(p1.w, q1.w);
+  }
+  // Pass 1 (rows primed): the minimum and range of this warp's rows.
+  __device__ void stats(Smem& s) const {
+    for (int i = 0; i < nr; ++i) {
+      cp_async_wait<RS - 1>();  // row i's group has landed
+      float t[8];
+      row(i, t);
+      float lo = t[0], hi = t[0];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) t[e] = sub_rn(p[e], q[e]);
-  };
-  // pass 1: row statistics
-  for (int i = 0; i < RS; ++i) issue(i);
-  for (int i = 0; i < nr; ++i) {
-    cp_async_wait<RS - 1>();  // row i's group has landed
-    float t[8];
-    row(i, t);
-    float lo = t[0], hi = t[0];
-#pragma unroll
-    for (int e = 1; e < 8; ++e) {
-      lo = fminf(lo, t[e]);
-      hi = fmaxf(hi, t[e]);
+      for (int e = 1; e < 8; ++e) {
+        lo = fminf(lo, t[e]);
+        hi = fmaxf(hi, t[e]);
+      }
+      const int m = warp + kWarpsPerBlock * i;
+      const float mn = warp_min(lo);
+      // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
+      const float mx = sub_rn(warp_max(hi), mn);
+      if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
+      issue(i + RS);  // into the slot just read (this lane's own pieces)
     }
-    const int m = warp + nwarps * i;
-    const float mn = warp_min(lo);
-    // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
-    const float mx = sub_rn(warp_max(hi), mn);
-    if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
-    issue(i + RS);  // into the slot just read (this lane's own pieces)
+    cp_async_wait<0>();
   }
-  cp_async_wait<0>();
-  __syncthreads();
-  const float s32 = pair_scale<false>(M, b, s.rowmax, s.sc);
-  // pass 2: levels
-  for (int i = 0; i < RS; ++i) issue(i);
-  for (int i = 0; i < nr; ++i) {
-    cp_async_wait<RS - 1>();
-    float t[8];
-    row(i, t);
-    const int m = warp + nwarps * i;
-    uint32_t n[8];
-    quantise8(t, s.bias[m], s32, n);
-    store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub, lane);
-    issue(i + RS);
+  // Pass 2 (rows primed, every row's statistics visible to the block): the
+  // shared step, this warp's levels and zero padding rows, and (warp 0) the
+  // offset. The caller synchronises before the scan reads them.
+  __device__ void levels(int M, int Mp, int b, float d2, Smem& s) const {
+    const float s32 = pair_scale<false>(M, b, s.rowmax, s.sc);
+    for (int i = 0; i < nr; ++i) {
+      cp_async_wait<RS - 1>();
+      float t[8];
+      row(i, t);
+      const int m = warp + kWarpsPerBlock * i;
+      uint32_t n[8];
+      quantise8(t, s.bias[m], s32, n);
+      store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub, lane);
+      issue(i + RS);
+    }
+    cp_async_wait<0>();
+    for (int m = M + ((warp - M % kWarpsPerBlock + kWarpsPerBlock) % kWarpsPerBlock); m < Mp; m += kWarpsPerBlock) {
+      const uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};  // padding rows: level 0
+      store_levels(b, z, (uint8_t*)s.q + (size_t)m * kKsub, lane);
+    }
+    if (warp == 0) pair_offset(M, d2, s.bias, s.sc);
   }
-  cp_async_wait<0>();
-  for (int m = M + ((warp - M % nwarps + nwarps) % nwarps); m < Mp; m += nwarps) {  // padding rows: level 0
-    const uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    store_levels(b, z, (uint8_t*)s.q + (size_t)m * kKsub, lane);
-  }
-  if (warp == 0) pair_offset(M, d2, s.bias, s.sc);
-}
+};
 
 template <int NCHUNK>
 __device__ __forceinline__ void load_tile(const uint8_t* __restrict__ tile, int lane, uint4 (&w)[NCHUNK]) {
@@ -514,20 +533,41 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
     // kModeNarrow: no vector beyond the k-th distance of the query's other
     // pairs can enter the final top-k (equal distances are kept: the id decides)
     const float bnd = MODE == kModeNarrow && a.part_d && kq > 0 ? a.part_d[q * a.k + kq - 1] : INFINITY;
-    for (int e = 0; e < npairs; ++e) {
+    // kModeNarrow runs pair e as [barrier] levels of e, request of the rows
+    // of e + 1 [barrier] scan of e, statistics of e + 1, second request of its
+    // rows (iteration -1 takes the statistics of pair 0): two block barriers
+    // a pair instead of three, the first rows of each pass requested before
+    // the work that precedes it, and the warps that finish their tiles first
+    // go on to the next statistics
+    using Narrow = NarrowBuild<ring_rows(R)>;
+    const float* qt2 = a.qt + q * tstride;
+    if constexpr (MODE == kModeNarrow) {
+      if (npairs > 0) Narrow(a.ltab + (size_t)s.plist[0].x * tstride, qt2, a.M, s).prime();
+    }
+    for (int e = MODE == kModeNarrow ? -1 : 0; e < npairs; ++e) {
+      if (MODE == kModeNarrow && e < 0) {
+        if (npairs > 0) {
+          const Narrow nb(a.ltab + (size_t)s.plist[0].x * tstride, qt2, a.M, s);
+          nb.stats(s);
+          nb.prime();
+        }
+        continue;
+      }
       const int4 pe = s.plist[e];
       const int l = pe.x, n_l = pe.y, b = pe.z;
       const float d2 = __int_as_float(pe.w);
       const int64_t tile0 = a.tile_off[l], vec0 = a.vec_off[l];  // requested before the table build
       if constexpr (MODE == kModeNarrow) {
-        build_lut_2pass<ring_rows(R)>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
+        __syncthreads();  // every row's statistics of this pair are in; the previous scan is over
+        Narrow(a.ltab + (size_t)l * tstride, qt2, a.M, s).levels(a.M, a.Mp, b, d2, s);
+        if (e + 1 < npairs) Narrow(a.ltab + (size_t)s.plist[e + 1].x * tstride, qt2, a.M, s).prime();
         __syncthreads();
       } else if constexpr (NCHUNK <= 2) {
-        build_lut_regs<NCHUNK * 16 / kWarps>(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, b, d2,
+        build_lut_regs<NCHUNK * 16 / kWarps>(a.ltab + (size_t)l * tstride, qt2, a.M, b, d2,
                                              s.T, s.q, s.bias, s.rowmax, s.sc);
         __syncthreads();
       } else {
-        build_lut(a.ltab + (size_t)l * tstride, a.qt + q * tstride, a.M, a.Mp, b, d2, s);
+        build_lut(a.ltab + (size_t)l * tstride, qt2, a.M, a.Mp, b, d2, s);
       }
       const PairScal sc = *s.sc;
       const int ntile = (n_l + kTileVecs - 1) / kTileVecs;
@@ -557,7 +597,15 @@ __global__ void __launch_bounds__(kThreads, qm_blocks<MODE, NCHUNK, R>()) search
           }
         }
       }
-      __syncthreads();  // the next pair overwrites the LUT
+      if constexpr (MODE == kModeNarrow) {
+        if (e + 1 < npairs) {
+          const Narrow nb(a.ltab + (size_t)s.plist[e + 1].x * tstride, qt2, a.M, s);
+          nb.stats(s);  // writes only row statistics, which no scan reads
+          nb.prime();
+        }
+      } else {
+        __syncthreads();  // the next pair overwrites the LUT
+      }
     }
     merge_and_write<R, IdT>(a, s, top, q, kq, thd, thi);
   }
