@@ -746,11 +746,18 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     # over the rest
     pb = pair_bytes(index, probes_ad, cfg["M"])
     narrow = (bits_ad >= 1) & (bits_ad <= 8)
-    narrow[:, 0] = False
     st_ms = [v / max(cnt, 1) for v in stage_ms]
+    split = tuned is not None and tuned["kernel"] == "split"
+    if not split:
+        narrow[:, 0] = False  # the grouped search's query-major pass takes every rank-0 pair
     nib = narrow & (bits_ad <= 4) if st_ms[5] > 0.0 else np.zeros_like(narrow)
     cands = []
-    if st_ms[4] > 0.0 or st_ms[5] > 0.0:
+    if split:
+        cands.append(("search_kernel (split search, wide pass: FP32 tables; LUT + scan + top-k)", "search.cu",
+                      st_ms[3], int(pb[~narrow].sum())))
+        cands.append(("search_kernel (split search, narrow pass: 1..8-bit byte tables; two-pass build + scan "
+                      "+ top-k)", "search.cu", st_ms[4], int(pb[narrow].sum())))
+    elif st_ms[4] > 0.0 or st_ms[5] > 0.0:
         cands.append(("search_kernel (query-major pass of the grouped search: rank 0 + wide pairs)", "search.cu",
                       st_ms[3], int(pb[~narrow].sum())))
         cands.append(("packed_kernel (grouped: four queries' 5..8-bit tables per gather; build + scan + top-k)",
@@ -829,8 +836,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_plain.items()},
         "stage_ms_per_step": {n: round(v, 4) for n, v in
                               zip(("cl_distances", "cl_select (the whole tensor-core CL)",
-                                   "precision_choice+query_tables", "search_before_grouped (invert + query-major)",
-                                   "grouped_kernel_5to8bit", "grouped_kernel_4bit_nibble", "grouped_merge"),
+                                   "precision_choice+query_tables")
+                                  + (("split_wide_pass (query-major, FP32 tables)",
+                                      "split_narrow_pass (query-major, 1..8-bit byte tables)") if split else
+                                     ("search_before_grouped (invert + query-major)", "grouped_kernel_5to8bit",
+                                      "grouped_kernel_4bit_nibble", "grouped_merge")),
                                   st_ms)},
         "roofline": roof,
         "e2e": {"value": round(qps_e2e, 1), "unit": "queries/s", "h2d_bytes_per_step": int(Qh.numel() * 4),
