@@ -334,41 +334,54 @@ struct NarrowBuild {
     t[0] = sub_rn(p0.x, q0.x); t[1] = sub_rn(p0.y, q0.y); t[2] = sub_rn(p0.z, q0.z); t[3] = sub_rn(p0.w, q0.w);
     t[4] = sub_rn(p1.x, q1.x); t[5] = sub_rn(p1.y, q1.y); t[6] = sub_rn(p1.z, q1.z); t[7] = sub_rn(p1.w, q1.w);
   }
-  // Pass 1 (rows primed): the minimum and range of this warp's rows.
+  // Pass 1 (rows primed): the minimum and range of this warp's rows, taken
+  // RS at a time (slot j holds row index i0 + j).
   __device__ void stats(Smem& s) const {
-    for (int i = 0; i < nr; ++i) {
-      cp_async_wait<RS - 1>();  // row i's group has landed
-      float t[8];
-      row(i, t);
-      float lo = t[0], hi = t[0];
+    for (int i0 = 0;; i0 += RS) {
 #pragma unroll
-      for (int e = 1; e < 8; ++e) {
-        lo = fminf(lo, t[e]);
-        hi = fmaxf(hi, t[e]);
+      for (int j = 0; j < RS; ++j) {
+        const int i = i0 + j;
+        if (i >= nr) {
+          cp_async_wait<0>();
+          return;
+        }
+        cp_async_wait<RS - 1>();  // row i's group has landed
+        float t[8];
+        row(j, t);
+        float lo = t[0], hi = t[0];
+#pragma unroll
+        for (int e = 1; e < 8; ++e) {
+          lo = fminf(lo, t[e]);
+          hi = fmaxf(hi, t[e]);
+        }
+        const int m = warp + kWarpsPerBlock * i;
+        const float mn = warp_min(lo);
+        // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
+        const float mx = sub_rn(warp_max(hi), mn);
+        if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
+        issue(i + RS);  // into the slot just read (this lane's own pieces)
       }
-      const int m = warp + kWarpsPerBlock * i;
-      const float mn = warp_min(lo);
-      // max over entries of fl32(t - mn) = fl32(max t - mn): rounding is monotone
-      const float mx = sub_rn(warp_max(hi), mn);
-      if (lane == 0) { s.bias[m] = mn; s.rowmax[m] = mx; }
-      issue(i + RS);  // into the slot just read (this lane's own pieces)
     }
-    cp_async_wait<0>();
   }
   // Pass 2 (rows primed, every row's statistics visible to the block): the
   // shared step, this warp's levels and zero padding rows, and (warp 0) the
   // offset. The caller synchronises before the scan reads them.
   __device__ void levels(int M, int Mp, int b, float d2, Smem& s) const {
     const float s32 = pair_scale<false>(M, b, s.rowmax, s.sc);
-    for (int i = 0; i < nr; ++i) {
-      cp_async_wait<RS - 1>();
-      float t[8];
-      row(i, t);
-      const int m = warp + kWarpsPerBlock * i;
-      uint32_t n[8];
-      quantise8(t, s.bias[m], s32, n);
-      store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub, lane);
-      issue(i + RS);
+    for (int i0 = 0; i0 < nr; i0 += RS) {
+#pragma unroll
+      for (int j = 0; j < RS; ++j) {
+        const int i = i0 + j;
+        if (i >= nr) break;
+        cp_async_wait<RS - 1>();
+        float t[8];
+        row(j, t);
+        const int m = warp + kWarpsPerBlock * i;
+        uint32_t n[8];
+        quantise8(t, s.bias[m], s32, n);
+        store_levels(b, n, (uint8_t*)s.q + (size_t)m * kKsub, lane);
+        issue(i + RS);
+      }
     }
     cp_async_wait<0>();
     for (int m = M + ((warp - M % kWarpsPerBlock + kWarpsPerBlock) % kWarpsPerBlock); m < Mp; m += kWarpsPerBlock) {
