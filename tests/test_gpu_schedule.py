@@ -330,3 +330,27 @@ def test_wide_ids_with_128_entry_lists(amp, small_a):
     finally:
         g.set_kernel("auto")
         g.close()
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_split_narrow_pass_few_table_rows(amp, M):
+    """The split search's narrow pass with fewer table rows than warps (M = 4:
+    warps 4..7 stream no row and rows 4..15 pad the table) and with one row a
+    warp (M = 8), under 128-entry and 32-entry warp lists, against the oracle."""
+    from workloads import make_dataset, train_ivfpq
+    d = make_dataset("A", n=3000, nq=12)
+    ix = train_ivfpq(d["base"], 16, M, iters=3, seed=2, device="cpu")
+    g = amp.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"], device=0)
+    o = ivfpq.Index(ix["centroids"], ix["codebooks"], ix["codes"], ix["list_of"])
+    Q = d["queries"]
+    try:
+        g.set_kernel("split")
+        for bits in (0, 4, 8):
+            pol = amp.policy("plain") if bits == 0 else amp.policy("fixed", bits=bits)
+            for k in (10, 100):
+                ids, dists = g.search(cuda(Q), 6, k, pol)
+                ri, rd = ivfpq.search(o, Q, 6, k, bits=bits)
+                np.testing.assert_array_equal(ids.cpu().numpy(), ri, err_msg=f"M {M} bits {bits} k {k}")
+                np.testing.assert_array_equal(dists.cpu().numpy(), rd, err_msg=f"M {M} bits {bits} k {k}")
+    finally:
+        g.close()
