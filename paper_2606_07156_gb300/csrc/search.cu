@@ -326,7 +326,7 @@ struct NarrowBuild {
 #pragma unroll
     for (int i = 0; i < RS; ++i) issue(i);
   }
-  // T' of this lane's 8 entries of row index i (landed in its slot)
+  // T' of this lane's 8 entries of the row in slot i % RS (landed)
   __device__ __forceinline__ void row(int i, float (&t)[8]) const {
     const float* d = slots + (i % RS) * 2 * kKsub;
     const float4 p0 = *(const float4*)(d + row_at(lane, 0)), p1 = *(const float4*)(d + row_at(lane, 1));
