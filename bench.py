@@ -481,6 +481,45 @@ def subspace_sweep(amp, index, W, cfg, nprobe: int, k: int, dev, nq: int = 2000)
                    "note": "integer tables of uint8 operands (the codebook's map); all-8-bit is the map's own loss"}}
 
 
+STAGES_CL = ("cl_distances", "cl_select (the whole tensor-core CL)", "precision_choice+query_tables")
+
+
+def search_stages(kernel, st_ms, bits: np.ndarray, pb: np.ndarray):
+    """Names of the profile stages (anns_profile) for the search that ran, and
+    the candidates for the roofline's dominant kernel: (label, source file, ms
+    per step, algorithmic code bytes). `kernel` is the autotuner's choice
+    ("split", "grouped", ...; None: the automatic one), `st_ms` the stage
+    times, `bits` and `pb` the pairs' table widths and code bytes [nq, nprobe].
+    The split search runs its wide pairs (stage 3) and then every 1..8-bit pair
+    (stage 4); the grouped search runs every rank-0 pair and the wide pairs in
+    its query-major pass (stage 3), the other 1..8-bit pairs in the byte-table
+    (stage 4) and nibble (stage 5) kernels; the other searches have stage 3
+    alone."""
+    narrow = (bits >= 1) & (bits <= 8)
+    if kernel == "split":
+        names = STAGES_CL + ("split_wide_pass (query-major, FP32 tables)",
+                             "split_narrow_pass (query-major, 1..8-bit byte tables)")
+        return names, [
+            ("search_kernel (split search, wide pass: FP32 tables; LUT + scan + top-k)", "search.cu",
+             st_ms[3], int(pb[~narrow].sum())),
+            ("search_kernel (split search, narrow pass: 1..8-bit byte tables; two-pass build + scan + top-k)",
+             "search.cu", st_ms[4], int(pb[narrow].sum()))]
+    names = STAGES_CL + ("search_before_grouped (invert + query-major)", "grouped_kernel_5to8bit",
+                         "grouped_kernel_4bit_nibble", "grouped_merge")
+    if not (st_ms[4] > 0.0 or st_ms[5] > 0.0):
+        return names, [("search_kernel (LUT build + quantise + ADC scan + top-k)", "search.cu", st_ms[3],
+                        int(pb.sum()))]
+    narrow[:, 0] = False
+    nib = narrow & (bits <= 4) if st_ms[5] > 0.0 else np.zeros_like(narrow)
+    return names, [
+        ("search_kernel (query-major pass of the grouped search: rank 0 + wide pairs)", "search.cu",
+         st_ms[3], int(pb[~narrow].sum())),
+        ("packed_kernel (grouped: four queries' 5..8-bit tables per gather; build + scan + top-k)",
+         "search_grouped.cu", st_ms[4], int(pb[narrow & ~nib].sum())),
+        ("nibble_kernel (grouped: eight queries' 4-bit tables per gather; build + scan + top-k)",
+         "search_grouped.cu", st_ms[5], int(pb[nib].sum()))]
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     import __graft_entry__
@@ -740,33 +779,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         return None
     qps = weak_scaling_qps(totals, world, nq, args.steps)
     qps_e2e = world * nq * args.steps / total_e2e
-    # roofline of the dominant kernel of the adaptive step: a grouped kernel
-    # (stage 4: 5..8-bit tables, stage 5: 4-bit tables eight to a word) over
-    # its narrow pairs of probe rank >= 1, or the query-major kernel (stage 3)
-    # over the rest
+    # roofline of the dominant kernel of the adaptive step (search_stages)
     pb = pair_bytes(index, probes_ad, cfg["M"])
-    narrow = (bits_ad >= 1) & (bits_ad <= 8)
     st_ms = [v / max(cnt, 1) for v in stage_ms]
-    split = tuned is not None and tuned["kernel"] == "split"
-    if not split:
-        narrow[:, 0] = False  # the grouped search's query-major pass takes every rank-0 pair
-    nib = narrow & (bits_ad <= 4) if st_ms[5] > 0.0 else np.zeros_like(narrow)
-    cands = []
-    if split:
-        cands.append(("search_kernel (split search, wide pass: FP32 tables; LUT + scan + top-k)", "search.cu",
-                      st_ms[3], int(pb[~narrow].sum())))
-        cands.append(("search_kernel (split search, narrow pass: 1..8-bit byte tables; two-pass build + scan "
-                      "+ top-k)", "search.cu", st_ms[4], int(pb[narrow].sum())))
-    elif st_ms[4] > 0.0 or st_ms[5] > 0.0:
-        cands.append(("search_kernel (query-major pass of the grouped search: rank 0 + wide pairs)", "search.cu",
-                      st_ms[3], int(pb[~narrow].sum())))
-        cands.append(("packed_kernel (grouped: four queries' 5..8-bit tables per gather; build + scan + top-k)",
-                      "search_grouped.cu", st_ms[4], int(pb[narrow & ~nib].sum())))
-        cands.append(("nibble_kernel (grouped: eight queries' 4-bit tables per gather; build + scan + top-k)",
-                      "search_grouped.cu", st_ms[5], int(pb[nib].sum())))
-    else:
-        cands.append(("search_kernel (LUT build + quantise + ADC scan + top-k)", "search.cu", st_ms[3],
-                      int(pb.sum())))
+    stage_names, cands = search_stages(tuned["kernel"] if tuned is not None else None, st_ms, bits_ad, pb)
     kname, kfile, kms, nbytes = max(cands, key=lambda c: c[2])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
@@ -834,14 +850,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                       "margin_calibration_recall_loss_pts": {str(a): b for a, b in tried.items()},
                       "recall_loss_budget_pts": LOSS_BUDGET},
         "plain_nn_in_top10_sweep": {str(a): round(b, 4) for a, b in nn_plain.items()},
-        "stage_ms_per_step": {n: round(v, 4) for n, v in
-                              zip(("cl_distances", "cl_select (the whole tensor-core CL)",
-                                   "precision_choice+query_tables")
-                                  + (("split_wide_pass (query-major, FP32 tables)",
-                                      "split_narrow_pass (query-major, 1..8-bit byte tables)") if split else
-                                     ("search_before_grouped (invert + query-major)", "grouped_kernel_5to8bit",
-                                      "grouped_kernel_4bit_nibble", "grouped_merge")),
-                                  st_ms)},
+        "stage_ms_per_step": {n: round(v, 4) for n, v in zip(stage_names, st_ms)},
         "roofline": roof,
         "e2e": {"value": round(qps_e2e, 1), "unit": "queries/s", "h2d_bytes_per_step": int(Qh.numel() * 4),
                 "d2h_bytes_per_step": int(ih.numel() * 8 + dh.numel() * 4), "recall_at_10": round(rec_e2e, 4)},

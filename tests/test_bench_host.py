@@ -120,3 +120,23 @@ def test_oracle_all_cores_equals_in_process_oracle(small_a, tmp_path, monkeypatc
     np.testing.assert_array_equal(ids, ri)
     np.testing.assert_array_equal(dists, rd)
     assert secs > 0
+
+
+def test_search_stages_name_the_kernel_that_ran():
+    """The split search's passes, the grouped search's kernels and the other
+    searches' single stage each get their own stage names and roofline
+    candidates, with every pair's code bytes counted where that pair ran."""
+    bits = np.array([[4, 4, 0, 8], [8, 0, 4, 4]], dtype=np.uint8)
+    pb = np.array([[10, 20, 30, 40], [50, 60, 70, 80]], dtype=np.int64)
+    names, c = bench.search_stages("split", [0.0, 0.1, 0.2, 1.0, 5.0, 0.0, 0.0], bits, pb)
+    assert len(names) == 5 and names[3].startswith("split_wide") and names[4].startswith("split_narrow")
+    assert [x[3] for x in c] == [30 + 60, 10 + 20 + 40 + 50 + 70 + 80]   # the narrow pass takes rank 0 too
+    assert max(c, key=lambda x: x[2])[0].startswith("search_kernel (split search, narrow pass")
+    names, c = bench.search_stages("grouped", [0.0, 0.1, 0.2, 1.0, 0.5, 4.0, 0.1], bits, pb)
+    assert len(names) == 7 and names[5] == "grouped_kernel_4bit_nibble"
+    # query-major pass: rank 0 and the FP32 pairs; byte tables: the 8-bit pair of
+    # rank >= 1; nibbles: the 4-bit pairs of rank >= 1
+    assert [x[3] for x in c] == [10 + 30 + 50 + 60, 40, 20 + 70 + 80]
+    assert max(c, key=lambda x: x[2])[0].startswith("nibble_kernel")
+    names, c = bench.search_stages(None, [0.0, 0.1, 0.2, 2.0, 0.0, 0.0, 0.0], bits, pb)
+    assert len(c) == 1 and c[0][3] == int(pb.sum()) and c[0][0].startswith("search_kernel (LUT build")
